@@ -1,0 +1,215 @@
+"""FP64 CPU oracle for one RK2 cycle of ideal MHD -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may import
+this package.  It shares no code with the CUDA path; both consume the seeded
+inputs of ``paper_2304_13746_b300.inputs`` and nothing else.
+
+Method: IDEFIX paper (Lesur et al. 2023), Eqs. (1)-(6), (9), (10), Table 1,
+Secs. 2.3, 2.4, 2.7; HLLD of Miyoshi & Kusano (2005); E^c EMF of Gardiner &
+Stone (2005).  Every array is numpy float64 with shape (nz, ny, nx), periodic.
+"""
+import ctypes
+import math
+
+import numpy as np
+
+from .build import build as _build
+
+_lib = None
+
+OK, EINVAL, ENONPHYS = 0, -1, -3
+FIELDS = ("rho", "mx", "my", "mz", "E", "Bx", "By", "Bz")
+PRIM_FIELDS = ("rho", "vx", "vy", "vz", "P", "Bx", "By", "Bz")
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code, bad_cell=-1):
+        super().__init__(f"oracle error {code} (bad cell {bad_cell})")
+        self.code = code
+        self.bad_cell = bad_cell
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double)]
+
+
+_P8 = ctypes.c_void_p * 8
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build()
+        L = ctypes.CDLL(path)
+        G = ctypes.POINTER(_Grid)
+        L.ora_cons_from_prims.argtypes = [G, ctypes.c_double, _P8, _P8]
+        L.ora_prims.argtypes = [G, ctypes.c_double, _P8, _P8, ctypes.POINTER(ctypes.c_long)]
+        L.ora_vanleer.argtypes = [ctypes.c_double] * 3
+        L.ora_vanleer.restype = ctypes.c_double
+        L.ora_hlld.argtypes = [_D, _D, ctypes.c_double, ctypes.c_double, _D, _D, _D]
+        L.ora_phys_flux.argtypes = [_D, ctypes.c_double, ctypes.c_double, _D]
+        L.ora_emf_ec.argtypes = [_D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_double]
+        L.ora_emf_ec.restype = ctypes.c_double
+        L.ora_speed_pass.argtypes = [G, ctypes.c_double, _P8, _D, ctypes.POINTER(ctypes.c_long)]
+        L.ora_stage.argtypes = [G, ctypes.c_double, ctypes.c_double, _P8, _P8, ctypes.c_double,
+                                ctypes.c_double, _P8, _D, ctypes.POINTER(ctypes.c_long)]
+        L.ora_cycle.argtypes = [G, ctypes.c_double, ctypes.c_double, _P8, _D, ctypes.c_double, _D,
+                                ctypes.POINTER(ctypes.c_long)]
+        L.ora_count_cycle.argtypes = [G, ctypes.c_double, ctypes.c_double, _P8, ctypes.c_double, _D]
+        L.ora_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _grid(shape, lengths):
+    nz, ny, nx = shape
+    lx, ly, lz = lengths
+    return _Grid(nx, ny, nz, lx, ly, lz)
+
+
+def _ptrs(arrays):
+    for a in arrays:
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    return _P8(*[a.ctypes.data for a in arrays])
+
+
+def _new(shape):
+    return [np.zeros(shape, dtype=np.float64) for _ in range(8)]
+
+
+def _c(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(code, bad=None):
+    if code != OK:
+        raise OracleError(code, -1 if bad is None else bad.value)
+
+
+def cons_from_prims(prim, lengths, gamma):
+    """(rho, vx, vy, vz, P, Bx_face, By_face, Bz_face) -> conserved 8-list."""
+    prim = [_c(a) for a in prim]
+    out = _new(prim[0].shape)
+    _check(lib().ora_cons_from_prims(ctypes.byref(_grid(prim[0].shape, lengths)), gamma,
+                                     _ptrs(prim), _ptrs(out)))
+    return out
+
+
+def prims(cons, lengths, gamma):
+    cons = [_c(a) for a in cons]
+    out = _new(cons[0].shape)
+    bad = ctypes.c_long(-1)
+    _check(lib().ora_prims(ctypes.byref(_grid(cons[0].shape, lengths)), gamma, _ptrs(cons),
+                           _ptrs(out), ctypes.byref(bad)), bad)
+    return out
+
+
+def vanleer(wm, w0, wp):
+    return lib().ora_vanleer(float(wm), float(w0), float(wp))
+
+
+def _arr(x, n):
+    return (ctypes.c_double * n)(*[float(v) for v in x])
+
+
+def hlld(wL, wR, bn, gamma):
+    """Single interface.  wL, wR = (rho, u, v, w, P, Bt1, Bt2); returns (F[7], sL, sR)."""
+    F = (ctypes.c_double * 7)()
+    sL, sR = ctypes.c_double(), ctypes.c_double()
+    _check(lib().ora_hlld(_arr(wL, 7), _arr(wR, 7), float(bn), float(gamma), F,
+                          ctypes.byref(sL), ctypes.byref(sR)))
+    return np.array(F[:]), sL.value, sR.value
+
+
+def phys_flux(w, bn, gamma):
+    F = (ctypes.c_double * 7)()
+    _check(lib().ora_phys_flux(_arr(w, 7), float(bn), float(gamma), F))
+    return np.array(F[:])
+
+
+def emf_ec(X, Y, C, Fa, Fb, da, db):
+    """C indexed C[c][r]: c = 0 (I), 1 (I-1); r = 0 (J), 1 (J-1)."""
+    Cf = _arr(np.asarray(C, dtype=float).ravel(), 4)
+    return lib().ora_emf_ec(_arr(X, 2), _arr(Y, 2), Cf, _arr(Fa, 2), _arr(Fb, 2), float(da),
+                            float(db))
+
+
+def speed_pass(cons, lengths, gamma):
+    cons = [_c(a) for a in cons]
+    inv = ctypes.c_double()
+    bad = ctypes.c_long(-1)
+    _check(lib().ora_speed_pass(ctypes.byref(_grid(cons[0].shape, lengths)), gamma, _ptrs(cons),
+                                ctypes.byref(inv), ctypes.byref(bad)), bad)
+    return inv.value
+
+
+def stage(uin, lengths, gamma, dt, u0=None, w=1.0, w0=0.0):
+    uin = [_c(a) for a in uin]
+    out = _new(uin[0].shape)
+    keep = [_c(a) for a in u0] if u0 is not None else None
+    p0 = _ptrs(keep) if keep is not None else _P8()
+    inv = ctypes.c_double()
+    bad = ctypes.c_long(-1)
+    _check(lib().ora_stage(ctypes.byref(_grid(uin[0].shape, lengths)), gamma, dt, _ptrs(uin), p0,
+                           w, w0, _ptrs(out), ctypes.byref(inv), ctypes.byref(bad)), bad)
+    return out, inv.value
+
+
+class Sim:
+    """Oracle simulation: state, time, and the inverse CFL time carried between cycles."""
+
+    def __init__(self, cons, lengths, gamma, cfl):
+        self.u = [_c(a).copy() for a in cons]
+        self.lengths = tuple(float(x) for x in lengths)
+        self.gamma = float(gamma)
+        self.cfl = float(cfl)
+        self.t = 0.0
+        self.nsteps = 0
+        self.inv_dt = speed_pass(self.u, self.lengths, self.gamma)
+
+    @classmethod
+    def from_prims(cls, prim, lengths, gamma, cfl):
+        return cls(cons_from_prims(prim, lengths, gamma), lengths, gamma, cfl)
+
+    def step(self, dt_max=math.inf):
+        inv = ctypes.c_double(self.inv_dt)
+        dt = ctypes.c_double()
+        bad = ctypes.c_long(-1)
+        _check(lib().ora_cycle(ctypes.byref(_grid(self.u[0].shape, self.lengths)), self.gamma,
+                               self.cfl, _ptrs(self.u), ctypes.byref(inv), float(dt_max),
+                               ctypes.byref(dt), ctypes.byref(bad)), bad)
+        self.inv_dt = inv.value
+        self.nsteps += 1
+        return dt.value
+
+    def advance(self, t_end, max_steps=10**7):
+        """Cycles until t == t_end; the last dt is clamped to t_end - t."""
+        n = 0
+        while self.t < t_end and n < max_steps:
+            remaining = t_end - self.t
+            dt = self.step(dt_max=remaining)
+            if dt >= remaining:
+                self.t = t_end
+            else:
+                self.t += dt
+            n += 1
+        return n
+
+    def next_dt(self):
+        return self.cfl / self.inv_dt
+
+
+def count_cycle(cons, lengths, gamma, cfl):
+    """Per cell-update counts: dict(add, mul, div, sqrt, cmp) for one RK2 cycle."""
+    cons = [_c(a) for a in cons]
+    inv = speed_pass(cons, lengths, gamma)
+    out = (ctypes.c_double * 5)()
+    _check(lib().ora_count_cycle(ctypes.byref(_grid(cons[0].shape, lengths)), gamma, cfl,
+                                 _ptrs(cons), inv, out))
+    return dict(zip(("add", "mul", "div", "sqrt", "cmp"), out[:]))
+
+
+def threads():
+    return lib().ora_threads()

@@ -1,0 +1,97 @@
+/*
+ * oracle.h -- C interface of the FP64 CPU oracle for one RK2 cycle of ideal MHD.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is the plain, slow, obviously-correct
+ * reference that the CUDA path is checked against.  Only the test suite, the
+ * smoke check and the CPU-baseline leg of the benchmark may load it.  It shares
+ * no code, header, table or helper with the CUDA path.
+ *
+ * Method (IDEFIX paper, Lesur et al. 2023):
+ *   Eq. (1)-(4)  ideal-MHD conservation laws (no 4*pi in the units),
+ *   Eq. (5)      Godunov finite-volume form,
+ *   Sec. 2.3     reconstruction on primitives (PLM, van Leer), HLLD Riemann solver,
+ *                pressure kept inside the momentum flux,
+ *   Sec. 2.4     constrained transport on face-centred B, E^c edge EMF (Eq. 6),
+ *   Sec. 2.7     method-of-lines RK2 (Eq. 9, Table 1) and the CFL time step (Eq. 10).
+ *
+ * Layout: every field is double[nz][ny][nx] (x fastest), periodic in all three
+ * directions.  Conserved set: rho, mx, my, mz, E (cell averages) and Bx, By, Bz
+ * (face averages: Bx[k][j][i] sits on the x-face at i-1/2, By on the y-face at
+ * j-1/2, Bz on the z-face at k-1/2).  A direction with n_d == 1 is not integrated.
+ *
+ * Return codes: 0 ok; ORA_EINVAL bad argument; ORA_ENONPHYS rho<=0, P<=0 or a
+ * non-finite value found while recovering primitives (the flat cell index is
+ * written to *bad_cell when the pointer is given).
+ */
+#ifndef IDX_ORACLE_H
+#define IDX_ORACLE_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORA_OK 0
+#define ORA_EINVAL (-1)
+#define ORA_ENONPHYS (-3)
+
+typedef struct {
+  int nx, ny, nz;      /* cells per direction, >= 1 */
+  double lx, ly, lz;   /* box lengths; cell size = l/n */
+} ora_grid;
+
+/* Primitive input (rho, vx, vy, vz, P at cell centres; Bx, By, Bz on faces)
+ * -> conserved (rho, mx, my, mz, E, Bx, By, Bz).  E uses the face-averaged
+ * cell-centre B, exactly as primitive recovery inverts it. */
+int ora_cons_from_prims(const ora_grid* g, double gamma, const double* const prim[8],
+                        double* const cons[8]);
+
+/* Conserved -> primitives (rho, vx, vy, vz, P, Bcx, Bcy, Bcz), all cell-centred. */
+int ora_prims(const ora_grid* g, double gamma, const double* const cons[8], double* const w[8],
+              long* bad_cell);
+
+/* van Leer limited slope of one variable from the values at i-1, i, i+1. */
+double ora_vanleer(double wm, double w0, double wp);
+
+/* HLLD flux at one interface whose normal is "x".  wL, wR = (rho, u, v, w, P, Bt1, Bt2);
+ * bn = normal field.  F = fluxes of (rho, m_n, m_t1, m_t2, E, Bt1, Bt2).  sL, sR = the
+ * outer wave-speed estimates. */
+int ora_hlld(const double wL[7], const double wR[7], double bn, double gamma, double F[7],
+             double* sL, double* sR);
+
+/* Ideal-MHD physical flux along "x" of one state (same ordering as ora_hlld). */
+int ora_phys_flux(const double w[7], double bn, double gamma, double F[7]);
+
+/* E^c edge EMF of Gardiner & Stone (2005) for one edge, generic first/second directions
+ * a, b: X[r] a-face EMFs at b-index J (r=0) and J-1 (r=1); Y[c] b-face EMFs at a-index
+ * I (c=0) and I-1 (c=1); C[c][r] cell-centre EMFs; Fa[r], Fb[c] the matching mass
+ * fluxes; da, db cell sizes. */
+double ora_emf_ec(const double X[2], const double Y[2], const double C[2][2], const double Fa[2],
+                  const double Fb[2], double da, double db);
+
+/* Signal-speed-only pass on a state: returns max over cells of
+ * sum_d max(c_face(i-1/2), c_face(i+1/2)) / dl_d  (the inverse CFL time). */
+int ora_speed_pass(const ora_grid* g, double gamma, const double* const cons[8], double* inv_dt,
+                   long* bad_cell);
+
+/* One stage: uout = w * S_dt(uin) + w0 * u0 (u0 may be NULL when w0 == 0).
+ * *inv_dt receives the stage's inverse CFL time. */
+int ora_stage(const ora_grid* g, double gamma, double dt, const double* const uin[8],
+              const double* const u0[8], double w, double w0, double* const uout[8],
+              double* inv_dt, long* bad_cell);
+
+/* One RK2 cycle in place.  dt = min(cfl / *inv_dt, dt_max); on return *inv_dt holds
+ * max(inv of stage 1, inv of stage 2), the input of the next cycle's dt. */
+int ora_cycle(const ora_grid* g, double gamma, double cfl, double* const u[8], double* inv_dt,
+              double dt_max, double* dt_taken, long* bad_cell);
+
+/* Operation count of one RK2 cycle on the given state, per cell-update:
+ * counts[0] add/sub, [1] mul, [2] div, [3] sqrt, [4] compare. */
+int ora_count_cycle(const ora_grid* g, double gamma, double cfl, const double* const u[8],
+                    double inv_dt, double counts[5]);
+
+/* Number of host threads the oracle uses (OpenMP), for reporting. */
+int ora_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

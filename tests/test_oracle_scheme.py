@@ -1,0 +1,241 @@
+"""Pins of the whole oracle cycle against what the paper and the mathematics fix.
+
+  * Sod shock tube (Sec. 4.1; P_L read as 1.0): L1 error against the exact Riemann
+    solution falls with resolution; star state; identical along x, y and z (bitwise).
+  * Conservation (Eq. 5 in flux form on a periodic box): total mass, momentum, energy
+    and the face-B flux through every face plane are constant to round-off.
+  * Constrained transport (Sec. 2.4): the discrete divergence of B stays at round-off.
+  * Uniform states stay bitwise uniform.
+  * Linear MHD waves (Sec. 4.2, Eq. 14): second-order convergence of the error.
+  * RK2 (Sec. 2.7, Eq. 9, Table 1): second-order temporal convergence at fixed grid.
+  * CFL time step (Eq. 10) and its clamp to the end time.
+  * Primitive <-> conserved round trip (Sec. 2.1 definition of E).
+"""
+import math
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2304_13746_b300 import inputs
+
+sys.path.insert(0, os.path.dirname(__file__))
+import exact_riemann  # noqa: E402
+
+
+def div_b(u, lengths):
+    nz, ny, nx = u[0].shape
+    dx, dy, dz = lengths[0] / nx, lengths[1] / ny, lengths[2] / nz
+    return ((np.roll(u[5], -1, 2) - u[5]) / dx + (np.roll(u[6], -1, 1) - u[6]) / dy +
+            (np.roll(u[7], -1, 0) - u[7]) / dz)
+
+
+def test_prim_cons_round_trip():
+    ic = inputs.random_smooth((6, 5, 7), seed=3)
+    cons = oracle.cons_from_prims(ic.prim, ic.lengths, ic.gamma)
+    w = oracle.prims(cons, ic.lengths, ic.gamma)
+    for f in (0, 1, 2, 3, 4):
+        np.testing.assert_allclose(w[f], ic.prim[f], rtol=4e-15, atol=4e-15)
+    # cell-centre B is the mean of the two bounding faces
+    np.testing.assert_allclose(w[5], 0.5 * (ic.prim[5] + np.roll(ic.prim[5], -1, 2)), rtol=1e-15)
+    np.testing.assert_allclose(w[6], 0.5 * (ic.prim[6] + np.roll(ic.prim[6], -1, 1)), rtol=1e-15)
+    np.testing.assert_allclose(w[7], 0.5 * (ic.prim[7] + np.roll(ic.prim[7], -1, 0)), rtol=1e-15)
+
+
+def test_nonphysical_state_is_reported():
+    ic = inputs.random_smooth((4, 4, 4), seed=1)
+    cons = oracle.cons_from_prims(ic.prim, ic.lengths, ic.gamma)
+    cons[4][2, 1, 3] = -1.0  # negative energy -> negative pressure
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.prims(cons, ic.lengths, ic.gamma)
+    assert e.value.code == oracle.ENONPHYS and e.value.bad_cell == (2 * 4 + 1) * 4 + 3
+
+
+def test_uniform_state_stays_bitwise_uniform():
+    ic = inputs.uniform((4, 5, 6), lengths=(1.0, 1.3, 0.7))
+    sim = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, 0.4)
+    u0 = [a.copy() for a in sim.u]
+    for _ in range(3):
+        sim.step()
+    for f in range(8):
+        assert np.all(sim.u[f] == sim.u[f].flat[0]), f
+        assert sim.u[f].flat[0] == pytest.approx(u0[f].flat[0], rel=1e-15, abs=1e-15)
+
+
+@pytest.mark.parametrize("shape", [(8, 8, 8), (6, 5, 7), (1, 12, 10)])
+def test_conservation_and_div_b(shape):
+    lengths = (1.0, 1.2, 0.9)
+    ic = inputs.random_smooth(shape, seed=5, lengths=lengths)
+    sim = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, 0.4)
+    tot0 = [float(np.sum(sim.u[f])) for f in range(5)]
+    bmax = max(float(np.max(np.abs(sim.u[f]))) for f in (5, 6, 7))
+    dl = min(lengths[0] / shape[2], lengths[1] / shape[1], lengths[2] / shape[0])
+    plane0 = [sim.u[5].sum(axis=(0, 1)), sim.u[6].sum(axis=(0, 2)), sim.u[7].sum(axis=(1, 2))]
+    assert np.max(np.abs(div_b(sim.u, lengths))) < 1e-13 * bmax / dl
+    for _ in range(20):
+        sim.step()
+    for f in range(5):
+        scale = float(np.sum(np.abs(sim.u[f])))
+        assert abs(float(np.sum(sim.u[f])) - tot0[f]) <= 1e-13 * scale, f
+    assert np.max(np.abs(div_b(sim.u, lengths))) < 1e-13 * bmax / dl
+    # magnetic flux through every x-face plane (and y, z) is conserved by CT
+    plane1 = [sim.u[5].sum(axis=(0, 1)), sim.u[6].sum(axis=(0, 2)), sim.u[7].sum(axis=(1, 2))]
+    for a, b in zip(plane0, plane1):
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-13 * bmax * np.prod(shape))
+
+
+def test_orszag_tang_div_b_and_point_symmetry():
+    ic = inputs.orszag_tang_2d(32)
+    sim = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, 0.4)
+    assert np.max(np.abs(div_b(sim.u, ic.lengths))) == 0.0
+    sim.advance(0.1)
+    assert np.max(np.abs(div_b(sim.u, ic.lengths))) < 1e-12
+    # ideal MHD keeps the point symmetry of the OT state: rho(x) = rho(1 - x), m(x) = -m(1 - x)
+    rho = sim.u[0][0]
+    assert np.max(np.abs(rho - rho[::-1, ::-1])) < 1e-10
+    mx = sim.u[1][0]
+    assert np.max(np.abs(mx + mx[::-1, ::-1])) < 1e-10
+
+
+def _run_sod(n_per_unit, axis):
+    ic = inputs.sod_double_tube(n_per_unit, axis=axis)
+    sim = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, 0.4)
+    sim.advance(0.2)
+    return ic, sim
+
+
+def _sod_l1(n_per_unit):
+    _, sim = _run_sod(n_per_unit, 0)
+    rho = sim.u[0][0, 0, :]
+    n = rho.size
+    x = (np.arange(n) + 0.5) * (2.0 / n)
+    sel = (x >= 1.0) & (x < 2.0)  # the L|R interface at x = 1.5
+    ex, _, _ = exact_riemann.sample((x[sel] - 1.5) / 0.2, 1.0, 0.0, 1.0, 0.125, 0.0, 0.1, 1.4)
+    return float(np.mean(np.abs(rho[sel] - ex))), sim
+
+
+def test_sod_exact_solution_convergence():
+    errs = [_sod_l1(n)[0] for n in (50, 100, 200)]
+    # first-order convergence at discontinuities; errors fall by ~2 per doubling
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 0.012
+    assert math.log2(errs[1] / errs[2]) > 0.6
+
+
+def test_sod_star_state_values():
+    # mid-plateau between contact and shock (xi = 1.5): u = 0.92745, p = 0.30313
+    _, sim = _sod_l1(200)
+    n = sim.u[0].shape[2]
+    x = (np.arange(n) + 0.5) * (2.0 / n)
+    i = int(np.argmin(np.abs(x - (1.5 + 0.2 * 1.5))))
+    rho, mx, E = sim.u[0][0, 0, i], sim.u[1][0, 0, i], sim.u[4][0, 0, i]
+    u = mx / rho
+    p = 0.4 * (E - 0.5 * rho * u * u)
+    ps, us = exact_riemann.star_state(1.0, 0.0, 1.0, 0.125, 0.0, 0.1, 1.4)
+    assert u == pytest.approx(us, rel=2e-3)
+    assert p == pytest.approx(ps, rel=2e-3)
+
+
+def test_sod_axis_permutation_bitwise():
+    res = []
+    for axis in range(3):
+        _, sim = _run_sod(40, axis)
+        others = [sim.u[1 + a] for a in range(3) if a != axis]
+        assert all(np.all(o == 0.0) for o in others)
+        res.append((sim.u[0].reshape(-1), sim.u[1 + axis].reshape(-1), sim.u[4].reshape(-1),
+                    sim.nsteps))
+    for r in res[1:]:
+        assert r[3] == res[0][3]
+        for a, b in zip(r[:3], res[0][:3]):
+            assert np.array_equal(a, b)
+
+
+def linear_wave_error(ic, cfl=0.4):
+    """Eq. (14): root-sum-square over the perturbed components of the mean absolute
+    change after one crossing time, normalised by eps, divided by their number."""
+    sim = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, cfl)
+    q0 = oracle.prims(sim.u, ic.lengths, ic.gamma)
+    sim.advance(ic.meta["t_cross"])
+    q1 = oracle.prims(sim.u, ic.lengths, ic.gamma)
+    eps = ic.meta["eps"]
+    acc, ncomp = 0.0, 0
+    for f in range(8):
+        if np.max(np.abs(q0[f] - np.mean(q0[f]))) < 1e-3 * eps:
+            continue
+        ncomp += 1
+        acc += (np.sum(np.abs(q0[f] - q1[f])) / (eps * ic.ncells)) ** 2
+    return math.sqrt(acc) / max(ncomp, 1)
+
+
+@pytest.mark.parametrize("mode", ["fast", "alfven", "entropy"])
+def test_linear_wave_second_order_3d(mode):
+    e8 = linear_wave_error(inputs.linear_wave(8, mode))
+    e16 = linear_wave_error(inputs.linear_wave(16, mode))
+    assert math.log2(e8 / e16) > 1.8, (e8, e16)
+
+
+@pytest.mark.slow
+def test_linear_wave_second_order_3d_slow_mode():
+    e8 = linear_wave_error(inputs.linear_wave(8, "slow"))
+    e16 = linear_wave_error(inputs.linear_wave(16, "slow"))
+    assert math.log2(e8 / e16) > 1.8
+
+
+@pytest.mark.parametrize("mode", ["fast", "alfven", "slow", "entropy"])
+def test_linear_wave_second_order_asymptotic_1d(mode):
+    # The van Leer limiter clips slopes at the extrema of the sine; its effect fades
+    # only above ~30 cells per wavelength, where the rate settles at 2.
+    e = [linear_wave_error(inputs.linear_wave_1d(N, mode)) for N in (32, 64, 128)]
+    assert math.log2(e[1] / e[2]) >= 1.9, e
+
+
+def test_rk2_temporal_order():
+    # Fixed grid, smooth state: the differences between runs at CFL sigma and a
+    # reference at small sigma isolate the time-integration error; RK2 (Table 1)
+    # must give slope ~2.
+    ic = inputs.random_smooth((1, 16, 16), seed=8, amp=0.1)
+
+    def run(cfl, t_end=0.05):
+        sim = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, cfl)
+        sim.advance(t_end)
+        return sim.u
+
+    ref = run(0.025)
+    e = []
+    for cfl in (0.4, 0.2, 0.1):
+        u = run(cfl)
+        e.append(max(float(np.max(np.abs(u[f] - ref[f]))) for f in range(8)))
+    s1, s2 = math.log2(e[0] / e[1]), math.log2(e[1] / e[2])
+    assert s1 > 1.7 and s2 > 1.7, (e, s1, s2)
+
+
+def test_first_dt_from_speed_pass():
+    # dt of the first cycle = sigma / max_cells sum_d max(c_face)/dl (Eq. 10, eta = 0);
+    # at rest with B = 0 every face speed is the sound speed
+    ic = inputs.uniform((4, 4, 4), lengths=(1.0, 2.0, 4.0), v=(0.0, 0.0, 0.0),
+                        B=(0.0, 0.0, 0.0), rho=1.0, P=0.6)
+    sim = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, 0.4)
+    c = math.sqrt(ic.gamma * 0.6)
+    inv = c / 0.25 + c / 0.5 + c / 1.0
+    assert sim.inv_dt == pytest.approx(inv, rel=1e-15)
+    assert sim.step() == pytest.approx(0.4 / inv, rel=1e-15)
+
+
+def test_dt_clamped_to_end_time():
+    ic = inputs.random_smooth((4, 4, 4), seed=2)
+    sim = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, 0.4)
+    dt0 = sim.next_dt()
+    n = sim.advance(2.5 * dt0)
+    assert sim.t == 2.5 * dt0
+    assert n >= 3
+
+
+def test_op_count_is_stable():
+    ic = inputs.turbulent_box(8, seed=0)
+    cons = oracle.cons_from_prims(ic.prim, ic.lengths, ic.gamma)
+    c = oracle.count_cycle(cons, ic.lengths, ic.gamma, 0.4)
+    flops = c["add"] + c["mul"] + c["div"] + c["sqrt"]
+    assert 1500 < flops < 8000
+    assert c["div"] > 20 and c["sqrt"] > 5
