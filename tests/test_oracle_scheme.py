@@ -239,3 +239,36 @@ def test_op_count_is_stable():
     flops = c["add"] + c["mul"] + c["div"] + c["sqrt"]
     assert 1500 < flops < 8000
     assert c["div"] > 20 and c["sqrt"] > 5
+
+
+def test_speed_pass_brute_force_from_single_interfaces():
+    # Assemble Eq. (10) by hand from the pinned single-interface pieces: van Leer face
+    # states of the primitives, HLLD outer speeds, c_face = max(|S_L|, |S_R|), per cell
+    # sum over directions of max(lower face, upper face) / dl, max over cells.
+    shape, lengths = (4, 5, 6), (1.0, 1.3, 0.8)
+    ic = inputs.random_smooth(shape, seed=12, lengths=lengths)
+    cons = oracle.cons_from_prims(ic.prim, lengths, ic.gamma)
+    W = oracle.prims(cons, lengths, ic.gamma)
+    nz, ny, nx = shape
+    dl = (lengths[0] / nx, lengths[1] / ny, lengths[2] / nz)
+    axis = {0: 2, 1: 1, 2: 0}  # direction -> numpy axis
+    cface = np.zeros((3,) + shape)
+    for d in range(3):
+        t1, t2 = (d + 1) % 3, (d + 2) % 3
+        var = [0, 1 + d, 1 + t1, 1 + t2, 4, 5 + t1, 5 + t2]
+
+        def cell(q, k, j, i, s):
+            idx = [k, j, i]
+            idx[axis[d]] += s
+            return W[q][idx[0] % nz, idx[1] % ny, idx[2] % nx]
+        for k in range(nz):
+            for j in range(ny):
+                for i in range(nx):
+                    wl = [cell(q, k, j, i, -1) + 0.5 * oracle.vanleer(cell(q, k, j, i, -2),
+                          cell(q, k, j, i, -1), cell(q, k, j, i, 0)) for q in var]
+                    wr = [cell(q, k, j, i, 0) - 0.5 * oracle.vanleer(cell(q, k, j, i, -1),
+                          cell(q, k, j, i, 0), cell(q, k, j, i, 1)) for q in var]
+                    _, sL, sR = oracle.hlld(wl, wr, cons[5 + d][k, j, i], ic.gamma)
+                    cface[d, k, j, i] = max(abs(sL), abs(sR))
+    inv = sum(np.maximum(cface[d], np.roll(cface[d], -1, axis[d])) / dl[d] for d in range(3))
+    assert oracle.speed_pass(cons, lengths, ic.gamma) == pytest.approx(float(inv.max()), rel=1e-14)
