@@ -1,0 +1,298 @@
+#!/usr/bin/env python3
+"""Benchmark: ideal-MHD RK2 cell-updates/s on B300 (one JSON line on rank 0).
+
+Workload (default): 3D periodic turbulent box 256^3, FP64, rho = 1, P = 1/gamma,
+uniform B0 along x at beta = 1, seeded random-phase solenoidal velocity with
+E(k) ~ k^-2 for 1 <= |k| <= 8 at rms Mach 1, gamma = 5/3, CFL 0.4.  A "step" is one
+full RK2 cycle (two stages: primitives, PLM, HLLD on x/y/z faces, E^c EMFs, CT and
+cell update, CFL reduction, dt).  value = cells x cycles / device time, summed over
+ranks.  Inputs (state 134 MB plus intermediates of several GB) are larger than the
+126 MB L2, so no flush is needed between cycles.
+
+Multi-GPU: the method does not shard here -- `--gpus N` under torchrun runs N
+independent replicas (one box per rank, no data-path collective); a barrier and a
+max over ranks bracket the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--n 256] [--precision fp64|fp32]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on host cores, same metric
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ideal-MHD cell-updates/s per B300 (FP64 vs FP32, plain vs served) + p50/p99"
+UNIT = "cell-updates/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--n", type=int, default=256)
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--impl", default="idx", choices=["idx", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def workload_config(args):
+    return {"workload": f"3D periodic turbulent box {args.n}^3, ideal MHD, "
+                        f"{'FP64' if args.precision == 'fp64' else 'FP32 bulk / FP64 accumulation'}, "
+                        "beta=1 B0 along x, random-phase solenoidal v, E(k)~k^-2 (k=1..8), "
+                        "rms Mach 1, gamma=5/3, PLM+HLLD+E^c CT+RK2, CFL 0.4",
+            "n": args.n, "cells": args.n ** 3, "precision": args.precision, "seed": 0,
+            "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas"}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- CPU baseline
+def cpu_baseline(n=96, cycles=3):
+    """The FP64 oracle as it stands on this host's cores: a bounded sample of the same
+    workload (an n^3 box of the same recipe, `cycles` RK2 cycles)."""
+    import oracle
+    from paper_2304_13746_b300 import inputs
+    ic = inputs.turbulent_box(n, seed=0)
+    sim = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, 0.4)
+    t0 = time.perf_counter()
+    for _ in range(cycles):
+        sim.step()
+    el = time.perf_counter() - t0
+    return {"value": ic.ncells * cycles / el, "unit": UNIT, "cores": oracle.threads(),
+            "kind": "oracle",
+            "sample": f"turbulent box {n}^3 (same recipe, seed 0), {cycles} FP64 RK2 cycles, "
+                      f"{el:.1f} s wall"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2304_13746_b300 import inputs
+    n = 64
+    ic = inputs.turbulent_box(n, seed=0)
+    sim = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, 0.4)
+    for _ in range(args.warmup):
+        sim.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.step()
+    el = time.perf_counter() - t0
+    value = ic.ncells * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(),
+                             "kind": "oracle",
+                             "sample": f"each step one RK2 cycle of a {n}^3 box of the same "
+                                       "recipe on the host cores (bounded sample)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def alg_flops_per_face(cons, lengths, gamma):
+    """Algorithmic flops per face of each direction from the oracle's op counter on a
+    small box of the same recipe: HLLD + half of the two-sided reconstruction (each
+    cell's slope counted once)."""
+    import oracle
+    out = []
+    for d in range(3):
+        h, r = oracle.count_faces(cons, lengths, gamma, d)
+        out.append(sum(h[k] for k in ("add", "mul", "div", "sqrt")) +
+                   0.5 * sum(r[k] for k in ("add", "mul", "div", "sqrt")))
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_2304_13746_b300 import build as idx_build
+    from paper_2304_13746_b300 import idx, inputs
+    if rank == 0:
+        idx_build.build()
+    if dist:
+        dist.barrier()
+    idx.lib()
+
+    ic = inputs.turbulent_box(args.n, seed=0)
+    ncell = ic.ncells
+    stream = torch.cuda.Stream()
+    sim = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, args.precision, stream=stream.cuda_stream)
+    sim.set_primitive(ic.prim)
+    cons_host = sim.get_state()
+
+    for _ in range(args.warmup):
+        sim.step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sim.step()
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    sim.time()  # surfaces any device error of the timed cycles
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ncell * args.steps * world / (ms * 1e-3)
+    n_active = sum(1 for s in ic.shape if s > 1)
+    launches_per_cycle = 2 + 2 * (3 + n_active)
+
+    # dominant kernel: per-launch device time of each kernel (events between launches)
+    kt = sim.kernel_times(reps=2)
+    flops_face = alg_flops_per_face(
+        [np.ascontiguousarray(a[:32, :32, :32]) for a in cons_host] if args.n > 32 else cons_host,
+        (32 / args.n,) * 3 if args.n > 32 else ic.lengths, ic.gamma)
+    sweep_ms = {d: kt[f"sweep_{d}"] for d in "xyz"}
+    dom = max(sweep_ms, key=sweep_ms.get)
+    d_i = "xyz".index(dom)
+    achieved_gflops = flops_face[d_i] * ncell / (sweep_ms[dom] * 1e-3) / 1e9
+    rates = idx.pipe_rates()
+    if args.precision == "fp64":
+        peak = 2 * rates["fma64"] / 1e9
+        peak_note = "measured FP64 FMA rate x 2 flop (idx_pipe_rates, this GPU)"
+    else:
+        peak = 2 * rates["fma32"] / 1e9
+        peak_note = "measured FP32 FMA rate x 2 flop (idx_pipe_rates, this GPU)"
+    roofline = {"bound": "alu", "kernel": f"k_sweep<{'double' if args.precision == 'fp64' else 'float'},{dom}>",
+                "achieved": achieved_gflops, "peak": peak, "unit": "GFLOP/s",
+                "frac": achieved_gflops / peak, "traffic": None,
+                "alg_flops_per_face": flops_face[d_i], "launch_ms": sweep_ms[dom],
+                "peak_source": peak_note, "kernel_ms": kt,
+                "pipe_rates_gops": {k: v / 1e9 for k, v in rates.items()}}
+
+    # end to end through the C ABI with host buffers: H2D state, one cycle, D2H state
+    pinned = [torch.from_numpy(a).pin_memory().numpy() for a in cons_host]
+    out_pinned = [torch.empty(ic.shape, dtype=torch.float64).pin_memory().numpy() for _ in range(8)]
+    e2e_steps = max(3, min(args.steps, 10))
+    sim.set_state(pinned)
+    sim.step()
+    sim.get_state(out=out_pinned)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.set_state(pinned)
+        sim.step()
+        sim.get_state(out=out_pinned)
+    el = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([el], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    e2e = {"value": ncell * e2e_steps * world / el, "unit": UNIT,
+           "h2d_bytes_per_step": 8 * 8 * ncell, "d2h_bytes_per_step": 8 * 8 * ncell,
+           "note": "per step: idx_set_state from pinned host (incl. its signal-speed pass), "
+                   "idx_step, idx_get_state to pinned host"}
+    sim.close()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else "f32/f64",
+                "data": "synthetic", "config": workload_config(args),
+                "gpu_launches": launches_per_cycle * args.steps,
+                "clocks": clk, "roofline": roofline, "e2e": e2e}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,128 @@
+/*
+ * idx.h -- C ABI of the B300 (sm_103a) ideal-MHD RK2 stage library (libidx.so).
+ *
+ * One simulation ("sim") is one periodic Cartesian box of ideal MHD advanced by the
+ * Godunov scheme of the IDEFIX paper (Lesur et al. 2023):
+ *   Eqs. (1)-(4)  ideal-MHD conservation laws (units without 4*pi),
+ *   Eq. (5)       finite-volume update of cell averages,
+ *   Sec. 2.3      PLM reconstruction of the primitives with the van Leer limiter,
+ *                 HLLD Riemann solver (Miyoshi & Kusano 2005), pressure in the flux,
+ *   Sec. 2.4      constrained transport of face-centred B with the E^c edge EMF
+ *                 (Gardiner & Stone 2005), Eq. (6),
+ *   Sec. 2.7      RK2 stages U_s = w_s U* + w0_s U_0 (Eq. 9, Table 1: w = 1, 0; 1/2, 1/2)
+ *                 and the CFL step dt = sigma / max_V sum_d c_max,d / dl_d (Eq. 10).
+ *
+ * Layout (every field): double[nz][ny][nx], x fastest, periodic in x, y and z.
+ * The 8 state fields, in this order: rho, mx, my, mz, E (cell averages), then
+ * Bx, By, Bz (face averages: Bx[k][j][i] on the x-face at i-1/2, By[k][j][i] on the
+ * y-face at j-1/2, Bz[k][j][i] on the z-face at k-1/2).  A direction with a single
+ * cell is not integrated (nz == 1 is the 2D case).
+ *
+ * Time step: the first cycle after idx_set_state / idx_set_primitive takes its dt
+ * from a signal-speed pass on the new state; every later cycle takes
+ * dt = cfl / inv, where inv is the larger of the two stages' values of
+ * max over cells of sum_d max(c at the two d-faces) / dl_d of the previous cycle,
+ * with c = max(|S_L|, |S_R|) of the HLLD outer speeds.
+ *
+ * Return codes: 0 on success, a negative IDX_E* code otherwise (idx_strerror()).
+ * Ownership: the library owns all device memory of a sim (allocated in idx_create,
+ * freed in idx_destroy); callers own every buffer they pass in, and set/get copy.
+ * Threading: a sim is not thread-safe; distinct sims are independent.  All work of
+ * a sim runs on its stream (the caller's, or one the library creates).
+ */
+#ifndef IDX_H
+#define IDX_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IDX_OK 0
+#define IDX_EINVAL (-1)    /* bad sizes, gamma <= 1, cfl outside (0,1), NULL, unsupported solver */
+#define IDX_ENOMEM (-2)    /* device allocation failed                                        */
+#define IDX_ENONPHYS (-3)  /* rho <= 0, P <= 0 or non-finite found on the device             */
+#define IDX_ECUDA (-4)     /* a CUDA runtime call failed                                      */
+#define IDX_ETIMEOUT (-5)  /* a bounded wait expired                                          */
+
+typedef struct {
+  int nx, ny, nz;      /* cells per direction, each >= 1, nx*ny*nz < 2^31 */
+  double lx, ly, lz;   /* box [0,lx) x [0,ly) x [0,lz); cell size l/n      */
+} idx_grid;
+
+typedef enum {
+  IDX_FP64 = 0,       /* every step in FP64                                                  */
+  IDX_FP32_BULK = 1   /* reconstruction, HLLD and EMFs in FP32; primitive recovery, the
+                         conserved/face-B accumulation and the dt reduction in FP64          */
+} idx_precision;
+
+typedef struct {
+  int recon;       /* 1 = PLM with the van Leer limiter (Sec. 2.3); the only value accepted */
+  int riemann;     /* 4 = HLLD (Sec. 2.3); the only value accepted                         */
+  int emf;         /* 2 = E^c (Sec. 2.4); the only value accepted                          */
+  int rk_order;    /* 2 = RK2 (Table 1); the only value accepted                           */
+  double cfl;      /* sigma of Eq. (10), 0 < cfl < 1                                       */
+  int precision;   /* idx_precision                                                         */
+} idx_solver;
+
+typedef struct idx_sim idx_sim; /* opaque */
+
+/* Create a sim: validates the arguments, allocates its device buffers on the current
+ * CUDA device.  stream: a cudaStream_t to run on, or NULL for a library-owned stream.
+ * The state is undefined until idx_set_state / idx_set_primitive. */
+int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, void* stream,
+               idx_sim** out);
+
+/* Copy in the conserved state (8 fields in the order and layout above).  on_device != 0:
+ * the pointers are device memory, else host memory.  Resets t = 0 and the step count and
+ * runs the signal-speed pass that fixes the first dt.  Synchronises the sim's stream.
+ * IDX_ENONPHYS if the state has rho <= 0, P <= 0 or a non-finite value. */
+int idx_set_state(idx_sim* sim, const double* const fields[8], int on_device);
+
+/* Same, from primitives: rho, vx, vy, vz, P (cell centres) and Bx, By, Bz (faces).
+ * E = P/(gamma-1) + rho|v|^2/2 + |B_c|^2/2 with B_c the mean of the two faces that
+ * bound the cell (the inverse of the primitive recovery). */
+int idx_set_primitive(idx_sim* sim, const double* const fields[8], int on_device);
+
+/* Copy out the conserved state.  Synchronises the sim's stream; reports a pending
+ * device error (IDX_ENONPHYS) of earlier asynchronous steps. */
+int idx_get_state(const idx_sim* sim, double* const fields[8], int on_device);
+
+/* One RK2 cycle (two stages with the same dt).  Asynchronous when dt_taken is NULL
+ * (errors surface at the next synchronising call); otherwise waits and writes dt. */
+int idx_step(idx_sim* sim, double* dt_taken);
+
+/* Cycles until t == t_end; the last dt is clamped to t_end - t and t is then set to
+ * t_end exactly.  nsteps (nullable) receives the cycles taken by this call. */
+int idx_advance(idx_sim* sim, double t_end, int64_t* nsteps);
+
+/* Current time and the dt the next cycle will take (before any clamp).  Synchronises. */
+int idx_time(const idx_sim* sim, double* t, double* next_dt);
+
+/* Flat index k*ny*nx + j*nx + i of the first (lowest-index) cell found non-physical by
+ * the last failing call, or -1. */
+int idx_last_error_cell(const idx_sim* sim, int64_t* cell);
+
+/* Device time per launch of each kernel of the stage, averaged over the 2 * reps stages
+ * of `reps` cycles launched kernel by kernel with CUDA events between them on the sim's
+ * stream: ms[0] primitive recovery, [1] x sweep (PLM + HLLD), [2] y sweep, [3] z sweep,
+ * [4] E^c edge EMFs, [5] update (0 for a direction that is not integrated).  The cycles
+ * are real: the sim advances by `reps` cycles.  A measurement aid, not part of the method. */
+int idx_kernel_times(idx_sim* sim, int reps, double ms[6]);
+
+/* Free the sim and its device memory (and its stream, if the library made it). */
+void idx_destroy(idx_sim* sim);
+
+const char* idx_strerror(int code);
+
+/* Measured throughput of the current device's arithmetic pipes, in operations per
+ * second: rates[0] FP64 fused multiply-add, [1] FP64 divide, [2] FP64 square root,
+ * [3] FP32 fused multiply-add, [4] FP32 divide, [5] FP32 square root.  Each comes
+ * from a short kernel of independent operations timed with CUDA events (a few ms).
+ * Not part of the method: it supplies the denominators of the ALU roofline. */
+int idx_pipe_rates(double rates[6]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

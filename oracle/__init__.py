@@ -58,6 +58,7 @@ def lib():
         L.ora_cycle.argtypes = [G, ctypes.c_double, ctypes.c_double, _P8, _D, ctypes.c_double, _D,
                                 ctypes.POINTER(ctypes.c_long)]
         L.ora_count_cycle.argtypes = [G, ctypes.c_double, ctypes.c_double, _P8, ctypes.c_double, _D]
+        L.ora_count_faces.argtypes = [G, ctypes.c_double, _P8, ctypes.c_int, _D, _D]
         L.ora_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -209,6 +210,16 @@ def count_cycle(cons, lengths, gamma, cfl):
     _check(lib().ora_count_cycle(ctypes.byref(_grid(cons[0].shape, lengths)), gamma, cfl,
                                  _ptrs(cons), inv, out))
     return dict(zip(("add", "mul", "div", "sqrt", "cmp"), out[:]))
+
+
+def count_faces(cons, lengths, gamma, d):
+    """Per-face op counts of direction d: (hlld dict, reconstruction dict)."""
+    cons = [_c(a) for a in cons]
+    a, b = (ctypes.c_double * 5)(), (ctypes.c_double * 5)()
+    _check(lib().ora_count_faces(ctypes.byref(_grid(cons[0].shape, lengths)), gamma, _ptrs(cons),
+                                 int(d), a, b))
+    keys = ("add", "mul", "div", "sqrt", "cmp")
+    return dict(zip(keys, a[:])), dict(zip(keys, b[:]))
 
 
 def threads():

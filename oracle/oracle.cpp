@@ -766,6 +766,49 @@ int ora_count_cycle(const ora_grid* g, double gamma, double cfl, const double* c
   return st;
 }
 
+int ora_count_faces(const ora_grid* g, double gamma, const double* const u[8], int d,
+                    double counts_hlld[5], double counts_recon[5]) {
+  if (!grid_ok(g) || !(gamma > 1.0) || !ptrs_ok((const void* const*)u) || d < 0 || d > 2 ||
+      !counts_hlld || !counts_recon)
+    return ORA_EINVAL;
+  const Grid G = make_grid(g);
+  std::vector<double> U[8], W[8];
+  load(G, u, U);
+  for (int f = 0; f < 8; ++f) W[f].assign(G.ncell, 0.0);
+  long bad = -1;
+  const int st = prims(G, gamma, U, W, &bad);
+  if (st != ORA_OK) return st;
+  std::vector<Counted> Wc[8];
+  for (int f = 0; f < 8; ++f) {
+    Wc[f].resize(G.ncell);
+    for (long p = 0; p < G.ncell; ++p) Wc[f][p] = Counted(W[f][p]);
+  }
+  Tally recon, riemann;
+  for (int k = 0; k < G.n[2]; ++k)
+    for (int j = 0; j < G.n[1]; ++j)
+      for (int i = 0; i < G.n[0]; ++i) {
+        State<Counted> L, R;
+        g_tally = Tally();
+        face_state(G, Wc, i, j, k, d, -1, &L);
+        face_state(G, Wc, i, j, k, d, +1, &R);
+        recon.add += g_tally.add; recon.mul += g_tally.mul; recon.div += g_tally.div;
+        recon.sqrt += g_tally.sqrt; recon.cmp += g_tally.cmp;
+        g_tally = Tally();
+        Counted F[7], sL, sR;
+        hlld(L, R, Counted(u[5 + d][at(G, i, j, k)]), gamma, F, &sL, &sR);
+        riemann.add += g_tally.add; riemann.mul += g_tally.mul; riemann.div += g_tally.div;
+        riemann.sqrt += g_tally.sqrt; riemann.cmp += g_tally.cmp;
+      }
+  const double n = (double)G.ncell;
+  const Tally* t[2] = {&riemann, &recon};
+  double* out[2] = {counts_hlld, counts_recon};
+  for (int q = 0; q < 2; ++q) {
+    out[q][0] = t[q]->add / n; out[q][1] = t[q]->mul / n; out[q][2] = t[q]->div / n;
+    out[q][3] = t[q]->sqrt / n; out[q][4] = t[q]->cmp / n;
+  }
+  return ORA_OK;
+}
+
 int ora_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -88,6 +88,12 @@ int ora_cycle(const ora_grid* g, double gamma, double cfl, double* const u[8], d
 int ora_count_cycle(const ora_grid* g, double gamma, double cfl, const double* const u[8],
                     double inv_dt, double counts[5]);
 
+/* Operation counts per face of direction d (0, 1, 2) on the given state, split into the
+ * HLLD solve and the reconstruction of the two face states (which evaluates the slope of
+ * both adjacent cells): [0] add/sub, [1] mul, [2] div, [3] sqrt, [4] compare. */
+int ora_count_faces(const ora_grid* g, double gamma, const double* const u[8], int d,
+                    double counts_hlld[5], double counts_recon[5]);
+
 /* Number of host threads the oracle uses (OpenMP), for reporting. */
 int ora_threads(void);
 

@@ -1,0 +1,844 @@
+// idx_stage.cu -- sm_103a kernels of one RK2 cycle of ideal MHD and the C ABI (include/idx.h).
+//
+// The FP64 stage is bound by the FP64 pipe (1/64 of the FP32 rate on this part), not
+// by HBM: it moves ~2.4 KB per cell-update against ~0.5 us of FP64 arithmetic.  So the
+// stage is split into kernels that each compute every quantity exactly once --
+// primitives per cell, PLM slopes per cell and direction, one HLLD per face, one E^c
+// per edge -- and hand their results through HBM, instead of one fused tile kernel
+// that would recompute halo faces.  Per stage:
+//
+//   k_prims      U (8 fields)            -> W: rho, v, P, cell-centre B      (Secs. 2.1, 2.3)
+//   k_sweep<d>   W along d, face B_d     -> F_d: 7 HLLD fluxes + face speed  (Sec. 2.3)
+//                (one thread marches a pencil segment: slopes computed once per cell)
+//   k_emf        F_a, F_b, W             -> edge EMFs E_e (E^c)               (Sec. 2.4)
+//   k_update     U, F_d, E_e [, U_0]     -> U_out = w U* + w0 U_0; block max of the
+//                                           inverse CFL time -> atomicMax    (Eqs. 5, 6, 9, 10)
+//
+// A cycle is k_begin (dt from the previous cycle's speeds, clamp to t_end) + 2 stages +
+// k_end (t, step count, speeds for the next dt), captured once into a CUDA graph and
+// replayed; time, dt and the error flag stay on the device.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+
+#include "../../include/idx.h"
+#include "mhd_math.cuh"
+
+using namespace idx;
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kSeg = 16;  // faces per thread along the sweep direction
+
+// Device control block of one sim.
+struct Ctrl {
+  double t;
+  double t_end;
+  double dt;                       // dt of the running cycle; 0 means "skip"
+  double cfl;
+  double last_dt;                  // dt of the last completed cycle
+  unsigned long long inv_prev;     // bits of the inverse CFL time for the next dt
+  unsigned long long inv_acc;      // running max (bits) over the current cycle's stages
+  unsigned long long bad_cell;     // min flat index of a non-physical cell
+  long long nsteps;
+  int done;
+  int err;
+  int clamped;
+  int pad;
+};
+
+struct Geo {
+  int n[3];        // nx, ny, nz
+  int stride[3];   // 1, nx, nx*ny
+  int ncell;
+  int active[3];   // n_d > 1
+  double inv_dl[3];
+  double gamma;
+};
+
+template <typename T> struct Ptr8 {
+  T* f[8];
+};
+
+__device__ __forceinline__ void coords(const Geo& g, int c, int& i, int& j, int& k) {
+  const int nxy = g.n[0] * g.n[1];
+  k = c / nxy;
+  const int r = c - k * nxy;
+  j = r / g.n[0];
+  i = r - j * g.n[0];
+}
+
+// Cell index shifted by s (|s| <= 2) along d with periodic wrap; needs n_d >= 2 for
+// |s| == 2 and n_d >= 1 for |s| <= 1.
+__device__ __forceinline__ int shifted(const Geo& g, int c, int coord, int d, int s) {
+  int q = coord + s;
+  const int n = g.n[d];
+  if (q < 0) q += n;
+  if (q < 0) q += n;
+  if (q >= n) q -= n;
+  if (q >= n) q -= n;
+  return c + (q - coord) * g.stride[d];
+}
+
+__device__ __forceinline__ void flag_bad(Ctrl* ctrl, int c) {
+  atomicCAS(&ctrl->err, 0, IDX_ENONPHYS);
+  atomicMin(&ctrl->bad_cell, (unsigned long long)c);
+}
+
+// ---------------------------------------------------------------------------
+// Primitive recovery (FP64 for both variants): rho, v = m/rho, P from E, and the
+// cell-centre B as the mean of the two bounding faces.  W is stored as T.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_prims(Geo g, Ptr8<const double> U, Ptr8<T> W,
+                                                    Ctrl* ctrl, int check_dt) {
+  if (check_dt && !(ctrl->dt > 0.0)) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  int i, j, k;
+  coords(g, c, i, j, k);
+  const double rho = U.f[0][c];
+  const double ir = 1.0 / rho;
+  const double vx = U.f[1][c] * ir, vy = U.f[2][c] * ir, vz = U.f[3][c] * ir;
+  const double bx = 0.5 * (U.f[5][c] + U.f[5][shifted(g, c, i, 0, 1)]);
+  const double by = 0.5 * (U.f[6][c] + U.f[6][shifted(g, c, j, 1, 1)]);
+  const double bz = 0.5 * (U.f[7][c] + U.f[7][shifted(g, c, k, 2, 1)]);
+  const double kin = 0.5 * rho * (vx * vx + vy * vy + vz * vz);
+  const double mag = 0.5 * (bx * bx + by * by + bz * bz);
+  const double P = (g.gamma - 1.0) * (U.f[4][c] - kin - mag);
+  if (!(rho > 0.0) || !(P > 0.0) || !isfinite(rho) || !isfinite(P) || !isfinite(vx) ||
+      !isfinite(vy) || !isfinite(vz))
+    flag_bad(ctrl, c);
+  W.f[0][c] = T(rho); W.f[1][c] = T(vx); W.f[2][c] = T(vy); W.f[3][c] = T(vz);
+  W.f[4][c] = T(P);   W.f[5][c] = T(bx); W.f[6][c] = T(by); W.f[7][c] = T(bz);
+}
+
+// Conserved state from primitives (cell-centre rho, v, P; face B).
+__global__ void __launch_bounds__(kThreads) k_cons_from_prims(Geo g, Ptr8<const double> P,
+                                                              Ptr8<double> U) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  int i, j, k;
+  coords(g, c, i, j, k);
+  const double rho = P.f[0][c], vx = P.f[1][c], vy = P.f[2][c], vz = P.f[3][c];
+  const double bx = 0.5 * (P.f[5][c] + P.f[5][shifted(g, c, i, 0, 1)]);
+  const double by = 0.5 * (P.f[6][c] + P.f[6][shifted(g, c, j, 1, 1)]);
+  const double bz = 0.5 * (P.f[7][c] + P.f[7][shifted(g, c, k, 2, 1)]);
+  U.f[0][c] = rho;
+  U.f[1][c] = rho * vx;
+  U.f[2][c] = rho * vy;
+  U.f[3][c] = rho * vz;
+  U.f[4][c] = P.f[4][c] / (g.gamma - 1.0) + 0.5 * rho * (vx * vx + vy * vy + vz * vz) +
+              0.5 * (bx * bx + by * by + bz * bz);
+  U.f[5][c] = P.f[5][c];
+  U.f[6][c] = P.f[6][c];
+  U.f[7][c] = P.f[7][c];
+}
+
+// ---------------------------------------------------------------------------
+// Sweep along direction D: a thread owns a segment of up to kSeg faces of one pencil,
+// marches along D keeping three cells' primitives and one slope in registers, and
+// computes each cell's van Leer slopes once and each face's HLLD flux once.
+// Face f of a pencil is the lower D-face of cell f.  Output (rotated order): F[0..6]
+// = fluxes of rho, m_n, m_t1, m_t2, E, B_t1, B_t2 with t1 = D+1, t2 = D+2; F[7] = c.
+// ---------------------------------------------------------------------------
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads) k_sweep(Geo g, Ptr8<const T> W, const double* bface,
+                                                    Ptr8<T> F, const Ctrl* ctrl, int check_dt) {
+  if (check_dt && !(ctrl->dt > 0.0)) return;
+  constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
+  const int nd = g.n[D];
+  const int npencil = g.n[A] * g.n[B];
+  const int nseg = (nd + kSeg - 1) / kSeg;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npencil * nseg) return;
+  const int pencil = t % npencil, seg = t / npencil;
+  // pencil -> coordinates of the two other directions, x fastest for coalescing
+  int cA, cB;
+  if (D == 0) {  // other dims y (A), z (B)
+    cA = pencil % g.n[1]; cB = pencil / g.n[1];
+  } else if (D == 1) {  // A = z, B = x: x fastest
+    cB = pencil % g.n[0]; cA = pencil / g.n[0];
+  } else {  // D == 2: A = x, B = y
+    cA = pencil % g.n[0]; cB = pencil / g.n[0];
+  }
+  const int base = cA * g.stride[A] + cB * g.stride[B];
+  const int sd = g.stride[D];
+  const int f0 = seg * kSeg;
+  const int f1 = min(f0 + kSeg, nd);
+  auto cell = [&](int q) {  // flat index of cell q (wrapped) along the pencil
+    q = (q < 0) ? q + nd : q;
+    q = (q < 0) ? q + nd : q;
+    q = (q >= nd) ? q - nd : q;
+    q = (q >= nd) ? q - nd : q;
+    return base + q * sd;
+  };
+  // rotated variable slots in W: rho, v_n, v_t1, v_t2, P, B_t1, B_t2
+  constexpr int var[7] = {0, 1 + D, 1 + A, 1 + B, 4, 5 + A, 5 + B};
+  const T gamma = T(g.gamma);
+  const T gm1inv = T(1.0 / (g.gamma - 1.0));
+
+  T wm[7], w0[7], wp[7], slope_m[7];
+  {
+    const int cm2 = cell(f0 - 2), cm1 = cell(f0 - 1), c0 = cell(f0);
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      const T a = W.f[var[q]][cm2];
+      wm[q] = W.f[var[q]][cm1];
+      w0[q] = W.f[var[q]][c0];
+      slope_m[q] = vanleer(wm[q] - a, w0[q] - wm[q]);
+    }
+  }
+  for (int f = f0; f < f1; ++f) {
+    const int cf = cell(f), cp = cell(f + 1);
+    Side<T> L, R;
+    T slope0[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      wp[q] = W.f[var[q]][cp];
+      slope0[q] = vanleer(w0[q] - wm[q], wp[q] - w0[q]);
+    }
+    L.r = wm[0] + T(0.5) * slope_m[0]; R.r = w0[0] - T(0.5) * slope0[0];
+    L.u = wm[1] + T(0.5) * slope_m[1]; R.u = w0[1] - T(0.5) * slope0[1];
+    L.v = wm[2] + T(0.5) * slope_m[2]; R.v = w0[2] - T(0.5) * slope0[2];
+    L.w = wm[3] + T(0.5) * slope_m[3]; R.w = w0[3] - T(0.5) * slope0[3];
+    L.p = wm[4] + T(0.5) * slope_m[4]; R.p = w0[4] - T(0.5) * slope0[4];
+    L.b1 = wm[5] + T(0.5) * slope_m[5]; R.b1 = w0[5] - T(0.5) * slope0[5];
+    L.b2 = wm[6] + T(0.5) * slope_m[6]; R.b2 = w0[6] - T(0.5) * slope0[6];
+    const T bn = T(bface[cf]);
+    T flux[7], cmax;
+    hlld(L, R, bn, gamma, gm1inv, flux, cmax);
+#pragma unroll
+    for (int q = 0; q < 7; ++q) F.f[q][cf] = flux[q];
+    F.f[7][cf] = cmax;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      wm[q] = w0[q];
+      w0[q] = wp[q];
+      slope_m[q] = slope0[q];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Edge EMFs: E_e at the edge along e bounded by the lower a- and b-faces of cell c,
+// a = e+1, b = e+2.  a-face EMF = -F_a[B_b] (rotated slot 5 of direction a), b-face
+// EMF = +F_b[B_a] (slot 6 of direction b), cell-centre EMF = -(v_a B_b - v_b B_a).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T edge_emf(const Geo& g, int e, int c, const int ijk[3],
+                                      const Ptr8<const T>& W, const Ptr8<const T>* F) {
+  const int a = (e + 1) % 3, b = (e + 2) % 3;
+  const Ptr8<const T>& Fa = F[a];
+  const Ptr8<const T>& Fb = F[b];
+  const int cb = shifted(g, c, ijk[b], b, -1);   // c - e_b
+  const int ca = shifted(g, c, ijk[a], a, -1);   // c - e_a
+  const int cab = shifted(g, ca, ijk[b], b, -1); // c - e_a - e_b
+  const T X0 = -Fa.f[5][c], X1 = -Fa.f[5][cb];
+  const T Y0 = Fb.f[6][c], Y1 = Fb.f[6][ca];
+  const T Fa0 = Fa.f[0][c], Fa1 = Fa.f[0][cb];
+  const T Fb0 = Fb.f[0][c], Fb1 = Fb.f[0][ca];
+  auto cc = [&](int q) { return -(W.f[1 + a][q] * W.f[5 + b][q] - W.f[1 + b][q] * W.f[5 + a][q]); };
+  const T C00 = cc(c), C01 = cc(cb), C10 = cc(ca), C11 = cc(cab);
+  return emf_ec(X0, X1, Y0, Y1, C00, C01, C10, C11, Fa0, Fa1, Fb0, Fb1);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_emf(Geo g, Ptr8<const T> W, Ptr8<const T> Fx,
+                                                  Ptr8<const T> Fy, Ptr8<const T> Fz, T* Ex,
+                                                  T* Ey, T* Ez, const Ctrl* ctrl) {
+  if (!(ctrl->dt > 0.0)) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  int ijk[3];
+  coords(g, c, ijk[0], ijk[1], ijk[2]);
+  const Ptr8<const T> F[3] = {Fx, Fy, Fz};
+  T* out[3] = {Ex, Ey, Ez};
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const int a = (e + 1) % 3, b = (e + 2) % 3;
+    if (g.active[a] && g.active[b]) out[e][c] = edge_emf(g, e, c, ijk, W, F);
+  }
+}
+
+// Rotated flux slot of conserved field f (0..4) or face field 5+m for direction d.
+__device__ __forceinline__ int slot(int f, int d) {
+  if (f == 0) return 0;
+  if (f == 4) return 4;
+  if (f <= 3) {  // momentum component m = f-1
+    const int m = f - 1;
+    return m == d ? 1 : (m == (d + 1) % 3 ? 2 : 3);
+  }
+  const int m = f - 5;  // field component, tangential to d
+  return m == (d + 1) % 3 ? 5 : 6;
+}
+
+// ---------------------------------------------------------------------------
+// Update: U* = U - dt div F (cell fields), B* = B - dt curl E (face fields, Eq. 6),
+// U_out = w U* + w0 U_0 (Eq. 9), and the stage's inverse CFL time (Eq. 10).
+// Arithmetic in FP64 for both variants.
+// ---------------------------------------------------------------------------
+template <typename T, bool COMBINE>
+__global__ void __launch_bounds__(kThreads) k_update(Geo g, Ptr8<const double> Uin,
+                                                     Ptr8<const double> U0, Ptr8<const T> Fx,
+                                                     Ptr8<const T> Fy, Ptr8<const T> Fz,
+                                                     const T* Ex, const T* Ey, const T* Ez,
+                                                     Ptr8<double> Uout, Ctrl* ctrl) {
+  const double dt = ctrl->dt;
+  if (!(dt > 0.0)) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  double inv = 0.0;
+  if (c < g.ncell) {
+    int ijk[3];
+    coords(g, c, ijk[0], ijk[1], ijk[2]);
+    const Ptr8<const T> F[3] = {Fx, Fy, Fz};
+    const T* E[3] = {Ex, Ey, Ez};
+    int up[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) up[d] = shifted(g, c, ijk[d], d, 1);
+    double out[8];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+      double div = 0.0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (!g.active[d]) continue;
+        const int s = slot(f, d);
+        div += (double(F[d].f[s][up[d]]) - double(F[d].f[s][c])) * g.inv_dl[d];
+      }
+      out[f] = Uin.f[f][c] - dt * div;
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+      double curl = 0.0;
+      if (g.active[d]) {
+        if (g.active[t1]) curl += (double(E[t2][up[t1]]) - double(E[t2][c])) * g.inv_dl[t1];
+        if (g.active[t2]) curl -= (double(E[t1][up[t2]]) - double(E[t1][c])) * g.inv_dl[t2];
+      } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          if (a == d || !g.active[a]) continue;
+          const int s = slot(5 + d, a);
+          curl += (double(F[a].f[s][up[a]]) - double(F[a].f[s][c])) * g.inv_dl[a];
+        }
+      }
+      out[5 + d] = Uin.f[5 + d][c] - dt * curl;
+    }
+#pragma unroll
+    for (int f = 0; f < 8; ++f) Uout.f[f][c] = COMBINE ? fma(0.5, out[f], 0.5 * U0.f[f][c]) : out[f];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if (g.active[d])
+        inv += fmax(double(F[d].f[7][c]), double(F[d].f[7][up[d]])) * g.inv_dl[d];
+  }
+  // block max -> one atomic per block (positive doubles order like their bit patterns)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) inv = fmax(inv, __shfl_xor_sync(0xffffffffu, inv, o));
+  __shared__ double wmax[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = inv;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = wmax[0];
+    for (int w = 1; w < kThreads / 32; ++w) m = fmax(m, wmax[w]);
+    atomicMax(&ctrl->inv_acc, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+// Inverse CFL time of a state from the face speeds alone (first cycle).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_inv_only(Geo g, Ptr8<const T> Fx, Ptr8<const T> Fy,
+                                                       Ptr8<const T> Fz, Ctrl* ctrl) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  double inv = 0.0;
+  if (c < g.ncell) {
+    int ijk[3];
+    coords(g, c, ijk[0], ijk[1], ijk[2]);
+    const Ptr8<const T> F[3] = {Fx, Fy, Fz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if (g.active[d]) {
+        const int u = shifted(g, c, ijk[d], d, 1);
+        inv += fmax(double(F[d].f[7][c]), double(F[d].f[7][u])) * g.inv_dl[d];
+      }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) inv = fmax(inv, __shfl_xor_sync(0xffffffffu, inv, o));
+  __shared__ double wmax[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = inv;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = wmax[0];
+    for (int w = 1; w < kThreads / 32; ++w) m = fmax(m, wmax[w]);
+    atomicMax(&ctrl->inv_prev, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+// Cycle prologue: dt = cfl / inv (Eq. 10), clamped to t_end - t.
+__global__ void k_begin(Ctrl* c) {
+  if (c->err != 0 || c->done) {
+    c->dt = 0.0;
+    c->done = 1;
+    return;
+  }
+  const double inv = __longlong_as_double((long long)c->inv_prev);
+  double dt = c->cfl / inv;
+  const double rem = c->t_end - c->t;
+  int clamped = 0;
+  if (dt > rem) dt = rem;
+  if (dt >= rem) clamped = 1;
+  if (!(dt > 0.0)) {
+    c->dt = 0.0;
+    c->done = 1;
+    return;
+  }
+  c->dt = dt;
+  c->clamped = clamped;
+  c->inv_acc = 0ull;
+}
+
+// Cycle epilogue: advance t, keep the larger stage speed bound for the next dt.
+__global__ void k_end(Ctrl* c) {
+  if (!(c->dt > 0.0)) return;
+  c->t = c->clamped ? c->t_end : c->t + c->dt;
+  c->last_dt = c->dt;
+  c->inv_prev = c->inv_acc;
+  c->nsteps += 1;
+  if (c->clamped) c->done = 1;
+  c->dt = 0.0;
+}
+
+}  // namespace
+
+// ===========================================================================
+// Host side
+// ===========================================================================
+struct idx_sim {
+  idx_grid grid;
+  double gamma;
+  idx_solver solver;
+  Geo geo;
+  cudaStream_t stream;
+  bool own_stream;
+  int device;
+  void* mem;            // single device allocation
+  size_t mem_bytes;
+  Ptr8<double> U, U1;   // state and first-stage result (FP64)
+  Ptr8<double> Wd, Fd[3];
+  Ptr8<float> Wf, Ff[3];
+  double* Ed[3];
+  float* Ef[3];
+  Ctrl* ctrl;           // device
+  Ctrl* host_ctrl;      // pinned mirror
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  int64_t last_bad;
+};
+
+namespace {
+
+#define IDX_TRY(x)                                  \
+  do {                                              \
+    cudaError_t e_ = (x);                           \
+    if (e_ != cudaSuccess) return IDX_ECUDA;        \
+  } while (0)
+
+unsigned blocks_for(long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+template <typename T> Ptr8<const T> cst(const Ptr8<T>& p) {
+  Ptr8<const T> q;
+  for (int f = 0; f < 8; ++f) q.f[f] = p.f[f];
+  return q;
+}
+
+template <typename T>
+void launch_fluxes(idx_sim* s, const Ptr8<double>& Uin, const Ptr8<T>& W, Ptr8<T>* F,
+                   int check_dt) {
+  const Geo& g = s->geo;
+  k_prims<T><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), W, s->ctrl, check_dt);
+  for (int d = 0; d < 3; ++d) {
+    if (!g.active[d]) continue;
+    const int a = (d + 1) % 3, b = (d + 2) % 3;
+    const long nthr = (long)g.n[a] * g.n[b] * ((g.n[d] + kSeg - 1) / kSeg);
+    const unsigned nb = blocks_for(nthr);
+    if (d == 0)
+      k_sweep<T, 0><<<nb, kThreads, 0, s->stream>>>(g, cst(W), Uin.f[5], F[0], s->ctrl, check_dt);
+    else if (d == 1)
+      k_sweep<T, 1><<<nb, kThreads, 0, s->stream>>>(g, cst(W), Uin.f[6], F[1], s->ctrl, check_dt);
+    else
+      k_sweep<T, 2><<<nb, kThreads, 0, s->stream>>>(g, cst(W), Uin.f[7], F[2], s->ctrl, check_dt);
+  }
+}
+
+template <typename T>
+void launch_stage(idx_sim* s, const Ptr8<double>& Uin, const Ptr8<double>& Uout, bool combine,
+                  const Ptr8<T>& W, Ptr8<T>* F, T** E) {
+  const Geo& g = s->geo;
+  launch_fluxes<T>(s, Uin, W, F, 1);
+  k_emf<T><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(W), cst(F[0]), cst(F[1]),
+                                                            cst(F[2]), E[0], E[1], E[2], s->ctrl);
+  if (combine)
+    k_update<T, true><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
+        g, cst(Uin), cst(s->U), cst(F[0]), cst(F[1]), cst(F[2]), E[0], E[1], E[2], Uout, s->ctrl);
+  else
+    k_update<T, false><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
+        g, cst(Uin), cst(s->U), cst(F[0]), cst(F[1]), cst(F[2]), E[0], E[1], E[2], Uout, s->ctrl);
+}
+
+void launch_cycle(idx_sim* s) {
+  k_begin<<<1, 1, 0, s->stream>>>(s->ctrl);
+  if (s->solver.precision == IDX_FP32_BULK) {
+    launch_stage<float>(s, s->U, s->U1, false, s->Wf, s->Ff, s->Ef);
+    launch_stage<float>(s, s->U1, s->U, true, s->Wf, s->Ff, s->Ef);
+  } else {
+    launch_stage<double>(s, s->U, s->U1, false, s->Wd, s->Fd, s->Ed);
+    launch_stage<double>(s, s->U1, s->U, true, s->Wd, s->Fd, s->Ed);
+  }
+  k_end<<<1, 1, 0, s->stream>>>(s->ctrl);
+}
+
+int build_graph(idx_sim* s) {
+  if (s->exec) return IDX_OK;
+  IDX_TRY(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+  launch_cycle(s);
+  cudaError_t e = cudaStreamEndCapture(s->stream, &s->graph);
+  if (e != cudaSuccess) return IDX_ECUDA;
+  IDX_TRY(cudaGraphInstantiate(&s->exec, s->graph, 0));
+  return IDX_OK;
+}
+
+int sync_ctrl(const idx_sim* s) {
+  IDX_TRY(cudaMemcpyAsync(s->host_ctrl, s->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s->stream));
+  IDX_TRY(cudaStreamSynchronize(s->stream));
+  return IDX_OK;
+}
+
+int pending_error(idx_sim* s) {
+  if (s->host_ctrl->err != 0) {
+    s->last_bad = (int64_t)s->host_ctrl->bad_cell;
+    return s->host_ctrl->err;
+  }
+  return IDX_OK;
+}
+
+// Reset time/flags and run the signal-speed pass on the current state U.
+int after_new_state(idx_sim* s) {
+  Ctrl c;
+  std::memset(&c, 0, sizeof(c));
+  c.t = 0.0;
+  c.t_end = std::numeric_limits<double>::infinity();
+  c.cfl = s->solver.cfl;
+  c.bad_cell = ~0ull;
+  IDX_TRY(cudaMemcpyAsync(s->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s->stream));
+  const Geo& g = s->geo;
+  if (s->solver.precision == IDX_FP32_BULK) {
+    launch_fluxes<float>(s, s->U, s->Wf, s->Ff, 0);
+    k_inv_only<float><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
+        g, cst(s->Ff[0]), cst(s->Ff[1]), cst(s->Ff[2]), s->ctrl);
+  } else {
+    launch_fluxes<double>(s, s->U, s->Wd, s->Fd, 0);
+    k_inv_only<double><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
+        g, cst(s->Fd[0]), cst(s->Fd[1]), cst(s->Fd[2]), s->ctrl);
+  }
+  IDX_TRY(cudaGetLastError());
+  int rc = sync_ctrl(s);
+  if (rc != IDX_OK) return rc;
+  s->last_bad = -1;
+  return pending_error(s);
+}
+
+bool valid_solver(const idx_solver* v) {
+  return v && v->recon == 1 && v->riemann == 4 && v->emf == 2 && v->rk_order == 2 &&
+         v->cfl > 0.0 && v->cfl < 1.0 &&
+         (v->precision == IDX_FP64 || v->precision == IDX_FP32_BULK);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* idx_strerror(int code) {
+  switch (code) {
+    case IDX_OK: return "ok";
+    case IDX_EINVAL: return "invalid argument";
+    case IDX_ENOMEM: return "device allocation failed";
+    case IDX_ENONPHYS: return "non-physical state (rho <= 0, P <= 0 or non-finite)";
+    case IDX_ECUDA: return "CUDA runtime error";
+    case IDX_ETIMEOUT: return "bounded wait expired";
+    default: return "unknown error";
+  }
+}
+
+int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, void* stream,
+               idx_sim** out) {
+  if (!out) return IDX_EINVAL;
+  *out = nullptr;
+  if (!grid || !valid_solver(solver) || !(gamma > 1.0) || !std::isfinite(gamma)) return IDX_EINVAL;
+  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return IDX_EINVAL;
+  if (!(grid->lx > 0) || !(grid->ly > 0) || !(grid->lz > 0)) return IDX_EINVAL;
+  const long long ncell = (long long)grid->nx * grid->ny * grid->nz;
+  if (ncell >= (1ll << 31)) return IDX_EINVAL;
+
+  idx_sim* s = new idx_sim();
+  std::memset(s, 0, sizeof(*s));
+  s->grid = *grid;
+  s->gamma = gamma;
+  s->solver = *solver;
+  s->last_bad = -1;
+  if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return IDX_ECUDA; }
+  Geo& g = s->geo;
+  g.n[0] = grid->nx; g.n[1] = grid->ny; g.n[2] = grid->nz;
+  g.stride[0] = 1; g.stride[1] = grid->nx; g.stride[2] = grid->nx * grid->ny;
+  g.ncell = (int)ncell;
+  const double l[3] = {grid->lx, grid->ly, grid->lz};
+  for (int d = 0; d < 3; ++d) {
+    g.active[d] = g.n[d] > 1;
+    g.inv_dl[d] = (double)g.n[d] / l[d];
+  }
+  g.gamma = gamma;
+
+  // memory plan: U, U1 (16 doubles/cell) + W, F (3 x 8), E (3) in the bulk type
+  const bool f32 = solver->precision == IDX_FP32_BULK;
+  const size_t tsz = f32 ? sizeof(float) : sizeof(double);
+  auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t arr_d = align(sizeof(double) * ncell), arr_t = align(tsz * ncell);
+  const size_t bytes = 16 * arr_d + (8 + 24 + 3) * arr_t + align(sizeof(Ctrl));
+  if (cudaMalloc(&s->mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    return IDX_ENOMEM;
+  }
+  s->mem_bytes = bytes;
+  char* p = (char*)s->mem;
+  for (int f = 0; f < 8; ++f) { s->U.f[f] = (double*)p; p += arr_d; }
+  for (int f = 0; f < 8; ++f) { s->U1.f[f] = (double*)p; p += arr_d; }
+  if (f32) {
+    for (int f = 0; f < 8; ++f) { s->Wf.f[f] = (float*)p; p += arr_t; }
+    for (int d = 0; d < 3; ++d)
+      for (int f = 0; f < 8; ++f) { s->Ff[d].f[f] = (float*)p; p += arr_t; }
+    for (int d = 0; d < 3; ++d) { s->Ef[d] = (float*)p; p += arr_t; }
+  } else {
+    for (int f = 0; f < 8; ++f) { s->Wd.f[f] = (double*)p; p += arr_t; }
+    for (int d = 0; d < 3; ++d)
+      for (int f = 0; f < 8; ++f) { s->Fd[d].f[f] = (double*)p; p += arr_t; }
+    for (int d = 0; d < 3; ++d) { s->Ed[d] = (double*)p; p += arr_t; }
+  }
+  s->ctrl = (Ctrl*)p;
+  int rc = IDX_OK;
+  if (cudaMemset(s->mem, 0, bytes) != cudaSuccess) rc = IDX_ECUDA;
+  if (rc == IDX_OK && cudaMallocHost(&s->host_ctrl, sizeof(Ctrl)) != cudaSuccess) rc = IDX_ENOMEM;
+  if (rc == IDX_OK) {
+    if (stream) {
+      s->stream = (cudaStream_t)stream;
+      s->own_stream = false;
+    } else {
+      if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) rc = IDX_ECUDA;
+      s->own_stream = true;
+    }
+  }
+  if (rc != IDX_OK) {
+    idx_destroy(s);
+    return rc;
+  }
+  *out = s;
+  return IDX_OK;
+}
+
+void idx_destroy(idx_sim* s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->exec) cudaGraphExecDestroy(s->exec);
+  if (s->graph) cudaGraphDestroy(s->graph);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  if (s->host_ctrl) cudaFreeHost(s->host_ctrl);
+  if (s->mem) cudaFree(s->mem);
+  delete s;
+}
+
+static int copy_fields_in(idx_sim* s, Ptr8<double> dst, const double* const fields[8],
+                          int on_device) {
+  for (int f = 0; f < 8; ++f)
+    if (!fields[f]) return IDX_EINVAL;
+  const size_t bytes = sizeof(double) * (size_t)s->geo.ncell;
+  for (int f = 0; f < 8; ++f)
+    IDX_TRY(cudaMemcpyAsync(dst.f[f], fields[f], bytes,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            s->stream));
+  return IDX_OK;
+}
+
+int idx_set_state(idx_sim* s, const double* const fields[8], int on_device) {
+  if (!s || !fields) return IDX_EINVAL;
+  int rc = copy_fields_in(s, s->U, fields, on_device);
+  if (rc != IDX_OK) return rc;
+  return after_new_state(s);
+}
+
+int idx_set_primitive(idx_sim* s, const double* const fields[8], int on_device) {
+  if (!s || !fields) return IDX_EINVAL;
+  // stage the primitives in U1 (scratch at this point), convert into U
+  int rc = copy_fields_in(s, s->U1, fields, on_device);
+  if (rc != IDX_OK) return rc;
+  k_cons_from_prims<<<blocks_for(s->geo.ncell), kThreads, 0, s->stream>>>(s->geo, cst(s->U1), s->U);
+  IDX_TRY(cudaGetLastError());
+  return after_new_state(s);
+}
+
+int idx_get_state(const idx_sim* cs, double* const fields[8], int on_device) {
+  idx_sim* s = const_cast<idx_sim*>(cs);
+  if (!s || !fields) return IDX_EINVAL;
+  for (int f = 0; f < 8; ++f)
+    if (!fields[f]) return IDX_EINVAL;
+  const size_t bytes = sizeof(double) * (size_t)s->geo.ncell;
+  for (int f = 0; f < 8; ++f)
+    IDX_TRY(cudaMemcpyAsync(fields[f], s->U.f[f], bytes,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            s->stream));
+  int rc = sync_ctrl(s);
+  if (rc != IDX_OK) return rc;
+  return pending_error(s);
+}
+
+int idx_step(idx_sim* s, double* dt_taken) {
+  if (!s) return IDX_EINVAL;
+  int rc = build_graph(s);
+  if (rc != IDX_OK) return rc;
+  IDX_TRY(cudaGraphLaunch(s->exec, s->stream));
+  if (!dt_taken) return IDX_OK;
+  rc = sync_ctrl(s);
+  if (rc != IDX_OK) return rc;
+  rc = pending_error(s);
+  if (rc != IDX_OK) return rc;
+  *dt_taken = s->host_ctrl->last_dt;
+  return IDX_OK;
+}
+
+int idx_advance(idx_sim* s, double t_end, int64_t* nsteps) {
+  if (!s || !(t_end >= 0.0) || !std::isfinite(t_end)) return IDX_EINVAL;
+  int rc = build_graph(s);
+  if (rc != IDX_OK) return rc;
+  rc = sync_ctrl(s);
+  if (rc != IDX_OK) return rc;
+  rc = pending_error(s);
+  if (rc != IDX_OK) return rc;
+  const long long n0 = s->host_ctrl->nsteps;
+  // arm the end time
+  Ctrl c = *s->host_ctrl;
+  c.t_end = t_end;
+  c.done = (c.t >= t_end) ? 1 : 0;
+  IDX_TRY(cudaMemcpyAsync(s->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s->stream));
+  int chunk = 4;
+  while (true) {
+    for (int q = 0; q < chunk; ++q) IDX_TRY(cudaGraphLaunch(s->exec, s->stream));
+    rc = sync_ctrl(s);
+    if (rc != IDX_OK) return rc;
+    if (s->host_ctrl->err) break;
+    if (s->host_ctrl->done) break;
+    if (chunk < 256) chunk *= 2;
+  }
+  // disarm: later idx_step calls run unclamped
+  c = *s->host_ctrl;
+  c.t_end = std::numeric_limits<double>::infinity();
+  c.done = 0;
+  IDX_TRY(cudaMemcpyAsync(s->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s->stream));
+  IDX_TRY(cudaStreamSynchronize(s->stream));
+  if (nsteps) *nsteps = (int64_t)(c.nsteps - n0);
+  return pending_error(s);
+}
+
+int idx_time(const idx_sim* cs, double* t, double* next_dt) {
+  idx_sim* s = const_cast<idx_sim*>(cs);
+  if (!s) return IDX_EINVAL;
+  int rc = sync_ctrl(s);
+  if (rc != IDX_OK) return rc;
+  if (t) *t = s->host_ctrl->t;
+  if (next_dt) {
+    double inv;
+    std::memcpy(&inv, &s->host_ctrl->inv_prev, sizeof(double));
+    *next_dt = s->solver.cfl / inv;
+  }
+  return pending_error(s);
+}
+
+int idx_kernel_times(idx_sim* s, int reps, double ms[6]) {
+  if (!s || !ms || reps < 1) return IDX_EINVAL;
+  int rc = sync_ctrl(s);
+  if (rc != IDX_OK) return rc;
+  rc = pending_error(s);
+  if (rc != IDX_OK) return rc;
+  cudaEvent_t ev[7];
+  for (int q = 0; q < 7; ++q) IDX_TRY(cudaEventCreate(&ev[q]));
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  int n_stage = 0;
+  const Geo& g = s->geo;
+  const bool f32 = s->solver.precision == IDX_FP32_BULK;
+  for (int r = 0; r < reps; ++r) {
+    k_begin<<<1, 1, 0, s->stream>>>(s->ctrl);
+    for (int st = 0; st < 2; ++st) {
+      const Ptr8<double>& Uin = st == 0 ? s->U : s->U1;
+      const Ptr8<double>& Uout = st == 0 ? s->U1 : s->U;
+      IDX_TRY(cudaEventRecord(ev[0], s->stream));
+      if (f32) {
+        k_prims<float><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), s->Wf, s->ctrl, 1);
+      } else {
+        k_prims<double><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), s->Wd, s->ctrl, 1);
+      }
+      IDX_TRY(cudaEventRecord(ev[1], s->stream));
+      for (int d = 0; d < 3; ++d) {
+        if (g.active[d]) {
+          const int a = (d + 1) % 3, b = (d + 2) % 3;
+          const unsigned nb = blocks_for((long)g.n[a] * g.n[b] * ((g.n[d] + kSeg - 1) / kSeg));
+          if (f32) {
+            if (d == 0) k_sweep<float, 0><<<nb, kThreads, 0, s->stream>>>(g, cst(s->Wf), Uin.f[5], s->Ff[0], s->ctrl, 1);
+            if (d == 1) k_sweep<float, 1><<<nb, kThreads, 0, s->stream>>>(g, cst(s->Wf), Uin.f[6], s->Ff[1], s->ctrl, 1);
+            if (d == 2) k_sweep<float, 2><<<nb, kThreads, 0, s->stream>>>(g, cst(s->Wf), Uin.f[7], s->Ff[2], s->ctrl, 1);
+          } else {
+            if (d == 0) k_sweep<double, 0><<<nb, kThreads, 0, s->stream>>>(g, cst(s->Wd), Uin.f[5], s->Fd[0], s->ctrl, 1);
+            if (d == 1) k_sweep<double, 1><<<nb, kThreads, 0, s->stream>>>(g, cst(s->Wd), Uin.f[6], s->Fd[1], s->ctrl, 1);
+            if (d == 2) k_sweep<double, 2><<<nb, kThreads, 0, s->stream>>>(g, cst(s->Wd), Uin.f[7], s->Fd[2], s->ctrl, 1);
+          }
+        }
+        IDX_TRY(cudaEventRecord(ev[2 + d], s->stream));
+      }
+      if (f32) {
+        k_emf<float><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(s->Wf), cst(s->Ff[0]), cst(s->Ff[1]), cst(s->Ff[2]), s->Ef[0], s->Ef[1], s->Ef[2], s->ctrl);
+      } else {
+        k_emf<double><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(s->Wd), cst(s->Fd[0]), cst(s->Fd[1]), cst(s->Fd[2]), s->Ed[0], s->Ed[1], s->Ed[2], s->ctrl);
+      }
+      IDX_TRY(cudaEventRecord(ev[5], s->stream));
+      if (f32) {
+        if (st == 0) k_update<float, false><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), cst(s->U), cst(s->Ff[0]), cst(s->Ff[1]), cst(s->Ff[2]), s->Ef[0], s->Ef[1], s->Ef[2], Uout, s->ctrl);
+        else k_update<float, true><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), cst(s->U), cst(s->Ff[0]), cst(s->Ff[1]), cst(s->Ff[2]), s->Ef[0], s->Ef[1], s->Ef[2], Uout, s->ctrl);
+      } else {
+        if (st == 0) k_update<double, false><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), cst(s->U), cst(s->Fd[0]), cst(s->Fd[1]), cst(s->Fd[2]), s->Ed[0], s->Ed[1], s->Ed[2], Uout, s->ctrl);
+        else k_update<double, true><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), cst(s->U), cst(s->Fd[0]), cst(s->Fd[1]), cst(s->Fd[2]), s->Ed[0], s->Ed[1], s->Ed[2], Uout, s->ctrl);
+      }
+      IDX_TRY(cudaEventRecord(ev[6], s->stream));
+      IDX_TRY(cudaEventSynchronize(ev[6]));
+      float t[6];
+      for (int q = 0; q < 6; ++q) IDX_TRY(cudaEventElapsedTime(&t[q], ev[q], ev[q + 1]));
+      for (int q = 0; q < 6; ++q) acc[q] += t[q];
+      ++n_stage;
+    }
+    k_end<<<1, 1, 0, s->stream>>>(s->ctrl);
+  }
+  IDX_TRY(cudaGetLastError());
+  for (int q = 0; q < 7; ++q) cudaEventDestroy(ev[q]);
+  for (int q = 0; q < 6; ++q) ms[q] = acc[q] / n_stage;
+  rc = sync_ctrl(s);
+  if (rc != IDX_OK) return rc;
+  return pending_error(s);
+}
+
+int idx_last_error_cell(const idx_sim* s, int64_t* cell) {
+  if (!s || !cell) return IDX_EINVAL;
+  *cell = s->last_bad;
+  return IDX_OK;
+}
+
+}  // extern "C"

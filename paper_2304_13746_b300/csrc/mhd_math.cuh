@@ -1,0 +1,203 @@
+// mhd_math.cuh -- per-face and per-edge arithmetic of the ideal-MHD stage (device code).
+//
+// Written for the FP64 pipe of sm_103a (and its FP32 pipe in the FP32-bulk variant):
+// reciprocals are formed once and reused, only the upwind side's physical flux and
+// star state are built, and the E^c edge formula uses the cancelled form (the cell
+// sizes drop out).  The scalar type T is double (FP64 path) or float (FP32 bulk).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace idx {
+
+template <typename T> struct Eps;
+template <> struct Eps<double> {
+  // HLLD degeneracy thresholds (relative): D_alpha ~ 0 and Bx^2 ~ 0 (HLLC limit)
+  static constexpr double degen = 1e-12;
+  static constexpr double hllc = 1e-12;
+};
+template <> struct Eps<float> {
+  // FP32 keeps ~7 digits: the same tests with a threshold above its rounding level
+  static constexpr float degen = 2e-6f;
+  static constexpr float hllc = 2e-6f;
+};
+
+template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a < b ? b : a; }
+template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return b < a ? b : a; }
+__device__ __forceinline__ double tsqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float tsqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ double tabs(double a) { return fabs(a); }
+__device__ __forceinline__ float tabs(float a) { return fabsf(a); }
+
+// van Leer (harmonic) limited slope from the two one-sided differences (Sec. 2.3).
+template <typename T> __device__ __forceinline__ T vanleer(T dl, T dr) {
+  const T prod = dl * dr;
+  return prod > T(0) ? T(2) * prod / (dl + dr) : T(0);
+}
+
+// Primitive state on one side of a face, rotated so that "u" is the normal velocity.
+template <typename T> struct Side {
+  T r, u, v, w, p, b1, b2;  // rho, v_n, v_t1, v_t2, P, B_t1, B_t2
+};
+
+// HLLD flux (Miyoshi & Kusano 2005) at a face with normal field bx.  Output order:
+// rho, m_n, m_t1, m_t2, E, B_t1, B_t2; c = max(|S_L|, |S_R|) for the CFL condition.
+template <typename T>
+__device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T gamma,
+                                     T gm1inv, T F[7], T& c) {
+  const T bx2 = bx * bx;
+  const T magL = T(0.5) * (bx2 + L.b1 * L.b1 + L.b2 * L.b2);
+  const T magR = T(0.5) * (bx2 + R.b1 * R.b1 + R.b2 * R.b2);
+  const T pTL = L.p + magL, pTR = R.p + magR;
+
+  // outer speeds from the fast magnetosonic speeds (MK05 eq. 67)
+  const T gpL = gamma * L.p, gpR = gamma * R.p;
+  const T aL = gpL + T(2) * magL, aR = gpR + T(2) * magR;
+  const T dL = tmax(aL * aL - T(4) * gpL * bx2, T(0));
+  const T dR = tmax(aR * aR - T(4) * gpR * bx2, T(0));
+  const T cfL = tsqrt((aL + tsqrt(dL)) * (T(0.5) / L.r));
+  const T cfR = tsqrt((aR + tsqrt(dR)) * (T(0.5) / R.r));
+  const T cfm = tmax(cfL, cfR);
+  const T SL = tmin(L.u, R.u) - cfm;
+  const T SR = tmax(L.u, R.u) + cfm;
+  c = tmax(tabs(SL), tabs(SR));
+
+  if (SL > T(0) || SR < T(0)) {  // supersonic: upwind physical flux
+    const Side<T>& s = (SL > T(0)) ? L : R;
+    const T pT = (SL > T(0)) ? pTL : pTR;
+    const T E = s.p * gm1inv + T(0.5) * s.r * (s.u * s.u + s.v * s.v + s.w * s.w) +
+                ((SL > T(0)) ? magL : magR);
+    const T vb = s.u * bx + s.v * s.b1 + s.w * s.b2;
+    const T ru = s.r * s.u;
+    F[0] = ru;
+    F[1] = ru * s.u + pT - bx2;
+    F[2] = ru * s.v - bx * s.b1;
+    F[3] = ru * s.w - bx * s.b2;
+    F[4] = (E + pT) * s.u - bx * vb;
+    F[5] = s.b1 * s.u - bx * s.v;
+    F[6] = s.b2 * s.u - bx * s.w;
+    return;
+  }
+
+  // contact speed and star total pressure
+  const T sLu = SL - L.u, sRu = SR - R.u;
+  const T qL = sLu * L.r, qR = sRu * R.r;
+  const T SM = (qR * R.u - qL * L.u - pTR + pTL) / (qR - qL);
+  const T pTs = pTL + qL * (SM - L.u);
+
+  // single-star transverse states, both sides (needed by the double-star average)
+  const T iL = T(1) / (SL - SM), iR = T(1) / (SR - SM);
+  const T rsL = qL * iL, rsR = qR * iR;  // rho*
+  T vsL, wsL, b1sL, b2sL, vsR, wsR, b1sR, b2sR;
+  {
+    const T q = qL * (SL - SM);
+    const T D = q - bx2;
+    if (tabs(D) <= Eps<T>::degen * (tabs(q) + bx2)) {
+      vsL = L.v; wsL = L.w; b1sL = L.b1; b2sL = L.b2;
+    } else {
+      const T iD = T(1) / D;
+      const T t = bx * (SM - L.u) * iD;
+      vsL = L.v - L.b1 * t;
+      wsL = L.w - L.b2 * t;
+      const T g = (qL * sLu - bx2) * iD;
+      b1sL = L.b1 * g;
+      b2sL = L.b2 * g;
+    }
+  }
+  {
+    const T q = qR * (SR - SM);
+    const T D = q - bx2;
+    if (tabs(D) <= Eps<T>::degen * (tabs(q) + bx2)) {
+      vsR = R.v; wsR = R.w; b1sR = R.b1; b2sR = R.b2;
+    } else {
+      const T iD = T(1) / D;
+      const T t = bx * (SM - R.u) * iD;
+      vsR = R.v - R.b1 * t;
+      wsR = R.w - R.b2 * t;
+      const T g = (qR * sRu - bx2) * iD;
+      b1sR = R.b1 * g;
+      b2sR = R.b2 * g;
+    }
+  }
+
+  // Alfven fan speeds
+  const T sqL = tsqrt(rsL), sqR = tsqrt(rsR);
+  const T abx = tabs(bx);
+  const T SsL = SM - abx / sqL;
+  const T SsR = SM + abx / sqR;
+
+  // the side that contains x/t = 0
+  const bool left = SM >= T(0);
+  const Side<T>& s = left ? L : R;
+  const T S = left ? SL : SR;
+  const T su = left ? sLu : sRu;
+  const T is = left ? iL : iR;
+  const T rs = left ? rsL : rsR;
+  const T pT = left ? pTL : pTR;
+  const T vs = left ? vsL : vsR, ws = left ? wsL : wsR;
+  const T b1s = left ? b1sL : b1sR, b2s = left ? b2sL : b2sR;
+
+  const T E = s.p * gm1inv + T(0.5) * s.r * (s.u * s.u + s.v * s.v + s.w * s.w) +
+              (left ? magL : magR);
+  const T vb = s.u * bx + s.v * s.b1 + s.w * s.b2;
+  const T vbs = SM * bx + vs * b1s + ws * b2s;
+  const T Es = (su * E - pT * s.u + pTs * SM + bx * (vb - vbs)) * is;
+
+  // physical flux and conserved vector of the side
+  const T ru = s.r * s.u;
+  T Fs[7], Us[7], Ustar[7];
+  Fs[0] = ru;
+  Fs[1] = ru * s.u + pT - bx2;
+  Fs[2] = ru * s.v - bx * s.b1;
+  Fs[3] = ru * s.w - bx * s.b2;
+  Fs[4] = (E + pT) * s.u - bx * vb;
+  Fs[5] = s.b1 * s.u - bx * s.v;
+  Fs[6] = s.b2 * s.u - bx * s.w;
+  Us[0] = s.r; Us[1] = ru; Us[2] = s.r * s.v; Us[3] = s.r * s.w; Us[4] = E;
+  Us[5] = s.b1; Us[6] = s.b2;
+  Ustar[0] = rs; Ustar[1] = rs * SM; Ustar[2] = rs * vs; Ustar[3] = rs * ws; Ustar[4] = Es;
+  Ustar[5] = b1s; Ustar[6] = b2s;
+#pragma unroll
+  for (int q = 0; q < 7; ++q) F[q] = Fs[q] + S * (Ustar[q] - Us[q]);
+
+  const bool dbl = left ? (SsL < T(0)) : (SsR >= T(0));
+  if (dbl && !(T(0.5) * bx2 < Eps<T>::hllc * pTs)) {
+    const T sgn = bx < T(0) ? T(-1) : T(1);
+    const T isum = T(1) / (sqL + sqR);
+    const T v2 = (sqL * vsL + sqR * vsR + (b1sR - b1sL) * sgn) * isum;
+    const T w2 = (sqL * wsL + sqR * wsR + (b2sR - b2sL) * sgn) * isum;
+    const T sLR = sqL * sqR;
+    const T b12 = (sqL * b1sR + sqR * b1sL + sLR * (vsR - vsL) * sgn) * isum;
+    const T b22 = (sqL * b2sR + sqR * b2sL + sLR * (wsR - wsL) * sgn) * isum;
+    const T vb2 = SM * bx + v2 * b12 + w2 * b22;
+    const T sq = left ? sqL : sqR;
+    const T E2 = left ? Es - sq * (vbs - vb2) * sgn : Es + sq * (vbs - vb2) * sgn;
+    const T Ss = left ? SsL : SsR;
+    F[2] += Ss * (rs * v2 - Ustar[2]);
+    F[3] += Ss * (rs * w2 - Ustar[3]);
+    F[4] += Ss * (E2 - Es);
+    F[5] += Ss * (b12 - b1s);
+    F[6] += Ss * (b22 - b2s);
+    // rho and m_n are continuous across the rotational waves: no change in F[0], F[1]
+  }
+}
+
+// E^c EMF at one edge (Gardiner & Stone 2005), cancelled form: with X, Y the a- and
+// b-face EMFs, C the cell-centre EMFs and the upwind choice of each one-sided
+// derivative taken from the sign of the matching face mass flux (mean at zero),
+//   E = 1/4 [X0 + X1 + Y0 + Y1 + (dB3 - dB1) + (dA3 - dA1)]
+// where dB1 = C(c,J) - Y(c), dB3 = Y(c) - C(c,J-1), dA1 = C(I,r) - X(r),
+// dA3 = X(r) - C(I-1,r).  Index 0 = J or I, index 1 = J-1 or I-1; C[c][r].
+template <typename T>
+__device__ __forceinline__ T emf_ec(T X0, T X1, T Y0, T Y1, T C00, T C01, T C10, T C11, T Fa0,
+                                    T Fa1, T Fb0, T Fb1) {
+  auto pick = [](T f, T up, T dn) {
+    return f > T(0) ? up : (f < T(0) ? dn : T(0.5) * (up + dn));
+  };
+  const T dB1 = pick(Fa0, C10 - Y1, C00 - Y0);
+  const T dB3 = pick(Fa1, Y1 - C11, Y0 - C01);
+  const T dA1 = pick(Fb0, C01 - X1, C00 - X0);
+  const T dA3 = pick(Fb1, X1 - C11, X0 - C10);
+  return T(0.25) * ((X0 + X1) + (Y0 + Y1) + (dB3 - dB1) + (dA3 - dA1));
+}
+
+}  // namespace idx

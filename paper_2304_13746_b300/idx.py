@@ -1,0 +1,204 @@
+"""Python binding of libidx.so (include/idx.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; this module converts
+numpy arrays / torch CUDA tensors to pointers and return codes to exceptions.
+There is no fallback: if libidx.so cannot be loaded, ``lib()`` raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libidx.so")
+
+IDX_OK, IDX_EINVAL, IDX_ENOMEM, IDX_ENONPHYS, IDX_ECUDA, IDX_ETIMEOUT = 0, -1, -2, -3, -4, -5
+IDX_FP64, IDX_FP32_BULK = 0, 1
+PRECISIONS = {"fp64": IDX_FP64, "fp32": IDX_FP32_BULK, "fp32_bulk": IDX_FP32_BULK}
+
+_lib = None
+
+
+class IdxError(RuntimeError):
+    def __init__(self, code, where, cell=-1):
+        msg = f"{where}: {strerror(code) if _lib else code} (code {code})"
+        if cell >= 0:
+            msg += f", cell {cell}"
+        super().__init__(msg)
+        self.code = code
+        self.cell = cell
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double)]
+
+
+class Solver(ctypes.Structure):
+    _fields_ = [("recon", ctypes.c_int), ("riemann", ctypes.c_int), ("emf", ctypes.c_int),
+                ("rk_order", ctypes.c_int), ("cfl", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+P8 = ctypes.c_void_p * 8
+
+
+def lib(path=LIB_PATH):
+    """Load libidx.so (built by paper_2304_13746_b300.build); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libidx.so not found at {path}: build it with "
+                           "python -m paper_2304_13746_b300.build (no CPU fallback exists)")
+    L = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    L.idx_create.argtypes = [ctypes.POINTER(Grid), ctypes.c_double, ctypes.POINTER(Solver), vp,
+                             ctypes.POINTER(vp)]
+    L.idx_set_state.argtypes = [vp, P8, ctypes.c_int]
+    L.idx_set_primitive.argtypes = [vp, P8, ctypes.c_int]
+    L.idx_get_state.argtypes = [vp, P8, ctypes.c_int]
+    L.idx_step.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.idx_advance.argtypes = [vp, ctypes.c_double, ctypes.POINTER(ctypes.c_int64)]
+    L.idx_time.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.idx_last_error_cell.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    L.idx_destroy.argtypes = [vp]
+    L.idx_destroy.restype = None
+    L.idx_strerror.argtypes = [ctypes.c_int]
+    L.idx_strerror.restype = ctypes.c_char_p
+    L.idx_pipe_rates.argtypes = [ctypes.POINTER(ctypes.c_double)]
+    L.idx_kernel_times.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    _lib = L
+    return L
+
+
+def strerror(code):
+    return lib().idx_strerror(code).decode()
+
+
+def pipe_rates():
+    """Measured FP64/FP32 pipe throughputs (ops/s): fma64, div64, sqrt64, fma32, div32, sqrt32."""
+    out = (ctypes.c_double * 6)()
+    rc = lib().idx_pipe_rates(out)
+    if rc != IDX_OK:
+        raise IdxError(rc, "idx_pipe_rates")
+    keys = ("fma64", "div64", "sqrt64", "fma32", "div32", "sqrt32")
+    return dict(zip(keys, out[:]))
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _torch_sync():
+    import torch
+    torch.cuda.current_stream().synchronize()
+
+
+class Sim:
+    """One periodic MHD box on the current CUDA device.
+
+    shape = (nz, ny, nx); lengths = (lx, ly, lz).  Fields are 8 arrays of that shape:
+    numpy float64 (host) or contiguous torch float64 CUDA tensors (device).
+    """
+
+    def __init__(self, shape, lengths, gamma=5.0 / 3.0, cfl=0.4, precision="fp64", stream=None):
+        L = lib()
+        nz, ny, nx = (int(s) for s in shape)
+        self.shape = (nz, ny, nx)
+        self.lengths = tuple(float(x) for x in lengths)
+        self.gamma = float(gamma)
+        self.cfl = float(cfl)
+        self.precision = precision
+        g = Grid(nx, ny, nz, *self.lengths)
+        s = Solver(1, 4, 2, 2, self.cfl, PRECISIONS[precision])
+        h = ctypes.c_void_p()
+        rc = L.idx_create(ctypes.byref(g), self.gamma, ctypes.byref(s),
+                          ctypes.c_void_p(stream) if stream else None, ctypes.byref(h))
+        if rc != IDX_OK:
+            raise IdxError(rc, "idx_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().idx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, where):
+        if rc != IDX_OK:
+            cell = ctypes.c_int64(-1)
+            lib().idx_last_error_cell(self._h, ctypes.byref(cell))
+            raise IdxError(rc, where, cell.value)
+
+    def _ptrs(self, fields, writable=False):
+        assert len(fields) == 8
+        if all(_is_torch(a) for a in fields):
+            import torch
+            for a in fields:
+                assert a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()
+                assert tuple(a.shape) == self.shape
+            _torch_sync()
+            return P8(*[a.data_ptr() for a in fields]), 1, fields
+        arrs = []
+        for a in fields:
+            a = np.asarray(a)
+            assert a.dtype == np.float64 and a.flags.c_contiguous and a.shape == self.shape, \
+                (a.dtype, a.shape)
+            if writable:
+                assert a.flags.writeable
+            arrs.append(a)
+        return P8(*[a.ctypes.data for a in arrs]), 0, arrs
+
+    def set_state(self, cons):
+        p, dev, keep = self._ptrs(cons)
+        self._check(lib().idx_set_state(self._h, p, dev), "idx_set_state")
+
+    def set_primitive(self, prim):
+        p, dev, keep = self._ptrs([np.ascontiguousarray(a, dtype=np.float64)
+                                   if not _is_torch(a) else a for a in prim])
+        self._check(lib().idx_set_primitive(self._h, p, dev), "idx_set_primitive")
+
+    def get_state(self, out=None, device=False):
+        if out is None:
+            if device:
+                import torch
+                out = [torch.empty(self.shape, dtype=torch.float64, device="cuda")
+                       for _ in range(8)]
+            else:
+                out = [np.empty(self.shape, dtype=np.float64) for _ in range(8)]
+        p, dev, keep = self._ptrs(out, writable=True)
+        self._check(lib().idx_get_state(self._h, p, dev), "idx_get_state")
+        return out
+
+    def step(self, want_dt=False):
+        if want_dt:
+            dt = ctypes.c_double()
+            self._check(lib().idx_step(self._h, ctypes.byref(dt)), "idx_step")
+            return dt.value
+        self._check(lib().idx_step(self._h, None), "idx_step")
+        return None
+
+    def advance(self, t_end):
+        n = ctypes.c_int64()
+        self._check(lib().idx_advance(self._h, float(t_end), ctypes.byref(n)), "idx_advance")
+        return n.value
+
+    def kernel_times(self, reps=2):
+        """Per-launch device ms of each kernel (events between launches); advances reps cycles."""
+        out = (ctypes.c_double * 6)()
+        self._check(lib().idx_kernel_times(self._h, int(reps), out), "idx_kernel_times")
+        return dict(zip(("prims", "sweep_x", "sweep_y", "sweep_z", "emf", "update"), out[:]))
+
+    def time(self):
+        t, dt = ctypes.c_double(), ctypes.c_double()
+        self._check(lib().idx_time(self._h, ctypes.byref(t), ctypes.byref(dt)), "idx_time")
+        return t.value, dt.value

@@ -1,0 +1,84 @@
+"""The C-ABI library loads on the CPU, exports every entry point include/idx.h declares,
+and rejects invalid arguments before touching the GPU (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2304_13746_b300 import build as idx_build
+from paper_2304_13746_b300 import idx
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "idx.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(idx_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    idx_build.build()
+    return idx.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_symbols()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_strerror_covers_codes(L):
+    for code in (0, -1, -2, -3, -4, -5):
+        assert idx.strerror(code) not in ("", "unknown error")
+    assert idx.strerror(-99) == "unknown error"
+
+
+def _create(L, grid, gamma=5 / 3, solver=None):
+    s = solver or idx.Solver(1, 4, 2, 2, 0.4, 0)
+    h = ctypes.c_void_p()
+    rc = L.idx_create(ctypes.byref(grid) if grid is not None else None, gamma,
+                      ctypes.byref(s), None, ctypes.byref(h))
+    return rc, h
+
+
+@pytest.mark.parametrize("grid,gamma,solver", [
+    (idx.Grid(0, 4, 4, 1, 1, 1), 5 / 3, None),
+    (idx.Grid(4, 4, 4, 1, -1, 1), 5 / 3, None),
+    (idx.Grid(4, 4, 4, 1, 1, 1), 1.0, None),
+    (idx.Grid(4, 4, 4, 1, 1, 1), float("nan"), None),
+    (idx.Grid(2048, 2048, 1024, 1, 1, 1), 5 / 3, None),           # >= 2^31 cells
+    (idx.Grid(4, 4, 4, 1, 1, 1), 5 / 3, idx.Solver(2, 4, 2, 2, 0.4, 0)),  # recon
+    (idx.Grid(4, 4, 4, 1, 1, 1), 5 / 3, idx.Solver(1, 3, 2, 2, 0.4, 0)),  # riemann
+    (idx.Grid(4, 4, 4, 1, 1, 1), 5 / 3, idx.Solver(1, 4, 1, 2, 0.4, 0)),  # emf
+    (idx.Grid(4, 4, 4, 1, 1, 1), 5 / 3, idx.Solver(1, 4, 2, 3, 0.4, 0)),  # rk order
+    (idx.Grid(4, 4, 4, 1, 1, 1), 5 / 3, idx.Solver(1, 4, 2, 2, 1.0, 0)),  # cfl
+    (idx.Grid(4, 4, 4, 1, 1, 1), 5 / 3, idx.Solver(1, 4, 2, 2, 0.4, 7)),  # precision
+])
+def test_create_rejects_invalid_arguments(L, grid, gamma, solver):
+    rc, h = _create(L, grid, gamma, solver)
+    assert rc == idx.IDX_EINVAL and not h.value
+
+
+def test_null_arguments(L):
+    assert L.idx_create(None, 5 / 3, None, None, None) == idx.IDX_EINVAL
+    rc, _ = _create(L, None)
+    assert rc == idx.IDX_EINVAL
+    assert L.idx_step(None, None) == idx.IDX_EINVAL
+    assert L.idx_advance(None, 1.0, None) == idx.IDX_EINVAL
+    assert L.idx_set_state(None, idx.P8(), 0) == idx.IDX_EINVAL
+    assert L.idx_pipe_rates(None) == idx.IDX_EINVAL
+    L.idx_destroy(None)
+
+
+def test_binding_refuses_to_run_without_library(tmp_path):
+    saved = idx._lib
+    idx._lib = None
+    try:
+        with pytest.raises(RuntimeError, match="no CPU fallback"):
+            idx.lib(str(tmp_path / "missing.so"))
+    finally:
+        idx._lib = saved
