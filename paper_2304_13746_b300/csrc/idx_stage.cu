@@ -630,8 +630,7 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
   }
   s->ctrl = (Ctrl*)p;
   int rc = IDX_OK;
-  if (cudaMemset(s->mem, 0, bytes) != cudaSuccess) rc = IDX_ECUDA;
-  if (rc == IDX_OK && cudaMallocHost(&s->host_ctrl, sizeof(Ctrl)) != cudaSuccess) rc = IDX_ENOMEM;
+  if (cudaMallocHost(&s->host_ctrl, sizeof(Ctrl)) != cudaSuccess) rc = IDX_ENOMEM;
   if (rc == IDX_OK) {
     if (stream) {
       s->stream = (cudaStream_t)stream;
@@ -641,6 +640,10 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
       s->own_stream = true;
     }
   }
+  // clear on the sim's own stream: a non-blocking stream is not ordered after work
+  // on the legacy default stream, so a plain cudaMemset could race the first upload
+  if (rc == IDX_OK && cudaMemsetAsync(s->mem, 0, bytes, s->stream) != cudaSuccess) rc = IDX_ECUDA;
+  if (rc == IDX_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = IDX_ECUDA;
   if (rc != IDX_OK) {
     idx_destroy(s);
     return rc;
