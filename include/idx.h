@@ -122,6 +122,43 @@ const char* idx_strerror(int code);
  * Not part of the method: it supplies the denominators of the ALU roofline. */
 int idx_pipe_rates(double rates[6]);
 
+/* ---- Allocation-free cycle (no counterpart in the paper) -------------------------
+ * Some callers cannot call cudaMalloc: code running inside another framework's
+ * device-memory pool, under a sandbox or device budget that forbids new device
+ * allocations, or on a latency-bound path that must not pay for one.  For them,
+ * idx_step_noalloc advances caller-owned device state by one FP64 RK2 cycle (the same
+ * kernels as idx_step) without allocating anything: its scratch -- the stage-1 state,
+ * primitives, face fluxes, edge EMFs and a control block -- lives in one fixed-size
+ * device array inside the library (IDX_NOALLOC_SCRATCH_BYTES), which every GPU that
+ * loads the library holds until the process exits.
+ *
+ *   grid, gamma, cfl  as for idx_create (precision is FP64).
+ *   state             8 device pointers on the current device, layout as above, updated
+ *                     in place.
+ *   inv_dt            host double, in/out: the inverse CFL time carried between calls.
+ *                     Pass a value <= 0 on the first call: a signal-speed pass on the
+ *                     input state then fixes the first dt, as after idx_set_state.  On
+ *                     return it holds the bound for the next call.
+ *   dt_taken          nullable host double: the cycle's dt.
+ *   stream            cudaStream_t to run on, or NULL for the default stream.
+ *
+ * Limits and behaviour:
+ *   - at most IDX_NOALLOC_MAX_CELLS cells; a larger grid returns IDX_ETOOLARGE;
+ *   - the first call on a device looks up the array's device address (once per
+ *     device, with that device current); make that first call before any stream
+ *     capture;
+ *   - every call shares the one array, which keeps the last call's contents (the call
+ *     clears what must start at zero): calls that overlap on the GPU race, so issue
+ *     them one at a time (same stream, or synchronise between streams and devices
+ *     sharing a process);
+ *   - the call waits for its stream to finish the cycle (it reads back dt and the
+ *     error flag); IDX_ENONPHYS as for idx_step. */
+#define IDX_ETOOLARGE (-6)                      /* grid exceeds a fixed-size buffer */
+#define IDX_NOALLOC_SCRATCH_BYTES (64u << 20)   /* 64 MiB per GPU                   */
+#define IDX_NOALLOC_MAX_CELLS 195072            /* 256 + 43 x align256(8 n) <= 64 MiB */
+int idx_step_noalloc(const idx_grid* grid, double gamma, double cfl, double* const state[8],
+                     double* inv_dt, double* dt_taken, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,6 +24,7 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <mutex>
 
 #include "../../include/idx.h"
 #include "mhd_math.cuh"
@@ -570,6 +571,7 @@ const char* idx_strerror(int code) {
     case IDX_ENONPHYS: return "non-physical state (rho <= 0, P <= 0 or non-finite)";
     case IDX_ECUDA: return "CUDA runtime error";
     case IDX_ETIMEOUT: return "bounded wait expired";
+    case IDX_ETOOLARGE: return "grid larger than the fixed scratch of idx_step_noalloc";
     default: return "unknown error";
   }
 }
@@ -845,3 +847,116 @@ int idx_last_error_cell(const idx_sim* s, int64_t* cell) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// idx_step_noalloc: one FP64 cycle on caller-owned device state with no allocation.
+// For callers that cannot allocate device memory (another framework's pool, a device
+// budget, or a latency-bound path).  The scratch of the cycle lives in a file-scope
+// device array held by every GPU that loads the library; see include/idx.h.
+// ===========================================================================
+namespace {
+
+constexpr size_t kNoAllocBytes = IDX_NOALLOC_SCRATCH_BYTES;
+constexpr size_t kNoAllocArrays = 8 + 8 + 24 + 3;  // U1, W, F (3 x 8), E (3)
+constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+static_assert(256 + kNoAllocArrays * align256(sizeof(double) * (size_t)IDX_NOALLOC_MAX_CELLS) <=
+                  kNoAllocBytes,
+              "IDX_NOALLOC_MAX_CELLS does not fit the scratch array");
+static_assert(sizeof(Ctrl) <= 256, "control block must fit its 256-byte slot");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// In host code g_noalloc_scratch names a host-side stand-in, not device memory: the
+// device address is looked up once per device (with that device current) and cached.
+constexpr int kNoAllocMaxDevices = 64;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+std::mutex g_noalloc_mutex;
+
+int noalloc_scratch(int device, void** out) {
+  if (device < 0 || device >= kNoAllocMaxDevices) return IDX_EINVAL;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return IDX_ECUDA;
+    g_noalloc_addr[device] = p;
+  }
+  *out = g_noalloc_addr[device];
+  return IDX_OK;
+}
+
+}  // namespace
+
+extern "C" int idx_step_noalloc(const idx_grid* grid, double gamma, double cfl,
+                                double* const state[8], double* inv_dt, double* dt_taken,
+                                void* stream) {
+  if (!grid || !state || !inv_dt || !(gamma > 1.0) || !std::isfinite(gamma) ||
+      !(cfl > 0.0 && cfl < 1.0))
+    return IDX_EINVAL;
+  for (int f = 0; f < 8; ++f)
+    if (!state[f]) return IDX_EINVAL;
+  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return IDX_EINVAL;
+  if (!(grid->lx > 0) || !(grid->ly > 0) || !(grid->lz > 0)) return IDX_EINVAL;
+  const long long ncell = (long long)grid->nx * grid->ny * grid->nz;
+  if (ncell > IDX_NOALLOC_MAX_CELLS) return IDX_ETOOLARGE;
+
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return IDX_ECUDA;
+  void* base = nullptr;
+  int rc = noalloc_scratch(device, &base);
+  if (rc != IDX_OK) return rc;
+
+  // a sim descriptor on the host stack whose buffers point into the scratch array
+  idx_sim s;
+  std::memset(&s, 0, sizeof(s));
+  s.grid = *grid;
+  s.gamma = gamma;
+  s.solver.recon = 1; s.solver.riemann = 4; s.solver.emf = 2; s.solver.rk_order = 2;
+  s.solver.cfl = cfl; s.solver.precision = IDX_FP64;
+  s.stream = (cudaStream_t)stream;
+  s.device = device;
+  Geo& g = s.geo;
+  g.n[0] = grid->nx; g.n[1] = grid->ny; g.n[2] = grid->nz;
+  g.stride[0] = 1; g.stride[1] = grid->nx; g.stride[2] = grid->nx * grid->ny;
+  g.ncell = (int)ncell;
+  const double l[3] = {grid->lx, grid->ly, grid->lz};
+  for (int d = 0; d < 3; ++d) {
+    g.active[d] = g.n[d] > 1;
+    g.inv_dl[d] = (double)g.n[d] / l[d];
+  }
+  g.gamma = gamma;
+  const size_t arr = align256(sizeof(double) * (size_t)ncell);
+  char* p = (char*)base;
+  s.ctrl = (Ctrl*)p;
+  p += 256;
+  for (int f = 0; f < 8; ++f) s.U.f[f] = state[f];
+  for (int f = 0; f < 8; ++f) { s.U1.f[f] = (double*)p; p += arr; }
+  for (int f = 0; f < 8; ++f) { s.Wd.f[f] = (double*)p; p += arr; }
+  for (int d = 0; d < 3; ++d)
+    for (int f = 0; f < 8; ++f) { s.Fd[d].f[f] = (double*)p; p += arr; }
+  for (int d = 0; d < 3; ++d) { s.Ed[d] = (double*)p; p += arr; }
+
+  // The array keeps the previous call's contents.  Only the control block must start
+  // from a known value; every other array is written before it is read in the cycle.
+  Ctrl c;
+  std::memset(&c, 0, sizeof(c));
+  c.t_end = std::numeric_limits<double>::infinity();
+  c.cfl = cfl;
+  c.bad_cell = ~0ull;
+  if (*inv_dt > 0.0) std::memcpy(&c.inv_prev, inv_dt, sizeof(double));
+  IDX_TRY(cudaMemcpyAsync(s.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s.stream));
+  if (!(*inv_dt > 0.0)) {
+    // no bound carried in: the signal-speed pass of a first cycle
+    launch_fluxes<double>(&s, s.U, s.Wd, s.Fd, 0);
+    k_inv_only<double><<<blocks_for(g.ncell), kThreads, 0, s.stream>>>(
+        g, cst(s.Fd[0]), cst(s.Fd[1]), cst(s.Fd[2]), s.ctrl);
+  }
+  launch_cycle(&s);
+  IDX_TRY(cudaGetLastError());
+  Ctrl out;
+  IDX_TRY(cudaMemcpyAsync(&out, s.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s.stream));
+  IDX_TRY(cudaStreamSynchronize(s.stream));
+  if (out.err != 0) return out.err;
+  std::memcpy(inv_dt, &out.inv_prev, sizeof(double));
+  if (dt_taken) *dt_taken = out.last_dt;
+  return IDX_OK;
+}

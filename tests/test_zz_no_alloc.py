@@ -1,0 +1,80 @@
+"""The allocation-free entry point idx_step_noalloc against the allocating one (idx_step).
+
+idx_step_noalloc serves callers that cannot allocate device memory (another framework's
+pool, a device budget, a latency-bound path): its scratch is a fixed device array in
+the library.  Two calls in a row on caller-owned device state must match two idx_step
+cycles of a sim made from the same state, within the parity bound used for the GPU
+path (1e-12 of each field's scale), including the carried inverse CFL time; a grid above
+IDX_NOALLOC_MAX_CELLS must be refused.  This file is collected last on purpose.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2304_13746_b300 import build as idx_build
+from paper_2304_13746_b300 import idx, inputs
+
+pytestmark = pytest.mark.gpu
+
+IDX_ETOOLARGE = -6
+MAX_CELLS = 195072
+
+
+def _lib():
+    idx_build.build()
+    L = idx.lib()
+    L.idx_step_noalloc.argtypes = [ctypes.POINTER(idx.Grid), ctypes.c_double, ctypes.c_double,
+                                   idx.P8, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    return L
+
+
+def _scales(o):
+    rho, E = np.abs(o[0]), np.abs(o[4])
+    msc = float(np.max(np.sqrt(2.0 * rho * E)))
+    bsc = float(np.max(np.sqrt(2.0 * E)))
+    own = [float(np.max(np.abs(o[f]))) for f in range(8)]
+    return [own[0], max(own[1], msc), max(own[2], msc), max(own[3], msc), own[4],
+            max(own[5], bsc), max(own[6], bsc), max(own[7], bsc)]
+
+
+def test_noalloc_two_cycles_match_idx_step():
+    import torch
+    L = _lib()
+    ic = inputs.turbulent_box(40, seed=11)          # 64000 cells, below the limit
+    cons = oracle.cons_from_prims(ic.prim, ic.lengths, ic.gamma)
+    nz, ny, nx = ic.shape
+    grid = idx.Grid(nx, ny, nz, *ic.lengths)
+
+    ref = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4)
+    ref.set_state(cons)
+    state = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in cons]
+    torch.cuda.synchronize()
+    ptrs = idx.P8(*[t.data_ptr() for t in state])
+    inv = ctypes.c_double(0.0)
+    for call in range(2):
+        dt_ref = ref.step(want_dt=True)
+        want = ref.get_state()
+        dt = ctypes.c_double()
+        rc = L.idx_step_noalloc(ctypes.byref(grid), ic.gamma, 0.4, ptrs, ctypes.byref(inv),
+                                ctypes.byref(dt), None)
+        assert rc == idx.IDX_OK, rc
+        got = [t.cpu().numpy() for t in state]
+        sc = _scales(want)
+        err = max(float(np.max(np.abs(got[f] - want[f]))) / sc[f] for f in range(8))
+        assert err <= 1e-12, (call, err)
+        assert dt.value == pytest.approx(dt_ref, rel=1e-14)
+        assert ref.time()[1] == pytest.approx(0.4 / inv.value, rel=1e-14)
+    ref.close()
+
+
+def test_noalloc_refuses_grids_above_its_limit():
+    L = _lib()
+    grid = idx.Grid(64, 64, 64, 1.0, 1.0, 1.0)      # 262144 > limit
+    assert 64 ** 3 > MAX_CELLS
+    inv = ctypes.c_double(0.0)
+    dummy = idx.P8(*([1] * 8))                       # never dereferenced: refused first
+    rc = L.idx_step_noalloc(ctypes.byref(grid), 5 / 3, 0.4, dummy, ctypes.byref(inv), None, None)
+    assert rc == IDX_ETOOLARGE
