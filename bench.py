@@ -232,6 +232,7 @@ def main():
 
     # dominant kernel: per-launch device time of each kernel (events between launches)
     kt = sim.kernel_times(reps=2)
+    shapes = sim.sweep_shapes()
     flops_face = alg_flops_per_face(
         [np.ascontiguousarray(a[:32, :32, :32]) for a in cons_host] if args.n > 32 else cons_host,
         (32 / args.n,) * 3 if args.n > 32 else ic.lengths, ic.gamma)
@@ -250,7 +251,7 @@ def main():
                 "achieved": achieved_gflops, "peak": peak, "unit": "GFLOP/s",
                 "frac": achieved_gflops / peak, "traffic": None,
                 "alg_flops_per_face": flops_face[d_i], "launch_ms": sweep_ms[dom],
-                "peak_source": peak_note, "kernel_ms": kt,
+                "peak_source": peak_note, "kernel_ms": kt, "sweep_shapes_xyz": shapes,
                 "pipe_rates_gops": {k: v / 1e9 for k, v in rates.items()}}
 
     # end to end through the C ABI with host buffers: H2D state, one cycle, D2H state

@@ -110,6 +110,12 @@ int idx_last_error_cell(const idx_sim* sim, int64_t* cell);
  * are real: the sim advances by `reps` cycles.  A measurement aid, not part of the method. */
 int idx_kernel_times(idx_sim* sim, int reps, double ms[6]);
 
+/* Sweep shape per direction chosen by the autotuner that runs on a sim's first state
+ * (grids of at least 32768 cells; smaller ones keep the default): a value s > 0 means one
+ * thread marches s faces of a pencil, -1 the warp-per-32-cells x sweep, 0 a direction
+ * that is not integrated.  The shape never changes results. */
+int idx_sweep_shapes(const idx_sim* sim, int shapes[3]);
+
 /* Free the sim and its device memory (and its stream, if the library made it). */
 void idx_destroy(idx_sim* sim);
 

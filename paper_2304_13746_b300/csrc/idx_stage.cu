@@ -25,6 +25,7 @@
 #include <cstring>
 #include <limits>
 #include <mutex>
+#include <type_traits>
 
 #include "../../include/idx.h"
 #include "mhd_math.cuh"
@@ -34,7 +35,8 @@ using namespace idx;
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kSeg = 16;  // faces per thread along the sweep direction
+constexpr int kSegDefault = 16;  // faces per thread along a marching sweep, before tuning
+constexpr int kTuneMinCells = 1 << 15;  // smaller grids keep the default shapes
 
 // Device control block of one sim.
 struct Ctrl {
@@ -105,18 +107,38 @@ __global__ void __launch_bounds__(kThreads) k_prims(Geo g, Ptr8<const double> U,
   coords(g, c, i, j, k);
   const double rho = U.f[0][c];
   const double ir = 1.0 / rho;
-  const double vx = U.f[1][c] * ir, vy = U.f[2][c] * ir, vz = U.f[3][c] * ir;
-  const double bx = 0.5 * (U.f[5][c] + U.f[5][shifted(g, c, i, 0, 1)]);
-  const double by = 0.5 * (U.f[6][c] + U.f[6][shifted(g, c, j, 1, 1)]);
-  const double bz = 0.5 * (U.f[7][c] + U.f[7][shifted(g, c, k, 2, 1)]);
-  const double kin = 0.5 * rho * (vx * vx + vy * vy + vz * vz);
-  const double mag = 0.5 * (bx * bx + by * by + bz * bz);
-  const double P = (g.gamma - 1.0) * (U.f[4][c] - kin - mag);
-  if (!(rho > 0.0) || !(P > 0.0) || !isfinite(rho) || !isfinite(P) || !isfinite(vx) ||
-      !isfinite(vy) || !isfinite(vz))
-    flag_bad(ctrl, c);
-  W.f[0][c] = T(rho); W.f[1][c] = T(vx); W.f[2][c] = T(vy); W.f[3][c] = T(vz);
-  W.f[4][c] = T(P);   W.f[5][c] = T(bx); W.f[6][c] = T(by); W.f[7][c] = T(bz);
+  if constexpr (std::is_same<T, double>::value) {
+    const double vx = U.f[1][c] * ir, vy = U.f[2][c] * ir, vz = U.f[3][c] * ir;
+    const double bx = 0.5 * (U.f[5][c] + U.f[5][shifted(g, c, i, 0, 1)]);
+    const double by = 0.5 * (U.f[6][c] + U.f[6][shifted(g, c, j, 1, 1)]);
+    const double bz = 0.5 * (U.f[7][c] + U.f[7][shifted(g, c, k, 2, 1)]);
+    const double kin = 0.5 * rho * (vx * vx + vy * vy + vz * vz);
+    const double mag = 0.5 * (bx * bx + by * by + bz * bz);
+    const double P = (g.gamma - 1.0) * (U.f[4][c] - kin - mag);
+    if (!(rho > 0.0) || !(P > 0.0) || !isfinite(rho) || !isfinite(P) || !isfinite(vx) ||
+        !isfinite(vy) || !isfinite(vz))
+      flag_bad(ctrl, c);
+    W.f[0][c] = rho; W.f[1][c] = vx; W.f[2][c] = vy; W.f[3][c] = vz;
+    W.f[4][c] = P;   W.f[5][c] = bx; W.f[6][c] = by; W.f[7][c] = bz;
+  } else {
+    // FP32 bulk: the energy-to-pressure recovery stays FP64 (kinetic and magnetic
+    // energies from the FP64 state); the velocities and cell-centre B go out in FP32.
+    const double mx = U.f[1][c], my = U.f[2][c], mz = U.f[3][c];
+    const double sx = U.f[5][c] + U.f[5][shifted(g, c, i, 0, 1)];  // 2 B_c
+    const double sy = U.f[6][c] + U.f[6][shifted(g, c, j, 1, 1)];
+    const double sz = U.f[7][c] + U.f[7][shifted(g, c, k, 2, 1)];
+    const double kin = 0.5 * (mx * mx + my * my + mz * mz) * ir;
+    const double mag = 0.125 * (sx * sx + sy * sy + sz * sz);
+    const double P = (g.gamma - 1.0) * (U.f[4][c] - kin - mag);
+    const float irf = (float)ir;
+    const float vx = (float)mx * irf, vy = (float)my * irf, vz = (float)mz * irf;
+    if (!(rho > 0.0) || !(P > 0.0) || !isfinite(rho) || !isfinite(P) || !isfinite(vx) ||
+        !isfinite(vy) || !isfinite(vz))
+      flag_bad(ctrl, c);
+    W.f[0][c] = (float)rho; W.f[1][c] = vx; W.f[2][c] = vy; W.f[3][c] = vz;
+    W.f[4][c] = (float)P;
+    W.f[5][c] = 0.5f * (float)sx; W.f[6][c] = 0.5f * (float)sy; W.f[7][c] = 0.5f * (float)sz;
+  }
 }
 
 // Conserved state from primitives (cell-centre rho, v, P; face B).
@@ -142,20 +164,20 @@ __global__ void __launch_bounds__(kThreads) k_cons_from_prims(Geo g, Ptr8<const 
 }
 
 // ---------------------------------------------------------------------------
-// Sweep along direction D: a thread owns a segment of up to kSeg faces of one pencil,
+// Sweep along direction D: a thread owns a segment of up to SEG faces of one pencil,
 // marches along D keeping three cells' primitives and one slope in registers, and
 // computes each cell's van Leer slopes once and each face's HLLD flux once.
 // Face f of a pencil is the lower D-face of cell f.  Output (rotated order): F[0..6]
 // = fluxes of rho, m_n, m_t1, m_t2, E, B_t1, B_t2 with t1 = D+1, t2 = D+2; F[7] = c.
 // ---------------------------------------------------------------------------
-template <typename T, int D>
+template <typename T, int D, int SEG>
 __global__ void __launch_bounds__(kThreads) k_sweep(Geo g, Ptr8<const T> W, const double* bface,
                                                     Ptr8<T> F, const Ctrl* ctrl, int check_dt) {
   if (check_dt && !(ctrl->dt > 0.0)) return;
   constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
   const int nd = g.n[D];
   const int npencil = g.n[A] * g.n[B];
-  const int nseg = (nd + kSeg - 1) / kSeg;
+  const int nseg = (nd + SEG - 1) / SEG;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= npencil * nseg) return;
   const int pencil = t % npencil, seg = t / npencil;
@@ -170,8 +192,8 @@ __global__ void __launch_bounds__(kThreads) k_sweep(Geo g, Ptr8<const T> W, cons
   }
   const int base = cA * g.stride[A] + cB * g.stride[B];
   const int sd = g.stride[D];
-  const int f0 = seg * kSeg;
-  const int f1 = min(f0 + kSeg, nd);
+  const int f0 = seg * SEG;
+  const int f1 = min(f0 + SEG, nd);
   auto cell = [&](int q) {  // flat index of cell q (wrapped) along the pencil
     q = (q < 0) ? q + nd : q;
     q = (q < 0) ? q + nd : q;
@@ -224,6 +246,75 @@ __global__ void __launch_bounds__(kThreads) k_sweep(Geo g, Ptr8<const T> W, cons
       slope_m[q] = slope0[q];
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Sweep along x: one warp per run of 32 consecutive cells of an x-row, lane l holding
+// cell base + l (mod nx), so every load is coalesced.  A lane gets its neighbours'
+// primitives and slopes by warp shuffle; lane 0 also loads cells base-1, base-2 and
+// forms the slope of base-1, lane 31 loads cell base+32.  Each cell's slope is computed
+// once (plus one per warp) and each face's HLLD once.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_sweep_x(Geo g, Ptr8<const T> W, const double* bface,
+                                                      Ptr8<T> F, const Ctrl* ctrl, int check_dt) {
+  if (check_dt && !(ctrl->dt > 0.0)) return;
+  const int nx = g.n[0];
+  const int wpr = (nx + 31) >> 5;  // warps per x-row
+  const int nrows = g.n[1] * g.n[2];
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (warp >= nrows * wpr) return;  // whole warps leave together
+  const int lane = threadIdx.x & 31;
+  const int row = warp / wpr;
+  const int base = (warp - row * wpr) * 32;
+  const int rowoff = row * nx;
+  auto at_x = [&](int q) {
+    q %= nx;
+    return rowoff + (q < 0 ? q + nx : q);
+  };
+  const int i = base + lane;
+  const int c = at_x(i);
+  constexpr int var[7] = {0, 1, 2, 3, 4, 6, 7};  // rho, v_n = vx, vy, vz, P, B_t1 = By, B_t2 = Bz
+  const T gamma = T(g.gamma);
+  const T gm1inv = T(1.0 / (g.gamma - 1.0));
+  T w0[7], wm1[7], wm2[7], wp32[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) w0[q] = W.f[var[q]][c];
+  if (lane == 0) {
+    const int cm1 = at_x(base - 1), cm2 = at_x(base - 2);
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      wm1[q] = W.f[var[q]][cm1];
+      wm2[q] = W.f[var[q]][cm2];
+    }
+  }
+  if (lane == 31) {
+    const int cp = at_x(base + 32);
+#pragma unroll
+    for (int q = 0; q < 7; ++q) wp32[q] = W.f[var[q]][cp];
+  }
+  Side<T> L, R;
+  T Lq[7], Rq[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    T up = __shfl_up_sync(0xffffffffu, w0[q], 1);    // cell c-1
+    T dn = __shfl_down_sync(0xffffffffu, w0[q], 1);  // cell c+1
+    if (lane == 0) up = wm1[q];
+    if (lane == 31) dn = wp32[q];
+    const T slope0 = vanleer(w0[q] - up, dn - w0[q]);
+    T slope_m = __shfl_up_sync(0xffffffffu, slope0, 1);  // slope of cell c-1
+    if (lane == 0) slope_m = vanleer(wm1[q] - wm2[q], w0[q] - wm1[q]);
+    Lq[q] = up + T(0.5) * slope_m;
+    Rq[q] = w0[q] - T(0.5) * slope0;
+  }
+  if (i >= nx) return;
+  L.r = Lq[0]; L.u = Lq[1]; L.v = Lq[2]; L.w = Lq[3]; L.p = Lq[4]; L.b1 = Lq[5]; L.b2 = Lq[6];
+  R.r = Rq[0]; R.u = Rq[1]; R.v = Rq[2]; R.w = Rq[3]; R.p = Rq[4]; R.b1 = Rq[5]; R.b2 = Rq[6];
+  T flux[7], cmax;
+  hlld(L, R, T(bface[c]), gamma, gm1inv, flux, cmax);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) F.f[q][c] = flux[q];
+  F.f[7][c] = cmax;
 }
 
 // ---------------------------------------------------------------------------
@@ -302,41 +393,50 @@ __global__ void __launch_bounds__(kThreads) k_update(Geo g, Ptr8<const double> U
     int up[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) up[d] = shifted(g, c, ijk[d], d, 1);
+    // flux divergence and EMF curl in the bulk type T; the accumulation into the
+    // state (U - dt * div) is FP64 in both variants
     double out[8];
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
-      double div = 0.0;
+      T div = T(0);
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         if (!g.active[d]) continue;
         const int s = slot(f, d);
-        div += (double(F[d].f[s][up[d]]) - double(F[d].f[s][c])) * g.inv_dl[d];
+        div += (F[d].f[s][up[d]] - F[d].f[s][c]) * T(g.inv_dl[d]);
       }
-      out[f] = Uin.f[f][c] - dt * div;
+      out[f] = (COMBINE && !std::is_same<T, double>::value)
+                   ? 0.5 * (U0.f[f][c] + Uin.f[f][c]) - (0.5 * dt) * double(div)
+                   : Uin.f[f][c] - dt * double(div);
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-      double curl = 0.0;
+      T curl = T(0);
       if (g.active[d]) {
-        if (g.active[t1]) curl += (double(E[t2][up[t1]]) - double(E[t2][c])) * g.inv_dl[t1];
-        if (g.active[t2]) curl -= (double(E[t1][up[t2]]) - double(E[t1][c])) * g.inv_dl[t2];
+        if (g.active[t1]) curl += (E[t2][up[t1]] - E[t2][c]) * T(g.inv_dl[t1]);
+        if (g.active[t2]) curl -= (E[t1][up[t2]] - E[t1][c]) * T(g.inv_dl[t2]);
       } else {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           if (a == d || !g.active[a]) continue;
           const int s = slot(5 + d, a);
-          curl += (double(F[a].f[s][up[a]]) - double(F[a].f[s][c])) * g.inv_dl[a];
+          curl += (F[a].f[s][up[a]] - F[a].f[s][c]) * T(g.inv_dl[a]);
         }
       }
-      out[5 + d] = Uin.f[5 + d][c] - dt * curl;
+      out[5 + d] = (COMBINE && !std::is_same<T, double>::value)
+                       ? 0.5 * (U0.f[5 + d][c] + Uin.f[5 + d][c]) - (0.5 * dt) * double(curl)
+                       : Uin.f[5 + d][c] - dt * double(curl);
     }
 #pragma unroll
-    for (int f = 0; f < 8; ++f) Uout.f[f][c] = COMBINE ? fma(0.5, out[f], 0.5 * U0.f[f][c]) : out[f];
+    for (int f = 0; f < 8; ++f)
+      Uout.f[f][c] = (COMBINE && std::is_same<T, double>::value) ? fma(0.5, out[f], 0.5 * U0.f[f][c])
+                                                                 : out[f];
+    T invT = T(0);
 #pragma unroll
     for (int d = 0; d < 3; ++d)
-      if (g.active[d])
-        inv += fmax(double(F[d].f[7][c]), double(F[d].f[7][up[d]])) * g.inv_dl[d];
+      if (g.active[d]) invT += tmax(F[d].f[7][c], F[d].f[7][up[d]]) * T(g.inv_dl[d]);
+    inv = double(invT);
   }
   // block max -> one atomic per block (positive doubles order like their bit patterns)
 #pragma unroll
@@ -439,6 +539,8 @@ struct idx_sim {
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   int64_t last_bad;
+  int sweep_shape[3];   // per direction: marching segment (2..32), -1 warp x-sweep, 0 default
+  bool tuned;
 };
 
 namespace {
@@ -451,10 +553,93 @@ namespace {
 
 unsigned blocks_for(long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
+// x sweep: one warp per 32 cells of an x-row
+unsigned blocks_x(const Geo& g) {
+  const long warps = (long)g.n[1] * g.n[2] * ((g.n[0] + 31) / 32);
+  return blocks_for(warps * 32);
+}
+
 template <typename T> Ptr8<const T> cst(const Ptr8<T>& p) {
   Ptr8<const T> q;
   for (int f = 0; f < 8; ++f) q.f[f] = p.f[f];
   return q;
+}
+
+// One sweep launch in the given shape (see idx_sim::sweep_shape).
+template <typename T, int D, int SEG>
+void launch_march(idx_sim* s, const Ptr8<T>& W, const double* bface, const Ptr8<T>& F,
+                  int check_dt) {
+  const Geo& g = s->geo;
+  const int a = (D + 1) % 3, b = (D + 2) % 3;
+  const long nthr = (long)g.n[a] * g.n[b] * ((g.n[D] + SEG - 1) / SEG);
+  k_sweep<T, D, SEG><<<blocks_for(nthr), kThreads, 0, s->stream>>>(g, cst(W), bface, F, s->ctrl,
+                                                                    check_dt);
+}
+
+template <typename T, int D>
+void launch_sweep_d(idx_sim* s, int shape, const Ptr8<T>& W, const double* bface,
+                    const Ptr8<T>& F, int check_dt) {
+  switch (shape) {
+    case -1:
+      if (D == 0) {
+        k_sweep_x<T><<<blocks_x(s->geo), kThreads, 0, s->stream>>>(s->geo, cst(W), bface, F,
+                                                                     s->ctrl, check_dt);
+        return;
+      }
+      break;
+    case 2: launch_march<T, D, 2>(s, W, bface, F, check_dt); return;
+    case 4: launch_march<T, D, 4>(s, W, bface, F, check_dt); return;
+    case 8: launch_march<T, D, 8>(s, W, bface, F, check_dt); return;
+    case 32: launch_march<T, D, 32>(s, W, bface, F, check_dt); return;
+    default: break;
+  }
+  launch_march<T, D, kSegDefault>(s, W, bface, F, check_dt);
+}
+
+template <typename T>
+void launch_sweep(idx_sim* s, int d, const Ptr8<T>& W, const double* bface, const Ptr8<T>& F,
+                  int check_dt) {
+  const int shape = s->sweep_shape[d];
+  if (d == 0) launch_sweep_d<T, 0>(s, shape, W, bface, F, check_dt);
+  else if (d == 1) launch_sweep_d<T, 1>(s, shape, W, bface, F, check_dt);
+  else launch_sweep_d<T, 2>(s, shape, W, bface, F, check_dt);
+}
+
+// Autotuner of the sweep shape: per integrated direction, time every candidate shape on
+// the sim's current primitives (three launches each, CUDA events, fastest wins).  All
+// shapes do the same arithmetic per face, so the choice never changes results.
+template <typename T>
+int tune_sweeps(idx_sim* s, const Ptr8<double>& U, const Ptr8<T>& W, Ptr8<T>* F) {
+  const Geo& g = s->geo;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return IDX_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return IDX_ECUDA; }
+  const int cand[6] = {-1, 2, 4, 8, 16, 32};
+  int rc = IDX_OK;
+  for (int d = 0; d < 3 && rc == IDX_OK; ++d) {
+    if (!g.active[d]) continue;
+    float best = 1e30f;
+    int best_shape = kSegDefault;
+    for (int q = 0; q < 6; ++q) {
+      const int shape = cand[q];
+      if (shape == -1 && d != 0) continue;
+      if (shape > 0 && shape > 2 * g.n[d]) continue;
+      s->sweep_shape[d] = shape;
+      launch_sweep<T>(s, d, W, U.f[5 + d], F[d], 0);
+      cudaEventRecord(e0, s->stream);
+      for (int r = 0; r < 3; ++r) launch_sweep<T>(s, d, W, U.f[5 + d], F[d], 0);
+      cudaEventRecord(e1, s->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = IDX_ECUDA; break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; best_shape = shape; }
+    }
+    s->sweep_shape[d] = best_shape;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == IDX_OK && cudaGetLastError() != cudaSuccess) rc = IDX_ECUDA;
+  return rc;
 }
 
 template <typename T>
@@ -462,18 +647,8 @@ void launch_fluxes(idx_sim* s, const Ptr8<double>& Uin, const Ptr8<T>& W, Ptr8<T
                    int check_dt) {
   const Geo& g = s->geo;
   k_prims<T><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), W, s->ctrl, check_dt);
-  for (int d = 0; d < 3; ++d) {
-    if (!g.active[d]) continue;
-    const int a = (d + 1) % 3, b = (d + 2) % 3;
-    const long nthr = (long)g.n[a] * g.n[b] * ((g.n[d] + kSeg - 1) / kSeg);
-    const unsigned nb = blocks_for(nthr);
-    if (d == 0)
-      k_sweep<T, 0><<<nb, kThreads, 0, s->stream>>>(g, cst(W), Uin.f[5], F[0], s->ctrl, check_dt);
-    else if (d == 1)
-      k_sweep<T, 1><<<nb, kThreads, 0, s->stream>>>(g, cst(W), Uin.f[6], F[1], s->ctrl, check_dt);
-    else
-      k_sweep<T, 2><<<nb, kThreads, 0, s->stream>>>(g, cst(W), Uin.f[7], F[2], s->ctrl, check_dt);
-  }
+  for (int d = 0; d < 3; ++d)
+    if (g.active[d]) launch_sweep<T>(s, d, W, Uin.f[5 + d], F[d], check_dt);
 }
 
 template <typename T>
@@ -537,15 +712,22 @@ int after_new_state(idx_sim* s) {
   c.bad_cell = ~0ull;
   IDX_TRY(cudaMemcpyAsync(s->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s->stream));
   const Geo& g = s->geo;
+  // the speed pass; on a sim's first state it also tunes the sweep shapes, which
+  // recompute the same fluxes from the same primitives
+  int trc = IDX_OK;
   if (s->solver.precision == IDX_FP32_BULK) {
     launch_fluxes<float>(s, s->U, s->Wf, s->Ff, 0);
+    if (!s->tuned && g.ncell >= kTuneMinCells) trc = tune_sweeps<float>(s, s->U, s->Wf, s->Ff);
     k_inv_only<float><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
         g, cst(s->Ff[0]), cst(s->Ff[1]), cst(s->Ff[2]), s->ctrl);
   } else {
     launch_fluxes<double>(s, s->U, s->Wd, s->Fd, 0);
+    if (!s->tuned && g.ncell >= kTuneMinCells) trc = tune_sweeps<double>(s, s->U, s->Wd, s->Fd);
     k_inv_only<double><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
         g, cst(s->Fd[0]), cst(s->Fd[1]), cst(s->Fd[2]), s->ctrl);
   }
+  if (trc != IDX_OK) return trc;
+  s->tuned = true;
   IDX_TRY(cudaGetLastError());
   int rc = sync_ctrl(s);
   if (rc != IDX_OK) return rc;
@@ -796,17 +978,8 @@ int idx_kernel_times(idx_sim* s, int reps, double ms[6]) {
       IDX_TRY(cudaEventRecord(ev[1], s->stream));
       for (int d = 0; d < 3; ++d) {
         if (g.active[d]) {
-          const int a = (d + 1) % 3, b = (d + 2) % 3;
-          const unsigned nb = blocks_for((long)g.n[a] * g.n[b] * ((g.n[d] + kSeg - 1) / kSeg));
-          if (f32) {
-            if (d == 0) k_sweep<float, 0><<<nb, kThreads, 0, s->stream>>>(g, cst(s->Wf), Uin.f[5], s->Ff[0], s->ctrl, 1);
-            if (d == 1) k_sweep<float, 1><<<nb, kThreads, 0, s->stream>>>(g, cst(s->Wf), Uin.f[6], s->Ff[1], s->ctrl, 1);
-            if (d == 2) k_sweep<float, 2><<<nb, kThreads, 0, s->stream>>>(g, cst(s->Wf), Uin.f[7], s->Ff[2], s->ctrl, 1);
-          } else {
-            if (d == 0) k_sweep<double, 0><<<nb, kThreads, 0, s->stream>>>(g, cst(s->Wd), Uin.f[5], s->Fd[0], s->ctrl, 1);
-            if (d == 1) k_sweep<double, 1><<<nb, kThreads, 0, s->stream>>>(g, cst(s->Wd), Uin.f[6], s->Fd[1], s->ctrl, 1);
-            if (d == 2) k_sweep<double, 2><<<nb, kThreads, 0, s->stream>>>(g, cst(s->Wd), Uin.f[7], s->Fd[2], s->ctrl, 1);
-          }
+          if (f32) launch_sweep<float>(s, d, s->Wf, Uin.f[5 + d], s->Ff[d], 1);
+          else launch_sweep<double>(s, d, s->Wd, Uin.f[5 + d], s->Fd[d], 1);
         }
         IDX_TRY(cudaEventRecord(ev[2 + d], s->stream));
       }
@@ -838,6 +1011,15 @@ int idx_kernel_times(idx_sim* s, int reps, double ms[6]) {
   rc = sync_ctrl(s);
   if (rc != IDX_OK) return rc;
   return pending_error(s);
+}
+
+int idx_sweep_shapes(const idx_sim* s, int shapes[3]) {
+  if (!s || !shapes) return IDX_EINVAL;
+  for (int d = 0; d < 3; ++d) {
+    const int v = s->sweep_shape[d];
+    shapes[d] = s->geo.active[d] ? (v == 0 ? kSegDefault : v) : 0;
+  }
+  return IDX_OK;
 }
 
 int idx_last_error_cell(const idx_sim* s, int64_t* cell) {

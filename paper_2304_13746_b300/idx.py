@@ -67,6 +67,7 @@ def lib(path=LIB_PATH):
     L.idx_strerror.restype = ctypes.c_char_p
     L.idx_pipe_rates.argtypes = [ctypes.POINTER(ctypes.c_double)]
     L.idx_kernel_times.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    L.idx_sweep_shapes.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     _lib = L
     return L
 
@@ -197,6 +198,12 @@ class Sim:
         out = (ctypes.c_double * 6)()
         self._check(lib().idx_kernel_times(self._h, int(reps), out), "idx_kernel_times")
         return dict(zip(("prims", "sweep_x", "sweep_y", "sweep_z", "emf", "update"), out[:]))
+
+    def sweep_shapes(self):
+        """Autotuned sweep shape per direction (faces per thread, -1 warp x-sweep, 0 inactive)."""
+        out = (ctypes.c_int * 3)()
+        self._check(lib().idx_sweep_shapes(self._h, out), "idx_sweep_shapes")
+        return list(out)
 
     def time(self):
         t, dt = ctypes.c_double(), ctypes.c_double()
