@@ -44,6 +44,10 @@ def parse():
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     p.add_argument("--impl", default="idx", choices=["idx", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--mode", default="plain", choices=["plain", "batched"],
+                   help="plain: one box (the headline line); batched: the 64-instance mix, "
+                        "batched vs one at a time")
+    p.add_argument("--cycles", type=int, default=100, help="cycles per instance (batched mode)")
     return p.parse_args()
 
 
@@ -176,10 +180,97 @@ def alg_flops_per_face(cons, lengths, gamma):
     return out
 
 
+def c4_instances(seed=4):
+    """The batched workload: 64 independent instances, 32 Orszag-Tang 2D boxes with N
+    log-uniform in [64, 512] and 32 turbulent 3D boxes with N log-uniform in [32, 128]
+    (N rounded to a multiple of 8), the boxes seeded 1..32."""
+    from paper_2304_13746_b300 import inputs
+    rng = np.random.Generator(np.random.PCG64(seed))
+
+    def r8(x):
+        return int(max(8, 8 * round(x / 8)))
+    ics = []
+    for i in range(32):
+        ics.append(inputs.orszag_tang_2d(r8(math.exp(rng.uniform(math.log(64), math.log(512))))))
+    for i in range(32):
+        n = r8(math.exp(rng.uniform(math.log(32), math.log(128))))
+        ics.append(inputs.turbulent_box(n, seed=i + 1))
+    return ics
+
+
+def run_batched(args):
+    import torch
+    from paper_2304_13746_b300 import build as idx_build
+    from paper_2304_13746_b300 import idx
+    idx_build.build()
+    idx.lib()
+    ics = c4_instances()
+    cells = sum(ic.ncells for ic in ics)
+    K = args.cycles
+    results = {}
+    for precision in ("fp64", "fp32"):
+        stream = torch.cuda.Stream()
+        # one batch for all 64 instances
+        sims = [idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, precision, stream=stream.cuda_stream)
+                for ic in ics]
+        for s, ic in zip(sims, ics):
+            s.set_primitive(ic.prim)
+        b = idx.Batch(precision, stream=stream.cuda_stream)
+        for s in sims:
+            b.add(s)
+        b.step(args.warmup)
+        b.poll()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(K)
+        e1.record(stream)
+        e1.synchronize()
+        ms_b = e0.elapsed_time(e1)
+        shapes = b.shapes()
+        for s in sims:
+            b.remove(s)
+        b.close()
+        for s in sims:
+            s.close()
+        # the same instances one at a time (each a graph of its own cycle)
+        sims = [idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, precision, stream=stream.cuda_stream)
+                for ic in ics]
+        for s, ic in zip(sims, ics):
+            s.set_primitive(ic.prim)
+            for _ in range(args.warmup):
+                s.step()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for s in sims:
+            for _ in range(K):
+                s.step()
+        e1.record(stream)
+        e1.synchronize()
+        ms_s = e0.elapsed_time(e1)
+        for s in sims:
+            s.close()
+        results[precision] = {
+            "batched": cells * K / (ms_b * 1e-3), "sequential": cells * K / (ms_s * 1e-3),
+            "speedup": ms_s / ms_b, "ms_batched": ms_b, "ms_sequential": ms_s,
+            "batch_sweep_shapes_xyz": shapes}
+    line = {"metric": METRIC, "value": results["fp64"]["batched"], "unit": UNIT, "n_gpus": 1,
+            "steps": K, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batched: 64 independent instances (32 Orszag-Tang 2D, N "
+                                   "log-uniform 64..512; 32 turbulent 3D boxes, N log-uniform "
+                                   "32..128), own CFL dt each, one batch vs one at a time",
+                       "instances": len(ics), "cells": cells, "cycles_per_instance": K},
+            "batched": results}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "batched":
+        return run_batched(args)
     rank, world, local = dist_env()
     import torch
     torch.cuda.set_device(local)
@@ -279,6 +370,25 @@ def main():
                    "idx_step, idx_get_state to pinned host"}
     sim.close()
 
+    variants = {}
+    if args.precision == "fp64":
+        # the FP32-bulk variant on the same box (same timing rules)
+        s32 = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, "fp32", stream=stream.cuda_stream)
+        s32.set_primitive(ic.prim)
+        for _ in range(args.warmup):
+            s32.step()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            s32.step()
+        e1.record(stream)
+        e1.synchronize()
+        ms32 = e0.elapsed_time(e1)
+        variants["fp32_bulk"] = {"value": ncell * args.steps * world / (ms32 * 1e-3), "unit": UNIT,
+                                 "ms_per_step": ms32 / args.steps,
+                                 "sweep_shapes_xyz": s32.sweep_shapes()}
+        s32.close()
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -286,7 +396,7 @@ def main():
                 "dtype": "f64" if args.precision == "fp64" else "f32/f64",
                 "data": "synthetic", "config": workload_config(args),
                 "gpu_launches": launches_per_cycle * args.steps,
-                "clocks": clk, "roofline": roofline, "e2e": e2e}
+                "clocks": clk, "roofline": roofline, "e2e": e2e, "variants": variants}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

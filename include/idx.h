@@ -113,7 +113,9 @@ int idx_kernel_times(idx_sim* sim, int reps, double ms[6]);
 /* Sweep shape per direction chosen by the autotuner that runs on a sim's first state
  * (grids of at least 32768 cells; smaller ones keep the default): a value s > 0 means one
  * thread marches s faces of a pencil, -1 the warp-per-32-cells x sweep, 0 a direction
- * that is not integrated.  The shape never changes results. */
+ * that is not integrated.  Every shape does the same arithmetic per face; results differ
+ * between shapes at most by rounding (the compiler may contract products into FMAs
+ * differently in each kernel instantiation). */
 int idx_sweep_shapes(const idx_sim* sim, int shapes[3]);
 
 /* Free the sim and its device memory (and its stream, if the library made it). */
@@ -127,6 +129,42 @@ const char* idx_strerror(int code);
  * from a short kernel of independent operations timed with CUDA events (a few ms).
  * Not part of the method: it supplies the denominators of the ALU roofline. */
 int idx_pipe_rates(double rates[6]);
+
+/* ---- Batched stepping (many independent boxes advanced together) --------------------
+ * A batch advances a set of sims together: per RK2 stage each kernel type is launched
+ * once over a device work-list of all members, and every member keeps its own grid,
+ * state, CFL dt (Eq. 10) and end time.  The arithmetic per cell is that of idx_step (up to
+ * the compiler's choice of FMA contractions in each kernel instantiation), so a sim gives
+ * the same result, to rounding, alone and in a batch.  The work-list is read at run time, so
+ * sims join and leave between steps without re-capturing the batch's CUDA graph.  The
+ * sweep shapes are autotuned on the batch when its membership first changes.
+ * Members must share the batch's precision and device; a member must not be stepped by
+ * idx_step/idx_advance, nor read with idx_get_state/idx_time, until idx_batch_poll or
+ * idx_batch_remove has synchronised the batch. */
+typedef struct idx_batch idx_batch; /* opaque */
+
+/* precision: idx_precision; stream: a cudaStream_t, or NULL for a library-owned one. */
+int idx_batch_create(int precision, void* stream, idx_batch** out);
+
+/* Add a sim whose state is set; it will advance until its time reaches t_end (the last dt
+ * clamped, as in idx_advance).  Pass t_end = INFINITY for an open-ended member. */
+int idx_batch_add(idx_batch* batch, idx_sim* sim, double t_end);
+
+/* Remove a member (waits for the batch's work); it goes back to unclamped idx_step. */
+int idx_batch_remove(idx_batch* batch, idx_sim* sim);
+
+/* Enqueue ncycles batched RK2 cycles (asynchronous); finished members idle. */
+int idx_batch_step(idx_batch* batch, int ncycles);
+
+/* Synchronise the batch and list the members that reached their end time or failed
+ * (up to cap of them in finished[]); n_finished and n_active are nullable. */
+int idx_batch_poll(idx_batch* batch, idx_sim** finished, int cap, int* n_finished,
+                   int* n_active);
+
+/* Sweep shapes chosen by the batch's autotuner (as idx_sweep_shapes). */
+int idx_batch_shapes(const idx_batch* batch, int shapes[3]);
+
+void idx_batch_destroy(idx_batch* batch);
 
 /* ---- Allocation-free cycle (no counterpart in the paper) -------------------------
  * Some callers cannot call cudaMalloc: code running inside another framework's

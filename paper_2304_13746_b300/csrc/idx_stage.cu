@@ -26,6 +26,7 @@
 #include <limits>
 #include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "../../include/idx.h"
 #include "mhd_math.cuh"
@@ -98,11 +99,8 @@ __device__ __forceinline__ void flag_bad(Ctrl* ctrl, int c) {
 // cell-centre B as the mean of the two bounding faces.  W is stored as T.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_prims(Geo g, Ptr8<const double> U, Ptr8<T> W,
-                                                    Ctrl* ctrl, int check_dt) {
-  if (check_dt && !(ctrl->dt > 0.0)) return;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.ncell) return;
+__device__ __forceinline__ void prims_body(const Geo& g, const Ptr8<const double>& U,
+                                           const Ptr8<T>& W, Ctrl* ctrl, int c) {
   int i, j, k;
   coords(g, c, i, j, k);
   const double rho = U.f[0][c];
@@ -141,6 +139,14 @@ __global__ void __launch_bounds__(kThreads) k_prims(Geo g, Ptr8<const double> U,
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_prims(Geo g, Ptr8<const double> U, Ptr8<T> W,
+                                                    Ctrl* ctrl, int check_dt) {
+  if (check_dt && !(ctrl->dt > 0.0)) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < g.ncell) prims_body<T>(g, U, W, ctrl, c);
+}
+
 // Conserved state from primitives (cell-centre rho, v, P; face B).
 __global__ void __launch_bounds__(kThreads) k_cons_from_prims(Geo g, Ptr8<const double> P,
                                                               Ptr8<double> U) {
@@ -170,15 +176,18 @@ __global__ void __launch_bounds__(kThreads) k_cons_from_prims(Geo g, Ptr8<const 
 // Face f of a pencil is the lower D-face of cell f.  Output (rotated order): F[0..6]
 // = fluxes of rho, m_n, m_t1, m_t2, E, B_t1, B_t2 with t1 = D+1, t2 = D+2; F[7] = c.
 // ---------------------------------------------------------------------------
+// number of threads of a marching sweep of direction d with segment seg
+__host__ __device__ __forceinline__ int march_threads(const Geo& g, int d, int seg) {
+  return g.n[(d + 1) % 3] * g.n[(d + 2) % 3] * ((g.n[d] + seg - 1) / seg);
+}
+
 template <typename T, int D, int SEG>
-__global__ void __launch_bounds__(kThreads) k_sweep(Geo g, Ptr8<const T> W, const double* bface,
-                                                    Ptr8<T> F, const Ctrl* ctrl, int check_dt) {
-  if (check_dt && !(ctrl->dt > 0.0)) return;
+__device__ __forceinline__ void sweep_body(const Geo& g, const Ptr8<const T>& W,
+                                           const double* bface, const Ptr8<T>& F, int t) {
   constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
   const int nd = g.n[D];
   const int npencil = g.n[A] * g.n[B];
   const int nseg = (nd + SEG - 1) / SEG;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= npencil * nseg) return;
   const int pencil = t % npencil, seg = t / npencil;
   // pencil -> coordinates of the two other directions, x fastest for coalescing
@@ -248,6 +257,13 @@ __global__ void __launch_bounds__(kThreads) k_sweep(Geo g, Ptr8<const T> W, cons
   }
 }
 
+template <typename T, int D, int SEG>
+__global__ void __launch_bounds__(kThreads) k_sweep(Geo g, Ptr8<const T> W, const double* bface,
+                                                    Ptr8<T> F, const Ctrl* ctrl, int check_dt) {
+  if (check_dt && !(ctrl->dt > 0.0)) return;
+  sweep_body<T, D, SEG>(g, W, bface, F, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // Sweep along x: one warp per run of 32 consecutive cells of an x-row, lane l holding
 // cell base + l (mod nx), so every load is coalesced.  A lane gets its neighbours'
@@ -255,16 +271,20 @@ __global__ void __launch_bounds__(kThreads) k_sweep(Geo g, Ptr8<const T> W, cons
 // forms the slope of base-1, lane 31 loads cell base+32.  Each cell's slope is computed
 // once (plus one per warp) and each face's HLLD once.
 // ---------------------------------------------------------------------------
+// threads of the warp x sweep (a multiple of 32)
+__host__ __device__ __forceinline__ int warpx_threads(const Geo& g) {
+  return g.n[1] * g.n[2] * ((g.n[0] + 31) / 32) * 32;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_sweep_x(Geo g, Ptr8<const T> W, const double* bface,
-                                                      Ptr8<T> F, const Ctrl* ctrl, int check_dt) {
-  if (check_dt && !(ctrl->dt > 0.0)) return;
+__device__ __forceinline__ void sweep_x_body(const Geo& g, const Ptr8<const T>& W,
+                                             const double* bface, const Ptr8<T>& F, int t) {
   const int nx = g.n[0];
   const int wpr = (nx + 31) >> 5;  // warps per x-row
   const int nrows = g.n[1] * g.n[2];
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int warp = t >> 5;
   if (warp >= nrows * wpr) return;  // whole warps leave together
-  const int lane = threadIdx.x & 31;
+  const int lane = t & 31;
   const int row = warp / wpr;
   const int base = (warp - row * wpr) * 32;
   const int rowoff = row * nx;
@@ -317,6 +337,13 @@ __global__ void __launch_bounds__(kThreads) k_sweep_x(Geo g, Ptr8<const T> W, co
   F.f[7][c] = cmax;
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_sweep_x(Geo g, Ptr8<const T> W, const double* bface,
+                                                      Ptr8<T> F, const Ctrl* ctrl, int check_dt) {
+  if (check_dt && !(ctrl->dt > 0.0)) return;
+  sweep_x_body<T>(g, W, bface, F, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // Edge EMFs: E_e at the edge along e bounded by the lower a- and b-faces of cell c,
 // a = e+1, b = e+2.  a-face EMF = -F_a[B_b] (rotated slot 5 of direction a), b-face
@@ -341,12 +368,9 @@ __device__ __forceinline__ T edge_emf(const Geo& g, int e, int c, const int ijk[
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_emf(Geo g, Ptr8<const T> W, Ptr8<const T> Fx,
-                                                  Ptr8<const T> Fy, Ptr8<const T> Fz, T* Ex,
-                                                  T* Ey, T* Ez, const Ctrl* ctrl) {
-  if (!(ctrl->dt > 0.0)) return;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.ncell) return;
+__device__ __forceinline__ void emf_body(const Geo& g, const Ptr8<const T>& W,
+                                         const Ptr8<const T>& Fx, const Ptr8<const T>& Fy,
+                                         const Ptr8<const T>& Fz, T* Ex, T* Ey, T* Ez, int c) {
   int ijk[3];
   coords(g, c, ijk[0], ijk[1], ijk[2]);
   const Ptr8<const T> F[3] = {Fx, Fy, Fz};
@@ -356,6 +380,15 @@ __global__ void __launch_bounds__(kThreads) k_emf(Geo g, Ptr8<const T> W, Ptr8<c
     const int a = (e + 1) % 3, b = (e + 2) % 3;
     if (g.active[a] && g.active[b]) out[e][c] = edge_emf(g, e, c, ijk, W, F);
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_emf(Geo g, Ptr8<const T> W, Ptr8<const T> Fx,
+                                                  Ptr8<const T> Fy, Ptr8<const T> Fz, T* Ex,
+                                                  T* Ey, T* Ez, const Ctrl* ctrl) {
+  if (!(ctrl->dt > 0.0)) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < g.ncell) emf_body<T>(g, W, Fx, Fy, Fz, Ex, Ey, Ez, c);
 }
 
 // Rotated flux slot of conserved field f (0..4) or face field 5+m for direction d.
@@ -375,15 +408,29 @@ __device__ __forceinline__ int slot(int f, int d) {
 // U_out = w U* + w0 U_0 (Eq. 9), and the stage's inverse CFL time (Eq. 10).
 // Arithmetic in FP64 for both variants.
 // ---------------------------------------------------------------------------
+// block-wide max of a non-negative double into *bits (as its bit pattern)
+__device__ __forceinline__ void block_max_to(unsigned long long* bits, double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __shared__ double wmax[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = wmax[0];
+    for (int w = 1; w < kThreads / 32; ++w) m = fmax(m, wmax[w]);
+    atomicMax(bits, (unsigned long long)__double_as_longlong(m));
+  }
+  __syncthreads();  // wmax is reused by the next call of the block
+}
+
+// Returns the cell's inverse CFL contribution (0 outside the grid).
 template <typename T, bool COMBINE>
-__global__ void __launch_bounds__(kThreads) k_update(Geo g, Ptr8<const double> Uin,
-                                                     Ptr8<const double> U0, Ptr8<const T> Fx,
-                                                     Ptr8<const T> Fy, Ptr8<const T> Fz,
-                                                     const T* Ex, const T* Ey, const T* Ez,
-                                                     Ptr8<double> Uout, Ctrl* ctrl) {
-  const double dt = ctrl->dt;
-  if (!(dt > 0.0)) return;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ double update_body(const Geo& g, const Ptr8<const double>& Uin,
+                                              const Ptr8<const double>& U0,
+                                              const Ptr8<const T>& Fx, const Ptr8<const T>& Fy,
+                                              const Ptr8<const T>& Fz, const T* Ex, const T* Ey,
+                                              const T* Ez, const Ptr8<double>& Uout, double dt,
+                                              int c) {
   double inv = 0.0;
   if (c < g.ncell) {
     int ijk[3];
@@ -438,17 +485,22 @@ __global__ void __launch_bounds__(kThreads) k_update(Geo g, Ptr8<const double> U
       if (g.active[d]) invT += tmax(F[d].f[7][c], F[d].f[7][up[d]]) * T(g.inv_dl[d]);
     inv = double(invT);
   }
+  return inv;
+}
+
+template <typename T, bool COMBINE>
+__global__ void __launch_bounds__(kThreads) k_update(Geo g, Ptr8<const double> Uin,
+                                                     Ptr8<const double> U0, Ptr8<const T> Fx,
+                                                     Ptr8<const T> Fy, Ptr8<const T> Fz,
+                                                     const T* Ex, const T* Ey, const T* Ez,
+                                                     Ptr8<double> Uout, Ctrl* ctrl) {
+  const double dt = ctrl->dt;
+  if (!(dt > 0.0)) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const double inv =
+      update_body<T, COMBINE>(g, Uin, U0, Fx, Fy, Fz, Ex, Ey, Ez, Uout, dt, c);
   // block max -> one atomic per block (positive doubles order like their bit patterns)
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) inv = fmax(inv, __shfl_xor_sync(0xffffffffu, inv, o));
-  __shared__ double wmax[kThreads / 32];
-  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = inv;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double m = wmax[0];
-    for (int w = 1; w < kThreads / 32; ++w) m = fmax(m, wmax[w]);
-    atomicMax(&ctrl->inv_acc, (unsigned long long)__double_as_longlong(m));
-  }
+  block_max_to(&ctrl->inv_acc, inv);
 }
 
 // Inverse CFL time of a state from the face speeds alone (first cycle).
@@ -481,7 +533,7 @@ __global__ void __launch_bounds__(kThreads) k_inv_only(Geo g, Ptr8<const T> Fx, 
 }
 
 // Cycle prologue: dt = cfl / inv (Eq. 10), clamped to t_end - t.
-__global__ void k_begin(Ctrl* c) {
+__device__ __forceinline__ void begin_body(Ctrl* c) {
   if (c->err != 0 || c->done) {
     c->dt = 0.0;
     c->done = 1;
@@ -504,7 +556,7 @@ __global__ void k_begin(Ctrl* c) {
 }
 
 // Cycle epilogue: advance t, keep the larger stage speed bound for the next dt.
-__global__ void k_end(Ctrl* c) {
+__device__ __forceinline__ void end_body(Ctrl* c) {
   if (!(c->dt > 0.0)) return;
   c->t = c->clamped ? c->t_end : c->t + c->dt;
   c->last_dt = c->dt;
@@ -513,6 +565,9 @@ __global__ void k_end(Ctrl* c) {
   if (c->clamped) c->done = 1;
   c->dt = 0.0;
 }
+
+__global__ void k_begin(Ctrl* c) { begin_body(c); }
+__global__ void k_end(Ctrl* c) { end_body(c); }
 
 }  // namespace
 
@@ -607,7 +662,7 @@ void launch_sweep(idx_sim* s, int d, const Ptr8<T>& W, const double* bface, cons
 
 // Autotuner of the sweep shape: per integrated direction, time every candidate shape on
 // the sim's current primitives (three launches each, CUDA events, fastest wins).  All
-// shapes do the same arithmetic per face, so the choice never changes results.
+// shapes do the same arithmetic per face (up to the compiler's FMA contractions).
 template <typename T>
 int tune_sweeps(idx_sim* s, const Ptr8<double>& U, const Ptr8<T>& W, Ptr8<T>* F) {
   const Geo& g = s->geo;
@@ -1142,3 +1197,467 @@ extern "C" int idx_step_noalloc(const idx_grid* grid, double gamma, double cfl,
   if (dt_taken) *dt_taken = out.last_dt;
   return IDX_OK;
 }
+
+// ===========================================================================
+// Batched stepping (idx_batch_*): many sims -- each with its own grid, state,
+// scratch, control block, dt and end time -- advanced together.  Per stage every
+// kernel type is launched once, as a grid-stride loop of resident blocks over a
+// device work-list of (instance, first index) items of kThreads cells or sweep
+// threads.  The work-list is read at run time, so one captured graph of a batched
+// cycle serves every membership: instances join and leave between graph replays by
+// rewriting the list, without re-capture.  The per-cell arithmetic is the same device
+// code as the single-sim kernels, so a sim gives the same result, to rounding (FMA
+// contraction may differ between kernel instantiations), alone and in a batch.
+// ===========================================================================
+namespace {
+
+template <typename T> struct InstT {
+  Geo g;
+  Ptr8<double> U, U1;
+  Ptr8<T> W;
+  Ptr8<T> F[3];
+  T* E[3];
+  Ctrl* ctrl;
+};
+
+struct Item {
+  int inst;
+  int begin;
+};
+
+template <typename T> struct BatchDev {
+  InstT<T>* inst;
+  Item* cell;      // items of kThreads cells
+  Item* sweep[3];  // items of kThreads sweep threads, per direction
+  Ctrl* gather;    // poll buffer, one Ctrl per instance
+  int n_inst;
+  int n_cell;
+  int n_sweep[3];
+};
+
+template <typename T> __device__ __forceinline__ Ptr8<const T> dconst(const Ptr8<T>& p) {
+  Ptr8<const T> q;
+#pragma unroll
+  for (int f = 0; f < 8; ++f) q.f[f] = p.f[f];
+  return q;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) kb_prims(const BatchDev<T>* B, int stage, int check) {
+  const int n = B->n_cell;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const Item w = B->cell[it];
+    const InstT<T>* I = &B->inst[w.inst];
+    if (check && !(I->ctrl->dt > 0.0)) continue;
+    const Geo g = I->g;
+    const int c = w.begin + threadIdx.x;
+    if (c < g.ncell) prims_body<T>(g, dconst(stage ? I->U1 : I->U), I->W, I->ctrl, c);
+  }
+}
+
+template <typename T, int D, int SEG>
+__global__ void __launch_bounds__(kThreads) kb_sweep(const BatchDev<T>* B, int stage, int check) {
+  const int n = B->n_sweep[D];
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const Item w = B->sweep[D][it];
+    const InstT<T>* I = &B->inst[w.inst];
+    if (check && !(I->ctrl->dt > 0.0)) continue;
+    const Geo g = I->g;
+    const double* bface = (stage ? I->U1 : I->U).f[5 + D];
+    if (SEG > 0)
+      sweep_body<T, D, (SEG > 0 ? SEG : 1)>(g, dconst(I->W), bface, I->F[D], w.begin + threadIdx.x);
+    else
+      sweep_x_body<T>(g, dconst(I->W), bface, I->F[D], w.begin + threadIdx.x);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) kb_emf(const BatchDev<T>* B) {
+  const int n = B->n_cell;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const Item w = B->cell[it];
+    const InstT<T>* I = &B->inst[w.inst];
+    if (!(I->ctrl->dt > 0.0)) continue;
+    const Geo g = I->g;
+    const int c = w.begin + threadIdx.x;
+    if (c < g.ncell)
+      emf_body<T>(g, dconst(I->W), dconst(I->F[0]), dconst(I->F[1]), dconst(I->F[2]), I->E[0],
+                  I->E[1], I->E[2], c);
+  }
+}
+
+template <typename T, bool COMBINE>
+__global__ void __launch_bounds__(kThreads) kb_update(const BatchDev<T>* B) {
+  const int n = B->n_cell;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const Item w = B->cell[it];
+    const InstT<T>* I = &B->inst[w.inst];
+    const double dt = I->ctrl->dt;
+    if (!(dt > 0.0)) continue;  // uniform over the block: one item per block
+    const Geo g = I->g;
+    const double inv = update_body<T, COMBINE>(
+        g, dconst(COMBINE ? I->U1 : I->U), dconst(I->U), dconst(I->F[0]), dconst(I->F[1]),
+        dconst(I->F[2]), I->E[0], I->E[1], I->E[2], COMBINE ? I->U : I->U1, dt,
+        w.begin + threadIdx.x);
+    block_max_to(&I->ctrl->inv_acc, inv);
+  }
+}
+
+template <typename T> __global__ void kb_begin(const BatchDev<T>* B) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B->n_inst; i += gridDim.x * blockDim.x)
+    begin_body(B->inst[i].ctrl);
+}
+
+template <typename T> __global__ void kb_end(const BatchDev<T>* B) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B->n_inst; i += gridDim.x * blockDim.x)
+    end_body(B->inst[i].ctrl);
+}
+
+template <typename T> __global__ void kb_gather(const BatchDev<T>* B) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B->n_inst; i += gridDim.x * blockDim.x)
+    B->gather[i] = *B->inst[i].ctrl;
+}
+
+}  // namespace
+
+struct idx_batch {
+  int precision;
+  cudaStream_t stream;
+  bool own_stream;
+  int device;
+  int sms;
+  std::vector<idx_sim*> sims;
+  void* header;        // BatchDev<T>, fixed address (captured by the graph)
+  void* lists;         // instances, items, poll buffer (reallocated as the batch grows)
+  size_t lists_cap;
+  Ctrl* host_gather;   // pinned
+  size_t host_cap;
+  bool dirty;
+  bool tuned;
+  int shape[3];        // sweep shape per direction (marching segment, or -1 warp x sweep)
+  int graph_shape[3];
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  int grid_cell, grid_sweep;
+};
+
+namespace {
+
+template <typename T> InstT<T> inst_of(idx_sim* s);
+template <> InstT<double> inst_of<double>(idx_sim* s) {
+  InstT<double> I;
+  I.g = s->geo; I.U = s->U; I.U1 = s->U1; I.W = s->Wd;
+  for (int d = 0; d < 3; ++d) { I.F[d] = s->Fd[d]; I.E[d] = s->Ed[d]; }
+  I.ctrl = s->ctrl;
+  return I;
+}
+template <> InstT<float> inst_of<float>(idx_sim* s) {
+  InstT<float> I;
+  I.g = s->geo; I.U = s->U; I.U1 = s->U1; I.W = s->Wf;
+  for (int d = 0; d < 3; ++d) { I.F[d] = s->Ff[d]; I.E[d] = s->Ef[d]; }
+  I.ctrl = s->ctrl;
+  return I;
+}
+
+int sweep_threads(const Geo& g, int d, int shape) {
+  if (shape == -1 && d == 0) return warpx_threads(g);
+  return march_threads(g, d, shape > 0 ? shape : kSegDefault);
+}
+
+// Build the work-lists on the host and upload them with the header.
+template <typename T> int batch_upload(idx_batch* b) {
+  const int n = (int)b->sims.size();
+  std::vector<InstT<T>> inst(n);
+  std::vector<Item> cell, sweep[3];
+  for (int i = 0; i < n; ++i) {
+    idx_sim* s = b->sims[i];
+    inst[i] = inst_of<T>(s);
+    for (int c0 = 0; c0 < s->geo.ncell; c0 += kThreads) cell.push_back({i, c0});
+    for (int d = 0; d < 3; ++d) {
+      if (!s->geo.active[d]) continue;
+      const int nt = sweep_threads(s->geo, d, b->shape[d]);
+      for (int t0 = 0; t0 < nt; t0 += kThreads) sweep[d].push_back({i, t0});
+    }
+  }
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t need = al(sizeof(InstT<T>) * (n + 1)) + al(sizeof(Item) * (cell.size() + 1)) +
+                      al(sizeof(Item) * (sweep[0].size() + 1)) +
+                      al(sizeof(Item) * (sweep[1].size() + 1)) +
+                      al(sizeof(Item) * (sweep[2].size() + 1)) + al(sizeof(Ctrl) * (n + 1));
+  if (need > b->lists_cap) {
+    IDX_TRY(cudaStreamSynchronize(b->stream));
+    if (b->lists) cudaFree(b->lists);
+    b->lists = nullptr;
+    b->lists_cap = 0;
+    if (cudaMalloc(&b->lists, 2 * need) != cudaSuccess) {
+      cudaGetLastError();
+      return IDX_ENOMEM;
+    }
+    b->lists_cap = 2 * need;
+  }
+  if ((size_t)n * sizeof(Ctrl) > b->host_cap) {
+    IDX_TRY(cudaStreamSynchronize(b->stream));
+    if (b->host_gather) cudaFreeHost(b->host_gather);
+    b->host_gather = nullptr;
+    b->host_cap = 0;
+    if (cudaMallocHost(&b->host_gather, 2 * (n + 1) * sizeof(Ctrl)) != cudaSuccess) return IDX_ENOMEM;
+    b->host_cap = 2 * (n + 1) * sizeof(Ctrl);
+  }
+  BatchDev<T> h;
+  char* p = (char*)b->lists;
+  h.inst = (InstT<T>*)p; p += al(sizeof(InstT<T>) * (n + 1));
+  h.cell = (Item*)p; p += al(sizeof(Item) * (cell.size() + 1));
+  for (int d = 0; d < 3; ++d) { h.sweep[d] = (Item*)p; p += al(sizeof(Item) * (sweep[d].size() + 1)); }
+  h.gather = (Ctrl*)p;
+  h.n_inst = n;
+  h.n_cell = (int)cell.size();
+  for (int d = 0; d < 3; ++d) h.n_sweep[d] = (int)sweep[d].size();
+  // pageable sources: each copy is staged before the call returns
+  if (n) IDX_TRY(cudaMemcpyAsync(h.inst, inst.data(), sizeof(InstT<T>) * n, cudaMemcpyHostToDevice, b->stream));
+  if (!cell.empty()) IDX_TRY(cudaMemcpyAsync(h.cell, cell.data(), sizeof(Item) * cell.size(), cudaMemcpyHostToDevice, b->stream));
+  for (int d = 0; d < 3; ++d)
+    if (!sweep[d].empty())
+      IDX_TRY(cudaMemcpyAsync(h.sweep[d], sweep[d].data(), sizeof(Item) * sweep[d].size(), cudaMemcpyHostToDevice, b->stream));
+  IDX_TRY(cudaMemcpyAsync(b->header, &h, sizeof(h), cudaMemcpyHostToDevice, b->stream));
+  IDX_TRY(cudaStreamSynchronize(b->stream));
+  return IDX_OK;
+}
+
+template <typename T, int D>
+void launch_batch_sweep_d(idx_batch* b, int shape, int stage, int check) {
+  const BatchDev<T>* B = (const BatchDev<T>*)b->header;
+  const int grid = b->grid_sweep;
+  switch (shape) {
+    case -1: if (D == 0) { kb_sweep<T, D, -1><<<grid, kThreads, 0, b->stream>>>(B, stage, check); return; } break;
+    case 2: kb_sweep<T, D, 2><<<grid, kThreads, 0, b->stream>>>(B, stage, check); return;
+    case 4: kb_sweep<T, D, 4><<<grid, kThreads, 0, b->stream>>>(B, stage, check); return;
+    case 8: kb_sweep<T, D, 8><<<grid, kThreads, 0, b->stream>>>(B, stage, check); return;
+    case 32: kb_sweep<T, D, 32><<<grid, kThreads, 0, b->stream>>>(B, stage, check); return;
+    default: break;
+  }
+  kb_sweep<T, D, kSegDefault><<<grid, kThreads, 0, b->stream>>>(B, stage, check);
+}
+
+template <typename T> void launch_batch_sweep(idx_batch* b, int d, int stage, int check) {
+  if (d == 0) launch_batch_sweep_d<T, 0>(b, b->shape[0], stage, check);
+  else if (d == 1) launch_batch_sweep_d<T, 1>(b, b->shape[1], stage, check);
+  else launch_batch_sweep_d<T, 2>(b, b->shape[2], stage, check);
+}
+
+template <typename T> void launch_batch_cycle(idx_batch* b) {
+  const BatchDev<T>* B = (const BatchDev<T>*)b->header;
+  kb_begin<T><<<b->sms, kThreads, 0, b->stream>>>(B);
+  for (int st = 0; st < 2; ++st) {
+    kb_prims<T><<<b->grid_cell, kThreads, 0, b->stream>>>(B, st, 1);
+    for (int d = 0; d < 3; ++d) launch_batch_sweep<T>(b, d, st, 1);
+    kb_emf<T><<<b->grid_cell, kThreads, 0, b->stream>>>(B);
+    if (st == 0) kb_update<T, false><<<b->grid_cell, kThreads, 0, b->stream>>>(B);
+    else kb_update<T, true><<<b->grid_cell, kThreads, 0, b->stream>>>(B);
+  }
+  kb_end<T><<<b->sms, kThreads, 0, b->stream>>>(B);
+}
+
+// Tile-shape autotuner of the batch: per direction, every candidate sweep shape is timed
+// on the whole batch (primitives of the current states, three launches each).
+template <typename T> int batch_tune(idx_batch* b) {
+  const BatchDev<T>* B = (const BatchDev<T>*)b->header;
+  int rc = batch_upload<T>(b);
+  if (rc != IDX_OK) return rc;
+  kb_prims<T><<<b->grid_cell, kThreads, 0, b->stream>>>(B, 0, 0);
+  cudaEvent_t e0, e1;
+  IDX_TRY(cudaEventCreate(&e0));
+  IDX_TRY(cudaEventCreate(&e1));
+  const int cand[6] = {-1, 2, 4, 8, 16, 32};
+  for (int d = 0; d < 3 && rc == IDX_OK; ++d) {
+    bool any = false;
+    for (idx_sim* s : b->sims) any = any || s->geo.active[d];
+    if (!any) continue;
+    float best = 1e30f;
+    int best_shape = kSegDefault;
+    for (int q = 0; q < 6 && rc == IDX_OK; ++q) {
+      if (cand[q] == -1 && d != 0) continue;
+      b->shape[d] = cand[q];
+      rc = batch_upload<T>(b);
+      if (rc != IDX_OK) break;
+      launch_batch_sweep<T>(b, d, 0, 0);
+      cudaEventRecord(e0, b->stream);
+      for (int r = 0; r < 3; ++r) launch_batch_sweep<T>(b, d, 0, 0);
+      cudaEventRecord(e1, b->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = IDX_ECUDA; break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; best_shape = cand[q]; }
+    }
+    b->shape[d] = best_shape;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != IDX_OK) return rc;
+  IDX_TRY(cudaGetLastError());
+  b->tuned = true;
+  return batch_upload<T>(b);
+}
+
+template <typename T> int batch_prepare(idx_batch* b) {
+  if (b->dirty) {
+    int rc = (!b->tuned && !b->sims.empty()) ? batch_tune<T>(b) : batch_upload<T>(b);
+    if (rc != IDX_OK) return rc;
+    b->dirty = false;
+  }
+  const bool same = b->exec && b->graph_shape[0] == b->shape[0] &&
+                    b->graph_shape[1] == b->shape[1] && b->graph_shape[2] == b->shape[2];
+  if (same) return IDX_OK;
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  IDX_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  launch_batch_cycle<T>(b);
+  IDX_TRY(cudaStreamEndCapture(b->stream, &b->graph));
+  IDX_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  for (int d = 0; d < 3; ++d) b->graph_shape[d] = b->shape[d];
+  return IDX_OK;
+}
+
+template <typename T> int batch_occupancy(idx_batch* b) {
+  int per_sm_cell = 0, per_sm_sweep = 0;
+  IDX_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_cell, kb_update<T, true>, kThreads, 0));
+  IDX_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_sweep, kb_sweep<T, 1, kSegDefault>, kThreads, 0));
+  b->grid_cell = b->sms * (per_sm_cell > 0 ? per_sm_cell : 1);
+  b->grid_sweep = b->sms * (per_sm_sweep > 0 ? per_sm_sweep : 1);
+  return IDX_OK;
+}
+
+// Set a member's end time (and clear its done flag when it still has time to go).
+int arm_end_time(cudaStream_t stream, idx_sim* s, double t_end) {
+  int rc = sync_ctrl(s);
+  if (rc != IDX_OK) return rc;
+  Ctrl c = *s->host_ctrl;
+  c.t_end = t_end;
+  c.done = (c.t >= t_end) ? 1 : 0;
+  IDX_TRY(cudaMemcpyAsync(s->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, stream));
+  IDX_TRY(cudaStreamSynchronize(stream));
+  return IDX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int idx_batch_create(int precision, void* stream, idx_batch** out) {
+  if (!out || (precision != IDX_FP64 && precision != IDX_FP32_BULK)) return IDX_EINVAL;
+  *out = nullptr;
+  idx_batch* b = new idx_batch();
+  b->precision = precision;
+  b->dirty = true;
+  for (int d = 0; d < 3; ++d) { b->shape[d] = kSegDefault; b->graph_shape[d] = 0; }
+  int rc = IDX_OK;
+  if (cudaGetDevice(&b->device) != cudaSuccess) rc = IDX_ECUDA;
+  if (rc == IDX_OK && cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) rc = IDX_ECUDA;
+  if (rc == IDX_OK) {
+    if (stream) {
+      b->stream = (cudaStream_t)stream;
+    } else {
+      b->own_stream = true;
+      if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) rc = IDX_ECUDA;
+    }
+  }
+  if (rc == IDX_OK && cudaMalloc(&b->header, 256) != cudaSuccess) rc = IDX_ENOMEM;
+  if (rc == IDX_OK) rc = precision == IDX_FP32_BULK ? batch_occupancy<float>(b) : batch_occupancy<double>(b);
+  if (rc != IDX_OK) {
+    idx_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return IDX_OK;
+}
+
+void idx_batch_destroy(idx_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->lists) cudaFree(b->lists);
+  if (b->header) cudaFree(b->header);
+  if (b->host_gather) cudaFreeHost(b->host_gather);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+int idx_batch_add(idx_batch* b, idx_sim* s, double t_end) {
+  if (!b || !s || !(t_end >= 0.0)) return IDX_EINVAL;
+  if (s->solver.precision != b->precision || s->device != b->device) return IDX_EINVAL;
+  for (idx_sim* m : b->sims)
+    if (m == s) return IDX_EINVAL;
+  IDX_TRY(cudaStreamSynchronize(b->stream));
+  IDX_TRY(cudaStreamSynchronize(s->stream));  // the sim's own work (its state upload) first
+  int rc = arm_end_time(b->stream, s, t_end);
+  if (rc != IDX_OK) return rc;
+  b->sims.push_back(s);
+  b->dirty = true;
+  return IDX_OK;
+}
+
+int idx_batch_remove(idx_batch* b, idx_sim* s) {
+  if (!b || !s) return IDX_EINVAL;
+  for (size_t i = 0; i < b->sims.size(); ++i) {
+    if (b->sims[i] != s) continue;
+    IDX_TRY(cudaStreamSynchronize(b->stream));
+    b->sims.erase(b->sims.begin() + i);
+    b->dirty = true;
+    // back to unclamped single-sim stepping
+    int rc = arm_end_time(b->stream, s, std::numeric_limits<double>::infinity());
+    if (rc != IDX_OK) return rc;
+    return IDX_OK;
+  }
+  return IDX_EINVAL;
+}
+
+int idx_batch_step(idx_batch* b, int ncycles) {
+  if (!b || ncycles < 0) return IDX_EINVAL;
+  if (b->sims.empty() || ncycles == 0) return IDX_OK;
+  const bool f32 = b->precision == IDX_FP32_BULK;
+  int rc = f32 ? batch_prepare<float>(b) : batch_prepare<double>(b);
+  if (rc != IDX_OK) return rc;
+  for (int q = 0; q < ncycles; ++q) IDX_TRY(cudaGraphLaunch(b->exec, b->stream));
+  return IDX_OK;
+}
+
+int idx_batch_poll(idx_batch* b, idx_sim** finished, int cap, int* n_finished, int* n_active) {
+  if (!b || (cap > 0 && !finished)) return IDX_EINVAL;
+  const bool f32 = b->precision == IDX_FP32_BULK;
+  int rc = f32 ? batch_prepare<float>(b) : batch_prepare<double>(b);
+  if (rc != IDX_OK) return rc;
+  const int n = (int)b->sims.size();
+  int nf = 0, na = 0;
+  if (n > 0) {
+    if (f32) kb_gather<float><<<1, kThreads, 0, b->stream>>>((const BatchDev<float>*)b->header);
+    else kb_gather<double><<<1, kThreads, 0, b->stream>>>((const BatchDev<double>*)b->header);
+    IDX_TRY(cudaGetLastError());
+    BatchDev<double> h;  // only the gather pointer is read; same layout for both types
+    IDX_TRY(cudaMemcpyAsync(&h, b->header, sizeof(h), cudaMemcpyDeviceToHost, b->stream));
+    IDX_TRY(cudaStreamSynchronize(b->stream));
+    IDX_TRY(cudaMemcpyAsync(b->host_gather, h.gather, sizeof(Ctrl) * n, cudaMemcpyDeviceToHost, b->stream));
+    IDX_TRY(cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < n; ++i) {
+      const Ctrl& c = b->host_gather[i];
+      idx_sim* s = b->sims[i];
+      *s->host_ctrl = c;  // keep the sim's mirror current
+      if (c.done || c.err) {
+        if (nf < cap) finished[nf] = s;
+        ++nf;
+      } else {
+        ++na;
+      }
+    }
+  }
+  if (n_finished) *n_finished = nf;
+  if (n_active) *n_active = na;
+  return IDX_OK;
+}
+
+int idx_batch_shapes(const idx_batch* b, int shapes[3]) {
+  if (!b || !shapes) return IDX_EINVAL;
+  for (int d = 0; d < 3; ++d) shapes[d] = b->shape[d];
+  return IDX_OK;
+}
+
+}  // extern "C"

@@ -68,6 +68,15 @@ def lib(path=LIB_PATH):
     L.idx_pipe_rates.argtypes = [ctypes.POINTER(ctypes.c_double)]
     L.idx_kernel_times.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     L.idx_sweep_shapes.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.idx_batch_create.argtypes = [ctypes.c_int, vp, ctypes.POINTER(vp)]
+    L.idx_batch_add.argtypes = [vp, vp, ctypes.c_double]
+    L.idx_batch_remove.argtypes = [vp, vp]
+    L.idx_batch_step.argtypes = [vp, ctypes.c_int]
+    L.idx_batch_poll.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_int)]
+    L.idx_batch_shapes.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.idx_batch_destroy.argtypes = [vp]
+    L.idx_batch_destroy.restype = None
     _lib = L
     return L
 
@@ -209,3 +218,57 @@ class Sim:
         t, dt = ctypes.c_double(), ctypes.c_double()
         self._check(lib().idx_time(self._h, ctypes.byref(t), ctypes.byref(dt)), "idx_time")
         return t.value, dt.value
+
+
+class Batch:
+    """Many sims stepped together (idx_batch_*): each keeps its own dt and end time."""
+
+    def __init__(self, precision="fp64", stream=None):
+        L = lib()
+        h = ctypes.c_void_p()
+        rc = L.idx_batch_create(PRECISIONS[precision], ctypes.c_void_p(stream) if stream else None,
+                                ctypes.byref(h))
+        if rc != IDX_OK:
+            raise IdxError(rc, "idx_batch_create")
+        self._h = h
+        self.members = {}
+
+    def _check(self, rc, where):
+        if rc != IDX_OK:
+            raise IdxError(rc, where)
+
+    def add(self, sim, t_end=float("inf")):
+        self._check(lib().idx_batch_add(self._h, sim.handle, float(t_end)), "idx_batch_add")
+        self.members[sim.handle.value] = sim
+
+    def remove(self, sim):
+        self._check(lib().idx_batch_remove(self._h, sim.handle), "idx_batch_remove")
+        self.members.pop(sim.handle.value, None)
+
+    def step(self, ncycles=1):
+        self._check(lib().idx_batch_step(self._h, int(ncycles)), "idx_batch_step")
+
+    def poll(self):
+        """Synchronise; returns (members that reached their end time or failed, n_active)."""
+        cap = max(1, len(self.members))
+        arr = (ctypes.c_void_p * cap)()
+        nf, na = ctypes.c_int(), ctypes.c_int()
+        self._check(lib().idx_batch_poll(self._h, arr, cap, ctypes.byref(nf), ctypes.byref(na)),
+                    "idx_batch_poll")
+        return [self.members[arr[i]] for i in range(min(nf.value, cap))], na.value
+
+    def shapes(self):
+        out = (ctypes.c_int * 3)()
+        self._check(lib().idx_batch_shapes(self._h, out), "idx_batch_shapes")
+        return list(out)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().idx_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
