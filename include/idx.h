@@ -99,6 +99,13 @@ int idx_advance(idx_sim* sim, double t_end, int64_t* nsteps);
 /* Current time and the dt the next cycle will take (before any clamp).  Synchronises. */
 int idx_time(const idx_sim* sim, double* t, double* next_dt);
 
+/* RK2 cycles taken since the last idx_set_state / idx_set_primitive.  Synchronises. */
+int idx_step_count(const idx_sim* sim, int64_t* nsteps);
+
+/* Device bytes idx_create allocates for this grid and precision (FP64 408 B per cell,
+ * FP32 bulk 268 B per cell, plus alignment); no device call.  For admission control. */
+int idx_footprint(const idx_grid* grid, int precision, uint64_t* bytes);
+
 /* Flat index k*ny*nx + j*nx + i of the first (lowest-index) cell found non-physical by
  * the last failing call, or -1. */
 int idx_last_error_cell(const idx_sim* sim, int64_t* cell);

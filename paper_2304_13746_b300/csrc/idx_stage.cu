@@ -790,6 +790,14 @@ int after_new_state(idx_sim* s) {
   return pending_error(s);
 }
 
+// Device bytes of one sim (the single allocation of idx_create).
+size_t sim_bytes(long long ncell, bool f32) {
+  auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t arr_d = align(sizeof(double) * ncell);
+  const size_t arr_t = align((f32 ? sizeof(float) : sizeof(double)) * ncell);
+  return 16 * arr_d + (8 + 24 + 3) * arr_t + align(sizeof(Ctrl));
+}
+
 bool valid_solver(const idx_solver* v) {
   return v && v->recon == 1 && v->riemann == 4 && v->emf == 2 && v->rk_order == 2 &&
          v->cfl > 0.0 && v->cfl < 1.0 &&
@@ -846,7 +854,7 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
   const size_t tsz = f32 ? sizeof(float) : sizeof(double);
   auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t arr_d = align(sizeof(double) * ncell), arr_t = align(tsz * ncell);
-  const size_t bytes = 16 * arr_d + (8 + 24 + 3) * arr_t + align(sizeof(Ctrl));
+  const size_t bytes = sim_bytes(ncell, f32);
   if (cudaMalloc(&s->mem, bytes) != cudaSuccess) {
     cudaGetLastError();
     delete s;
@@ -1074,6 +1082,24 @@ int idx_sweep_shapes(const idx_sim* s, int shapes[3]) {
     const int v = s->sweep_shape[d];
     shapes[d] = s->geo.active[d] ? (v == 0 ? kSegDefault : v) : 0;
   }
+  return IDX_OK;
+}
+
+int idx_step_count(const idx_sim* cs, int64_t* nsteps) {
+  idx_sim* s = const_cast<idx_sim*>(cs);
+  if (!s || !nsteps) return IDX_EINVAL;
+  int rc = sync_ctrl(s);
+  if (rc != IDX_OK) return rc;
+  *nsteps = (int64_t)s->host_ctrl->nsteps;
+  return pending_error(s);
+}
+
+int idx_footprint(const idx_grid* grid, int precision, uint64_t* bytes) {
+  if (!grid || !bytes || grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return IDX_EINVAL;
+  if (precision != IDX_FP64 && precision != IDX_FP32_BULK) return IDX_EINVAL;
+  const long long ncell = (long long)grid->nx * grid->ny * grid->nz;
+  if (ncell >= (1ll << 31)) return IDX_EINVAL;
+  *bytes = (uint64_t)sim_bytes(ncell, precision == IDX_FP32_BULK);
   return IDX_OK;
 }
 

@@ -68,6 +68,8 @@ def lib(path=LIB_PATH):
     L.idx_pipe_rates.argtypes = [ctypes.POINTER(ctypes.c_double)]
     L.idx_kernel_times.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     L.idx_sweep_shapes.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.idx_step_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    L.idx_footprint.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]
     L.idx_batch_create.argtypes = [ctypes.c_int, vp, ctypes.POINTER(vp)]
     L.idx_batch_add.argtypes = [vp, vp, ctypes.c_double]
     L.idx_batch_remove.argtypes = [vp, vp]
@@ -93,6 +95,17 @@ def pipe_rates():
         raise IdxError(rc, "idx_pipe_rates")
     keys = ("fma64", "div64", "sqrt64", "fma32", "div32", "sqrt32")
     return dict(zip(keys, out[:]))
+
+
+def footprint(shape, precision="fp64"):
+    """Device bytes a sim of this shape (nz, ny, nx) and precision allocates."""
+    nz, ny, nx = (int(v) for v in shape)
+    out = ctypes.c_uint64()
+    rc = lib().idx_footprint(ctypes.byref(Grid(nx, ny, nz, 1.0, 1.0, 1.0)), PRECISIONS[precision],
+                             ctypes.byref(out))
+    if rc != IDX_OK:
+        raise IdxError(rc, "idx_footprint")
+    return int(out.value)
 
 
 def _is_torch(a):
@@ -213,6 +226,11 @@ class Sim:
         out = (ctypes.c_int * 3)()
         self._check(lib().idx_sweep_shapes(self._h, out), "idx_sweep_shapes")
         return list(out)
+
+    def step_count(self):
+        n = ctypes.c_int64()
+        self._check(lib().idx_step_count(self._h, ctypes.byref(n)), "idx_step_count")
+        return n.value
 
     def time(self):
         t, dt = ctypes.c_double(), ctypes.c_double()

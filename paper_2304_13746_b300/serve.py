@@ -1,0 +1,252 @@
+"""Serving many ideal-MHD simulations on one GPU with continuous batching.
+
+Requests (an initial state, a grid, an end time) arrive over time.  The server admits
+them, oldest first, as device memory frees up under a fixed HBM budget; every admitted
+request joins the running batch (idx_batch_*), where all of them advance together, each
+with its own CFL dt, until its end time; a finished request's state is copied back to
+the host and its memory released, which lets the next ones in.  Latency is arrival to
+result-on-host.  The same stream can be served one request at a time for comparison.
+
+The scheduler talks to a backend (the real one wraps libidx; tests use a fake device
+and a fake clock), so its admission and accounting logic is tested without a GPU.
+"""
+from collections import deque
+from dataclasses import dataclass, field
+import math
+import time
+from typing import Optional
+
+import numpy as np
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float            # seconds after the start of the stream
+    kind: str                 # "2d" (Orszag-Tang) or "3d" (turbulent box)
+    n: int
+    t_end: float
+    seed: int
+    payload: Optional[object] = None   # inputs.IC, made before the stream starts
+    # filled in by the server
+    status: str = "pending"            # pending, running, done, failed, rejected
+    admitted: Optional[float] = None
+    finished: Optional[float] = None
+    cycles: int = 0
+    cells: int = 0
+    state: Optional[list] = None
+    error: Optional[str] = None
+
+
+def poisson_stream(n_requests, rate, seed=7, sizes_2d=(64, 512), sizes_3d=(32, 128),
+                   t_end=(0.01, 0.1), p2d=0.5):
+    """Seeded request stream: exponential inter-arrival times of mean 1/rate; kind 2D with
+    probability p2d; N log-uniform in the kind's range (a multiple of 8); t_end uniform."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for i in range(n_requests):
+        t += float(rng.exponential(1.0 / rate))
+        kind = "2d" if rng.uniform() < p2d else "3d"
+        lo, hi = sizes_2d if kind == "2d" else sizes_3d
+        n = int(max(8, 8 * round(math.exp(rng.uniform(math.log(lo), math.log(hi))) / 8)))
+        out.append(Request(i, t, kind, n, float(rng.uniform(*t_end)), seed=1000 + i))
+    return out
+
+
+def make_payloads(requests):
+    from . import inputs
+    for r in requests:
+        r.payload = (inputs.orszag_tang_2d(r.n) if r.kind == "2d"
+                     else inputs.turbulent_box(r.n, seed=r.seed))
+        r.cells = r.payload.ncells
+    return requests
+
+
+class WallClock:
+    def __init__(self):
+        self.t0 = time.perf_counter()
+
+    def now(self):
+        return time.perf_counter() - self.t0
+
+    def sleep_until(self, t):
+        dt = t - self.now()
+        if dt > 0:
+            time.sleep(dt)
+
+
+class IdxBackend:
+    """libidx: one batch; a request is a sim made, filled and added on admission."""
+
+    def __init__(self, precision="fp64", cfl=0.4, stream=None):
+        from . import idx
+        self.idx = idx
+        self.precision = precision
+        self.cfl = cfl
+        self.stream = stream
+        self.batch = idx.Batch(precision, stream=stream)
+        self.sims = {}
+
+    def footprint(self, req):
+        return self.idx.footprint(req.payload.shape, self.precision)
+
+    def start(self, req):
+        ic = req.payload
+        s = self.idx.Sim(ic.shape, ic.lengths, ic.gamma, self.cfl, self.precision,
+                         stream=self.stream)
+        try:
+            s.set_primitive(ic.prim)
+            self.batch.add(s, req.t_end)
+        except Exception:
+            s.close()
+            raise
+        self.sims[req.rid] = s
+
+    def step(self, ncycles):
+        self.batch.step(ncycles)
+
+    def poll(self):
+        finished, _ = self.batch.poll()
+        ids = {id(s): rid for rid, s in self.sims.items()}
+        return [ids[id(s)] for s in finished]
+
+    def finish(self, rid):
+        s = self.sims.pop(rid)
+        try:
+            self.batch.remove(s)
+            cycles = s.step_count()
+            state = s.get_state()
+        finally:
+            s.close()
+        return state, cycles
+
+    def close(self):
+        for rid in list(self.sims):
+            self.sims.pop(rid).close()
+        self.batch.close()
+
+
+class IdxSequential:
+    """libidx one request at a time: the same sims advanced alone (idx_advance)."""
+
+    def __init__(self, precision="fp64", cfl=0.4, stream=None):
+        from . import idx
+        self.idx = idx
+        self.precision = precision
+        self.cfl = cfl
+        self.stream = stream
+
+    def footprint(self, req):
+        return self.idx.footprint(req.payload.shape, self.precision)
+
+    def serve_one(self, req):
+        ic = req.payload
+        s = self.idx.Sim(ic.shape, ic.lengths, ic.gamma, self.cfl, self.precision,
+                         stream=self.stream)
+        try:
+            s.set_primitive(ic.prim)
+            s.advance(req.t_end)
+            return s.get_state(), s.step_count()
+        finally:
+            s.close()
+
+
+def _stats(requests, t_first, t_last):
+    done = [r for r in requests if r.status == "done"]
+    lat = np.array([r.finished - r.arrival for r in done]) if done else np.array([np.nan])
+    wait = np.array([r.admitted - r.arrival for r in done]) if done else np.array([np.nan])
+    work = float(sum(r.cells * r.cycles for r in done))
+    span = max(t_last - t_first, 1e-12)
+    return {"requests": len(requests), "done": len(done),
+            "failed": sum(r.status == "failed" for r in requests),
+            "rejected": sum(r.status == "rejected" for r in requests),
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(np.mean(lat)), "wait_p50_s": float(np.percentile(wait, 50)),
+            "cell_updates": work, "makespan_s": span, "cell_updates_per_s": work / span}
+
+
+class Server:
+    """Continuous batching under an HBM budget (oldest request first)."""
+
+    def __init__(self, backend, budget_bytes, clock=None, cycles_per_poll=8):
+        self.backend = backend
+        self.budget = int(budget_bytes)
+        self.clock = clock or WallClock()
+        self.k = int(cycles_per_poll)
+        self.used = 0
+        self.peak = 0
+
+    def run(self, requests):
+        pending = deque(sorted(requests, key=lambda r: r.arrival))
+        queue = deque()
+        running = {}
+        bytes_of = {}
+        t_first = pending[0].arrival if pending else 0.0
+        t_last = t_first
+        while pending or queue or running:
+            now = self.clock.now()
+            while pending and pending[0].arrival <= now:
+                queue.append(pending.popleft())
+            # admission, oldest first, while the budget allows
+            while queue:
+                r = queue[0]
+                need = self.backend.footprint(r)
+                if need > self.budget:
+                    queue.popleft()
+                    r.status, r.error = "rejected", f"needs {need} B > budget {self.budget} B"
+                    continue
+                if self.used + need > self.budget:
+                    break
+                queue.popleft()
+                try:
+                    self.backend.start(r)
+                except Exception as e:  # a request that fails to start is reported, not fatal
+                    r.status, r.error = "failed", str(e)
+                    r.finished = self.clock.now()
+                    continue
+                r.status, r.admitted = "running", self.clock.now()
+                running[r.rid] = r
+                bytes_of[r.rid] = need
+                self.used += need
+                self.peak = max(self.peak, self.used)
+            if running:
+                self.backend.step(self.k)
+                for rid in self.backend.poll():
+                    r = running.pop(rid)
+                    try:
+                        r.state, r.cycles = self.backend.finish(rid)
+                        r.status = "done"
+                    except Exception as e:
+                        r.status, r.error = "failed", str(e)
+                    r.finished = self.clock.now()
+                    t_last = max(t_last, r.finished)
+                    self.used -= bytes_of.pop(rid)
+            elif pending and not queue:
+                self.clock.sleep_until(pending[0].arrival)
+        stats = _stats(requests, t_first, t_last)
+        stats["peak_bytes"] = self.peak
+        stats["budget_bytes"] = self.budget
+        return stats
+
+
+def serve_sequential(backend, requests, clock=None, budget_bytes=None):
+    """The same stream, one request at a time, oldest first."""
+    clock = clock or WallClock()
+    reqs = sorted(requests, key=lambda r: r.arrival)
+    t_first = reqs[0].arrival if reqs else 0.0
+    t_last = t_first
+    for r in reqs:
+        clock.sleep_until(r.arrival)
+        if budget_bytes is not None and backend.footprint(r) > budget_bytes:
+            r.status, r.error = "rejected", "over budget"
+            continue
+        r.admitted = clock.now()
+        try:
+            r.state, r.cycles = backend.serve_one(r)
+            r.status = "done"
+        except Exception as e:
+            r.status, r.error = "failed", str(e)
+        r.finished = clock.now()
+        t_last = max(t_last, r.finished)
+    return _stats(requests, t_first, t_last)
