@@ -44,10 +44,12 @@ def parse():
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     p.add_argument("--impl", default="idx", choices=["idx", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--mode", default="plain", choices=["plain", "batched"],
+    p.add_argument("--mode", default="plain", choices=["plain", "batched", "serve", "accuracy"],
                    help="plain: one box (the headline line); batched: the 64-instance mix, "
                         "batched vs one at a time")
     p.add_argument("--cycles", type=int, default=100, help="cycles per instance (batched mode)")
+    p.add_argument("--requests", type=int, default=200, help="requests in the served stream")
+    p.add_argument("--budget-gb", type=float, default=120.0, help="HBM budget of the server")
     return p.parse_args()
 
 
@@ -265,12 +267,92 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Served stream: seeded Poisson arrivals of 2D/3D requests admitted under an HBM budget
+    into one running batch (continuous batching), against the same stream one at a time."""
+    import torch
+    from paper_2304_13746_b300 import build as idx_build
+    from paper_2304_13746_b300 import idx, serve
+    idx_build.build()
+    idx.lib()
+    budget = int(args.budget_gb * 1e9)
+    base = serve.make_payloads(serve.poisson_stream(args.requests, 20.0, seed=7))
+    stream = torch.cuda.Stream()
+
+    def clone(reqs, rate):
+        out = []
+        for r in reqs:
+            q = serve.Request(r.rid, r.arrival * 20.0 / rate, r.kind, r.n, r.t_end, r.seed,
+                              payload=r.payload)
+            q.cells = r.cells
+            out.append(q)
+        return out
+
+    def served(precision, rate):
+        be = serve.IdxBackend(precision, stream=stream.cuda_stream)
+        st = serve.Server(be, budget, cycles_per_poll=4, chunk_s=0.01).run(clone(base, rate))
+        be.close()
+        return st
+
+    results = {}
+    for precision in ("fp32", "fp64"):
+        cap = served(precision, 1e9)                    # everything arrives at once
+        mean_work = cap["cell_updates"] / max(cap["done"], 1)
+        capacity_rps = cap["cell_updates_per_s"] / mean_work
+        rate70 = 0.7 * capacity_rps
+        r = {"capacity_req_per_s": capacity_rps, "mean_cell_updates_per_request": mean_work,
+             "all_at_once": cap}
+        r["sequential_all_at_once"] = serve.serve_sequential(
+            serve.IdxSequential(precision, stream=stream.cuda_stream), clone(base, 1e9),
+            budget_bytes=budget)
+        r["served_70pct"] = dict(served(precision, rate70), rate=rate70)
+        r["sequential_70pct"] = dict(serve.serve_sequential(
+            serve.IdxSequential(precision, stream=stream.cuda_stream), clone(base, rate70),
+            budget_bytes=budget), rate=rate70)
+        if precision == "fp32":
+            r["served_20rps"] = dict(served(precision, 20.0), rate=20.0)
+        r["offered_load_at_20rps"] = 20.0 / capacity_rps
+        results[precision] = r
+    line = {"metric": METRIC, "value": results["fp64"]["served_70pct"]["cell_updates_per_s"],
+            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"served: {args.requests} requests, Poisson arrivals (seed 7), "
+                                   "kind 2D/3D p=1/2, 2D Orszag-Tang N log-uniform 64..512, 3D "
+                                   "turbulent box N log-uniform 32..128, t_end U[0.01, 0.1], "
+                                   f"HBM budget {args.budget_gb:g} GB, continuous batching vs "
+                                   "one at a time", "budget_bytes": budget},
+            "served": results}
+    print(json.dumps(line), flush=True)
+
+
+def run_accuracy(args):
+    """FP32-bulk error budget at n^3 (default 512^3): per-field L1 difference from FP64 vs
+    the Richardson estimate of the discretisation error (half-resolution FP64 run)."""
+    from paper_2304_13746_b300 import accuracy
+    from paper_2304_13746_b300 import build as idx_build
+    idx_build.build()
+    n = args.n if args.n != 256 else 512
+    t_end = 0.0175  # about 200 RK2 cycles of the 512^3 box
+    r = accuracy.fp32_error_budget(n, t_end)
+    line = {"metric": "FP32-bulk L1 error / discretisation error (per field)", "value": r["max_ratio"],
+            "unit": "ratio", "higher_is_better": False, "n_gpus": 1, "dtype": "f32/f64",
+            "data": "synthetic",
+            "config": {"workload": f"3D turbulent box {n}^3 to t={t_end} (FP32 bulk vs FP64, "
+                                   f"discretisation error from {n // 2}^3, p=2)"},
+            "accuracy": r}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "batched":
         return run_batched(args)
+    if args.mode == "serve":
+        return run_serve(args)
+    if args.mode == "accuracy":
+        return run_accuracy(args)
     rank, world, local = dist_env()
     import torch
     torch.cuda.set_device(local)

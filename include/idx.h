@@ -117,8 +117,9 @@ int idx_last_error_cell(const idx_sim* sim, int64_t* cell);
  * are real: the sim advances by `reps` cycles.  A measurement aid, not part of the method. */
 int idx_kernel_times(idx_sim* sim, int reps, double ms[6]);
 
-/* Sweep shape per direction chosen by the autotuner that runs on a sim's first state
- * (grids of at least 32768 cells; smaller ones keep the default): a value s > 0 means one
+/* Sweep shape per direction chosen by the autotuner, which runs before a sim's first
+ * idx_step / idx_advance (grids of at least 32768 cells; smaller ones keep the default;
+ * results are cached per grid, precision and device for the process): a value s > 0 means one
  * thread marches s faces of a pencil, -1 the warp-per-32-cells x sweep, 0 a direction
  * that is not integrated.  Every shape does the same arithmetic per face; results differ
  * between shapes at most by rounding (the compiler may contract products into FMAs

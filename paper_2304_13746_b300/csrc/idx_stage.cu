@@ -27,6 +27,9 @@
 #include <mutex>
 #include <type_traits>
 #include <vector>
+#include <array>
+#include <map>
+#include <tuple>
 
 #include "../../include/idx.h"
 #include "mhd_math.cuh"
@@ -733,8 +736,50 @@ void launch_cycle(idx_sim* s) {
   k_end<<<1, 1, 0, s->stream>>>(s->ctrl);
 }
 
+// Sweep shapes already tuned in this process, by grid, precision and device.
+struct TuneKey {
+  int nx, ny, nz, precision, device;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(nx, ny, nz, precision, device) < std::tie(o.nx, o.ny, o.nz, o.precision, o.device);
+  }
+};
+std::map<TuneKey, std::array<int, 3>> g_tune_cache;
+std::mutex g_tune_mutex;
+
+// Tune the sweep shapes of a sim before its first stepping (sims stepped only inside a
+// batch never need it).  The tuning sweeps recompute the current state's fluxes into
+// scratch; the cycle recomputes everything it reads.
+int tune_once(idx_sim* s) {
+  if (s->tuned) return IDX_OK;
+  s->tuned = true;
+  if (s->geo.ncell < kTuneMinCells) return IDX_OK;
+  const TuneKey key{s->grid.nx, s->grid.ny, s->grid.nz, s->solver.precision, s->device};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      for (int d = 0; d < 3; ++d) s->sweep_shape[d] = it->second[d];
+      return IDX_OK;
+    }
+  }
+  int rc;
+  if (s->solver.precision == IDX_FP32_BULK) {
+    launch_fluxes<float>(s, s->U, s->Wf, s->Ff, 0);
+    rc = tune_sweeps<float>(s, s->U, s->Wf, s->Ff);
+  } else {
+    launch_fluxes<double>(s, s->U, s->Wd, s->Fd, 0);
+    rc = tune_sweeps<double>(s, s->U, s->Wd, s->Fd);
+  }
+  if (rc != IDX_OK) return rc;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune_cache[key] = {s->sweep_shape[0], s->sweep_shape[1], s->sweep_shape[2]};
+  return IDX_OK;
+}
+
 int build_graph(idx_sim* s) {
   if (s->exec) return IDX_OK;
+  int trc = tune_once(s);
+  if (trc != IDX_OK) return trc;
   IDX_TRY(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
   launch_cycle(s);
   cudaError_t e = cudaStreamEndCapture(s->stream, &s->graph);
@@ -767,22 +812,16 @@ int after_new_state(idx_sim* s) {
   c.bad_cell = ~0ull;
   IDX_TRY(cudaMemcpyAsync(s->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s->stream));
   const Geo& g = s->geo;
-  // the speed pass; on a sim's first state it also tunes the sweep shapes, which
-  // recompute the same fluxes from the same primitives
-  int trc = IDX_OK;
+  // the speed pass of the first cycle
   if (s->solver.precision == IDX_FP32_BULK) {
     launch_fluxes<float>(s, s->U, s->Wf, s->Ff, 0);
-    if (!s->tuned && g.ncell >= kTuneMinCells) trc = tune_sweeps<float>(s, s->U, s->Wf, s->Ff);
     k_inv_only<float><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
         g, cst(s->Ff[0]), cst(s->Ff[1]), cst(s->Ff[2]), s->ctrl);
   } else {
     launch_fluxes<double>(s, s->U, s->Wd, s->Fd, 0);
-    if (!s->tuned && g.ncell >= kTuneMinCells) trc = tune_sweeps<double>(s, s->U, s->Wd, s->Fd);
     k_inv_only<double><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
         g, cst(s->Fd[0]), cst(s->Fd[1]), cst(s->Fd[2]), s->ctrl);
   }
-  if (trc != IDX_OK) return trc;
-  s->tuned = true;
   IDX_TRY(cudaGetLastError());
   int rc = sync_ctrl(s);
   if (rc != IDX_OK) return rc;
@@ -1017,7 +1056,9 @@ int idx_time(const idx_sim* cs, double* t, double* next_dt) {
 
 int idx_kernel_times(idx_sim* s, int reps, double ms[6]) {
   if (!s || !ms || reps < 1) return IDX_EINVAL;
-  int rc = sync_ctrl(s);
+  int rc = tune_once(s);
+  if (rc != IDX_OK) return rc;
+  rc = sync_ctrl(s);
   if (rc != IDX_OK) return rc;
   rc = pending_error(s);
   if (rc != IDX_OK) return rc;

@@ -169,11 +169,15 @@ def _stats(requests, t_first, t_last):
 class Server:
     """Continuous batching under an HBM budget (oldest request first)."""
 
-    def __init__(self, backend, budget_bytes, clock=None, cycles_per_poll=8):
+    def __init__(self, backend, budget_bytes, clock=None, cycles_per_poll=8, chunk_s=None):
+        """cycles_per_poll: batched cycles between polls; with chunk_s set, that number
+        adapts so that one chunk takes about chunk_s seconds (new arrivals and finished
+        requests are handled at chunk boundaries)."""
         self.backend = backend
         self.budget = int(budget_bytes)
         self.clock = clock or WallClock()
         self.k = int(cycles_per_poll)
+        self.chunk_s = chunk_s
         self.used = 0
         self.peak = 0
 
@@ -211,8 +215,13 @@ class Server:
                 self.used += need
                 self.peak = max(self.peak, self.used)
             if running:
+                t0 = self.clock.now()
                 self.backend.step(self.k)
-                for rid in self.backend.poll():
+                finished = self.backend.poll()
+                if self.chunk_s:
+                    el = max(self.clock.now() - t0, 1e-6)
+                    self.k = int(min(64, max(1, round(self.k * self.chunk_s / el))))
+                for rid in finished:
                     r = running.pop(rid)
                     try:
                         r.state, r.cycles = self.backend.finish(rid)
