@@ -66,6 +66,7 @@ struct Geo {
   int active[3];   // n_d > 1
   double inv_dl[3];
   double gamma;
+  float inv_dlf[3];  // 1/dl in FP32 for the FP32-bulk arithmetic
 };
 
 template <typename T> struct Ptr8 {
@@ -411,30 +412,32 @@ __device__ __forceinline__ int slot(int f, int d) {
 // U_out = w U* + w0 U_0 (Eq. 9), and the stage's inverse CFL time (Eq. 10).
 // Arithmetic in FP64 for both variants.
 // ---------------------------------------------------------------------------
-// block-wide max of a non-negative double into *bits (as its bit pattern)
-__device__ __forceinline__ void block_max_to(unsigned long long* bits, double v) {
+// block-wide max of non-negative values, reduced in their own type, into *bits (the bit
+// pattern of the max as a double: non-negative doubles order like their bit patterns)
+template <typename V>
+__device__ __forceinline__ void block_max_to(unsigned long long* bits, V v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  __shared__ double wmax[kThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) v = tmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __shared__ V wmax[kThreads / 32];
   if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double m = wmax[0];
-    for (int w = 1; w < kThreads / 32; ++w) m = fmax(m, wmax[w]);
-    atomicMax(bits, (unsigned long long)__double_as_longlong(m));
+    V m = wmax[0];
+    for (int w = 1; w < kThreads / 32; ++w) m = tmax(m, wmax[w]);
+    atomicMax(bits, (unsigned long long)__double_as_longlong((double)m));
   }
   __syncthreads();  // wmax is reused by the next call of the block
 }
 
-// Returns the cell's inverse CFL contribution (0 outside the grid).
+// Returns the cell's inverse CFL contribution (0 outside the grid), in the bulk type.
 template <typename T, bool COMBINE>
-__device__ __forceinline__ double update_body(const Geo& g, const Ptr8<const double>& Uin,
+__device__ __forceinline__ T update_body(const Geo& g, const Ptr8<const double>& Uin,
                                               const Ptr8<const double>& U0,
                                               const Ptr8<const T>& Fx, const Ptr8<const T>& Fy,
                                               const Ptr8<const T>& Fz, const T* Ex, const T* Ey,
                                               const T* Ez, const Ptr8<double>& Uout, double dt,
                                               int c) {
-  double inv = 0.0;
+  T inv = T(0);
   if (c < g.ncell) {
     int ijk[3];
     coords(g, c, ijk[0], ijk[1], ijk[2]);
@@ -444,7 +447,21 @@ __device__ __forceinline__ double update_body(const Geo& g, const Ptr8<const dou
 #pragma unroll
     for (int d = 0; d < 3; ++d) up[d] = shifted(g, c, ijk[d], d, 1);
     // flux divergence and EMF curl in the bulk type T; the accumulation into the
-    // state (U - dt * div) is FP64 in both variants
+    // state is FP64 in both variants.  FP32 bulk also forms dt * div in FP32 (the
+    // increment only needs FP32 precision) and adds it to the FP64 state.
+    auto idl = [&](int d) -> T {
+      if constexpr (std::is_same<T, double>::value) return g.inv_dl[d];
+      else return g.inv_dlf[d];
+    };
+    const float dtf = (float)dt;
+    auto accumulate = [&](int f, T div) -> double {
+      if constexpr (std::is_same<T, double>::value) {
+        return Uin.f[f][c] - dt * div;
+      } else {
+        if (COMBINE) return fma(0.5, U0.f[f][c] + Uin.f[f][c], (double)(-0.5f * dtf * div));
+        return Uin.f[f][c] + (double)(-dtf * div);
+      }
+    };
     double out[8];
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
@@ -453,30 +470,26 @@ __device__ __forceinline__ double update_body(const Geo& g, const Ptr8<const dou
       for (int d = 0; d < 3; ++d) {
         if (!g.active[d]) continue;
         const int s = slot(f, d);
-        div += (F[d].f[s][up[d]] - F[d].f[s][c]) * T(g.inv_dl[d]);
+        div += (F[d].f[s][up[d]] - F[d].f[s][c]) * idl(d);
       }
-      out[f] = (COMBINE && !std::is_same<T, double>::value)
-                   ? 0.5 * (U0.f[f][c] + Uin.f[f][c]) - (0.5 * dt) * double(div)
-                   : Uin.f[f][c] - dt * double(div);
+      out[f] = accumulate(f, div);
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
       T curl = T(0);
       if (g.active[d]) {
-        if (g.active[t1]) curl += (E[t2][up[t1]] - E[t2][c]) * T(g.inv_dl[t1]);
-        if (g.active[t2]) curl -= (E[t1][up[t2]] - E[t1][c]) * T(g.inv_dl[t2]);
+        if (g.active[t1]) curl += (E[t2][up[t1]] - E[t2][c]) * idl(t1);
+        if (g.active[t2]) curl -= (E[t1][up[t2]] - E[t1][c]) * idl(t2);
       } else {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           if (a == d || !g.active[a]) continue;
           const int s = slot(5 + d, a);
-          curl += (F[a].f[s][up[a]] - F[a].f[s][c]) * T(g.inv_dl[a]);
+          curl += (F[a].f[s][up[a]] - F[a].f[s][c]) * idl(a);
         }
       }
-      out[5 + d] = (COMBINE && !std::is_same<T, double>::value)
-                       ? 0.5 * (U0.f[5 + d][c] + Uin.f[5 + d][c]) - (0.5 * dt) * double(curl)
-                       : Uin.f[5 + d][c] - dt * double(curl);
+      out[5 + d] = accumulate(5 + d, curl);
     }
 #pragma unroll
     for (int f = 0; f < 8; ++f)
@@ -485,8 +498,8 @@ __device__ __forceinline__ double update_body(const Geo& g, const Ptr8<const dou
     T invT = T(0);
 #pragma unroll
     for (int d = 0; d < 3; ++d)
-      if (g.active[d]) invT += tmax(F[d].f[7][c], F[d].f[7][up[d]]) * T(g.inv_dl[d]);
-    inv = double(invT);
+      if (g.active[d]) invT += tmax(F[d].f[7][c], F[d].f[7][up[d]]) * idl(d);
+    inv = invT;
   }
   return inv;
 }
@@ -500,8 +513,7 @@ __global__ void __launch_bounds__(kThreads) k_update(Geo g, Ptr8<const double> U
   const double dt = ctrl->dt;
   if (!(dt > 0.0)) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const double inv =
-      update_body<T, COMBINE>(g, Uin, U0, Fx, Fy, Fz, Ex, Ey, Ez, Uout, dt, c);
+  const T inv = update_body<T, COMBINE>(g, Uin, U0, Fx, Fy, Fz, Ex, Ey, Ez, Uout, dt, c);
   // block max -> one atomic per block (positive doubles order like their bit patterns)
   block_max_to(&ctrl->inv_acc, inv);
 }
@@ -885,6 +897,7 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
   for (int d = 0; d < 3; ++d) {
     g.active[d] = g.n[d] > 1;
     g.inv_dl[d] = (double)g.n[d] / l[d];
+    g.inv_dlf[d] = (float)g.inv_dl[d];
   }
   g.gamma = gamma;
 
@@ -1226,6 +1239,7 @@ extern "C" int idx_step_noalloc(const idx_grid* grid, double gamma, double cfl,
   for (int d = 0; d < 3; ++d) {
     g.active[d] = g.n[d] > 1;
     g.inv_dl[d] = (double)g.n[d] / l[d];
+    g.inv_dlf[d] = (float)g.inv_dl[d];
   }
   g.gamma = gamma;
   const size_t arr = align256(sizeof(double) * (size_t)ncell);
@@ -1362,7 +1376,7 @@ __global__ void __launch_bounds__(kThreads) kb_update(const BatchDev<T>* B) {
     const double dt = I->ctrl->dt;
     if (!(dt > 0.0)) continue;  // uniform over the block: one item per block
     const Geo g = I->g;
-    const double inv = update_body<T, COMBINE>(
+    const T inv = update_body<T, COMBINE>(
         g, dconst(COMBINE ? I->U1 : I->U), dconst(I->U), dconst(I->F[0]), dconst(I->F[1]),
         dconst(I->F[2]), I->E[0], I->E[1], I->E[2], COMBINE ? I->U : I->U1, dt,
         w.begin + threadIdx.x);

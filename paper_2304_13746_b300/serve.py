@@ -188,6 +188,8 @@ class Server:
         bytes_of = {}
         t_first = pending[0].arrival if pending else 0.0
         t_last = t_first
+        phase = {"admit_s": 0.0, "step_s": 0.0, "poll_s": 0.0, "finish_s": 0.0, "idle_s": 0.0,
+                 "chunks": 0}
         while pending or queue or running:
             now = self.clock.now()
             while pending and pending[0].arrival <= now:
@@ -203,12 +205,15 @@ class Server:
                 if self.used + need > self.budget:
                     break
                 queue.popleft()
+                ta = self.clock.now()
                 try:
                     self.backend.start(r)
                 except Exception as e:  # a request that fails to start is reported, not fatal
                     r.status, r.error = "failed", str(e)
                     r.finished = self.clock.now()
+                    phase["admit_s"] += r.finished - ta
                     continue
+                phase["admit_s"] += self.clock.now() - ta
                 r.status, r.admitted = "running", self.clock.now()
                 running[r.rid] = r
                 bytes_of[r.rid] = need
@@ -217,25 +222,35 @@ class Server:
             if running:
                 t0 = self.clock.now()
                 self.backend.step(self.k)
+                t1 = self.clock.now()
                 finished = self.backend.poll()
+                t2 = self.clock.now()
+                phase["step_s"] += t1 - t0
+                phase["poll_s"] += t2 - t1
+                phase["chunks"] += 1
                 if self.chunk_s:
-                    el = max(self.clock.now() - t0, 1e-6)
+                    el = max(t2 - t0, 1e-6)
                     self.k = int(min(64, max(1, round(self.k * self.chunk_s / el))))
                 for rid in finished:
                     r = running.pop(rid)
+                    tf = self.clock.now()
                     try:
                         r.state, r.cycles = self.backend.finish(rid)
                         r.status = "done"
                     except Exception as e:
                         r.status, r.error = "failed", str(e)
                     r.finished = self.clock.now()
+                    phase["finish_s"] += r.finished - tf
                     t_last = max(t_last, r.finished)
                     self.used -= bytes_of.pop(rid)
             elif pending and not queue:
+                ti = self.clock.now()
                 self.clock.sleep_until(pending[0].arrival)
+                phase["idle_s"] += self.clock.now() - ti
         stats = _stats(requests, t_first, t_last)
         stats["peak_bytes"] = self.peak
         stats["budget_bytes"] = self.budget
+        stats["phases"] = phase
         return stats
 
 
