@@ -907,9 +907,21 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
   auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t arr_d = align(sizeof(double) * ncell), arr_t = align(tsz * ncell);
   const size_t bytes = sim_bytes(ncell, f32);
-  if (cudaMalloc(&s->mem, bytes) != cudaSuccess) {
+  if (stream) {
+    s->stream = (cudaStream_t)stream;
+    s->own_stream = false;
+  } else {
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete s;
+      return IDX_ECUDA;
+    }
+    s->own_stream = true;
+  }
+  // stream-ordered allocation: creating and freeing sims does not synchronise the device
+  if (cudaMallocAsync(&s->mem, bytes, s->stream) != cudaSuccess) {
     cudaGetLastError();
-    delete s;
+    s->mem = nullptr;
+    idx_destroy(s);
     return IDX_ENOMEM;
   }
   s->mem_bytes = bytes;
@@ -930,15 +942,6 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
   s->ctrl = (Ctrl*)p;
   int rc = IDX_OK;
   if (cudaMallocHost(&s->host_ctrl, sizeof(Ctrl)) != cudaSuccess) rc = IDX_ENOMEM;
-  if (rc == IDX_OK) {
-    if (stream) {
-      s->stream = (cudaStream_t)stream;
-      s->own_stream = false;
-    } else {
-      if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) rc = IDX_ECUDA;
-      s->own_stream = true;
-    }
-  }
   // clear on the sim's own stream: a non-blocking stream is not ordered after work
   // on the legacy default stream, so a plain cudaMemset could race the first upload
   if (rc == IDX_OK && cudaMemsetAsync(s->mem, 0, bytes, s->stream) != cudaSuccess) rc = IDX_ECUDA;
@@ -956,9 +959,12 @@ void idx_destroy(idx_sim* s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
   if (s->exec) cudaGraphExecDestroy(s->exec);
   if (s->graph) cudaGraphDestroy(s->graph);
-  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   if (s->host_ctrl) cudaFreeHost(s->host_ctrl);
-  if (s->mem) cudaFree(s->mem);
+  if (s->mem) {
+    cudaFreeAsync(s->mem, s->stream);
+    cudaStreamSynchronize(s->stream);
+  }
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   delete s;
 }
 

@@ -77,31 +77,37 @@ class WallClock:
 
 
 class IdxBackend:
-    """libidx: one batch; a request is a sim made, filled and added on admission."""
+    """libidx: one batch on its own stream; every request is a sim on a stream of its own,
+    so its upload and its read-back overlap the batch's running chunk (a finished member
+    is inert in the batch until it is retired at the next chunk boundary)."""
 
     def __init__(self, precision="fp64", cfl=0.4, stream=None):
         from . import idx
         self.idx = idx
         self.precision = precision
         self.cfl = cfl
-        self.stream = stream
         self.batch = idx.Batch(precision, stream=stream)
         self.sims = {}
+        self.ready = []        # uploaded, joining at the next boundary
 
     def footprint(self, req):
         return self.idx.footprint(req.payload.shape, self.precision)
 
     def start(self, req):
         ic = req.payload
-        s = self.idx.Sim(ic.shape, ic.lengths, ic.gamma, self.cfl, self.precision,
-                         stream=self.stream)
+        s = self.idx.Sim(ic.shape, ic.lengths, ic.gamma, self.cfl, self.precision)
         try:
             s.set_primitive(ic.prim)
-            self.batch.add(s, req.t_end)
         except Exception:
             s.close()
             raise
         self.sims[req.rid] = s
+        self.ready.append((req.rid, req.t_end))
+
+    def commit(self):
+        for rid, t_end in self.ready:
+            self.batch.add(self.sims[rid], t_end)
+        self.ready = []
 
     def step(self, ncycles):
         self.batch.step(ncycles)
@@ -112,14 +118,16 @@ class IdxBackend:
         return [ids[id(s)] for s in finished]
 
     def finish(self, rid):
+        """Read a finished member's result back (its own stream; the batch keeps running)."""
+        s = self.sims[rid]
+        return s.get_state(), s.step_count()
+
+    def retire(self, rid):
         s = self.sims.pop(rid)
         try:
             self.batch.remove(s)
-            cycles = s.step_count()
-            state = s.get_state()
         finally:
             s.close()
-        return state, cycles
 
     def close(self):
         for rid in list(self.sims):
@@ -182,19 +190,44 @@ class Server:
         self.peak = 0
 
     def run(self, requests):
+        """Pipelined loop: launch the next chunk of batched cycles, then -- while it runs --
+        read back the members that finished at the last boundary and upload new admissions;
+        at the boundary, retire the read-back members and let the uploaded ones join."""
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         queue = deque()
-        running = {}
+        running = {}       # in the batch (or joining at the next boundary)
         bytes_of = {}
+        to_read = []       # finished at the last boundary, results not read yet
         t_first = pending[0].arrival if pending else 0.0
         t_last = t_first
         phase = {"admit_s": 0.0, "step_s": 0.0, "poll_s": 0.0, "finish_s": 0.0, "idle_s": 0.0,
                  "chunks": 0}
-        while pending or queue or running:
+        commit = getattr(self.backend, "commit", None)
+        retire = getattr(self.backend, "retire", None)
+        while pending or queue or running or to_read:
             now = self.clock.now()
             while pending and pending[0].arrival <= now:
                 queue.append(pending.popleft())
-            # admission, oldest first, while the budget allows
+            in_batch = [rid for rid in running if rid not in to_read]
+            t0 = self.clock.now()
+            stepped = bool(in_batch)
+            if stepped:
+                self.backend.step(self.k)
+            t1 = self.clock.now()
+            phase["step_s"] += t1 - t0
+            # overlapped with the chunk: results of the members finished last time
+            for rid in to_read:
+                r = running.pop(rid)
+                tf = self.clock.now()
+                try:
+                    r.state, r.cycles = self.backend.finish(rid)
+                    r.status = "done"
+                except Exception as e:
+                    r.status, r.error = "failed", str(e)
+                r.finished = self.clock.now()
+                phase["finish_s"] += r.finished - tf
+                t_last = max(t_last, r.finished)
+            # overlapped with the chunk: admissions, oldest first, while the budget allows
             while queue:
                 r = queue[0]
                 need = self.backend.footprint(r)
@@ -219,31 +252,24 @@ class Server:
                 bytes_of[r.rid] = need
                 self.used += need
                 self.peak = max(self.peak, self.used)
-            if running:
-                t0 = self.clock.now()
-                self.backend.step(self.k)
-                t1 = self.clock.now()
-                finished = self.backend.poll()
-                t2 = self.clock.now()
-                phase["step_s"] += t1 - t0
-                phase["poll_s"] += t2 - t1
+            # boundary
+            t2 = self.clock.now()
+            finished = self.backend.poll() if stepped else []
+            t3 = self.clock.now()
+            phase["poll_s"] += t3 - t2
+            if stepped:
                 phase["chunks"] += 1
                 if self.chunk_s:
-                    el = max(t2 - t0, 1e-6)
+                    el = max(t3 - t0, 1e-6)
                     self.k = int(min(64, max(1, round(self.k * self.chunk_s / el))))
-                for rid in finished:
-                    r = running.pop(rid)
-                    tf = self.clock.now()
-                    try:
-                        r.state, r.cycles = self.backend.finish(rid)
-                        r.status = "done"
-                    except Exception as e:
-                        r.status, r.error = "failed", str(e)
-                    r.finished = self.clock.now()
-                    phase["finish_s"] += r.finished - tf
-                    t_last = max(t_last, r.finished)
-                    self.used -= bytes_of.pop(rid)
-            elif pending and not queue:
+            for rid in to_read:
+                if retire:
+                    retire(rid)
+                self.used -= bytes_of.pop(rid)
+            to_read = [rid for rid in finished if rid in running]
+            if commit:
+                commit()
+            if not stepped and not to_read and not running and pending and not queue:
                 ti = self.clock.now()
                 self.clock.sleep_until(pending[0].arrival)
                 phase["idle_s"] += self.clock.now() - ti

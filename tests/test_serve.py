@@ -118,8 +118,10 @@ def test_latency_hand_computed():
     for r in (a, b):
         r.cells = r.n * r.n
     st = serve.Server(be, 10 ** 9, clock, cycles_per_poll=1).run([a, b])
-    # a runs alone for its first cycle (t = 0..1); b joins at t = 1; both then take 2 s per
-    # cycle: a needs 11 more (t = 23); b has 11 by then and its 12th runs alone (t = 24)
+    # pipelined loop: a runs alone for two 1 s cycles (b arrives during the first and joins
+    # at the boundary t = 2); both then take 2 s per cycle, a's 12th cycle ends at t = 22
+    # and its result is read while b's 11th... b runs its last cycle alone (t = 23, 24):
+    # a is read back at t = 23, b finishes at t = 24
     assert a.finished == pytest.approx(23.0) and b.finished == pytest.approx(24.0)
     assert st["p50_s"] == pytest.approx(0.5 * ((23.0 - 0.0) + (24.0 - 0.5)))
 
