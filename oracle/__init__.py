@@ -58,6 +58,9 @@ def lib():
         L.ora_cycle.argtypes = [G, ctypes.c_double, ctypes.c_double, _P8, _D, ctypes.c_double, _D,
                                 ctypes.POINTER(ctypes.c_long)]
         L.ora_count_cycle.argtypes = [G, ctypes.c_double, ctypes.c_double, _P8, ctypes.c_double, _D]
+        L.ora_riemann.argtypes = [ctypes.c_int, _D, _D, ctypes.c_double, ctypes.c_double, _D, _D, _D]
+        L.ora_cycle_solver.argtypes = [G, ctypes.c_double, ctypes.c_double, ctypes.c_int, _P8, _D,
+                                       ctypes.c_double, _D, ctypes.POINTER(ctypes.c_long)]
         L.ora_count_faces.argtypes = [G, ctypes.c_double, _P8, ctypes.c_int, _D, _D]
         L.ora_threads.restype = ctypes.c_int
         _lib = L
@@ -124,6 +127,18 @@ def hlld(wL, wR, bn, gamma):
     return np.array(F[:]), sL.value, sR.value
 
 
+SOLVERS = {"rusanov": 1, "hll": 2, "hlld": 4}
+
+
+def riemann(solver, wL, wR, bn, gamma):
+    """Single interface with solver 'rusanov', 'hll' or 'hlld'; returns (F[7], sL, sR)."""
+    F = (ctypes.c_double * 7)()
+    sL, sR = ctypes.c_double(), ctypes.c_double()
+    _check(lib().ora_riemann(SOLVERS[solver], _arr(wL, 7), _arr(wR, 7), float(bn), float(gamma), F,
+                             ctypes.byref(sL), ctypes.byref(sR)))
+    return np.array(F[:]), sL.value, sR.value
+
+
 def phys_flux(w, bn, gamma):
     F = (ctypes.c_double * 7)()
     _check(lib().ora_phys_flux(_arr(w, 7), float(bn), float(gamma), F))
@@ -161,7 +176,8 @@ def stage(uin, lengths, gamma, dt, u0=None, w=1.0, w0=0.0):
 class Sim:
     """Oracle simulation: state, time, and the inverse CFL time carried between cycles."""
 
-    def __init__(self, cons, lengths, gamma, cfl):
+    def __init__(self, cons, lengths, gamma, cfl, solver="hlld"):
+        self.solver = SOLVERS[solver]
         self.u = [_c(a).copy() for a in cons]
         self.lengths = tuple(float(x) for x in lengths)
         self.gamma = float(gamma)
@@ -171,16 +187,17 @@ class Sim:
         self.inv_dt = speed_pass(self.u, self.lengths, self.gamma)
 
     @classmethod
-    def from_prims(cls, prim, lengths, gamma, cfl):
-        return cls(cons_from_prims(prim, lengths, gamma), lengths, gamma, cfl)
+    def from_prims(cls, prim, lengths, gamma, cfl, solver="hlld"):
+        return cls(cons_from_prims(prim, lengths, gamma), lengths, gamma, cfl, solver)
 
     def step(self, dt_max=math.inf):
         inv = ctypes.c_double(self.inv_dt)
         dt = ctypes.c_double()
         bad = ctypes.c_long(-1)
-        _check(lib().ora_cycle(ctypes.byref(_grid(self.u[0].shape, self.lengths)), self.gamma,
-                               self.cfl, _ptrs(self.u), ctypes.byref(inv), float(dt_max),
-                               ctypes.byref(dt), ctypes.byref(bad)), bad)
+        _check(lib().ora_cycle_solver(ctypes.byref(_grid(self.u[0].shape, self.lengths)),
+                                      self.gamma, self.cfl, self.solver, _ptrs(self.u),
+                                      ctypes.byref(inv), float(dt_max), ctypes.byref(dt),
+                                      ctypes.byref(bad)), bad)
         self.inv_dt = inv.value
         self.nsteps += 1
         return dt.value

@@ -323,6 +323,79 @@ void hlld(const State<R>& L, const State<R>& Rs, R bx, double gamma, R F[7], R* 
 }
 
 // ---------------------------------------------------------------------------
+// The two more diffusive solvers of Sec. 2.3 (the paper orders its solvers from most to
+// least diffusive: Rusanov, HLL, HLLC/HLLD, Roe).
+//   Rusanov (Lax-Friedrichs): F = (F_L + F_R)/2 - (S_max/2)(U_R - U_L),
+//     S_max = max(|u_L| + c_fL, |u_R| + c_fR).
+//   HLL (Harten, Lax, van Leer; Einfeldt et al. 1991): one intermediate state between the
+//     outer speeds S_L, S_R (the same estimates as HLLD):
+//     F = F_L if S_L > 0, F_R if S_R < 0, else
+//     F = (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L).
+// Both report c = max(|S_L|, |S_R|) of the HLLD estimates for the CFL condition, so the
+// time step does not depend on the solver choice.
+// ---------------------------------------------------------------------------
+template <class R>
+void outer_speeds(const State<R>& L, const State<R>& Rs, R bx, double gamma, R* SL, R* SR,
+                  R* cfL, R* cfR) {
+  *cfL = fast_speed(L, bx, gamma);
+  *cfR = fast_speed(Rs, bx, gamma);
+  const R cfmax = rmax(*cfL, *cfR);
+  *SL = rmin(L.u, Rs.u) - cfmax;
+  *SR = rmax(L.u, Rs.u) + cfmax;
+}
+
+template <class R>
+void rusanov(const State<R>& L, const State<R>& Rs, R bx, double gamma, R F[7], R* sL_out,
+             R* sR_out) {
+  R SL, SR, cfL, cfR;
+  outer_speeds(L, Rs, bx, gamma, &SL, &SR, &cfL, &cfR);
+  *sL_out = SL;
+  *sR_out = SR;
+  const R EL = total_energy(L, bx, gamma), ER = total_energy(Rs, bx, gamma);
+  R FL[7], FR[7], UL[7], UR[7];
+  physical_flux(L, bx, EL, FL);
+  physical_flux(Rs, bx, ER, FR);
+  cons_vec(L, EL, UL);
+  cons_vec(Rs, ER, UR);
+  const R smax = rmax(absval(L.u) + cfL, absval(Rs.u) + cfR);
+  for (int q = 0; q < 7; ++q) F[q] = R(0.5) * (FL[q] + FR[q]) - R(0.5) * smax * (UR[q] - UL[q]);
+}
+
+template <class R>
+void hll(const State<R>& L, const State<R>& Rs, R bx, double gamma, R F[7], R* sL_out,
+         R* sR_out) {
+  R SL, SR, cfL, cfR;
+  outer_speeds(L, Rs, bx, gamma, &SL, &SR, &cfL, &cfR);
+  *sL_out = SL;
+  *sR_out = SR;
+  const R EL = total_energy(L, bx, gamma), ER = total_energy(Rs, bx, gamma);
+  R FL[7], FR[7], UL[7], UR[7];
+  physical_flux(L, bx, EL, FL);
+  physical_flux(Rs, bx, ER, FR);
+  if (SL > R(0.0)) {
+    for (int q = 0; q < 7; ++q) F[q] = FL[q];
+    return;
+  }
+  if (SR < R(0.0)) {
+    for (int q = 0; q < 7; ++q) F[q] = FR[q];
+    return;
+  }
+  cons_vec(L, EL, UL);
+  cons_vec(Rs, ER, UR);
+  for (int q = 0; q < 7; ++q)
+    F[q] = (SR * FL[q] - SL * FR[q] + SL * SR * (UR[q] - UL[q])) / (SR - SL);
+}
+
+// Riemann solver selected by code: 1 Rusanov, 2 HLL, 4 HLLD.
+template <class R>
+void riemann(int solver, const State<R>& L, const State<R>& Rs, R bx, double gamma, R F[7],
+             R* sL, R* sR) {
+  if (solver == 1) rusanov(L, Rs, bx, gamma, F, sL, sR);
+  else if (solver == 2) hll(L, Rs, bx, gamma, F, sL, sR);
+  else hlld(L, Rs, bx, gamma, F, sL, sR);
+}
+
+// ---------------------------------------------------------------------------
 // E^c edge EMF (Gardiner & Stone 2005), default scheme of Sec. 2.4.
 // Generic edge along e with first direction a and second direction b.
 // The derivative of the EMF along b, taken on an a-face, is upwinded in a by the
@@ -398,7 +471,7 @@ void face_state(const Grid& G, const std::vector<R>* W, int i, int j, int k, int
 
 template <class R>
 void face_fluxes(const Grid& G, double gamma, const std::vector<R>* U, const std::vector<R>* W,
-                 int d, std::vector<R>* F /*8*/, std::vector<R>& cface) {
+                 int d, std::vector<R>* F /*8*/, std::vector<R>& cface, int solver) {
   const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
 #pragma omp parallel for if (kPar<R>)
   for (int k = 0; k < G.n[2]; ++k)
@@ -410,7 +483,7 @@ void face_fluxes(const Grid& G, double gamma, const std::vector<R>* U, const std
         face_state(G, W, i, j, k, d, +1, &Rr);
         const R bn = U[5 + d][p];
         R f[7], sL, sR;
-        hlld(L, Rr, bn, gamma, f, &sL, &sR);
+        riemann(solver, L, Rr, bn, gamma, f, &sL, &sR);
         F[RHO][p] = f[0];
         F[1 + d][p] = f[1];
         F[1 + t1][p] = f[2];
@@ -504,7 +577,7 @@ void edge_emf(const Grid& G, const std::vector<R>* W, const std::vector<R>* F /*
 // ---------------------------------------------------------------------------
 template <class R>
 int stage(const Grid& G, double gamma, R dt, const std::vector<R>* Uin, const std::vector<R>* U0,
-          double w, double w0, std::vector<R>* Uout, R* inv_dt, long* bad) {
+          double w, double w0, std::vector<R>* Uout, R* inv_dt, long* bad, int solver = 4) {
   const long N = G.ncell;
   std::vector<R> W[8];
   for (int f = 0; f < 8; ++f) W[f].assign(N, R(0.0));
@@ -516,7 +589,7 @@ int stage(const Grid& G, double gamma, R dt, const std::vector<R>* Uin, const st
   for (int q = 0; q < 24; ++q) F[q].assign(N, R(0.0));
   for (int d = 0; d < 3; ++d) {
     cface[d].assign(N, R(0.0));
-    if (G.active[d]) face_fluxes(G, gamma, Uin, W, d, &F[8 * d], cface[d]);
+    if (G.active[d]) face_fluxes(G, gamma, Uin, W, d, &F[8 * d], cface[d], solver);
   }
   *inv_dt = inverse_dt(G, cface);
 
@@ -579,16 +652,16 @@ int stage(const Grid& G, double gamma, R dt, const std::vector<R>* Uin, const st
 // One RK2 cycle (Table 1: w1 = 1, w0_1 = 0; w2 = 1/2, w0_2 = 1/2), same dt for both stages.
 template <class R>
 int cycle(const Grid& G, double gamma, double cfl, std::vector<R>* U, R* inv_dt, double dt_max,
-          R* dt_taken, long* bad) {
+          R* dt_taken, long* bad, int solver = 4) {
   R dt = R(cfl) / *inv_dt;
   if (value(dt) > dt_max) dt = R(dt_max);
   const long N = G.ncell;
   std::vector<R> U1[8], U2[8];
   for (int f = 0; f < 8; ++f) { U1[f].assign(N, R(0.0)); U2[f].assign(N, R(0.0)); }
   R inv1, inv2;
-  int st = stage(G, gamma, dt, U, (const std::vector<R>*)nullptr, 1.0, 0.0, U1, &inv1, bad);
+  int st = stage(G, gamma, dt, U, (const std::vector<R>*)nullptr, 1.0, 0.0, U1, &inv1, bad, solver);
   if (st != ORA_OK) return st;
-  st = stage(G, gamma, dt, U1, U, 0.5, 0.5, U2, &inv2, bad);
+  st = stage(G, gamma, dt, U1, U, 0.5, 0.5, U2, &inv2, bad, solver);
   if (st != ORA_OK) return st;
   for (int f = 0; f < 8; ++f) U[f] = U2[f];
   *inv_dt = rmax(inv1, inv2);
@@ -734,6 +807,35 @@ int ora_cycle(const ora_grid* g, double gamma, double cfl, double* const u[8], d
   load(G, (const double* const*)u, U);
   double inv = *inv_dt, dt = 0.0;
   const int st = cycle(G, gamma, cfl, U, &inv, dt_max, &dt, bad_cell);
+  if (st != ORA_OK) return st;
+  store(G, U, u);
+  *inv_dt = inv;
+  if (dt_taken) *dt_taken = dt;
+  return ORA_OK;
+}
+
+int ora_riemann(int solver, const double wL[7], const double wR[7], double bn, double gamma,
+                double F[7], double* sL, double* sR) {
+  if (!wL || !wR || !F || !sL || !sR || !(gamma > 1.0)) return ORA_EINVAL;
+  if (solver != 1 && solver != 2 && solver != 4) return ORA_EINVAL;
+  State<double> L{wL[0], wL[1], wL[2], wL[3], wL[4], wL[5], wL[6]};
+  State<double> R{wR[0], wR[1], wR[2], wR[3], wR[4], wR[5], wR[6]};
+  if (!(L.rho > 0) || !(R.rho > 0) || !(L.P > 0) || !(R.P > 0)) return ORA_ENONPHYS;
+  riemann(solver, L, R, bn, gamma, F, sL, sR);
+  return ORA_OK;
+}
+
+int ora_cycle_solver(const ora_grid* g, double gamma, double cfl, int solver, double* const u[8],
+                     double* inv_dt, double dt_max, double* dt_taken, long* bad_cell) {
+  if (!grid_ok(g) || !(gamma > 1.0) || !(cfl > 0.0 && cfl < 1.0) ||
+      !ptrs_ok((const void* const*)u) || !inv_dt || !(*inv_dt > 0.0) || !(dt_max >= 0.0))
+    return ORA_EINVAL;
+  if (solver != 1 && solver != 2 && solver != 4) return ORA_EINVAL;
+  const Grid G = make_grid(g);
+  std::vector<double> U[8];
+  load(G, (const double* const*)u, U);
+  double inv = *inv_dt, dt = 0.0;
+  const int st = cycle(G, gamma, cfl, U, &inv, dt_max, &dt, bad_cell, solver);
   if (st != ORA_OK) return st;
   store(G, U, u);
   *inv_dt = inv;

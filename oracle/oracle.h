@@ -57,6 +57,16 @@ double ora_vanleer(double wm, double w0, double wp);
 int ora_hlld(const double wL[7], const double wR[7], double bn, double gamma, double F[7],
              double* sL, double* sR);
 
+/* Any of the Riemann solvers of Sec. 2.3 that the build covers: solver 1 Rusanov
+ * (Lax-Friedrichs), 2 HLL, 4 HLLD; same arguments as ora_hlld.  All three report the
+ * HLLD outer speed estimates in sL, sR (the CFL condition does not depend on the solver). */
+int ora_riemann(int solver, const double wL[7], const double wR[7], double bn, double gamma,
+                double F[7], double* sL, double* sR);
+
+/* ora_cycle with a chosen Riemann solver (1, 2 or 4). */
+int ora_cycle_solver(const ora_grid* g, double gamma, double cfl, int solver, double* const u[8],
+                     double* inv_dt, double dt_max, double* dt_taken, long* bad_cell);
+
 /* Ideal-MHD physical flux along "x" of one state (same ordering as ora_hlld). */
 int ora_phys_flux(const double w[7], double bn, double gamma, double F[7]);
 
