@@ -61,6 +61,8 @@ def lib():
         L.ora_riemann.argtypes = [ctypes.c_int, _D, _D, ctypes.c_double, ctypes.c_double, _D, _D, _D]
         L.ora_cycle_solver.argtypes = [G, ctypes.c_double, ctypes.c_double, ctypes.c_int, _P8, _D,
                                        ctypes.c_double, _D, ctypes.POINTER(ctypes.c_long)]
+        L.ora_cycle_rk.argtypes = [G, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                   _P8, _D, ctypes.c_double, _D, ctypes.POINTER(ctypes.c_long)]
         L.ora_count_faces.argtypes = [G, ctypes.c_double, _P8, ctypes.c_int, _D, _D]
         L.ora_threads.restype = ctypes.c_int
         _lib = L
@@ -176,8 +178,9 @@ def stage(uin, lengths, gamma, dt, u0=None, w=1.0, w0=0.0):
 class Sim:
     """Oracle simulation: state, time, and the inverse CFL time carried between cycles."""
 
-    def __init__(self, cons, lengths, gamma, cfl, solver="hlld"):
+    def __init__(self, cons, lengths, gamma, cfl, solver="hlld", rk_order=2):
         self.solver = SOLVERS[solver]
+        self.rk_order = int(rk_order)
         self.u = [_c(a).copy() for a in cons]
         self.lengths = tuple(float(x) for x in lengths)
         self.gamma = float(gamma)
@@ -187,17 +190,17 @@ class Sim:
         self.inv_dt = speed_pass(self.u, self.lengths, self.gamma)
 
     @classmethod
-    def from_prims(cls, prim, lengths, gamma, cfl, solver="hlld"):
-        return cls(cons_from_prims(prim, lengths, gamma), lengths, gamma, cfl, solver)
+    def from_prims(cls, prim, lengths, gamma, cfl, solver="hlld", rk_order=2):
+        return cls(cons_from_prims(prim, lengths, gamma), lengths, gamma, cfl, solver, rk_order)
 
     def step(self, dt_max=math.inf):
         inv = ctypes.c_double(self.inv_dt)
         dt = ctypes.c_double()
         bad = ctypes.c_long(-1)
-        _check(lib().ora_cycle_solver(ctypes.byref(_grid(self.u[0].shape, self.lengths)),
-                                      self.gamma, self.cfl, self.solver, _ptrs(self.u),
-                                      ctypes.byref(inv), float(dt_max), ctypes.byref(dt),
-                                      ctypes.byref(bad)), bad)
+        _check(lib().ora_cycle_rk(ctypes.byref(_grid(self.u[0].shape, self.lengths)),
+                                  self.gamma, self.cfl, self.solver, self.rk_order, _ptrs(self.u),
+                                  ctypes.byref(inv), float(dt_max), ctypes.byref(dt),
+                                  ctypes.byref(bad)), bad)
         self.inv_dt = inv.value
         self.nsteps += 1
         return dt.value

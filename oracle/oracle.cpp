@@ -649,22 +649,35 @@ int stage(const Grid& G, double gamma, R dt, const std::vector<R>* Uin, const st
   return ORA_OK;
 }
 
-// One RK2 cycle (Table 1: w1 = 1, w0_1 = 0; w2 = 1/2, w0_2 = 1/2), same dt for both stages.
+// One RK cycle of Sec. 2.7, same dt for every stage, stage s: U_s = w_s S_dt(U_{s-1}) +
+// w0_s U_0 with the weights of Table 1 -- RK2: (1, 0), (1/2, 1/2); RK3: (1, 0),
+// (1/4, 3/4), (2/3, 1/3).  The next dt comes from the largest inverse CFL time of the
+// cycle's stages.
 template <class R>
 int cycle(const Grid& G, double gamma, double cfl, std::vector<R>* U, R* inv_dt, double dt_max,
-          R* dt_taken, long* bad, int solver = 4) {
+          R* dt_taken, long* bad, int solver = 4, int rk_order = 2) {
   R dt = R(cfl) / *inv_dt;
   if (value(dt) > dt_max) dt = R(dt_max);
   const long N = G.ncell;
-  std::vector<R> U1[8], U2[8];
-  for (int f = 0; f < 8; ++f) { U1[f].assign(N, R(0.0)); U2[f].assign(N, R(0.0)); }
-  R inv1, inv2;
-  int st = stage(G, gamma, dt, U, (const std::vector<R>*)nullptr, 1.0, 0.0, U1, &inv1, bad, solver);
-  if (st != ORA_OK) return st;
-  st = stage(G, gamma, dt, U1, U, 0.5, 0.5, U2, &inv2, bad, solver);
-  if (st != ORA_OK) return st;
-  for (int f = 0; f < 8; ++f) U[f] = U2[f];
-  *inv_dt = rmax(inv1, inv2);
+  const double w_rk2[2][2] = {{1.0, 0.0}, {0.5, 0.5}};
+  const double w_rk3[3][2] = {{1.0, 0.0}, {0.25, 0.75}, {2.0 / 3.0, 1.0 / 3.0}};
+  const int nst = rk_order == 3 ? 3 : 2;
+  std::vector<R> prev[8], next[8];
+  for (int f = 0; f < 8; ++f) prev[f] = U[f];
+  R inv = R(0.0);
+  for (int st = 0; st < nst; ++st) {
+    const double w = rk_order == 3 ? w_rk3[st][0] : w_rk2[st][0];
+    const double w0 = rk_order == 3 ? w_rk3[st][1] : w_rk2[st][1];
+    for (int f = 0; f < 8; ++f) next[f].assign(N, R(0.0));
+    R inv_s;
+    const int rc = stage(G, gamma, dt, prev, st == 0 ? (const std::vector<R>*)nullptr : U, w, w0,
+                         next, &inv_s, bad, solver);
+    if (rc != ORA_OK) return rc;
+    inv = rmax(inv, inv_s);
+    for (int f = 0; f < 8; ++f) prev[f].swap(next[f]);
+  }
+  for (int f = 0; f < 8; ++f) U[f] = prev[f];
+  *inv_dt = inv;
   *dt_taken = dt;
   return ORA_OK;
 }
@@ -822,6 +835,26 @@ int ora_riemann(int solver, const double wL[7], const double wR[7], double bn, d
   State<double> R{wR[0], wR[1], wR[2], wR[3], wR[4], wR[5], wR[6]};
   if (!(L.rho > 0) || !(R.rho > 0) || !(L.P > 0) || !(R.P > 0)) return ORA_ENONPHYS;
   riemann(solver, L, R, bn, gamma, F, sL, sR);
+  return ORA_OK;
+}
+
+int ora_cycle_rk(const ora_grid* g, double gamma, double cfl, int solver, int rk_order,
+                 double* const u[8], double* inv_dt, double dt_max, double* dt_taken,
+                 long* bad_cell) {
+  if (!grid_ok(g) || !(gamma > 1.0) || !(cfl > 0.0 && cfl < 1.0) ||
+      !ptrs_ok((const void* const*)u) || !inv_dt || !(*inv_dt > 0.0) || !(dt_max >= 0.0))
+    return ORA_EINVAL;
+  if ((solver != 1 && solver != 2 && solver != 4) || (rk_order != 2 && rk_order != 3))
+    return ORA_EINVAL;
+  const Grid G = make_grid(g);
+  std::vector<double> U[8];
+  load(G, (const double* const*)u, U);
+  double inv = *inv_dt, dt = 0.0;
+  const int st = cycle(G, gamma, cfl, U, &inv, dt_max, &dt, bad_cell, solver, rk_order);
+  if (st != ORA_OK) return st;
+  store(G, U, u);
+  *inv_dt = inv;
+  if (dt_taken) *dt_taken = dt;
   return ORA_OK;
 }
 

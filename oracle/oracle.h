@@ -67,6 +67,11 @@ int ora_riemann(int solver, const double wL[7], const double wR[7], double bn, d
 int ora_cycle_solver(const ora_grid* g, double gamma, double cfl, int solver, double* const u[8],
                      double* inv_dt, double dt_max, double* dt_taken, long* bad_cell);
 
+/* One cycle with a chosen solver (1, 2, 4) and RK order (2 or 3, Table 1). */
+int ora_cycle_rk(const ora_grid* g, double gamma, double cfl, int solver, int rk_order,
+                 double* const u[8], double* inv_dt, double dt_max, double* dt_taken,
+                 long* bad_cell);
+
 /* Ideal-MHD physical flux along "x" of one state (same ordering as ora_hlld). */
 int ora_phys_flux(const double w[7], double bn, double gamma, double F[7]);
 

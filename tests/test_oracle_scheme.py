@@ -272,3 +272,24 @@ def test_speed_pass_brute_force_from_single_interfaces():
                     cface[d, k, j, i] = max(abs(sL), abs(sR))
     inv = sum(np.maximum(cface[d], np.roll(cface[d], -1, axis[d])) / dl[d] for d in range(3))
     assert oracle.speed_pass(cons, lengths, ic.gamma) == pytest.approx(float(inv.max()), rel=1e-14)
+
+
+def test_rk3_temporal_order():
+    # Table 1 RK3 weights (1, 0), (1/4, 3/4), (2/3, 1/3): third order in time.  Measured on
+    # a linear wave where the van Leer switching at extrema stays below the temporal error
+    # (on richer flows that switching floors the temporal error near 1e-4).
+    ic = inputs.linear_wave_1d(32, "fast", eps=1e-2)
+
+    def run(cfl, rk):
+        sim = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, cfl, rk_order=rk)
+        sim.advance(0.25)
+        return sim.u
+
+    slopes = {}
+    for rk in (2, 3):
+        ref = run(0.025, rk)
+        e = [max(float(np.max(np.abs(u[f] - ref[f]))) for f in range(8))
+             for u in (run(c, rk) for c in (0.8, 0.4, 0.2))]
+        slopes[rk] = (math.log2(e[0] / e[1]), math.log2(e[1] / e[2]))
+    assert min(slopes[2]) > 1.8 and max(slopes[2]) < 3.4, slopes
+    assert slopes[3][1] > 2.7 and sum(slopes[3]) / 2 > 2.7, slopes
