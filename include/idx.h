@@ -58,9 +58,10 @@ typedef enum {
 
 typedef struct {
   int recon;       /* 1 = PLM with the van Leer limiter (Sec. 2.3); the only value accepted */
-  int riemann;     /* 4 = HLLD (Sec. 2.3); the only value accepted                         */
+  int riemann;     /* Riemann solver (Sec. 2.3): 4 = HLLD, 2 = HLL, 1 = Rusanov (Lax-
+                      Friedrichs).  All use the HLLD outer speed estimates for the CFL dt. */
   int emf;         /* 2 = E^c (Sec. 2.4); the only value accepted                          */
-  int rk_order;    /* 2 = RK2 (Table 1); the only value accepted                           */
+  int rk_order;    /* 2 = RK2 or 3 = RK3 (Table 1; RK3 adds a 64 B/cell state buffer)   */
   double cfl;      /* sigma of Eq. (10), 0 < cfl < 1                                       */
   int precision;   /* idx_precision                                                         */
 } idx_solver;
@@ -102,8 +103,9 @@ int idx_time(const idx_sim* sim, double* t, double* next_dt);
 /* RK2 cycles taken since the last idx_set_state / idx_set_primitive.  Synchronises. */
 int idx_step_count(const idx_sim* sim, int64_t* nsteps);
 
-/* Device bytes idx_create allocates for this grid and precision (FP64 408 B per cell,
- * FP32 bulk 268 B per cell, plus alignment); no device call.  For admission control. */
+/* Device bytes idx_create allocates for this grid and precision with RK2 (FP64 408 B per
+ * cell, FP32 bulk 268 B per cell, plus alignment; RK3 adds 64 B per cell); no device
+ * call.  For admission control. */
 int idx_footprint(const idx_grid* grid, int precision, uint64_t* bytes);
 
 /* Flat index k*ny*nx + j*nx + i of the first (lowest-index) cell found non-physical by
@@ -146,7 +148,7 @@ int idx_pipe_rates(double rates[6]);
  * the same result, to rounding, alone and in a batch.  The work-list is read at run time, so
  * sims join and leave between steps without re-capturing the batch's CUDA graph.  The
  * sweep shapes are autotuned on the batch when its membership first changes.
- * Members must share the batch's precision and device; a member must not be stepped by
+ * Members must share the batch's precision and device and use RK2; a member must not be stepped by
  * idx_step/idx_advance, nor read with idx_get_state/idx_time, until idx_batch_poll or
  * idx_batch_remove has synchronised the batch. */
 typedef struct idx_batch idx_batch; /* opaque */

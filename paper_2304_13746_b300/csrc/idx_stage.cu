@@ -67,6 +67,7 @@ struct Geo {
   double inv_dl[3];
   double gamma;
   float inv_dlf[3];  // 1/dl in FP32 for the FP32-bulk arithmetic
+  int riemann;       // 1 Rusanov, 2 HLL, 4 HLLD
 };
 
 template <typename T> struct Ptr8 {
@@ -248,7 +249,7 @@ __device__ __forceinline__ void sweep_body(const Geo& g, const Ptr8<const T>& W,
     L.b2 = wm[6] + T(0.5) * slope_m[6]; R.b2 = w0[6] - T(0.5) * slope0[6];
     const T bn = T(bface[cf]);
     T flux[7], cmax;
-    hlld(L, R, bn, gamma, gm1inv, flux, cmax);
+    riemann_flux(g.riemann, L, R, bn, gamma, gm1inv, flux, cmax);
 #pragma unroll
     for (int q = 0; q < 7; ++q) F.f[q][cf] = flux[q];
     F.f[7][cf] = cmax;
@@ -335,7 +336,7 @@ __device__ __forceinline__ void sweep_x_body(const Geo& g, const Ptr8<const T>& 
   L.r = Lq[0]; L.u = Lq[1]; L.v = Lq[2]; L.w = Lq[3]; L.p = Lq[4]; L.b1 = Lq[5]; L.b2 = Lq[6];
   R.r = Rq[0]; R.u = Rq[1]; R.v = Rq[2]; R.w = Rq[3]; R.p = Rq[4]; R.b1 = Rq[5]; R.b2 = Rq[6];
   T flux[7], cmax;
-  hlld(L, R, T(bface[c]), gamma, gm1inv, flux, cmax);
+  riemann_flux(g.riemann, L, R, T(bface[c]), gamma, gm1inv, flux, cmax);
 #pragma unroll
   for (int q = 0; q < 7; ++q) F.f[q][c] = flux[q];
   F.f[7][c] = cmax;
@@ -436,7 +437,7 @@ __device__ __forceinline__ T update_body(const Geo& g, const Ptr8<const double>&
                                               const Ptr8<const T>& Fx, const Ptr8<const T>& Fy,
                                               const Ptr8<const T>& Fz, const T* Ex, const T* Ey,
                                               const T* Ez, const Ptr8<double>& Uout, double dt,
-                                              int c) {
+                                              int c, double w = 0.5, double w0 = 0.5) {
   T inv = T(0);
   if (c < g.ncell) {
     int ijk[3];
@@ -458,7 +459,11 @@ __device__ __forceinline__ T update_body(const Geo& g, const Ptr8<const double>&
       if constexpr (std::is_same<T, double>::value) {
         return Uin.f[f][c] - dt * div;
       } else {
-        if (COMBINE) return fma(0.5, U0.f[f][c] + Uin.f[f][c], (double)(-0.5f * dtf * div));
+        if (COMBINE) {
+          const float wdt = (float)(w * dt);
+          if (w == w0) return fma(w, U0.f[f][c] + Uin.f[f][c], (double)(-wdt * div));
+          return fma(w0, U0.f[f][c], w * Uin.f[f][c]) + (double)(-wdt * div);
+        }
         return Uin.f[f][c] + (double)(-dtf * div);
       }
     };
@@ -493,7 +498,7 @@ __device__ __forceinline__ T update_body(const Geo& g, const Ptr8<const double>&
     }
 #pragma unroll
     for (int f = 0; f < 8; ++f)
-      Uout.f[f][c] = (COMBINE && std::is_same<T, double>::value) ? fma(0.5, out[f], 0.5 * U0.f[f][c])
+      Uout.f[f][c] = (COMBINE && std::is_same<T, double>::value) ? fma(w, out[f], w0 * U0.f[f][c])
                                                                  : out[f];
     T invT = T(0);
 #pragma unroll
@@ -509,11 +514,12 @@ __global__ void __launch_bounds__(kThreads) k_update(Geo g, Ptr8<const double> U
                                                      Ptr8<const double> U0, Ptr8<const T> Fx,
                                                      Ptr8<const T> Fy, Ptr8<const T> Fz,
                                                      const T* Ex, const T* Ey, const T* Ez,
-                                                     Ptr8<double> Uout, Ctrl* ctrl) {
+                                                     Ptr8<double> Uout, Ctrl* ctrl, double w,
+                                                     double w0) {
   const double dt = ctrl->dt;
   if (!(dt > 0.0)) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const T inv = update_body<T, COMBINE>(g, Uin, U0, Fx, Fy, Fz, Ex, Ey, Ez, Uout, dt, c);
+  const T inv = update_body<T, COMBINE>(g, Uin, U0, Fx, Fy, Fz, Ex, Ey, Ez, Uout, dt, c, w, w0);
   // block max -> one atomic per block (positive doubles order like their bit patterns)
   block_max_to(&ctrl->inv_acc, inv);
 }
@@ -600,6 +606,7 @@ struct idx_sim {
   void* mem;            // single device allocation
   size_t mem_bytes;
   Ptr8<double> U, U1;   // state and first-stage result (FP64)
+  Ptr8<double> U2;      // second-stage result of RK3 (FP64)
   Ptr8<double> Wd, Fd[3];
   Ptr8<float> Wf, Ff[3];
   double* Ed[3];
@@ -721,29 +728,64 @@ void launch_fluxes(idx_sim* s, const Ptr8<double>& Uin, const Ptr8<T>& W, Ptr8<T
     if (g.active[d]) launch_sweep<T>(s, d, W, Uin.f[5 + d], F[d], check_dt);
 }
 
+// The stages of one cycle (Sec. 2.7, Table 1): input, output and weights (w, w0) of
+// U_s = w S_dt(U_{s-1}) + w0 U_0.  RK2: U -> U1 -> U; RK3: U -> U1 -> U2 -> U.
+struct StagePlan {
+  int n;
+  const Ptr8<double>* in[3];
+  const Ptr8<double>* out[3];
+  double w[3], w0[3];
+};
+
+StagePlan stage_plan(const idx_sim* s) {
+  StagePlan p;
+  if (s->solver.rk_order == 3) {
+    p.n = 3;
+    p.in[0] = &s->U; p.out[0] = &s->U1; p.w[0] = 1.0; p.w0[0] = 0.0;
+    p.in[1] = &s->U1; p.out[1] = &s->U2; p.w[1] = 0.25; p.w0[1] = 0.75;
+    p.in[2] = &s->U2; p.out[2] = &s->U; p.w[2] = 2.0 / 3.0; p.w0[2] = 1.0 / 3.0;
+  } else {
+    p.n = 2;
+    p.in[0] = &s->U; p.out[0] = &s->U1; p.w[0] = 1.0; p.w0[0] = 0.0;
+    p.in[1] = &s->U1; p.out[1] = &s->U; p.w[1] = 0.5; p.w0[1] = 0.5;
+    p.in[2] = p.out[2] = nullptr; p.w[2] = p.w0[2] = 0.0;
+  }
+  return p;
+}
+
+template <typename T>
+void launch_update(idx_sim* s, const Ptr8<double>& Uin, const Ptr8<double>& Uout, bool combine,
+                   double w, double w0, Ptr8<T>* F, T** E) {
+  const Geo& g = s->geo;
+  if (combine)
+    k_update<T, true><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
+        g, cst(Uin), cst(s->U), cst(F[0]), cst(F[1]), cst(F[2]), E[0], E[1], E[2], Uout, s->ctrl,
+        w, w0);
+  else
+    k_update<T, false><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
+        g, cst(Uin), cst(s->U), cst(F[0]), cst(F[1]), cst(F[2]), E[0], E[1], E[2], Uout, s->ctrl,
+        w, w0);
+}
+
 template <typename T>
 void launch_stage(idx_sim* s, const Ptr8<double>& Uin, const Ptr8<double>& Uout, bool combine,
-                  const Ptr8<T>& W, Ptr8<T>* F, T** E) {
+                  double w, double w0, const Ptr8<T>& W, Ptr8<T>* F, T** E) {
   const Geo& g = s->geo;
   launch_fluxes<T>(s, Uin, W, F, 1);
   k_emf<T><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(W), cst(F[0]), cst(F[1]),
                                                             cst(F[2]), E[0], E[1], E[2], s->ctrl);
-  if (combine)
-    k_update<T, true><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
-        g, cst(Uin), cst(s->U), cst(F[0]), cst(F[1]), cst(F[2]), E[0], E[1], E[2], Uout, s->ctrl);
-  else
-    k_update<T, false><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
-        g, cst(Uin), cst(s->U), cst(F[0]), cst(F[1]), cst(F[2]), E[0], E[1], E[2], Uout, s->ctrl);
+  launch_update<T>(s, Uin, Uout, combine, w, w0, F, E);
 }
 
 void launch_cycle(idx_sim* s) {
   k_begin<<<1, 1, 0, s->stream>>>(s->ctrl);
-  if (s->solver.precision == IDX_FP32_BULK) {
-    launch_stage<float>(s, s->U, s->U1, false, s->Wf, s->Ff, s->Ef);
-    launch_stage<float>(s, s->U1, s->U, true, s->Wf, s->Ff, s->Ef);
-  } else {
-    launch_stage<double>(s, s->U, s->U1, false, s->Wd, s->Fd, s->Ed);
-    launch_stage<double>(s, s->U1, s->U, true, s->Wd, s->Fd, s->Ed);
+  const StagePlan p = stage_plan(s);
+  for (int st = 0; st < p.n; ++st) {
+    if (s->solver.precision == IDX_FP32_BULK)
+      launch_stage<float>(s, *p.in[st], *p.out[st], st > 0, p.w[st], p.w0[st], s->Wf, s->Ff, s->Ef);
+    else
+      launch_stage<double>(s, *p.in[st], *p.out[st], st > 0, p.w[st], p.w0[st], s->Wd, s->Fd,
+                           s->Ed);
   }
   k_end<<<1, 1, 0, s->stream>>>(s->ctrl);
 }
@@ -841,16 +883,17 @@ int after_new_state(idx_sim* s) {
   return pending_error(s);
 }
 
-// Device bytes of one sim (the single allocation of idx_create).
-size_t sim_bytes(long long ncell, bool f32) {
+// Device bytes of one sim (the single allocation of idx_create); RK3 adds a state.
+size_t sim_bytes(long long ncell, bool f32, bool rk3 = false) {
   auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t arr_d = align(sizeof(double) * ncell);
   const size_t arr_t = align((f32 ? sizeof(float) : sizeof(double)) * ncell);
-  return 16 * arr_d + (8 + 24 + 3) * arr_t + align(sizeof(Ctrl));
+  return (rk3 ? 24 : 16) * arr_d + (8 + 24 + 3) * arr_t + align(sizeof(Ctrl));
 }
 
 bool valid_solver(const idx_solver* v) {
-  return v && v->recon == 1 && v->riemann == 4 && v->emf == 2 && v->rk_order == 2 &&
+  return v && v->recon == 1 && (v->riemann == 1 || v->riemann == 2 || v->riemann == 4) &&
+         v->emf == 2 && (v->rk_order == 2 || v->rk_order == 3) &&
          v->cfl > 0.0 && v->cfl < 1.0 &&
          (v->precision == IDX_FP64 || v->precision == IDX_FP32_BULK);
 }
@@ -900,13 +943,15 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
     g.inv_dlf[d] = (float)g.inv_dl[d];
   }
   g.gamma = gamma;
+  g.riemann = solver->riemann;
 
   // memory plan: U, U1 (16 doubles/cell) + W, F (3 x 8), E (3) in the bulk type
   const bool f32 = solver->precision == IDX_FP32_BULK;
   const size_t tsz = f32 ? sizeof(float) : sizeof(double);
   auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t arr_d = align(sizeof(double) * ncell), arr_t = align(tsz * ncell);
-  const size_t bytes = sim_bytes(ncell, f32);
+  const bool rk3 = solver->rk_order == 3;
+  const size_t bytes = sim_bytes(ncell, f32, rk3);
   if (stream) {
     s->stream = (cudaStream_t)stream;
     s->own_stream = false;
@@ -928,6 +973,8 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
   char* p = (char*)s->mem;
   for (int f = 0; f < 8; ++f) { s->U.f[f] = (double*)p; p += arr_d; }
   for (int f = 0; f < 8; ++f) { s->U1.f[f] = (double*)p; p += arr_d; }
+  if (rk3)
+    for (int f = 0; f < 8; ++f) { s->U2.f[f] = (double*)p; p += arr_d; }
   if (f32) {
     for (int f = 0; f < 8; ++f) { s->Wf.f[f] = (float*)p; p += arr_t; }
     for (int d = 0; d < 3; ++d)
@@ -1089,9 +1136,10 @@ int idx_kernel_times(idx_sim* s, int reps, double ms[6]) {
   const bool f32 = s->solver.precision == IDX_FP32_BULK;
   for (int r = 0; r < reps; ++r) {
     k_begin<<<1, 1, 0, s->stream>>>(s->ctrl);
-    for (int st = 0; st < 2; ++st) {
-      const Ptr8<double>& Uin = st == 0 ? s->U : s->U1;
-      const Ptr8<double>& Uout = st == 0 ? s->U1 : s->U;
+    const StagePlan plan = stage_plan(s);
+    for (int st = 0; st < plan.n; ++st) {
+      const Ptr8<double>& Uin = *plan.in[st];
+      const Ptr8<double>& Uout = *plan.out[st];
       IDX_TRY(cudaEventRecord(ev[0], s->stream));
       if (f32) {
         k_prims<float><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), s->Wf, s->ctrl, 1);
@@ -1112,13 +1160,8 @@ int idx_kernel_times(idx_sim* s, int reps, double ms[6]) {
         k_emf<double><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(s->Wd), cst(s->Fd[0]), cst(s->Fd[1]), cst(s->Fd[2]), s->Ed[0], s->Ed[1], s->Ed[2], s->ctrl);
       }
       IDX_TRY(cudaEventRecord(ev[5], s->stream));
-      if (f32) {
-        if (st == 0) k_update<float, false><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), cst(s->U), cst(s->Ff[0]), cst(s->Ff[1]), cst(s->Ff[2]), s->Ef[0], s->Ef[1], s->Ef[2], Uout, s->ctrl);
-        else k_update<float, true><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), cst(s->U), cst(s->Ff[0]), cst(s->Ff[1]), cst(s->Ff[2]), s->Ef[0], s->Ef[1], s->Ef[2], Uout, s->ctrl);
-      } else {
-        if (st == 0) k_update<double, false><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), cst(s->U), cst(s->Fd[0]), cst(s->Fd[1]), cst(s->Fd[2]), s->Ed[0], s->Ed[1], s->Ed[2], Uout, s->ctrl);
-        else k_update<double, true><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), cst(s->U), cst(s->Fd[0]), cst(s->Fd[1]), cst(s->Fd[2]), s->Ed[0], s->Ed[1], s->Ed[2], Uout, s->ctrl);
-      }
+      if (f32) launch_update<float>(s, Uin, Uout, st > 0, plan.w[st], plan.w0[st], s->Ff, s->Ef);
+      else launch_update<double>(s, Uin, Uout, st > 0, plan.w[st], plan.w0[st], s->Fd, s->Ed);
       IDX_TRY(cudaEventRecord(ev[6], s->stream));
       IDX_TRY(cudaEventSynchronize(ev[6]));
       float t[6];
@@ -1248,6 +1291,7 @@ extern "C" int idx_step_noalloc(const idx_grid* grid, double gamma, double cfl,
     g.inv_dlf[d] = (float)g.inv_dl[d];
   }
   g.gamma = gamma;
+  g.riemann = 4;
   const size_t arr = align256(sizeof(double) * (size_t)ncell);
   char* p = (char*)base;
   s.ctrl = (Ctrl*)p;
@@ -1672,6 +1716,7 @@ void idx_batch_destroy(idx_batch* b) {
 int idx_batch_add(idx_batch* b, idx_sim* s, double t_end) {
   if (!b || !s || !(t_end >= 0.0)) return IDX_EINVAL;
   if (s->solver.precision != b->precision || s->device != b->device) return IDX_EINVAL;
+  if (s->solver.rk_order != 2) return IDX_EINVAL;  // batched cycles are RK2
   for (idx_sim* m : b->sims)
     if (m == s) return IDX_EINVAL;
   IDX_TRY(cudaStreamSynchronize(b->stream));

@@ -181,6 +181,91 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   }
 }
 
+// The two more diffusive solvers of the paper's list (Sec. 2.3), same interface as hlld
+// and the same outer speed estimates (so the CFL speed c does not depend on the solver):
+//   Rusanov:  F = (F_L + F_R)/2 - (S_max/2)(U_R - U_L), S_max = max(|u_L|+c_fL, |u_R|+c_fR)
+//   HLL:      F_L if S_L > 0, F_R if S_R < 0, else
+//             (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L)
+template <typename T>
+__device__ __forceinline__ void side_flux(const Side<T>& s, T bx, T gm1inv, T F[7], T U[7]) {
+  const T mag = T(0.5) * (bx * bx + s.b1 * s.b1 + s.b2 * s.b2);
+  const T pT = s.p + mag;
+  const T E = s.p * gm1inv + T(0.5) * s.r * (s.u * s.u + s.v * s.v + s.w * s.w) + mag;
+  const T vb = s.u * bx + s.v * s.b1 + s.w * s.b2;
+  const T ru = s.r * s.u;
+  F[0] = ru;
+  F[1] = ru * s.u + pT - bx * bx;
+  F[2] = ru * s.v - bx * s.b1;
+  F[3] = ru * s.w - bx * s.b2;
+  F[4] = (E + pT) * s.u - bx * vb;
+  F[5] = s.b1 * s.u - bx * s.v;
+  F[6] = s.b2 * s.u - bx * s.w;
+  U[0] = s.r; U[1] = ru; U[2] = s.r * s.v; U[3] = s.r * s.w; U[4] = E; U[5] = s.b1; U[6] = s.b2;
+}
+
+template <typename T>
+__device__ __forceinline__ void fast_speeds(const Side<T>& L, const Side<T>& R, T bx, T gamma,
+                                            T& cfL, T& cfR) {
+  const T bx2 = bx * bx;
+  const T gpL = gamma * L.p, gpR = gamma * R.p;
+  const T aL = gpL + bx2 + L.b1 * L.b1 + L.b2 * L.b2;
+  const T aR = gpR + bx2 + R.b1 * R.b1 + R.b2 * R.b2;
+  const T dL = tmax(aL * aL - T(4) * gpL * bx2, T(0));
+  const T dR = tmax(aR * aR - T(4) * gpR * bx2, T(0));
+  cfL = tsqrt((aL + tsqrt(dL)) * (T(0.5) / L.r));
+  cfR = tsqrt((aR + tsqrt(dR)) * (T(0.5) / R.r));
+}
+
+template <typename T>
+__device__ __forceinline__ void rusanov(const Side<T>& L, const Side<T>& R, T bx, T gamma,
+                                        T gm1inv, T F[7], T& c) {
+  T cfL, cfR;
+  fast_speeds(L, R, bx, gamma, cfL, cfR);
+  const T cfm = tmax(cfL, cfR);
+  c = tmax(tabs(tmin(L.u, R.u) - cfm), tabs(tmax(L.u, R.u) + cfm));
+  const T smax = tmax(tabs(L.u) + cfL, tabs(R.u) + cfR);
+  T FL[7], UL[7], FR[7], UR[7];
+  side_flux(L, bx, gm1inv, FL, UL);
+  side_flux(R, bx, gm1inv, FR, UR);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) F[q] = T(0.5) * (FL[q] + FR[q]) - T(0.5) * smax * (UR[q] - UL[q]);
+}
+
+template <typename T>
+__device__ __forceinline__ void hll(const Side<T>& L, const Side<T>& R, T bx, T gamma, T gm1inv,
+                                    T F[7], T& c) {
+  T cfL, cfR;
+  fast_speeds(L, R, bx, gamma, cfL, cfR);
+  const T cfm = tmax(cfL, cfR);
+  const T SL = tmin(L.u, R.u) - cfm;
+  const T SR = tmax(L.u, R.u) + cfm;
+  c = tmax(tabs(SL), tabs(SR));
+  T FL[7], UL[7], FR[7], UR[7];
+  side_flux(L, bx, gm1inv, FL, UL);
+  side_flux(R, bx, gm1inv, FR, UR);
+  if (SL > T(0)) {
+#pragma unroll
+    for (int q = 0; q < 7; ++q) F[q] = FL[q];
+  } else if (SR < T(0)) {
+#pragma unroll
+    for (int q = 0; q < 7; ++q) F[q] = FR[q];
+  } else {
+    const T inv = T(1) / (SR - SL);
+    const T sLR = SL * SR;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) F[q] = (SR * FL[q] - SL * FR[q] + sLR * (UR[q] - UL[q])) * inv;
+  }
+}
+
+// Riemann solver by code: 1 Rusanov, 2 HLL, 4 HLLD (uniform over a sim, so warp-uniform).
+template <typename T>
+__device__ __forceinline__ void riemann_flux(int solver, const Side<T>& L, const Side<T>& R, T bx,
+                                             T gamma, T gm1inv, T F[7], T& c) {
+  if (solver == 4) hlld(L, R, bx, gamma, gm1inv, F, c);
+  else if (solver == 2) hll(L, R, bx, gamma, gm1inv, F, c);
+  else rusanov(L, R, bx, gamma, gm1inv, F, c);
+}
+
 // E^c EMF at one edge (Gardiner & Stone 2005), cancelled form: with X, Y the a- and
 // b-face EMFs, C the cell-centre EMFs and the upwind choice of each one-sided
 // derivative taken from the sign of the matching face mass flux (mean at zero),

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libidx.so")
 IDX_OK, IDX_EINVAL, IDX_ENOMEM, IDX_ENONPHYS, IDX_ECUDA, IDX_ETIMEOUT = 0, -1, -2, -3, -4, -5
 IDX_FP64, IDX_FP32_BULK = 0, 1
 PRECISIONS = {"fp64": IDX_FP64, "fp32": IDX_FP32_BULK, "fp32_bulk": IDX_FP32_BULK}
+RIEMANN = {"rusanov": 1, "hll": 2, "hlld": 4}
 
 _lib = None
 
@@ -124,7 +125,8 @@ class Sim:
     numpy float64 (host) or contiguous torch float64 CUDA tensors (device).
     """
 
-    def __init__(self, shape, lengths, gamma=5.0 / 3.0, cfl=0.4, precision="fp64", stream=None):
+    def __init__(self, shape, lengths, gamma=5.0 / 3.0, cfl=0.4, precision="fp64", stream=None,
+                 riemann="hlld", rk_order=2):
         L = lib()
         nz, ny, nx = (int(s) for s in shape)
         self.shape = (nz, ny, nx)
@@ -133,7 +135,7 @@ class Sim:
         self.cfl = float(cfl)
         self.precision = precision
         g = Grid(nx, ny, nz, *self.lengths)
-        s = Solver(1, 4, 2, 2, self.cfl, PRECISIONS[precision])
+        s = Solver(1, RIEMANN[riemann], 2, int(rk_order), self.cfl, PRECISIONS[precision])
         h = ctypes.c_void_p()
         rc = L.idx_create(ctypes.byref(g), self.gamma, ctypes.byref(s),
                           ctypes.c_void_p(stream) if stream else None, ctypes.byref(h))

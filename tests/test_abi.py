@@ -53,8 +53,9 @@ def _create(L, grid, gamma=5 / 3, solver=None):
     (idx.Grid(2048, 2048, 1024, 1, 1, 1), 5 / 3, None),           # >= 2^31 cells
     (idx.Grid(4, 4, 4, 1, 1, 1), 5 / 3, idx.Solver(2, 4, 2, 2, 0.4, 0)),  # recon
     (idx.Grid(4, 4, 4, 1, 1, 1), 5 / 3, idx.Solver(1, 3, 2, 2, 0.4, 0)),  # riemann
+    (idx.Grid(4, 4, 4, 1, 1, 1), 5 / 3, idx.Solver(1, 0, 2, 2, 0.4, 0)),  # riemann
     (idx.Grid(4, 4, 4, 1, 1, 1), 5 / 3, idx.Solver(1, 4, 1, 2, 0.4, 0)),  # emf
-    (idx.Grid(4, 4, 4, 1, 1, 1), 5 / 3, idx.Solver(1, 4, 2, 3, 0.4, 0)),  # rk order
+    (idx.Grid(4, 4, 4, 1, 1, 1), 5 / 3, idx.Solver(1, 4, 2, 4, 0.4, 0)),  # rk order
     (idx.Grid(4, 4, 4, 1, 1, 1), 5 / 3, idx.Solver(1, 4, 2, 2, 1.0, 0)),  # cfl
     (idx.Grid(4, 4, 4, 1, 1, 1), 5 / 3, idx.Solver(1, 4, 2, 2, 0.4, 7)),  # precision
 ])

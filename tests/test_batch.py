@@ -148,3 +148,15 @@ def test_batched_result_matches_oracle():
     assert err <= 1e-11, (err, n)
     b.close()
     s.close()
+
+
+def test_batch_refuses_rk3_members():
+    ic = inputs.orszag_tang_2d(16)
+    s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, "fp64", rk_order=3)
+    s.set_primitive(ic.prim)
+    b = idx.Batch("fp64")
+    with pytest.raises(idx.IdxError) as e:
+        b.add(s)
+    assert e.value.code == idx.IDX_EINVAL
+    b.close()
+    s.close()

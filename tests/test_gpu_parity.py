@@ -173,6 +173,39 @@ def test_one_cycle_matches_oracle(name):
     s.close()
 
 
+@pytest.mark.parametrize("solver", ["hll", "rusanov"])
+@pytest.mark.parametrize("name", ["smooth_6x5x7", "smooth_2d_1x12x10", "turb_40cube", "ot2d_64",
+                                  "sod_z"])
+def test_one_cycle_other_solvers(solver, name):
+    ic = CASES[name]()
+    o = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, 0.4, solver=solver)
+    s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, "fp64", riemann=solver)
+    s.set_primitive(ic.prim)
+    assert s.time()[1] == pytest.approx(o.next_dt(), rel=1e-14)
+    for _ in range(3):
+        o.step()
+        s.step()
+    err = field_errors(s.get_state(), o.u)
+    print(f"{solver} {name}: max err {max(err):.2e}")
+    assert max(err) <= 3 * TOL_STEP, err
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["smooth_6x5x7", "turb_40cube", "ot2d_64", "sod_x"])
+def test_rk3_cycles(name):
+    ic = CASES[name]()
+    o = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, 0.4, rk_order=3)
+    s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, "fp64", rk_order=3)
+    s.set_primitive(ic.prim)
+    for _ in range(3):
+        dt_o = o.step()
+        assert s.step(want_dt=True) == pytest.approx(dt_o, rel=1e-12)
+    err = field_errors(s.get_state(), o.u)
+    print(f"rk3 {name}: max err {max(err):.2e}")
+    assert max(err) <= 3 * TOL_STEP, err
+    s.close()
+
+
 def test_hundred_cycles_orszag_tang_128():
     ic = inputs.orszag_tang_2d(128)
     o = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, 0.4)
