@@ -220,26 +220,31 @@ __device__ __forceinline__ void sweep_body(const Geo& g, const Ptr8<const T>& W,
   const T gamma = T(g.gamma);
   const T gm1inv = T(1.0 / (g.gamma - 1.0));
 
-  T wm[7], w0[7], wp[7], slope_m[7];
+  // cells f-1, f, f+1 in registers, cell f+2 prefetched one face ahead so that its
+  // loads overlap the current face's Riemann solve
+  T wm[7], w0[7], wp[7], wn[7], slope_m[7];
   {
-    const int cm2 = cell(f0 - 2), cm1 = cell(f0 - 1), c0 = cell(f0);
+    const int cm2 = cell(f0 - 2), cm1 = cell(f0 - 1), c0 = cell(f0), cp = cell(f0 + 1);
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
       const T a = W.f[var[q]][cm2];
       wm[q] = W.f[var[q]][cm1];
       w0[q] = W.f[var[q]][c0];
+      wp[q] = W.f[var[q]][cp];
       slope_m[q] = vanleer(wm[q] - a, w0[q] - wm[q]);
     }
   }
   for (int f = f0; f < f1; ++f) {
-    const int cf = cell(f), cp = cell(f + 1);
+    const int cf = cell(f);
+    if (f + 1 < f1) {
+      const int cn = cell(f + 2);
+#pragma unroll
+      for (int q = 0; q < 7; ++q) wn[q] = W.f[var[q]][cn];
+    }
     Side<T> L, R;
     T slope0[7];
 #pragma unroll
-    for (int q = 0; q < 7; ++q) {
-      wp[q] = W.f[var[q]][cp];
-      slope0[q] = vanleer(w0[q] - wm[q], wp[q] - w0[q]);
-    }
+    for (int q = 0; q < 7; ++q) slope0[q] = vanleer(w0[q] - wm[q], wp[q] - w0[q]);
     L.r = wm[0] + T(0.5) * slope_m[0]; R.r = w0[0] - T(0.5) * slope0[0];
     L.u = wm[1] + T(0.5) * slope_m[1]; R.u = w0[1] - T(0.5) * slope0[1];
     L.v = wm[2] + T(0.5) * slope_m[2]; R.v = w0[2] - T(0.5) * slope0[2];
@@ -257,13 +262,15 @@ __device__ __forceinline__ void sweep_body(const Geo& g, const Ptr8<const T>& W,
     for (int q = 0; q < 7; ++q) {
       wm[q] = w0[q];
       w0[q] = wp[q];
+      wp[q] = wn[q];
       slope_m[q] = slope0[q];
     }
   }
 }
 
 template <typename T, int D, int SEG>
-__global__ void __launch_bounds__(kThreads) k_sweep(Geo g, Ptr8<const T> W, const double* bface,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
+    k_sweep(Geo g, Ptr8<const T> W, const double* bface,
                                                     Ptr8<T> F, const Ctrl* ctrl, int check_dt) {
   if (check_dt && !(ctrl->dt > 0.0)) return;
   sweep_body<T, D, SEG>(g, W, bface, F, blockIdx.x * blockDim.x + threadIdx.x);

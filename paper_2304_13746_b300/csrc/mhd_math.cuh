@@ -27,6 +27,8 @@ __device__ __forceinline__ double tsqrt(double a) { return sqrt(a); }
 __device__ __forceinline__ float tsqrt(float a) { return sqrtf(a); }
 __device__ __forceinline__ double tabs(double a) { return fabs(a); }
 __device__ __forceinline__ float tabs(float a) { return fabsf(a); }
+__device__ __forceinline__ double trsqrt(double a) { return rsqrt(a); }
+__device__ __forceinline__ float trsqrt(float a) { return rsqrtf(a); }
 
 // van Leer (harmonic) limited slope from the two one-sided differences (Sec. 2.3).
 template <typename T> __device__ __forceinline__ T vanleer(T dl, T dr) {
@@ -54,8 +56,10 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   const T aL = gpL + T(2) * magL, aR = gpR + T(2) * magR;
   const T dL = tmax(aL * aL - T(4) * gpL * bx2, T(0));
   const T dR = tmax(aR * aR - T(4) * gpR * bx2, T(0));
-  const T cfL = tsqrt((aL + tsqrt(dL)) * (T(0.5) / L.r));
-  const T cfR = tsqrt((aR + tsqrt(dR)) * (T(0.5) / R.r));
+  // 0.5/rho_L and 0.5/rho_R from one division
+  const T hLR = T(0.5) / (L.r * R.r);
+  const T cfL = tsqrt((aL + tsqrt(dL)) * (R.r * hLR));
+  const T cfR = tsqrt((aR + tsqrt(dR)) * (L.r * hLR));
   const T cfm = tmax(cfL, cfR);
   const T SL = tmin(L.u, R.u) - cfm;
   const T SR = tmax(L.u, R.u) + cfm;
@@ -85,7 +89,10 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   const T pTs = pTL + qL * (SM - L.u);
 
   // single-star transverse states, both sides (needed by the double-star average)
-  const T iL = T(1) / (SL - SM), iR = T(1) / (SR - SM);
+  // 1/(S_L - S_M) and 1/(S_R - S_M) from one division (S_L < S_M < S_R: both O(c_f))
+  const T eL = SL - SM, eR = SR - SM;
+  const T iLR = T(1) / (eL * eR);
+  const T iL = eR * iLR, iR = eL * iLR;
   const T rsL = qL * iL, rsR = qR * iR;  // rho*
   T vsL, wsL, b1sL, b2sL, vsR, wsR, b1sR, b2sR;
   {
@@ -120,10 +127,12 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   }
 
   // Alfven fan speeds
-  const T sqL = tsqrt(rsL), sqR = tsqrt(rsR);
+  // sqrt(rho*) and |Bx|/sqrt(rho*) from one reciprocal square root per side
+  const T rqL = trsqrt(rsL), rqR = trsqrt(rsR);
+  const T sqL = rsL * rqL, sqR = rsR * rqR;
   const T abx = tabs(bx);
-  const T SsL = SM - abx / sqL;
-  const T SsR = SM + abx / sqR;
+  const T SsL = SM - abx * rqL;
+  const T SsR = SM + abx * rqR;
 
   // the side that contains x/t = 0
   const bool left = SM >= T(0);
