@@ -177,15 +177,19 @@ def _stats(requests, t_first, t_last):
 class Server:
     """Continuous batching under an HBM budget (oldest request first)."""
 
-    def __init__(self, backend, budget_bytes, clock=None, cycles_per_poll=8, chunk_s=None):
+    def __init__(self, backend, budget_bytes, clock=None, cycles_per_poll=8, chunk_s=None,
+                 max_active_cells=None):
         """cycles_per_poll: batched cycles between polls; with chunk_s set, that number
         adapts so that one chunk takes about chunk_s seconds (new arrivals and finished
-        requests are handled at chunk boundaries)."""
+        requests are handled at chunk boundaries).  max_active_cells: when set, a request
+        waits while the running ones already hold that many cells (enough work to keep
+        the device busy), so late arrivals do not slow down large running requests."""
         self.backend = backend
         self.budget = int(budget_bytes)
         self.clock = clock or WallClock()
         self.k = int(cycles_per_poll)
         self.chunk_s = chunk_s
+        self.max_cells = max_active_cells
         self.used = 0
         self.peak = 0
 
@@ -237,6 +241,10 @@ class Server:
                     continue
                 if self.used + need > self.budget:
                     break
+                if self.max_cells:
+                    active = sum(q.cells for q in running.values())
+                    if active > 0 and active + r.cells > self.max_cells:
+                        break
                 queue.popleft()
                 ta = self.clock.now()
                 try:

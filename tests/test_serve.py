@@ -141,3 +141,22 @@ def test_stream_is_seeded():
     b = serve.poisson_stream(20, 10.0, seed=7)
     assert [(r.arrival, r.kind, r.n, r.t_end) for r in a] == [(r.arrival, r.kind, r.n, r.t_end) for r in b]
     assert all(r.n % 8 == 0 for r in a)
+
+
+def test_active_cell_cap_limits_concurrency():
+    clock = FakeClock()
+    be = FakeBackend(clock)
+    reqs = stream(40, rate=500.0)
+    cap = 2 * 48 * 48
+    seen = []
+    orig_step = be.step
+
+    def step(k):
+        seen.append(sum(v[0].cells for v in be.active.values()
+                        if v[1] < FakeBackend.cycles_of(v[0])))
+        orig_step(k)
+    be.step = step
+    st = serve.Server(be, 10 ** 12, clock, max_active_cells=cap).run(reqs)
+    assert st["done"] == len(reqs)
+    biggest = max(r.cells for r in reqs)
+    assert max(seen) <= max(cap, biggest)
