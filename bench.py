@@ -189,6 +189,12 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+# DRAM bytes per face of the dominant kernel, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch, 192^3 box, scaled by faces): reported only while
+# the bench's dominant kernel is the variant that was captured.
+MEASURED_TRAFFIC_PER_FACE = {("fp64", "x", 32): (1.288331e9 + 0.780141e9) / 192 ** 3}
+
+
 def alg_flops_per_face(cons, lengths, gamma):
     """Algorithmic flops per face of each direction from the oracle's op counter on a
     small box of the same recipe: HLLD + half of the two-sided reconstruction (each
@@ -444,9 +450,11 @@ def main():
     else:
         peak = 2 * rates["fma32"] / 1e9
         peak_note = "measured FP32 FMA rate x 2 flop (idx_pipe_rates, this GPU)"
+    tpf = MEASURED_TRAFFIC_PER_FACE.get((args.precision, dom, shapes["xyz".index(dom)]))
     roofline = {"bound": "alu", "kernel": f"k_sweep<{'double' if args.precision == 'fp64' else 'float'},{dom}>",
                 "achieved": achieved_gflops, "peak": peak, "unit": "GFLOP/s",
-                "frac": achieved_gflops / peak, "traffic": None,
+                "frac": achieved_gflops / peak,
+                "traffic": tpf * ncell if tpf else None, "traffic_unit": "bytes per launch",
                 "alg_flops_per_face": flops_face[d_i], "launch_ms": sweep_ms[dom],
                 "peak_source": peak_note, "kernel_ms": kt, "sweep_shapes_xyz": shapes,
                 "pipe_rates_gops": {k: v / 1e9 for k, v in rates.items()}}
