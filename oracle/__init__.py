@@ -35,6 +35,7 @@ class _Grid(ctypes.Structure):
 
 
 _P8 = ctypes.c_void_p * 8
+_P3 = ctypes.c_void_p * 3
 _D = ctypes.POINTER(ctypes.c_double)
 
 
@@ -64,6 +65,10 @@ def lib():
         L.ora_cycle_rk.argtypes = [G, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                    _P8, _D, ctypes.c_double, _D, ctypes.POINTER(ctypes.c_long)]
         L.ora_count_faces.argtypes = [G, ctypes.c_double, _P8, ctypes.c_int, _D, _D]
+        L.ora_b_from_potential.argtypes = [G, _P3, _D, _P3]
+        L.ora_cycle_vp.argtypes = [G, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                   _P8, _P3, _P3, _D, ctypes.c_double, _D,
+                                   ctypes.POINTER(ctypes.c_long)]
         L.ora_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -78,7 +83,7 @@ def _grid(shape, lengths):
 def _ptrs(arrays):
     for a in arrays:
         assert a.dtype == np.float64 and a.flags.c_contiguous
-    return _P8(*[a.ctypes.data for a in arrays])
+    return (_P8 if len(arrays) == 8 else _P3)(*[a.ctypes.data for a in arrays])
 
 
 def _new(shape):
@@ -175,10 +180,31 @@ def stage(uin, lengths, gamma, dt, u0=None, w=1.0, w0=0.0):
     return out, inv.value
 
 
-class Sim:
-    """Oracle simulation: state, time, and the inverse CFL time carried between cycles."""
+def b_from_potential(A, bmean, lengths):
+    """Face field (Bx, By, Bz) = bmean + curl A (Sec. 2.4, Eq. 8); A = (Ax, Ay, Az) on edges."""
+    A = [_c(a) for a in A]
+    out = [np.zeros(A[0].shape) for _ in range(3)]
+    _check(lib().ora_b_from_potential(ctypes.byref(_grid(A[0].shape, lengths)), _ptrs(A),
+                                      _arr(bmean, 3), _ptrs(out)))
+    return out
 
-    def __init__(self, cons, lengths, gamma, cfl, solver="hlld", rk_order=2):
+
+INDUCTION = ("field", "potential")
+
+
+class Sim:
+    """Oracle simulation: state, time, and the inverse CFL time carried between cycles.
+
+    induction="field" steps the face field with the curl of the edge EMFs (Eq. 6);
+    induction="potential" steps an edge vector potential A with -E and sets the face
+    field to bref + curl A every stage (Eqs. 7-8).  Without an explicit A the potential
+    starts at 0 and bref is the initial face field.
+    """
+
+    def __init__(self, cons, lengths, gamma, cfl, solver="hlld", rk_order=2, induction="field",
+                 A=None, bref=None):
+        if induction not in INDUCTION:
+            raise ValueError(induction)
         self.solver = SOLVERS[solver]
         self.rk_order = int(rk_order)
         self.u = [_c(a).copy() for a in cons]
@@ -187,20 +213,45 @@ class Sim:
         self.cfl = float(cfl)
         self.t = 0.0
         self.nsteps = 0
+        self.induction = induction
+        if induction == "potential":
+            shape = self.u[0].shape
+            self.A = [np.zeros(shape) for _ in range(3)] if A is None else [_c(a).copy() for a in A]
+            self.bref = [self.u[5 + d].copy() for d in range(3)] if bref is None else \
+                [_c(b).copy() for b in bref]
         self.inv_dt = speed_pass(self.u, self.lengths, self.gamma)
 
     @classmethod
-    def from_prims(cls, prim, lengths, gamma, cfl, solver="hlld", rk_order=2):
-        return cls(cons_from_prims(prim, lengths, gamma), lengths, gamma, cfl, solver, rk_order)
+    def from_prims(cls, prim, lengths, gamma, cfl, solver="hlld", rk_order=2, induction="field"):
+        return cls(cons_from_prims(prim, lengths, gamma), lengths, gamma, cfl, solver, rk_order,
+                   induction)
+
+    @classmethod
+    def from_potential(cls, prim5, A, bmean, lengths, gamma, cfl, solver="hlld", rk_order=2,
+                       induction="potential"):
+        """Cells from (rho, vx, vy, vz, P), faces from bmean + curl A."""
+        B = b_from_potential(A, bmean, lengths)
+        cons = cons_from_prims(list(prim5) + B, lengths, gamma)
+        if induction == "field":
+            return cls(cons, lengths, gamma, cfl, solver, rk_order)
+        bref = [np.full(B[0].shape, float(bmean[d])) for d in range(3)]
+        return cls(cons, lengths, gamma, cfl, solver, rk_order, "potential", A, bref)
 
     def step(self, dt_max=math.inf):
         inv = ctypes.c_double(self.inv_dt)
         dt = ctypes.c_double()
         bad = ctypes.c_long(-1)
-        _check(lib().ora_cycle_rk(ctypes.byref(_grid(self.u[0].shape, self.lengths)),
-                                  self.gamma, self.cfl, self.solver, self.rk_order, _ptrs(self.u),
-                                  ctypes.byref(inv), float(dt_max), ctypes.byref(dt),
-                                  ctypes.byref(bad)), bad)
+        g = ctypes.byref(_grid(self.u[0].shape, self.lengths))
+        if self.induction == "potential":
+            rc = lib().ora_cycle_vp(g, self.gamma, self.cfl, self.solver, self.rk_order,
+                                    _ptrs(self.u), _ptrs(self.A), _ptrs(self.bref),
+                                    ctypes.byref(inv), float(dt_max), ctypes.byref(dt),
+                                    ctypes.byref(bad))
+        else:
+            rc = lib().ora_cycle_rk(g, self.gamma, self.cfl, self.solver, self.rk_order,
+                                    _ptrs(self.u), ctypes.byref(inv), float(dt_max),
+                                    ctypes.byref(dt), ctypes.byref(bad))
+        _check(rc, bad)
         self.inv_dt = inv.value
         self.nsteps += 1
         return dt.value

@@ -573,11 +573,61 @@ void edge_emf(const Grid& G, const std::vector<R>* W, const std::vector<R>* F /*
 }
 
 // ---------------------------------------------------------------------------
+// Vector-potential form of the induction equation (Sec. 2.4, Eqs. 7-8): A lives on
+// the cell edges where the EMF lives, dA/dt = -E there, and every face field is the
+// circulation of A around that face divided by its area (Stokes), B = curl A.  A_e is
+// stored like E_e: at the cell whose lower a- and b-faces bound the edge.  The face
+// field is Bref + curl A, Bref a fixed face field: a uniform mean field (which a
+// periodic A cannot represent), or the field a run started from with A = 0 there
+// (the gauge A = -integral of E dt from that moment).
+// A difference along a direction with one cell vanishes, so that term is dropped.
+// ---------------------------------------------------------------------------
+template <class R>
+void curl_faces(const Grid& G, const std::vector<R>* A, const std::vector<R>* Bref,
+                std::vector<R>* B) {
+  for (int k = 0; k < G.n[2]; ++k)
+    for (int j = 0; j < G.n[1]; ++j)
+      for (int i = 0; i < G.n[0]; ++i) {
+        const long p = at(G, i, j, k);
+        for (int d = 0; d < 3; ++d) {
+          const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+          R b = Bref[d][p];
+          if (G.active[t1]) b = b + (A[t2][shift(G, i, j, k, t1, 1)] - A[t2][p]) / R(G.dl[t1]);
+          if (G.active[t2]) b = b - (A[t1][shift(G, i, j, k, t2, 1)] - A[t1][p]) / R(G.dl[t2]);
+          B[d][p] = b;
+        }
+      }
+}
+
+// The EMF that drives A_e in a stage.  Both transverse directions a = e+1, b = e+2
+// integrated: the E^c edge EMF.  Only a integrated: the edge collapses onto the a-face
+// of the cell and E_e = -F_a[B_b] there; only b integrated: E_e = +F_b[B_a] on the
+// b-face (E = -v x B, and F_a[B_b] = v_a B_b - v_b B_a).  The curl of these is the
+// divergence of the face fluxes of the field normal to the thin direction, as in the
+// field form.  Neither integrated: A_e enters no face field; its EMF is taken as 0.
+template <class R>
+void potential_emf(const Grid& G, const std::vector<R>* W, const std::vector<R>* F /*[3][8]*/,
+                   int e, std::vector<R>& Ee) {
+  const int a = (e + 1) % 3, b = (e + 2) % 3;
+  if (G.active[a] && G.active[b]) {
+    edge_emf(G, W, F, e, Ee);
+  } else if (G.active[a]) {
+    for (long p = 0; p < G.ncell; ++p) Ee[p] = -F[8 * a + 5 + b][p];
+  } else if (G.active[b]) {
+    for (long p = 0; p < G.ncell; ++p) Ee[p] = F[8 * b + 5 + a][p];
+  } else {
+    for (long p = 0; p < G.ncell; ++p) Ee[p] = R(0.0);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // One stage of Sec. 2.7: U* = S_dt(Uin), Uout = w U* + w0 U0 (Eq. 9).
 // ---------------------------------------------------------------------------
 template <class R>
 int stage(const Grid& G, double gamma, R dt, const std::vector<R>* Uin, const std::vector<R>* U0,
-          double w, double w0, std::vector<R>* Uout, R* inv_dt, long* bad, int solver = 4) {
+          double w, double w0, std::vector<R>* Uout, R* inv_dt, long* bad, int solver = 4,
+          const std::vector<R>* Ain = nullptr, const std::vector<R>* A0 = nullptr,
+          std::vector<R>* Aout = nullptr, const std::vector<R>* Bref = nullptr) {
   const long N = G.ncell;
   std::vector<R> W[8];
   for (int f = 0; f < 8; ++f) W[f].assign(N, R(0.0));
@@ -646,6 +696,19 @@ int stage(const Grid& G, double gamma, R dt, const std::vector<R>* Uin, const st
       else
         Uout[f][p] = R(w) * Us[f][p] + R(w0) * U0[f][p];
     }
+  if (Ain == nullptr) return ORA_OK;
+
+  // Vector-potential form (Eqs. 7-8): A* = A - dt E, A_out = w A* + w0 A_0, and the
+  // face field is recomputed from A_out instead of being stepped itself.
+  for (int e = 0; e < 3; ++e) {
+    std::vector<R> Ee(N, R(0.0));
+    potential_emf(G, W, F, e, Ee);
+    for (long p = 0; p < N; ++p) {
+      const R As = Ain[e][p] - dt * Ee[p];
+      Aout[e][p] = (w0 == 0.0 && w == 1.0) ? As : R(w) * As + R(w0) * A0[e][p];
+    }
+  }
+  curl_faces(G, Aout, Bref, &Uout[5]);
   return ORA_OK;
 }
 
@@ -655,28 +718,38 @@ int stage(const Grid& G, double gamma, R dt, const std::vector<R>* Uin, const st
 // cycle's stages.
 template <class R>
 int cycle(const Grid& G, double gamma, double cfl, std::vector<R>* U, R* inv_dt, double dt_max,
-          R* dt_taken, long* bad, int solver = 4, int rk_order = 2) {
+          R* dt_taken, long* bad, int solver = 4, int rk_order = 2, std::vector<R>* A = nullptr,
+          const std::vector<R>* Bref = nullptr) {
   R dt = R(cfl) / *inv_dt;
   if (value(dt) > dt_max) dt = R(dt_max);
   const long N = G.ncell;
   const double w_rk2[2][2] = {{1.0, 0.0}, {0.5, 0.5}};
   const double w_rk3[3][2] = {{1.0, 0.0}, {0.25, 0.75}, {2.0 / 3.0, 1.0 / 3.0}};
   const int nst = rk_order == 3 ? 3 : 2;
-  std::vector<R> prev[8], next[8];
+  std::vector<R> prev[8], next[8], prevA[3], nextA[3];
   for (int f = 0; f < 8; ++f) prev[f] = U[f];
+  if (A)
+    for (int e = 0; e < 3; ++e) prevA[e] = A[e];
   R inv = R(0.0);
   for (int st = 0; st < nst; ++st) {
     const double w = rk_order == 3 ? w_rk3[st][0] : w_rk2[st][0];
     const double w0 = rk_order == 3 ? w_rk3[st][1] : w_rk2[st][1];
     for (int f = 0; f < 8; ++f) next[f].assign(N, R(0.0));
+    if (A)
+      for (int e = 0; e < 3; ++e) nextA[e].assign(N, R(0.0));
     R inv_s;
     const int rc = stage(G, gamma, dt, prev, st == 0 ? (const std::vector<R>*)nullptr : U, w, w0,
-                         next, &inv_s, bad, solver);
+                         next, &inv_s, bad, solver, A ? prevA : nullptr,
+                         (A && st > 0) ? A : nullptr, A ? nextA : nullptr, Bref);
     if (rc != ORA_OK) return rc;
     inv = rmax(inv, inv_s);
     for (int f = 0; f < 8; ++f) prev[f].swap(next[f]);
+    if (A)
+      for (int e = 0; e < 3; ++e) prevA[e].swap(nextA[e]);
   }
   for (int f = 0; f < 8; ++f) U[f] = prev[f];
+  if (A)
+    for (int e = 0; e < 3; ++e) A[e] = prevA[e];
   *inv_dt = inv;
   *dt_taken = dt;
   return ORA_OK;
@@ -871,6 +944,51 @@ int ora_cycle_solver(const ora_grid* g, double gamma, double cfl, int solver, do
   const int st = cycle(G, gamma, cfl, U, &inv, dt_max, &dt, bad_cell, solver);
   if (st != ORA_OK) return st;
   store(G, U, u);
+  *inv_dt = inv;
+  if (dt_taken) *dt_taken = dt;
+  return ORA_OK;
+}
+
+int ora_b_from_potential(const ora_grid* g, const double* const A[3], const double bmean[3],
+                         double* const B[3]) {
+  if (!grid_ok(g) || !A || !bmean || !B) return ORA_EINVAL;
+  for (int d = 0; d < 3; ++d)
+    if (!A[d] || !B[d]) return ORA_EINVAL;
+  const Grid G = make_grid(g);
+  std::vector<double> Av[3], Bref[3], Bv[3];
+  for (int d = 0; d < 3; ++d) {
+    Av[d].assign(A[d], A[d] + G.ncell);
+    Bref[d].assign(G.ncell, bmean[d]);
+    Bv[d].assign(G.ncell, 0.0);
+  }
+  curl_faces(G, Av, Bref, Bv);
+  for (int d = 0; d < 3; ++d) std::memcpy(B[d], Bv[d].data(), sizeof(double) * G.ncell);
+  return ORA_OK;
+}
+
+int ora_cycle_vp(const ora_grid* g, double gamma, double cfl, int solver, int rk_order,
+                 double* const u[8], double* const A[3], const double* const Bref[3],
+                 double* inv_dt, double dt_max, double* dt_taken, long* bad_cell) {
+  if (!grid_ok(g) || !(gamma > 1.0) || !(cfl > 0.0 && cfl < 1.0) ||
+      !ptrs_ok((const void* const*)u) || !inv_dt || !(*inv_dt > 0.0) || !(dt_max >= 0.0) ||
+      !A || !Bref)
+    return ORA_EINVAL;
+  for (int e = 0; e < 3; ++e)
+    if (!A[e] || !Bref[e]) return ORA_EINVAL;
+  if ((solver != 1 && solver != 2 && solver != 4) || (rk_order != 2 && rk_order != 3))
+    return ORA_EINVAL;
+  const Grid G = make_grid(g);
+  std::vector<double> U[8], Av[3], Br[3];
+  load(G, (const double* const*)u, U);
+  for (int e = 0; e < 3; ++e) {
+    Av[e].assign(A[e], A[e] + G.ncell);
+    Br[e].assign(Bref[e], Bref[e] + G.ncell);
+  }
+  double inv = *inv_dt, dt = 0.0;
+  const int st = cycle(G, gamma, cfl, U, &inv, dt_max, &dt, bad_cell, solver, rk_order, Av, Br);
+  if (st != ORA_OK) return st;
+  store(G, U, u);
+  for (int e = 0; e < 3; ++e) std::memcpy(A[e], Av[e].data(), sizeof(double) * G.ncell);
   *inv_dt = inv;
   if (dt_taken) *dt_taken = dt;
   return ORA_OK;

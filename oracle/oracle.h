@@ -72,6 +72,20 @@ int ora_cycle_rk(const ora_grid* g, double gamma, double cfl, int solver, int rk
                  double* const u[8], double* inv_dt, double dt_max, double* dt_taken,
                  long* bad_cell);
 
+/* Face field from an edge vector potential (Sec. 2.4, Eq. 8, discrete Stokes on each
+ * face): B_d = bmean_d + curl_d A.  A[e] is stored like the edge EMF E_e (at the cell
+ * whose lower (e+1)- and (e+2)-faces bound the edge); differences along a direction with
+ * one cell are dropped. */
+int ora_b_from_potential(const ora_grid* g, const double* const A[3], const double bmean[3],
+                         double* const B[3]);
+
+/* One cycle with the vector-potential induction (Sec. 2.4, Eqs. 7-8): every stage steps
+ * A on the edges with -E (RK weights of Table 1) and sets the face field of u to
+ * Bref + curl A.  u (8 fields) and A (3 edge fields) in/out; Bref (3 face fields) in. */
+int ora_cycle_vp(const ora_grid* g, double gamma, double cfl, int solver, int rk_order,
+                 double* const u[8], double* const A[3], const double* const Bref[3],
+                 double* inv_dt, double dt_max, double* dt_taken, long* bad_cell);
+
 /* Ideal-MHD physical flux along "x" of one state (same ordering as ora_hlld). */
 int ora_phys_flux(const double w[7], double bn, double gamma, double F[7]);
 

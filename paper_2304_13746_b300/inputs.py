@@ -337,6 +337,9 @@ def random_smooth(shape=(8, 8, 8), seed=0, lengths=(1.0, 1.0, 1.0), gamma=5.0 / 
     Az = np.broadcast_to(field_at(Xf, Yf, Z, 0.0, 0.05), shape)
     dBx, dBy, dBz = _curl_faces(Ax, Ay, Az, (lx / nx, ly / ny, lz / nz))
     b0 = rng.uniform(-0.6, 0.6, 3)
+    # the potential itself rides along for runs that start from (A, mean field)
+    A = tuple(np.ascontiguousarray(a) for a in (Ax, Ay, Az))
     return IC([rho, vx, vy, vz, P, np.ascontiguousarray(b0[0] + dBx),
                np.ascontiguousarray(b0[1] + dBy), np.ascontiguousarray(b0[2] + dBz)],
-              tuple(lengths), gamma, "random_smooth", {"seed": seed})
+              tuple(lengths), gamma, "random_smooth",
+              {"seed": seed, "A": A, "bmean": tuple(float(x) for x in b0)})
