@@ -8,7 +8,8 @@
  *   Sec. 2.3      PLM reconstruction of the primitives with the van Leer limiter,
  *                 HLLD Riemann solver (Miyoshi & Kusano 2005), pressure in the flux,
  *   Sec. 2.4      constrained transport of face-centred B with the E^c edge EMF
- *                 (Gardiner & Stone 2005), Eq. (6),
+ *                 (Gardiner & Stone 2005), Eq. (6); or its vector-potential form,
+ *                 Eqs. (7)-(8): an edge potential A stepped with -E, B = curl A,
  *   Sec. 2.7      RK2 stages U_s = w_s U* + w0_s U_0 (Eq. 9, Table 1: w = 1, 0; 1/2, 1/2)
  *                 and the CFL step dt = sigma / max_V sum_d c_max,d / dl_d (Eq. 10).
  *
@@ -56,6 +57,15 @@ typedef enum {
                          conserved/face-B accumulation and the dt reduction in FP64          */
 } idx_precision;
 
+typedef enum {
+  IDX_INDUCTION_FIELD = 0,     /* step the face field with the curl of the edge EMFs (Eq. 6)  */
+  IDX_INDUCTION_POTENTIAL = 1  /* step an edge vector potential with -E and set the face field
+                                  to Bref + curl A every stage (Eqs. 7-8).  Equal to the field
+                                  form in exact arithmetic; the discrete divergence of B then
+                                  stays at the rounding of one curl instead of accumulating.
+                                  Costs 72 B per cell (RK3: 96 B) for Bref and the potentials. */
+} idx_induction;
+
 typedef struct {
   int recon;       /* 1 = PLM with the van Leer limiter (Sec. 2.3); the only value accepted */
   int riemann;     /* Riemann solver (Sec. 2.3): 4 = HLLD, 2 = HLL, 1 = Rusanov (Lax-
@@ -64,6 +74,7 @@ typedef struct {
   int rk_order;    /* 2 = RK2 or 3 = RK3 (Table 1; RK3 adds a 64 B/cell state buffer)   */
   double cfl;      /* sigma of Eq. (10), 0 < cfl < 1                                       */
   int precision;   /* idx_precision                                                         */
+  int induction;   /* idx_induction                                                         */
 } idx_solver;
 
 typedef struct idx_sim idx_sim; /* opaque */
@@ -84,6 +95,24 @@ int idx_set_state(idx_sim* sim, const double* const fields[8], int on_device);
  * E = P/(gamma-1) + rho|v|^2/2 + |B_c|^2/2 with B_c the mean of the two faces that
  * bound the cell (the inverse of the primitive recovery). */
 int idx_set_primitive(idx_sim* sim, const double* const fields[8], int on_device);
+
+/* Same, with the field given by an edge vector potential (Sec. 2.4, Eq. 8): fields =
+ * rho, vx, vy, vz, P (cell centres), then Ax, Ay, Az on the cell edges -- Ax[k][j][i] on
+ * the x-edge at (i, j-1/2, k-1/2), Ay at (i-1/2, j, k-1/2), Az at (i-1/2, j-1/2, k)
+ * (along a direction with one cell the half offset is void) -- and bmean the uniform
+ * part of the field, which a periodic A cannot carry.  The face field is bmean +
+ * curl A (circulation over each face / its area; differences along a direction with one
+ * cell are dropped), so its discrete divergence vanishes to rounding.  Then as
+ * idx_set_primitive.  In the vector-potential form A is kept and Bref = bmean; in the
+ * field form A only shapes the initial field.  IDX_EINVAL for NULL or non-finite bmean. */
+int idx_set_potential(idx_sim* sim, const double* const fields[8], const double bmean[3],
+                      int on_device);
+
+/* Copy out the edge potential of a vector-potential sim (layout of idx_set_potential).
+ * After idx_set_state / idx_set_primitive the potential starts at 0 with Bref = the
+ * given face field (the gauge A = -integral of E dt from then on).  IDX_EINVAL for a
+ * field-form sim.  Synchronises; reports a pending device error. */
+int idx_get_potential(const idx_sim* sim, double* const A[3], int on_device);
 
 /* Copy out the conserved state.  Synchronises the sim's stream; reports a pending
  * device error (IDX_ENONPHYS) of earlier asynchronous steps. */
@@ -107,6 +136,10 @@ int idx_step_count(const idx_sim* sim, int64_t* nsteps);
  * cell, FP32 bulk 268 B per cell, plus alignment; RK3 adds 64 B per cell); no device
  * call.  For admission control. */
 int idx_footprint(const idx_grid* grid, int precision, uint64_t* bytes);
+
+/* Device bytes idx_create allocates for this grid and any valid solver (RK order and
+ * induction form included); no device call.  IDX_EINVAL for an invalid solver. */
+int idx_footprint_solver(const idx_grid* grid, const idx_solver* solver, uint64_t* bytes);
 
 /* Flat index k*ny*nx + j*nx + i of the first (lowest-index) cell found non-physical by
  * the last failing call, or -1. */
@@ -148,7 +181,8 @@ int idx_pipe_rates(double rates[6]);
  * the same result, to rounding, alone and in a batch.  The work-list is read at run time, so
  * sims join and leave between steps without re-capturing the batch's CUDA graph.  The
  * sweep shapes are autotuned on the batch when its membership first changes.
- * Members must share the batch's precision and device and use RK2; a member must not be stepped by
+ * Members must share the batch's precision and device and use RK2 in the field form
+ * (IDX_INDUCTION_FIELD; IDX_EINVAL otherwise); a member must not be stepped by
  * idx_step/idx_advance, nor read with idx_get_state/idx_time, until idx_batch_poll or
  * idx_batch_remove has synchronised the batch. */
 typedef struct idx_batch idx_batch; /* opaque */

@@ -416,6 +416,74 @@ __device__ __forceinline__ int slot(int f, int d) {
 }
 
 // ---------------------------------------------------------------------------
+// Vector-potential form of the induction equation (Sec. 2.4, Eqs. 7-8).  The edge
+// potential A sits where the edge EMF sits.  Per stage the EMF kernel steps it,
+// A_out = w (A_in - dt E) + w0 A_0, instead of storing E, and the update kernel sets
+// every face field to Bref + curl A_out (Stokes on the face) instead of stepping it.
+// With one transverse direction of an edge not integrated, the edge collapses onto a
+// face of the other one and the EMF there is the face flux of the field normal to
+// the thin direction: E_e = -F_a[B_b] on an a-face, +F_b[B_a] on a b-face.
+// ---------------------------------------------------------------------------
+struct Ptr3 {
+  double* f[3];
+};
+
+struct PotStage {
+  const double* in[3];    // A of the stage input
+  const double* a0[3];    // A at the start of the cycle (the w0 term)
+  double* out[3];         // A of the stage output
+  const double* bref[3];  // the fixed face field
+};
+
+template <typename T, bool COMBINE>
+__global__ void __launch_bounds__(kThreads) k_emf_pot(Geo g, Ptr8<const T> W, Ptr8<const T> Fx,
+                                                      Ptr8<const T> Fy, Ptr8<const T> Fz,
+                                                      PotStage P, const Ctrl* ctrl, double w,
+                                                      double w0) {
+  const double dt = ctrl->dt;
+  if (!(dt > 0.0)) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  int ijk[3];
+  coords(g, c, ijk[0], ijk[1], ijk[2]);
+  const Ptr8<const T> F[3] = {Fx, Fy, Fz};
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const int a = (e + 1) % 3, b = (e + 2) % 3;
+    double E = 0.0;  // neither transverse direction integrated: A_e enters no face field
+    if (g.active[a] && g.active[b]) E = (double)edge_emf(g, e, c, ijk, W, F);
+    else if (g.active[a]) E = -(double)F[a].f[slot(5 + b, a)][c];
+    else if (g.active[b]) E = (double)F[b].f[slot(5 + a, b)][c];
+    const double As = P.in[e][c] - dt * E;
+    P.out[e][c] = COMBINE ? fma(w, As, w0 * P.a0[e][c]) : As;
+  }
+}
+
+// Face field = bmean + curl A, for a state given by its potential.  Also fills the
+// fixed field Bref with bmean when bref is set.
+struct Vec3 {
+  double v[3];
+};
+__global__ void __launch_bounds__(kThreads) k_b_from_pot(Geo g, Ptr3 A, Vec3 bmean, Ptr3 B,
+                                                         Ptr3 bref, int fill_bref) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  int ijk[3];
+  coords(g, c, ijk[0], ijk[1], ijk[2]);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    double b = bmean.v[d];
+    if (g.active[t1])
+      b += (A.f[t2][shifted(g, c, ijk[t1], t1, 1)] - A.f[t2][c]) * g.inv_dl[t1];
+    if (g.active[t2])
+      b -= (A.f[t1][shifted(g, c, ijk[t2], t2, 1)] - A.f[t1][c]) * g.inv_dl[t2];
+    B.f[d][c] = b;
+    if (fill_bref) bref.f[d][c] = bmean.v[d];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Update: U* = U - dt div F (cell fields), B* = B - dt curl E (face fields, Eq. 6),
 // U_out = w U* + w0 U_0 (Eq. 9), and the stage's inverse CFL time (Eq. 10).
 // Arithmetic in FP64 for both variants.
@@ -438,13 +506,14 @@ __device__ __forceinline__ void block_max_to(unsigned long long* bits, V v) {
 }
 
 // Returns the cell's inverse CFL contribution (0 outside the grid), in the bulk type.
-template <typename T, bool COMBINE>
+template <typename T, bool COMBINE, bool POT = false>
 __device__ __forceinline__ T update_body(const Geo& g, const Ptr8<const double>& Uin,
                                               const Ptr8<const double>& U0,
                                               const Ptr8<const T>& Fx, const Ptr8<const T>& Fy,
                                               const Ptr8<const T>& Fz, const T* Ex, const T* Ey,
                                               const T* Ez, const Ptr8<double>& Uout, double dt,
-                                              int c, double w = 0.5, double w0 = 0.5) {
+                                              int c, double w = 0.5, double w0 = 0.5,
+                                              const PotStage* pot = nullptr) {
   T inv = T(0);
   if (c < g.ncell) {
     int ijk[3];
@@ -489,6 +558,14 @@ __device__ __forceinline__ T update_body(const Geo& g, const Ptr8<const double>&
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+      if constexpr (POT) {
+        // Eq. 8: the face field is the circulation of the stepped potential
+        double b = pot->bref[d][c];
+        if (g.active[t1]) b += (pot->out[t2][up[t1]] - pot->out[t2][c]) * g.inv_dl[t1];
+        if (g.active[t2]) b -= (pot->out[t1][up[t2]] - pot->out[t1][c]) * g.inv_dl[t2];
+        out[5 + d] = b;
+        continue;
+      }
       T curl = T(0);
       if (g.active[d]) {
         if (g.active[t1]) curl += (E[t2][up[t1]] - E[t2][c]) * idl(t1);
@@ -505,8 +582,9 @@ __device__ __forceinline__ T update_body(const Geo& g, const Ptr8<const double>&
     }
 #pragma unroll
     for (int f = 0; f < 8; ++f)
-      Uout.f[f][c] = (COMBINE && std::is_same<T, double>::value) ? fma(w, out[f], w0 * U0.f[f][c])
-                                                                 : out[f];
+      Uout.f[f][c] = (COMBINE && std::is_same<T, double>::value && !(POT && f >= 5))
+                         ? fma(w, out[f], w0 * U0.f[f][c])
+                         : out[f];
     T invT = T(0);
 #pragma unroll
     for (int d = 0; d < 3; ++d)
@@ -516,17 +594,18 @@ __device__ __forceinline__ T update_body(const Geo& g, const Ptr8<const double>&
   return inv;
 }
 
-template <typename T, bool COMBINE>
+template <typename T, bool COMBINE, bool POT = false>
 __global__ void __launch_bounds__(kThreads) k_update(Geo g, Ptr8<const double> Uin,
                                                      Ptr8<const double> U0, Ptr8<const T> Fx,
                                                      Ptr8<const T> Fy, Ptr8<const T> Fz,
                                                      const T* Ex, const T* Ey, const T* Ez,
                                                      Ptr8<double> Uout, Ctrl* ctrl, double w,
-                                                     double w0) {
+                                                     double w0, PotStage pot) {
   const double dt = ctrl->dt;
   if (!(dt > 0.0)) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const T inv = update_body<T, COMBINE>(g, Uin, U0, Fx, Fy, Fz, Ex, Ey, Ez, Uout, dt, c, w, w0);
+  const T inv = update_body<T, COMBINE, POT>(g, Uin, U0, Fx, Fy, Fz, Ex, Ey, Ez, Uout, dt, c, w,
+                                             w0, &pot);
   // block max -> one atomic per block (positive doubles order like their bit patterns)
   block_max_to(&ctrl->inv_acc, inv);
 }
@@ -618,6 +697,9 @@ struct idx_sim {
   Ptr8<float> Wf, Ff[3];
   double* Ed[3];
   float* Ef[3];
+  bool pot;             // vector-potential induction (Eqs. 7-8)
+  Ptr3 A, A1, A2;       // edge potential of the state and of the stage results
+  Ptr3 Bref;            // fixed face field: B = Bref + curl A
   Ctrl* ctrl;           // device
   Ctrl* host_ctrl;      // pinned mirror
   cudaGraph_t graph;
@@ -736,11 +818,14 @@ void launch_fluxes(idx_sim* s, const Ptr8<double>& Uin, const Ptr8<T>& W, Ptr8<T
 }
 
 // The stages of one cycle (Sec. 2.7, Table 1): input, output and weights (w, w0) of
-// U_s = w S_dt(U_{s-1}) + w0 U_0.  RK2: U -> U1 -> U; RK3: U -> U1 -> U2 -> U.
+// U_s = w S_dt(U_{s-1}) + w0 U_0.  RK2: U -> U1 -> U; RK3: U -> U1 -> U2 -> U.  The
+// edge potential of the vector-potential form follows the same registers (A, A1, A2).
 struct StagePlan {
   int n;
   const Ptr8<double>* in[3];
   const Ptr8<double>* out[3];
+  const Ptr3* ain[3];
+  const Ptr3* aout[3];
   double w[3], w0[3];
 };
 
@@ -751,37 +836,75 @@ StagePlan stage_plan(const idx_sim* s) {
     p.in[0] = &s->U; p.out[0] = &s->U1; p.w[0] = 1.0; p.w0[0] = 0.0;
     p.in[1] = &s->U1; p.out[1] = &s->U2; p.w[1] = 0.25; p.w0[1] = 0.75;
     p.in[2] = &s->U2; p.out[2] = &s->U; p.w[2] = 2.0 / 3.0; p.w0[2] = 1.0 / 3.0;
+    p.ain[0] = &s->A; p.aout[0] = &s->A1;
+    p.ain[1] = &s->A1; p.aout[1] = &s->A2;
+    p.ain[2] = &s->A2; p.aout[2] = &s->A;
   } else {
     p.n = 2;
     p.in[0] = &s->U; p.out[0] = &s->U1; p.w[0] = 1.0; p.w0[0] = 0.0;
     p.in[1] = &s->U1; p.out[1] = &s->U; p.w[1] = 0.5; p.w0[1] = 0.5;
     p.in[2] = p.out[2] = nullptr; p.w[2] = p.w0[2] = 0.0;
+    p.ain[0] = &s->A; p.aout[0] = &s->A1;
+    p.ain[1] = &s->A1; p.aout[1] = &s->A;
+    p.ain[2] = p.aout[2] = nullptr;
   }
   return p;
 }
 
+PotStage pot_stage(const idx_sim* s, const StagePlan& p, int st) {
+  PotStage P;
+  for (int e = 0; e < 3; ++e) {
+    P.in[e] = s->pot ? p.ain[st]->f[e] : nullptr;
+    P.a0[e] = s->pot ? s->A.f[e] : nullptr;
+    P.out[e] = s->pot ? p.aout[st]->f[e] : nullptr;
+    P.bref[e] = s->pot ? s->Bref.f[e] : nullptr;
+  }
+  return P;
+}
+
+// Edge EMFs of stage st (field form), or the potential step (vector-potential form).
 template <typename T>
-void launch_update(idx_sim* s, const Ptr8<double>& Uin, const Ptr8<double>& Uout, bool combine,
-                   double w, double w0, Ptr8<T>* F, T** E) {
+void launch_emf(idx_sim* s, const StagePlan& p, int st, const Ptr8<T>& W, Ptr8<T>* F, T** E) {
   const Geo& g = s->geo;
-  if (combine)
-    k_update<T, true><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
-        g, cst(Uin), cst(s->U), cst(F[0]), cst(F[1]), cst(F[2]), E[0], E[1], E[2], Uout, s->ctrl,
-        w, w0);
+  if (!s->pot) {
+    k_emf<T><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
+        g, cst(W), cst(F[0]), cst(F[1]), cst(F[2]), E[0], E[1], E[2], s->ctrl);
+    return;
+  }
+  const PotStage P = pot_stage(s, p, st);
+  if (st > 0)
+    k_emf_pot<T, true><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
+        g, cst(W), cst(F[0]), cst(F[1]), cst(F[2]), P, s->ctrl, p.w[st], p.w0[st]);
   else
-    k_update<T, false><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
-        g, cst(Uin), cst(s->U), cst(F[0]), cst(F[1]), cst(F[2]), E[0], E[1], E[2], Uout, s->ctrl,
-        w, w0);
+    k_emf_pot<T, false><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
+        g, cst(W), cst(F[0]), cst(F[1]), cst(F[2]), P, s->ctrl, p.w[st], p.w0[st]);
+}
+
+template <typename T, bool COMBINE, bool POT>
+void launch_update_k(idx_sim* s, const StagePlan& p, int st, Ptr8<T>* F, T** E) {
+  const Geo& g = s->geo;
+  k_update<T, COMBINE, POT><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
+      g, cst(*p.in[st]), cst(s->U), cst(F[0]), cst(F[1]), cst(F[2]), E[0], E[1], E[2],
+      *p.out[st], s->ctrl, p.w[st], p.w0[st], pot_stage(s, p, st));
 }
 
 template <typename T>
-void launch_stage(idx_sim* s, const Ptr8<double>& Uin, const Ptr8<double>& Uout, bool combine,
-                  double w, double w0, const Ptr8<T>& W, Ptr8<T>* F, T** E) {
-  const Geo& g = s->geo;
-  launch_fluxes<T>(s, Uin, W, F, 1);
-  k_emf<T><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(W), cst(F[0]), cst(F[1]),
-                                                            cst(F[2]), E[0], E[1], E[2], s->ctrl);
-  launch_update<T>(s, Uin, Uout, combine, w, w0, F, E);
+void launch_update(idx_sim* s, const StagePlan& p, int st, Ptr8<T>* F, T** E) {
+  const bool combine = st > 0;
+  if (s->pot) {
+    if (combine) launch_update_k<T, true, true>(s, p, st, F, E);
+    else launch_update_k<T, false, true>(s, p, st, F, E);
+  } else {
+    if (combine) launch_update_k<T, true, false>(s, p, st, F, E);
+    else launch_update_k<T, false, false>(s, p, st, F, E);
+  }
+}
+
+template <typename T>
+void launch_stage(idx_sim* s, const StagePlan& p, int st, const Ptr8<T>& W, Ptr8<T>* F, T** E) {
+  launch_fluxes<T>(s, *p.in[st], W, F, 1);
+  launch_emf<T>(s, p, st, W, F, E);
+  launch_update<T>(s, p, st, F, E);
 }
 
 void launch_cycle(idx_sim* s) {
@@ -789,10 +912,9 @@ void launch_cycle(idx_sim* s) {
   const StagePlan p = stage_plan(s);
   for (int st = 0; st < p.n; ++st) {
     if (s->solver.precision == IDX_FP32_BULK)
-      launch_stage<float>(s, *p.in[st], *p.out[st], st > 0, p.w[st], p.w0[st], s->Wf, s->Ff, s->Ef);
+      launch_stage<float>(s, p, st, s->Wf, s->Ff, s->Ef);
     else
-      launch_stage<double>(s, *p.in[st], *p.out[st], st > 0, p.w[st], p.w0[st], s->Wd, s->Fd,
-                           s->Ed);
+      launch_stage<double>(s, p, st, s->Wd, s->Fd, s->Ed);
   }
   k_end<<<1, 1, 0, s->stream>>>(s->ctrl);
 }
@@ -890,17 +1012,20 @@ int after_new_state(idx_sim* s) {
   return pending_error(s);
 }
 
-// Device bytes of one sim (the single allocation of idx_create); RK3 adds a state.
-size_t sim_bytes(long long ncell, bool f32, bool rk3 = false) {
+// Device bytes of one sim (the single allocation of idx_create); RK3 adds a state, the
+// vector-potential form adds Bref and one edge potential per RK register.
+size_t sim_bytes(long long ncell, bool f32, bool rk3 = false, bool pot = false) {
   auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t arr_d = align(sizeof(double) * ncell);
   const size_t arr_t = align((f32 ? sizeof(float) : sizeof(double)) * ncell);
-  return (rk3 ? 24 : 16) * arr_d + (8 + 24 + 3) * arr_t + align(sizeof(Ctrl));
+  const size_t pot_arrays = pot ? (rk3 ? 12 : 9) : 0;
+  return ((rk3 ? 24 : 16) + pot_arrays) * arr_d + (8 + 24 + 3) * arr_t + align(sizeof(Ctrl));
 }
 
 bool valid_solver(const idx_solver* v) {
   return v && v->recon == 1 && (v->riemann == 1 || v->riemann == 2 || v->riemann == 4) &&
          v->emf == 2 && (v->rk_order == 2 || v->rk_order == 3) &&
+         (v->induction == IDX_INDUCTION_FIELD || v->induction == IDX_INDUCTION_POTENTIAL) &&
          v->cfl > 0.0 && v->cfl < 1.0 &&
          (v->precision == IDX_FP64 || v->precision == IDX_FP32_BULK);
 }
@@ -958,7 +1083,8 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
   auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t arr_d = align(sizeof(double) * ncell), arr_t = align(tsz * ncell);
   const bool rk3 = solver->rk_order == 3;
-  const size_t bytes = sim_bytes(ncell, f32, rk3);
+  s->pot = solver->induction == IDX_INDUCTION_POTENTIAL;
+  const size_t bytes = sim_bytes(ncell, f32, rk3, s->pot);
   if (stream) {
     s->stream = (cudaStream_t)stream;
     s->own_stream = false;
@@ -982,6 +1108,13 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
   for (int f = 0; f < 8; ++f) { s->U1.f[f] = (double*)p; p += arr_d; }
   if (rk3)
     for (int f = 0; f < 8; ++f) { s->U2.f[f] = (double*)p; p += arr_d; }
+  if (s->pot) {
+    for (int e = 0; e < 3; ++e) { s->Bref.f[e] = (double*)p; p += arr_d; }
+    for (int e = 0; e < 3; ++e) { s->A.f[e] = (double*)p; p += arr_d; }
+    for (int e = 0; e < 3; ++e) { s->A1.f[e] = (double*)p; p += arr_d; }
+    if (rk3)
+      for (int e = 0; e < 3; ++e) { s->A2.f[e] = (double*)p; p += arr_d; }
+  }
   if (f32) {
     for (int f = 0; f < 8; ++f) { s->Wf.f[f] = (float*)p; p += arr_t; }
     for (int d = 0; d < 3; ++d)
@@ -1034,9 +1167,23 @@ static int copy_fields_in(idx_sim* s, Ptr8<double> dst, const double* const fiel
   return IDX_OK;
 }
 
+// Vector-potential form, state given by its face field: the gauge starts here, A = 0
+// and Bref = the face field of U.
+static int potential_from_field(idx_sim* s) {
+  if (!s->pot) return IDX_OK;
+  const size_t bytes = sizeof(double) * (size_t)s->geo.ncell;
+  for (int e = 0; e < 3; ++e) {
+    IDX_TRY(cudaMemcpyAsync(s->Bref.f[e], s->U.f[5 + e], bytes, cudaMemcpyDeviceToDevice,
+                            s->stream));
+    IDX_TRY(cudaMemsetAsync(s->A.f[e], 0, bytes, s->stream));
+  }
+  return IDX_OK;
+}
+
 int idx_set_state(idx_sim* s, const double* const fields[8], int on_device) {
   if (!s || !fields) return IDX_EINVAL;
   int rc = copy_fields_in(s, s->U, fields, on_device);
+  if (rc == IDX_OK) rc = potential_from_field(s);
   if (rc != IDX_OK) return rc;
   return after_new_state(s);
 }
@@ -1048,7 +1195,53 @@ int idx_set_primitive(idx_sim* s, const double* const fields[8], int on_device) 
   if (rc != IDX_OK) return rc;
   k_cons_from_prims<<<blocks_for(s->geo.ncell), kThreads, 0, s->stream>>>(s->geo, cst(s->U1), s->U);
   IDX_TRY(cudaGetLastError());
+  rc = potential_from_field(s);
+  if (rc != IDX_OK) return rc;
   return after_new_state(s);
+}
+
+int idx_set_potential(idx_sim* s, const double* const fields[8], const double bmean[3],
+                      int on_device) {
+  if (!s || !fields || !bmean) return IDX_EINVAL;
+  for (int f = 0; f < 8; ++f)
+    if (!fields[f]) return IDX_EINVAL;
+  for (int d = 0; d < 3; ++d)
+    if (!std::isfinite(bmean[d])) return IDX_EINVAL;
+  const size_t bytes = sizeof(double) * (size_t)s->geo.ncell;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  // cells staged in U1; the potential goes to A (vector-potential form) or, when it
+  // only shapes the initial field, to the face slots of U, which k_cons_from_prims
+  // overwrites after k_b_from_pot has read them
+  Ptr3 A;
+  for (int e = 0; e < 3; ++e) A.f[e] = s->pot ? s->A.f[e] : s->U.f[5 + e];
+  for (int f = 0; f < 5; ++f)
+    IDX_TRY(cudaMemcpyAsync(s->U1.f[f], fields[f], bytes, kind, s->stream));
+  for (int e = 0; e < 3; ++e)
+    IDX_TRY(cudaMemcpyAsync(A.f[e], fields[5 + e], bytes, kind, s->stream));
+  Vec3 b0;
+  for (int d = 0; d < 3; ++d) b0.v[d] = bmean[d];
+  Ptr3 B;
+  for (int d = 0; d < 3; ++d) B.f[d] = s->U1.f[5 + d];
+  k_b_from_pot<<<blocks_for(s->geo.ncell), kThreads, 0, s->stream>>>(s->geo, A, b0, B, s->Bref,
+                                                                    s->pot ? 1 : 0);
+  k_cons_from_prims<<<blocks_for(s->geo.ncell), kThreads, 0, s->stream>>>(s->geo, cst(s->U1), s->U);
+  IDX_TRY(cudaGetLastError());
+  return after_new_state(s);
+}
+
+int idx_get_potential(const idx_sim* cs, double* const A[3], int on_device) {
+  idx_sim* s = const_cast<idx_sim*>(cs);
+  if (!s || !A || !s->pot) return IDX_EINVAL;
+  for (int e = 0; e < 3; ++e)
+    if (!A[e]) return IDX_EINVAL;
+  const size_t bytes = sizeof(double) * (size_t)s->geo.ncell;
+  for (int e = 0; e < 3; ++e)
+    IDX_TRY(cudaMemcpyAsync(A[e], s->A.f[e], bytes,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            s->stream));
+  int rc = sync_ctrl(s);
+  if (rc != IDX_OK) return rc;
+  return pending_error(s);
 }
 
 int idx_get_state(const idx_sim* cs, double* const fields[8], int on_device) {
@@ -1146,7 +1339,6 @@ int idx_kernel_times(idx_sim* s, int reps, double ms[6]) {
     const StagePlan plan = stage_plan(s);
     for (int st = 0; st < plan.n; ++st) {
       const Ptr8<double>& Uin = *plan.in[st];
-      const Ptr8<double>& Uout = *plan.out[st];
       IDX_TRY(cudaEventRecord(ev[0], s->stream));
       if (f32) {
         k_prims<float><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), s->Wf, s->ctrl, 1);
@@ -1161,14 +1353,11 @@ int idx_kernel_times(idx_sim* s, int reps, double ms[6]) {
         }
         IDX_TRY(cudaEventRecord(ev[2 + d], s->stream));
       }
-      if (f32) {
-        k_emf<float><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(s->Wf), cst(s->Ff[0]), cst(s->Ff[1]), cst(s->Ff[2]), s->Ef[0], s->Ef[1], s->Ef[2], s->ctrl);
-      } else {
-        k_emf<double><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(s->Wd), cst(s->Fd[0]), cst(s->Fd[1]), cst(s->Fd[2]), s->Ed[0], s->Ed[1], s->Ed[2], s->ctrl);
-      }
+      if (f32) launch_emf<float>(s, plan, st, s->Wf, s->Ff, s->Ef);
+      else launch_emf<double>(s, plan, st, s->Wd, s->Fd, s->Ed);
       IDX_TRY(cudaEventRecord(ev[5], s->stream));
-      if (f32) launch_update<float>(s, Uin, Uout, st > 0, plan.w[st], plan.w0[st], s->Ff, s->Ef);
-      else launch_update<double>(s, Uin, Uout, st > 0, plan.w[st], plan.w0[st], s->Fd, s->Ed);
+      if (f32) launch_update<float>(s, plan, st, s->Ff, s->Ef);
+      else launch_update<double>(s, plan, st, s->Fd, s->Ed);
       IDX_TRY(cudaEventRecord(ev[6], s->stream));
       IDX_TRY(cudaEventSynchronize(ev[6]));
       float t[6];
@@ -1210,6 +1399,16 @@ int idx_footprint(const idx_grid* grid, int precision, uint64_t* bytes) {
   const long long ncell = (long long)grid->nx * grid->ny * grid->nz;
   if (ncell >= (1ll << 31)) return IDX_EINVAL;
   *bytes = (uint64_t)sim_bytes(ncell, precision == IDX_FP32_BULK);
+  return IDX_OK;
+}
+
+int idx_footprint_solver(const idx_grid* grid, const idx_solver* solver, uint64_t* bytes) {
+  if (!grid || !bytes || !valid_solver(solver) || grid->nx < 1 || grid->ny < 1 || grid->nz < 1)
+    return IDX_EINVAL;
+  const long long ncell = (long long)grid->nx * grid->ny * grid->nz;
+  if (ncell >= (1ll << 31)) return IDX_EINVAL;
+  *bytes = (uint64_t)sim_bytes(ncell, solver->precision == IDX_FP32_BULK, solver->rk_order == 3,
+                               solver->induction == IDX_INDUCTION_POTENTIAL);
   return IDX_OK;
 }
 
@@ -1723,7 +1922,8 @@ void idx_batch_destroy(idx_batch* b) {
 int idx_batch_add(idx_batch* b, idx_sim* s, double t_end) {
   if (!b || !s || !(t_end >= 0.0)) return IDX_EINVAL;
   if (s->solver.precision != b->precision || s->device != b->device) return IDX_EINVAL;
-  if (s->solver.rk_order != 2) return IDX_EINVAL;  // batched cycles are RK2
+  // batched cycles are RK2 in the field form
+  if (s->solver.rk_order != 2 || s->pot) return IDX_EINVAL;
   for (idx_sim* m : b->sims)
     if (m == s) return IDX_EINVAL;
   IDX_TRY(cudaStreamSynchronize(b->stream));

@@ -37,10 +37,13 @@ class Grid(ctypes.Structure):
 
 class Solver(ctypes.Structure):
     _fields_ = [("recon", ctypes.c_int), ("riemann", ctypes.c_int), ("emf", ctypes.c_int),
-                ("rk_order", ctypes.c_int), ("cfl", ctypes.c_double), ("precision", ctypes.c_int)]
+                ("rk_order", ctypes.c_int), ("cfl", ctypes.c_double), ("precision", ctypes.c_int),
+                ("induction", ctypes.c_int)]
 
 
 P8 = ctypes.c_void_p * 8
+P3 = ctypes.c_void_p * 3
+INDUCTION = {"field": 0, "potential": 1}
 
 
 def lib(path=LIB_PATH):
@@ -71,6 +74,10 @@ def lib(path=LIB_PATH):
     L.idx_sweep_shapes.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.idx_step_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
     L.idx_footprint.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]
+    L.idx_footprint_solver.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Solver),
+                                       ctypes.POINTER(ctypes.c_uint64)]
+    L.idx_set_potential.argtypes = [vp, P8, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+    L.idx_get_potential.argtypes = [vp, P3, ctypes.c_int]
     L.idx_batch_create.argtypes = [ctypes.c_int, vp, ctypes.POINTER(vp)]
     L.idx_batch_add.argtypes = [vp, vp, ctypes.c_double]
     L.idx_batch_remove.argtypes = [vp, vp]
@@ -98,14 +105,16 @@ def pipe_rates():
     return dict(zip(keys, out[:]))
 
 
-def footprint(shape, precision="fp64"):
-    """Device bytes a sim of this shape (nz, ny, nx) and precision allocates."""
+def footprint(shape, precision="fp64", rk_order=2, induction="field", riemann="hlld"):
+    """Device bytes a sim of this shape (nz, ny, nx) and configuration allocates."""
     nz, ny, nx = (int(v) for v in shape)
     out = ctypes.c_uint64()
-    rc = lib().idx_footprint(ctypes.byref(Grid(nx, ny, nz, 1.0, 1.0, 1.0)), PRECISIONS[precision],
-                             ctypes.byref(out))
+    s = Solver(1, RIEMANN[riemann], 2, int(rk_order), 0.4, PRECISIONS[precision],
+               INDUCTION[induction])
+    rc = lib().idx_footprint_solver(ctypes.byref(Grid(nx, ny, nz, 1.0, 1.0, 1.0)), ctypes.byref(s),
+                                    ctypes.byref(out))
     if rc != IDX_OK:
-        raise IdxError(rc, "idx_footprint")
+        raise IdxError(rc, "idx_footprint_solver")
     return int(out.value)
 
 
@@ -126,7 +135,7 @@ class Sim:
     """
 
     def __init__(self, shape, lengths, gamma=5.0 / 3.0, cfl=0.4, precision="fp64", stream=None,
-                 riemann="hlld", rk_order=2):
+                 riemann="hlld", rk_order=2, induction="field"):
         L = lib()
         nz, ny, nx = (int(s) for s in shape)
         self.shape = (nz, ny, nx)
@@ -135,7 +144,9 @@ class Sim:
         self.cfl = float(cfl)
         self.precision = precision
         g = Grid(nx, ny, nz, *self.lengths)
-        s = Solver(1, RIEMANN[riemann], 2, int(rk_order), self.cfl, PRECISIONS[precision])
+        self.induction = induction
+        s = Solver(1, RIEMANN[riemann], 2, int(rk_order), self.cfl, PRECISIONS[precision],
+                   INDUCTION[induction])
         h = ctypes.c_void_p()
         rc = L.idx_create(ctypes.byref(g), self.gamma, ctypes.byref(s),
                           ctypes.c_void_p(stream) if stream else None, ctypes.byref(h))
@@ -165,14 +176,15 @@ class Sim:
             raise IdxError(rc, where, cell.value)
 
     def _ptrs(self, fields, writable=False):
-        assert len(fields) == 8
+        assert len(fields) in (3, 8)
+        P = P8 if len(fields) == 8 else P3
         if all(_is_torch(a) for a in fields):
             import torch
             for a in fields:
                 assert a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()
                 assert tuple(a.shape) == self.shape
             _torch_sync()
-            return P8(*[a.data_ptr() for a in fields]), 1, fields
+            return P(*[a.data_ptr() for a in fields]), 1, fields
         arrs = []
         for a in fields:
             a = np.asarray(a)
@@ -181,7 +193,7 @@ class Sim:
             if writable:
                 assert a.flags.writeable
             arrs.append(a)
-        return P8(*[a.ctypes.data for a in arrs]), 0, arrs
+        return P(*[a.ctypes.data for a in arrs]), 0, arrs
 
     def set_state(self, cons):
         p, dev, keep = self._ptrs(cons)
@@ -191,6 +203,28 @@ class Sim:
         p, dev, keep = self._ptrs([np.ascontiguousarray(a, dtype=np.float64)
                                    if not _is_torch(a) else a for a in prim])
         self._check(lib().idx_set_primitive(self._h, p, dev), "idx_set_primitive")
+
+    def set_potential(self, prim5, A, bmean):
+        """Cells from (rho, vx, vy, vz, P), faces from bmean + curl A; A = (Ax, Ay, Az) on
+        the cell edges (layout of idx_set_potential)."""
+        fields = [a if _is_torch(a) else np.ascontiguousarray(a, dtype=np.float64)
+                  for a in list(prim5) + list(A)]
+        p, dev, keep = self._ptrs(fields)
+        b = (ctypes.c_double * 3)(*[float(x) for x in bmean])
+        self._check(lib().idx_set_potential(self._h, p, b, dev), "idx_set_potential")
+
+    def get_potential(self, out=None, device=False):
+        """Edge potential (Ax, Ay, Az) of a vector-potential sim."""
+        if out is None:
+            if device:
+                import torch
+                out = [torch.empty(self.shape, dtype=torch.float64, device="cuda")
+                       for _ in range(3)]
+            else:
+                out = [np.empty(self.shape, dtype=np.float64) for _ in range(3)]
+        p, dev, keep = self._ptrs(out, writable=True)
+        self._check(lib().idx_get_potential(self._h, p, dev), "idx_get_potential")
+        return out
 
     def get_state(self, out=None, device=False):
         if out is None:

@@ -58,6 +58,7 @@ def _create(L, grid, gamma=5 / 3, solver=None):
     (idx.Grid(4, 4, 4, 1, 1, 1), 5 / 3, idx.Solver(1, 4, 2, 4, 0.4, 0)),  # rk order
     (idx.Grid(4, 4, 4, 1, 1, 1), 5 / 3, idx.Solver(1, 4, 2, 2, 1.0, 0)),  # cfl
     (idx.Grid(4, 4, 4, 1, 1, 1), 5 / 3, idx.Solver(1, 4, 2, 2, 0.4, 7)),  # precision
+    (idx.Grid(4, 4, 4, 1, 1, 1), 5 / 3, idx.Solver(1, 4, 2, 2, 0.4, 0, 2)),  # induction
 ])
 def test_create_rejects_invalid_arguments(L, grid, gamma, solver):
     rc, h = _create(L, grid, gamma, solver)
@@ -72,7 +73,35 @@ def test_null_arguments(L):
     assert L.idx_advance(None, 1.0, None) == idx.IDX_EINVAL
     assert L.idx_set_state(None, idx.P8(), 0) == idx.IDX_EINVAL
     assert L.idx_pipe_rates(None) == idx.IDX_EINVAL
+    b = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+    assert L.idx_set_potential(None, idx.P8(), b, 0) == idx.IDX_EINVAL
+    assert L.idx_get_potential(None, idx.P3(), 0) == idx.IDX_EINVAL
     L.idx_destroy(None)
+
+
+@pytest.mark.parametrize("precision,rk,induction,per_cell", [
+    ("fp64", 2, "field", 408), ("fp32", 2, "field", 268),
+    ("fp64", 3, "field", 472), ("fp64", 2, "potential", 480),
+    ("fp64", 3, "potential", 568), ("fp32", 2, "potential", 340),
+])
+def test_footprint_per_cell(L, precision, rk, induction, per_cell):
+    # 64^3 cells: every array is a multiple of 256 B, so the count is exact bar the
+    # 256-byte control block
+    n = 64 ** 3
+    got = idx.footprint((64, 64, 64), precision, rk_order=rk, induction=induction)
+    assert got == per_cell * n + 256
+    if rk == 2 and induction == "field":
+        out = ctypes.c_uint64()
+        assert L.idx_footprint(ctypes.byref(idx.Grid(64, 64, 64, 1, 1, 1)), idx.PRECISIONS[precision],
+                               ctypes.byref(out)) == idx.IDX_OK
+        assert out.value == got
+
+
+def test_footprint_rejects_invalid_solver(L):
+    out = ctypes.c_uint64()
+    s = idx.Solver(1, 4, 2, 2, 0.4, 0, 5)
+    assert L.idx_footprint_solver(ctypes.byref(idx.Grid(8, 8, 8, 1, 1, 1)), ctypes.byref(s),
+                                  ctypes.byref(out)) == idx.IDX_EINVAL
 
 
 def test_binding_refuses_to_run_without_library(tmp_path):

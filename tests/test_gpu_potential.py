@@ -1,0 +1,241 @@
+"""Vector-potential induction (Sec. 2.4, Eqs. 7-8) on the GPU against the oracle.
+
+Same bar as the field form: per field, max|g - o| / scale <= 1e-12 after a few cycles,
+<= 1e-10 after 100.  The potential itself is compared against one scale for its three
+components (the largest |A| of the oracle), since a component may sit at exactly zero
+while the others carry the field.  B = Bref + curl A divides a difference of A by the
+cell size, so rounding in A reaches B amplified by about |A| / (|B| dl): at these grid
+sizes that stays well under the bar.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2304_13746_b300 import build as idx_build
+from paper_2304_13746_b300 import idx, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_STEP = 1e-12
+TOL_100 = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    idx_build.build()
+    idx.lib()
+
+
+def field_errors(g, o):
+    rho, E = np.abs(o[0]), np.abs(o[4])
+    msc = float(np.max(np.sqrt(2.0 * rho * E)))
+    bsc = float(np.max(np.sqrt(2.0 * E)))
+    own = [float(np.max(np.abs(o[f]))) for f in range(8)]
+    sc = [own[0], max(own[1], msc), max(own[2], msc), max(own[3], msc), own[4],
+          max(own[5], bsc), max(own[6], bsc), max(own[7], bsc)]
+    return [float(np.max(np.abs(np.asarray(g[f]) - o[f]))) / max(sc[f], 1e-300) for f in range(8)]
+
+
+def potential_error(g, o):
+    sc = max(float(np.max(np.abs(a))) for a in o)
+    if sc == 0.0:
+        return max(float(np.max(np.abs(a))) for a in g)
+    return max(float(np.max(np.abs(np.asarray(x) - y))) for x, y in zip(g, o)) / sc
+
+
+def pair_from_potential(ic, precision="fp64", riemann="hlld", rk_order=2):
+    A, bmean = ic.meta["A"], ic.meta["bmean"]
+    o = oracle.Sim.from_potential(ic.prim[:5], A, bmean, ic.lengths, ic.gamma, 0.4, riemann,
+                                  rk_order)
+    s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, precision, riemann=riemann,
+                rk_order=rk_order, induction="potential")
+    s.set_potential(ic.prim[:5], A, bmean)
+    return o, s
+
+
+def pair_from_field(ic, precision="fp64"):
+    o = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, 0.4, induction="potential")
+    s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, precision, induction="potential")
+    s.set_primitive(ic.prim)
+    return o, s
+
+
+POTENTIAL_CASES = {
+    "smooth_6x5x7": lambda: inputs.random_smooth((6, 5, 7), seed=1, lengths=(1.0, 1.3, 0.7)),
+    "smooth_8cube": lambda: inputs.random_smooth((8, 8, 8), seed=2),
+    "smooth_33x17x40": lambda: inputs.random_smooth((17, 33, 40), seed=5),
+    "smooth_2d_xy": lambda: inputs.random_smooth((1, 12, 10), seed=3),
+    "smooth_2d_xz": lambda: inputs.random_smooth((9, 1, 11), seed=6),
+    "smooth_2d_yz": lambda: inputs.random_smooth((10, 8, 1), seed=8),
+    "smooth_1d_x": lambda: inputs.random_smooth((1, 1, 24), seed=7),
+    "smooth_1d_y": lambda: inputs.random_smooth((1, 24, 1), seed=4),
+    "smooth_1d_z": lambda: inputs.random_smooth((24, 1, 1), seed=9),
+}
+
+
+@pytest.mark.parametrize("name", list(POTENTIAL_CASES))
+def test_from_potential_matches_oracle(name):
+    ic = POTENTIAL_CASES[name]()
+    o, s = pair_from_potential(ic)
+    # the initial state: faces from bmean + curl A, energy from the primitives
+    assert max(field_errors(s.get_state(), o.u)) <= 1e-14
+    assert potential_error(s.get_potential(), o.A) == 0.0
+    assert s.time()[1] == pytest.approx(o.next_dt(), rel=1e-13)
+    for _ in range(4):
+        dt_o = o.step()
+        assert s.step(want_dt=True) == pytest.approx(dt_o, rel=1e-12)
+    err = field_errors(s.get_state(), o.u)
+    ea = potential_error(s.get_potential(), o.A)
+    print(f"{name}: state {max(err):.2e}, potential {ea:.2e}")
+    assert max(err) <= TOL_STEP, err
+    assert ea <= TOL_STEP
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["turb_40cube", "ot2d_64", "sod_z"])
+def test_from_field_matches_oracle(name):
+    ic = {"turb_40cube": lambda: inputs.turbulent_box(40, seed=3),
+          "ot2d_64": lambda: inputs.orszag_tang_2d(64),
+          "sod_z": lambda: inputs.sod_double_tube(50, axis=2)}[name]()
+    o, s = pair_from_field(ic)
+    np.testing.assert_array_equal(s.get_potential()[0], 0.0)
+    for _ in range(4):
+        o.step()
+        s.step()
+    err = field_errors(s.get_state(), o.u)
+    ea = potential_error(s.get_potential(), o.A)
+    print(f"{name}: state {max(err):.2e}, potential {ea:.2e}")
+    assert max(err) <= TOL_STEP, err
+    assert ea <= TOL_STEP
+    s.close()
+
+
+@pytest.mark.parametrize("riemann,rk", [("hll", 3), ("rusanov", 2), ("hlld", 3)])
+def test_other_solvers_and_rk3(riemann, rk):
+    ic = POTENTIAL_CASES["smooth_6x5x7"]()
+    o, s = pair_from_potential(ic, riemann=riemann, rk_order=rk)
+    for _ in range(3):
+        o.step()
+        s.step()
+    err = field_errors(s.get_state(), o.u)
+    assert max(err) <= 3 * TOL_STEP, err
+    assert potential_error(s.get_potential(), o.A) <= 3 * TOL_STEP
+    s.close()
+
+
+def test_hundred_cycles_orszag_tang_128():
+    ic = inputs.orszag_tang_2d(128)
+    o, s = pair_from_field(ic)
+    for _ in range(100):
+        o.step()
+        s.step()
+    err = field_errors(s.get_state(), o.u)
+    assert max(err) <= TOL_100, err
+    assert potential_error(s.get_potential(), o.A) <= TOL_100
+    s.close()
+
+
+def test_potential_form_tracks_field_form_on_gpu():
+    # both forms on the GPU, 50 cycles of the 64^3 turbulent box: equal to rounding
+    ic = inputs.turbulent_box(64, seed=2)
+    f = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, "fp64")
+    p = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, "fp64", induction="potential")
+    f.set_primitive(ic.prim)
+    p.set_primitive(ic.prim)
+    for _ in range(50):
+        assert f.step(want_dt=True) == pytest.approx(p.step(want_dt=True), rel=1e-11)
+    err = field_errors(p.get_state(), f.get_state())
+    assert max(err) <= TOL_100, err
+    f.close()
+    p.close()
+
+
+def _div(B, lengths):
+    nz, ny, nx = B[0].shape
+    return ((np.roll(B[0], -1, 2) - B[0]) * (nx / lengths[0]) +
+            (np.roll(B[1], -1, 1) - B[1]) * (ny / lengths[1]) +
+            (np.roll(B[2], -1, 0) - B[2]) * (nz / lengths[2]))
+
+
+def test_divergence_stays_at_one_curl_of_rounding():
+    ic = inputs.random_smooth((48, 48, 48), seed=12)
+    s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, "fp64", induction="potential")
+    s.set_potential(ic.prim[:5], ic.meta["A"], ic.meta["bmean"])
+    h = 1.0 / 48
+    eps = np.finfo(float).eps
+    for _ in range(4):
+        for _ in range(50):
+            s.step()
+        u, A = s.get_state(), s.get_potential()
+        amax = max(np.abs(a).max() for a in A)
+        bmax = max(np.abs(b).max() for b in u[5:])
+        bound = 64 * eps * (bmax + 4 * amax / h) / h
+        assert np.abs(_div(u[5:], ic.lengths)).max() <= bound
+    s.close()
+
+
+def test_uniform_emf_grows_potential_on_gpu():
+    v, B = (0.3, -0.2, 0.1), (0.4, -0.5, 0.25)
+    ic = inputs.uniform((4, 5, 6), lengths=(1.0, 1.3, 0.7), v=v, B=B)
+    s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, "fp64", induction="potential")
+    s.set_primitive(ic.prim)
+    b0 = s.get_state()[5:]
+    t = sum(s.step(want_dt=True) for _ in range(7))
+    A = s.get_potential()
+    vxb = np.cross(v, B)
+    tol = 1e-13 * t * np.linalg.norm(v) * np.linalg.norm(B)
+    for e in range(3):
+        np.testing.assert_allclose(A[e], t * vxb[e], rtol=0, atol=tol)
+        np.testing.assert_array_equal(s.get_state()[5 + e], b0[e])
+    s.close()
+
+
+def test_fp32_bulk_potential_close_to_fp64():
+    ic = inputs.turbulent_box(32, seed=4)
+    o, s = pair_from_field(ic, precision="fp32")
+    o.step()
+    s.step()
+    err = field_errors(s.get_state(), o.u)
+    assert max(err) <= 1e-5, err
+    assert potential_error(s.get_potential(), o.A) <= 1e-5
+    s.close()
+
+
+def test_device_tensors_and_field_form_from_potential():
+    import torch
+    ic = POTENTIAL_CASES["smooth_8cube"]()
+    A, bmean = ic.meta["A"], ic.meta["bmean"]
+    # field form: the potential only shapes the initial field
+    o = oracle.Sim.from_potential(ic.prim[:5], A, bmean, ic.lengths, ic.gamma, 0.4,
+                                  induction="field")
+    s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, "fp64")
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in list(ic.prim[:5]) + list(A)]
+    s.set_potential(dev[:5], dev[5:], bmean)
+    assert max(field_errors(s.get_state(), o.u)) <= 1e-14
+    with pytest.raises(idx.IdxError) as e:
+        s.get_potential()
+    assert e.value.code == idx.IDX_EINVAL
+    o.step()
+    s.step()
+    assert max(field_errors(s.get_state(), o.u)) <= TOL_STEP
+    s.close()
+    # potential form, read back into device tensors
+    o, s = pair_from_potential(ic)
+    o.step()
+    s.step()
+    out = s.get_potential(device=True)
+    assert potential_error([a.cpu().numpy() for a in out], o.A) <= TOL_STEP
+    s.close()
+
+
+def test_batch_refuses_potential_form():
+    ic = POTENTIAL_CASES["smooth_8cube"]()
+    o, s = pair_from_potential(ic)
+    b = idx.Batch("fp64")
+    with pytest.raises(idx.IdxError) as e:
+        b.add(s, 1.0)
+    assert e.value.code == idx.IDX_EINVAL
+    b.close()
+    s.close()
