@@ -154,12 +154,23 @@ int idx_kernel_times(idx_sim* sim, int reps, double ms[6]);
 
 /* Sweep shape per direction chosen by the autotuner, which runs before a sim's first
  * idx_step / idx_advance (grids of at least 32768 cells; smaller ones keep the default;
- * results are cached per grid, precision and device for the process): a value s > 0 means one
- * thread marches s faces of a pencil, -1 the warp-per-32-cells x sweep, 0 a direction
- * that is not integrated.  Every shape does the same arithmetic per face; results differ
- * between shapes at most by rounding (the compiler may contract products into FMAs
- * differently in each kernel instantiation). */
+ * results are cached per grid, precision and device for the process):
+ *   2, 4, 8, 16, 32   one thread marches that many faces of a pencil (loads from HBM);
+ *   -1                x only: one warp per 32 cells of an x-row, neighbours by shuffle;
+ *   116, 132          y or z only: a block stages a tile of 32 x-cells by 16 / 32 faces
+ *                     (plus a 2-cell periodic halo) into shared memory with bulk tensor
+ *                     copies (TMA) and marches it there; needs nx % 32 == 0 and n_d a
+ *                     multiple of the tile length;
+ *   0                 a direction that is not integrated.
+ * Every shape does the same arithmetic per face; results differ between shapes at most by
+ * rounding (the compiler may contract products into FMAs differently in each kernel
+ * instantiation). */
 int idx_sweep_shapes(const idx_sim* sim, int shapes[3]);
+
+/* Fix the sweep shapes (values as above; ignored for a direction that is not integrated)
+ * instead of autotuning them.  IDX_EINVAL if a shape is unknown or does not fit the grid.
+ * A measurement and testing aid, not part of the method; call it before stepping. */
+int idx_set_sweep_shapes(idx_sim* sim, const int shapes[3]);
 
 /* Free the sim and its device memory (and its stream, if the library made it). */
 void idx_destroy(idx_sim* sim);

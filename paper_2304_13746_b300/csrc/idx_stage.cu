@@ -18,6 +18,7 @@
 // k_end (t, step count, speeds for the next dt), captured once into a CUDA graph and
 // replayed; time, dt and the error flag stay on the device.
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
 #include <cstdint>
@@ -33,6 +34,7 @@
 
 #include "../../include/idx.h"
 #include "mhd_math.cuh"
+#include "tma.cuh"
 
 using namespace idx;
 
@@ -274,6 +276,127 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
                                                     Ptr8<T> F, const Ctrl* ctrl, int check_dt) {
   if (check_dt && !(ctrl->dt > 0.0)) return;
   sweep_body<T, D, SEG>(g, W, bface, F, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// TMA-staged sweep along D = y or z.  A block owns a tile of 32 x-cells by L faces
+// along D at one coordinate of the third direction.  One thread copies the tile's
+// primitives (the 7 rotated variables, L cells plus a 2-cell periodic halo on each
+// side) from HBM into shared memory with bulk tensor copies -- body, low halo and high
+// halo as separate boxes, so every coordinate is in range and wraps by hand -- and the
+// block waits on an mbarrier (bounded).  Then warp w marches faces 4w..4w+3 of the tile
+// from shared memory, lane = x, with the same per-face arithmetic as k_sweep.  The
+// global loads of a marching thread wait ~1 us each; here a tile's loads are in flight
+// together and the march reads shared memory.
+// Tile shapes: L = 16 (128 threads) or 32 (256 threads); nx % 32 == 0, n_D % L == 0.
+// ---------------------------------------------------------------------------
+constexpr uint64_t kWaitNs = 50000000ull;  // bounded mbarrier wait: 50 ms, ~10^4 x a tile copy
+
+__device__ __forceinline__ void flag_timeout(Ctrl* ctrl) {
+  atomicCAS(&ctrl->err, 0, IDX_ETIMEOUT);
+}
+
+template <typename T, int D, int L>
+__global__ void __launch_bounds__(8 * L, sizeof(T) == 4 ? 96 / L : 1)
+    k_sweep_tma(Geo g, const __grid_constant__ CUtensorMap tm_body,
+                const __grid_constant__ CUtensorMap tm_halo, const double* bface, Ptr8<T> F,
+                Ctrl* ctrl, int check_dt) {
+  static_assert(D == 1 || D == 2, "staged sweeps run along y or z");
+  if (check_dt && !(ctrl->dt > 0.0)) return;
+  constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
+  constexpr int ROWS = L + 4, PLANE = ROWS * 32;
+  constexpr int O = (D == 1) ? 2 : 1;  // the transverse direction that is not x
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* tile = reinterpret_cast<T*>(smem_raw);  // [7][ROWS][32]: variable, row along D, x
+  __shared__ __align__(8) uint64_t bar;
+
+  const int ntx = g.n[0] >> 5, ntd = g.n[D] / L;
+  int b = blockIdx.x;
+  const int x0 = (b % ntx) * 32;
+  b /= ntx;
+  const int t0 = (b % ntd) * L;
+  const int co = b / ntd;  // coordinate along O
+  // rotated variable slots of W: rho, v_n, v_t1, v_t2, P, B_t1, B_t2
+  constexpr int var[7] = {0, 1 + D, 1 + A, 1 + B, 4, 5 + A, 5 + B};
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(&bar, 7u * PLANE * sizeof(T));
+    int lo = t0 - 2;
+    if (lo < 0) lo += g.n[D];
+    int hi = t0 + L;
+    if (hi >= g.n[D]) hi -= g.n[D];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      T* dst = tile + q * PLANE;
+      if (D == 1) {
+        tma_load_4d(dst, &tm_halo, x0, lo, co, var[q], &bar);
+        tma_load_4d(dst + 2 * 32, &tm_body, x0, t0, co, var[q], &bar);
+        tma_load_4d(dst + (L + 2) * 32, &tm_halo, x0, hi, co, var[q], &bar);
+      } else {
+        tma_load_4d(dst, &tm_halo, x0, co, lo, var[q], &bar);
+        tma_load_4d(dst + 2 * 32, &tm_body, x0, co, t0, var[q], &bar);
+        tma_load_4d(dst + (L + 2) * 32, &tm_halo, x0, co, hi, var[q], &bar);
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, f0 = (threadIdx.x >> 5) * 4;
+  // flat index of the cell whose lower D-face is face f of the tile
+  const int cbase = x0 + lane + co * g.stride[O];
+  T bn[4];  // the Riemann solves take the normal field in the bulk type
+#pragma unroll
+  for (int q = 0; q < 4; ++q) bn[q] = T(bface[cbase + (t0 + f0 + q) * g.stride[D]]);
+  if (!mbar_wait(&bar, 0, kWaitNs)) {
+    if (threadIdx.x == 0) flag_timeout(ctrl);
+    mbar_wait(&bar, 0, kWaitNs);  // let copies in flight land before the block leaves
+    return;
+  }
+  const T gamma = T(g.gamma);
+  const T gm1inv = T(1.0 / (g.gamma - 1.0));
+  auto ld = [&](int q, int row) { return tile[q * PLANE + row * 32 + lane]; };
+  // face f uses tile rows f .. f+3 (cells f-2 .. f+1)
+  T wm[7], w0[7], wp[7], slope_m[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    const T a = ld(q, f0);
+    wm[q] = ld(q, f0 + 1);
+    w0[q] = ld(q, f0 + 2);
+    wp[q] = ld(q, f0 + 3);
+    slope_m[q] = vanleer(wm[q] - a, w0[q] - wm[q]);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    Side<T> Ls, Rs;
+    T slope0[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) slope0[q] = vanleer(w0[q] - wm[q], wp[q] - w0[q]);
+    Ls.r = wm[0] + T(0.5) * slope_m[0]; Rs.r = w0[0] - T(0.5) * slope0[0];
+    Ls.u = wm[1] + T(0.5) * slope_m[1]; Rs.u = w0[1] - T(0.5) * slope0[1];
+    Ls.v = wm[2] + T(0.5) * slope_m[2]; Rs.v = w0[2] - T(0.5) * slope0[2];
+    Ls.w = wm[3] + T(0.5) * slope_m[3]; Rs.w = w0[3] - T(0.5) * slope0[3];
+    Ls.p = wm[4] + T(0.5) * slope_m[4]; Rs.p = w0[4] - T(0.5) * slope0[4];
+    Ls.b1 = wm[5] + T(0.5) * slope_m[5]; Rs.b1 = w0[5] - T(0.5) * slope0[5];
+    Ls.b2 = wm[6] + T(0.5) * slope_m[6]; Rs.b2 = w0[6] - T(0.5) * slope0[6];
+    T flux[7], cmax;
+    riemann_flux(g.riemann, Ls, Rs, bn[k], gamma, gm1inv, flux, cmax);
+    const int cf = cbase + (t0 + f0 + k) * g.stride[D];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) F.f[q][cf] = flux[q];
+    F.f[7][cf] = cmax;
+    if (k < 3) {
+#pragma unroll
+      for (int q = 0; q < 7; ++q) {
+        wm[q] = w0[q];
+        w0[q] = wp[q];
+        wp[q] = ld(q, f0 + k + 4);
+        slope_m[q] = slope0[q];
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -705,7 +828,11 @@ struct idx_sim {
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   int64_t last_bad;
-  int sweep_shape[3];   // per direction: marching segment (2..32), -1 warp x-sweep, 0 default
+  int sweep_shape[3];   // per direction: marching segment (2..32), -1 warp x-sweep,
+                        // 100 + L TMA-staged tile of L faces (y, z), 0 default
+  CUtensorMap tm_body[3][2];  // per direction (y, z used): box of L = 16 / 32 rows
+  CUtensorMap tm_halo[3];     // per direction: box of the 2 halo rows
+  bool tma_ok[3][2];          // maps encoded for L = 16 / 32 and nx % 32 == 0
   bool tuned;
 };
 
@@ -742,9 +869,37 @@ void launch_march(idx_sim* s, const Ptr8<T>& W, const double* bface, const Ptr8<
                                                                     check_dt);
 }
 
+template <typename T, int D, int L>
+void launch_tma(idx_sim* s, const double* bface, const Ptr8<T>& F, int check_dt) {
+  const Geo& g = s->geo;
+  const int nO = g.n[D == 1 ? 2 : 1];
+  const unsigned blocks = (unsigned)((g.n[0] / 32) * (g.n[D] / L) * nO);
+  const size_t smem = 7 * (L + 4) * 32 * sizeof(T);
+  k_sweep_tma<T, D, L><<<blocks, 8 * L, smem, s->stream>>>(
+      g, s->tm_body[D][L == 32 ? 1 : 0], s->tm_halo[D], bface, F, s->ctrl, check_dt);
+}
+
+// The FP64 tile of 32 rows takes 63 KB of shared memory, above the 48 KB default.
+void allow_tma_smem() {
+  const int big = 7 * (32 + 4) * 32 * (int)sizeof(double);
+  cudaFuncSetAttribute(k_sweep_tma<double, 1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_sweep_tma<double, 2, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaGetLastError();
+}
+
+// Shapes a direction can take: 100 + L only where the staged tiles fit the grid.
+bool tma_shape_ok(const idx_sim* s, int d, int shape) {
+  if (shape != 116 && shape != 132) return true;
+  return d != 0 && s->tma_ok[d][shape == 132 ? 1 : 0] && s->geo.n[d] % (shape - 100) == 0;
+}
+
 template <typename T, int D>
 void launch_sweep_d(idx_sim* s, int shape, const Ptr8<T>& W, const double* bface,
                     const Ptr8<T>& F, int check_dt) {
+  if (D != 0 && tma_shape_ok(s, D, shape)) {
+    if (shape == 116) { launch_tma<T, (D == 0 ? 1 : D), 16>(s, bface, F, check_dt); return; }
+    if (shape == 132) { launch_tma<T, (D == 0 ? 1 : D), 32>(s, bface, F, check_dt); return; }
+  }
   switch (shape) {
     case -1:
       if (D == 0) {
@@ -780,16 +935,17 @@ int tune_sweeps(idx_sim* s, const Ptr8<double>& U, const Ptr8<T>& W, Ptr8<T>* F)
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return IDX_ECUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return IDX_ECUDA; }
-  const int cand[6] = {-1, 2, 4, 8, 16, 32};
+  const int cand[8] = {-1, 2, 4, 8, 16, 32, 116, 132};
   int rc = IDX_OK;
   for (int d = 0; d < 3 && rc == IDX_OK; ++d) {
     if (!g.active[d]) continue;
     float best = 1e30f;
     int best_shape = kSegDefault;
-    for (int q = 0; q < 6; ++q) {
+    for (int q = 0; q < 8; ++q) {
       const int shape = cand[q];
       if (shape == -1 && d != 0) continue;
-      if (shape > 0 && shape > 2 * g.n[d]) continue;
+      if (shape > 100 && !tma_shape_ok(s, d, shape)) continue;
+      if (shape > 0 && shape < 100 && shape > 2 * g.n[d]) continue;
       s->sweep_shape[d] = shape;
       launch_sweep<T>(s, d, W, U.f[5 + d], F[d], 0);
       cudaEventRecord(e0, s->stream);
@@ -1022,6 +1178,56 @@ size_t sim_bytes(long long ncell, bool f32, bool rk3 = false, bool pot = false) 
   return ((rk3 ? 24 : 16) + pot_arrays) * arr_d + (8 + 24 + 3) * arr_t + align(sizeof(Ctrl));
 }
 
+using EncodeTiled = PFN_cuTensorMapEncodeTiled_v12000;
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda).
+EncodeTiled tensor_map_encoder() {
+  static EncodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor maps of the staged y/z sweeps: W seen as a 4D array (x, y, z, variable) with
+// the variables' arrays field_stride bytes apart; boxes of 32 x-cells by 16, 32 or 2
+// rows along the sweep direction, one variable deep.  Host-only encoding.
+void encode_sweep_maps(idx_sim* s, void* wbase, size_t elem, size_t field_stride) {
+  const Geo& g = s->geo;
+  for (int d = 0; d < 3; ++d) s->tma_ok[d][0] = s->tma_ok[d][1] = false;
+  if (g.n[0] % 32 != 0) return;
+  EncodeTiled enc = tensor_map_encoder();
+  if (!enc) return;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2], 8};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.n[0] * elem, (cuuint64_t)g.n[0] * g.n[1] * elem,
+                                 (cuuint64_t)field_stride};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUtensorMapDataType dt =
+      elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  for (int d = 1; d <= 2; ++d) {
+    if (!g.active[d]) continue;
+    auto encode = [&](unsigned rows, CUtensorMap* m) {
+      if ((int)rows > g.n[d]) return false;
+      cuuint32_t box[4] = {32, 1, 1, 1};
+      box[d] = rows;
+      return enc(m, dt, 4, wbase, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                 CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    const bool halo = encode(2, &s->tm_halo[d]);
+    s->tma_ok[d][0] = halo && encode(16, &s->tm_body[d][0]);
+    s->tma_ok[d][1] = halo && encode(32, &s->tm_body[d][1]);
+  }
+}
+
 bool valid_solver(const idx_solver* v) {
   return v && v->recon == 1 && (v->riemann == 1 || v->riemann == 2 || v->riemann == 4) &&
          v->emf == 2 && (v->rk_order == 2 || v->rk_order == 3) &&
@@ -1127,6 +1333,9 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
     for (int d = 0; d < 3; ++d) { s->Ed[d] = (double*)p; p += arr_t; }
   }
   s->ctrl = (Ctrl*)p;
+  if (f32) encode_sweep_maps(s, s->Wf.f[0], sizeof(float), arr_t);
+  else encode_sweep_maps(s, s->Wd.f[0], sizeof(double), arr_t);
+  allow_tma_smem();
   int rc = IDX_OK;
   if (cudaMallocHost(&s->host_ctrl, sizeof(Ctrl)) != cudaSuccess) rc = IDX_ENOMEM;
   // clear on the sim's own stream: a non-blocking stream is not ordered after work
@@ -1381,6 +1590,27 @@ int idx_sweep_shapes(const idx_sim* s, int shapes[3]) {
     const int v = s->sweep_shape[d];
     shapes[d] = s->geo.active[d] ? (v == 0 ? kSegDefault : v) : 0;
   }
+  return IDX_OK;
+}
+
+int idx_set_sweep_shapes(idx_sim* s, const int shapes[3]) {
+  if (!s || !shapes) return IDX_EINVAL;
+  const Geo& g = s->geo;
+  int v[3];
+  for (int d = 0; d < 3; ++d) {
+    v[d] = g.active[d] ? shapes[d] : 0;
+    if (!g.active[d]) continue;
+    const int x = v[d];
+    const bool march = x == 2 || x == 4 || x == 8 || x == 16 || x == 32;
+    const bool warpx = x == -1 && d == 0;
+    const bool staged = (x == 116 || x == 132) && tma_shape_ok(s, d, x);
+    if (!march && !warpx && !staged) return IDX_EINVAL;
+  }
+  for (int d = 0; d < 3; ++d) s->sweep_shape[d] = v[d];
+  s->tuned = true;
+  // the captured cycle holds the old shapes
+  if (s->exec) { cudaGraphExecDestroy(s->exec); s->exec = nullptr; }
+  if (s->graph) { cudaGraphDestroy(s->graph); s->graph = nullptr; }
   return IDX_OK;
 }
 

@@ -72,6 +72,7 @@ def lib(path=LIB_PATH):
     L.idx_pipe_rates.argtypes = [ctypes.POINTER(ctypes.c_double)]
     L.idx_kernel_times.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     L.idx_sweep_shapes.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.idx_set_sweep_shapes.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.idx_step_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
     L.idx_footprint.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]
     L.idx_footprint_solver.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Solver),
@@ -258,10 +259,16 @@ class Sim:
         return dict(zip(("prims", "sweep_x", "sweep_y", "sweep_z", "emf", "update"), out[:]))
 
     def sweep_shapes(self):
-        """Autotuned sweep shape per direction (faces per thread, -1 warp x-sweep, 0 inactive)."""
+        """Sweep shape per direction: faces per thread, -1 warp x-sweep, 116/132 TMA-staged tile,
+        0 inactive."""
         out = (ctypes.c_int * 3)()
         self._check(lib().idx_sweep_shapes(self._h, out), "idx_sweep_shapes")
         return list(out)
+
+    def set_sweep_shapes(self, shapes):
+        """Fix the sweep shapes (x, y, z) instead of autotuning them (see idx_sweep_shapes)."""
+        arr = (ctypes.c_int * 3)(*[int(v) for v in shapes])
+        self._check(lib().idx_set_sweep_shapes(self._h, arr), "idx_set_sweep_shapes")
 
     def step_count(self):
         n = ctypes.c_int64()
