@@ -120,7 +120,7 @@ __device__ __forceinline__ void prims_body(const Geo& g, const Ptr8<const double
     const double kin = 0.5 * rho * (vx * vx + vy * vy + vz * vz);
     const double mag = 0.5 * (bx * bx + by * by + bz * bz);
     const double P = (g.gamma - 1.0) * (U.f[4][c] - kin - mag);
-    if (!(rho > 0.0) || !(P > 0.0) || !isfinite(rho) || !isfinite(P) || !isfinite(vx) ||
+    if (!gt0(rho) || !gt0(P) || !isfinite(rho) || !isfinite(P) || !isfinite(vx) ||
         !isfinite(vy) || !isfinite(vz))
       flag_bad(ctrl, c);
     W.f[0][c] = rho; W.f[1][c] = vx; W.f[2][c] = vy; W.f[3][c] = vz;
@@ -137,7 +137,7 @@ __device__ __forceinline__ void prims_body(const Geo& g, const Ptr8<const double
     const double P = (g.gamma - 1.0) * (U.f[4][c] - kin - mag);
     const float irf = (float)ir;
     const float vx = (float)mx * irf, vy = (float)my * irf, vz = (float)mz * irf;
-    if (!(rho > 0.0) || !(P > 0.0) || !isfinite(rho) || !isfinite(P) || !isfinite(vx) ||
+    if (!gt0(rho) || !gt0(P) || !isfinite(rho) || !isfinite(P) || !isfinite(vx) ||
         !isfinite(vy) || !isfinite(vz))
       flag_bad(ctrl, c);
     W.f[0][c] = (float)rho; W.f[1][c] = vx; W.f[2][c] = vy; W.f[3][c] = vz;
@@ -616,13 +616,13 @@ __global__ void __launch_bounds__(kThreads) k_b_from_pot(Geo g, Ptr3 A, Vec3 bme
 template <typename V>
 __device__ __forceinline__ void block_max_to(unsigned long long* bits, V v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = tmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = max_nn(v, __shfl_xor_sync(0xffffffffu, v, o));
   __shared__ V wmax[kThreads / 32];
   if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
     V m = wmax[0];
-    for (int w = 1; w < kThreads / 32; ++w) m = tmax(m, wmax[w]);
+    for (int w = 1; w < kThreads / 32; ++w) m = max_nn(m, wmax[w]);
     atomicMax(bits, (unsigned long long)__double_as_longlong((double)m));
   }
   __syncthreads();  // wmax is reused by the next call of the block
@@ -711,7 +711,7 @@ __device__ __forceinline__ T update_body(const Geo& g, const Ptr8<const double>&
     T invT = T(0);
 #pragma unroll
     for (int d = 0; d < 3; ++d)
-      if (g.active[d]) invT += tmax(F[d].f[7][c], F[d].f[7][up[d]]) * idl(d);
+      if (g.active[d]) invT += max_nn(F[d].f[7][c], F[d].f[7][up[d]]) * idl(d);
     inv = invT;
   }
   return inv;

@@ -23,6 +23,41 @@ template <> struct Eps<float> {
 
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a < b ? b : a; }
 template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return b < a ? b : a; }
+
+// Sign and order tests on the bit pattern, run by the integer pipe.  On this part an
+// FP64 compare or min/max takes an FP64-pipe slot, like an FMA, and the FP64 stage is
+// bound by that pipe; the integer forms below cost a fraction of one.  For non-NaN
+// arguments each equals the IEEE comparison in its name, signed zeros included.
+__device__ __forceinline__ long long ibits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ int ibits(float x) { return __float_as_int(x); }
+template <typename T> __device__ __forceinline__ bool gt0(T x) { return ibits(x) > 0; }  // x > 0
+template <typename T> __device__ __forceinline__ bool lt0(T x) {                        // x < 0
+  const auto b = ibits(x);
+  return b < 0 && (b << 1) != 0;  // -0 is not < 0
+}
+template <typename T> __device__ __forceinline__ bool ge0(T x) { return !lt0(x); }    // x >= 0
+// Larger / smaller of two values that are >= 0 (non-negative doubles and floats order
+// like their bit patterns); a <= b for two such values.
+template <typename T> __device__ __forceinline__ T max_nn(T a, T b) {
+  return ibits(a) < ibits(b) ? b : a;
+}
+template <typename T> __device__ __forceinline__ bool le_nn(T a, T b) {
+  return ibits(a) <= ibits(b) || (ibits(a) << 1) == 0;  // +0 <= -0 too
+}
+template <typename T> __device__ __forceinline__ bool lt_nn(T a, T b) {
+  return ibits(a) < ibits(b) && (ibits(b) << 1) != 0;
+}
+// max(x, 0) for any x (a negative value or -0 gives +0)
+template <typename T> __device__ __forceinline__ T pos_part(T x) { return ibits(x) > 0 ? x : T(0); }
+// min / max of two values of any sign: integer keys that order like the values
+template <typename T> __device__ __forceinline__ auto okey(T x) {
+  const auto b = ibits(x);
+  using I = decltype(b);
+  constexpr I mag = ~(I(1) << (8 * sizeof(I) - 1));
+  return b < 0 ? I(b ^ mag) : b;  // negative values: reverse the magnitude order
+}
+template <typename T> __device__ __forceinline__ T imin(T a, T b) { return okey(b) < okey(a) ? b : a; }
+template <typename T> __device__ __forceinline__ T imax(T a, T b) { return okey(a) < okey(b) ? b : a; }
 __device__ __forceinline__ double tsqrt(double a) { return sqrt(a); }
 __device__ __forceinline__ float tsqrt(float a) { return sqrtf(a); }
 __device__ __forceinline__ double tabs(double a) { return fabs(a); }
@@ -33,7 +68,10 @@ __device__ __forceinline__ float trsqrt(float a) { return rsqrtf(a); }
 // van Leer (harmonic) limited slope from the two one-sided differences (Sec. 2.3).
 template <typename T> __device__ __forceinline__ T vanleer(T dl, T dr) {
   const T prod = dl * dr;
-  return prod > T(0) ? T(2) * prod / (dl + dr) : T(0);
+  // dl * dr > 0: same sign and both non-zero (tested on the bit patterns)
+  const auto a = ibits(dl), b = ibits(dr);
+  const bool same = (a ^ b) >= 0 && (a << 1) != 0 && (b << 1) != 0;
+  return same ? T(2) * prod / (dl + dr) : T(0);
 }
 
 // Primitive state on one side of a face, rotated so that "u" is the normal velocity.
@@ -54,22 +92,23 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   // outer speeds from the fast magnetosonic speeds (MK05 eq. 67)
   const T gpL = gamma * L.p, gpR = gamma * R.p;
   const T aL = gpL + T(2) * magL, aR = gpR + T(2) * magR;
-  const T dL = tmax(aL * aL - T(4) * gpL * bx2, T(0));
-  const T dR = tmax(aR * aR - T(4) * gpR * bx2, T(0));
+  const T dL = pos_part(aL * aL - T(4) * gpL * bx2);
+  const T dR = pos_part(aR * aR - T(4) * gpR * bx2);
   // 0.5/rho_L and 0.5/rho_R from one division
   const T hLR = T(0.5) / (L.r * R.r);
   const T cfL = tsqrt((aL + tsqrt(dL)) * (R.r * hLR));
   const T cfR = tsqrt((aR + tsqrt(dR)) * (L.r * hLR));
-  const T cfm = tmax(cfL, cfR);
-  const T SL = tmin(L.u, R.u) - cfm;
-  const T SR = tmax(L.u, R.u) + cfm;
-  c = tmax(tabs(SL), tabs(SR));
+  const T cfm = max_nn(cfL, cfR);
+  const T SL = imin(L.u, R.u) - cfm;
+  const T SR = imax(L.u, R.u) + cfm;
+  c = max_nn(tabs(SL), tabs(SR));
 
-  if (SL > T(0) || SR < T(0)) {  // supersonic: upwind physical flux
-    const Side<T>& s = (SL > T(0)) ? L : R;
-    const T pT = (SL > T(0)) ? pTL : pTR;
+  const bool sup_l = gt0(SL);
+  if (sup_l || lt0(SR)) {  // supersonic: upwind physical flux
+    const Side<T>& s = sup_l ? L : R;
+    const T pT = sup_l ? pTL : pTR;
     const T E = s.p * gm1inv + T(0.5) * s.r * (s.u * s.u + s.v * s.v + s.w * s.w) +
-                ((SL > T(0)) ? magL : magR);
+                (sup_l ? magL : magR);
     const T vb = s.u * bx + s.v * s.b1 + s.w * s.b2;
     const T ru = s.r * s.u;
     F[0] = ru;
@@ -98,7 +137,7 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   {
     const T q = qL * (SL - SM);
     const T D = q - bx2;
-    if (tabs(D) <= Eps<T>::degen * (tabs(q) + bx2)) {
+    if (le_nn(tabs(D), Eps<T>::degen * (tabs(q) + bx2))) {
       vsL = L.v; wsL = L.w; b1sL = L.b1; b2sL = L.b2;
     } else {
       const T iD = T(1) / D;
@@ -113,7 +152,7 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   {
     const T q = qR * (SR - SM);
     const T D = q - bx2;
-    if (tabs(D) <= Eps<T>::degen * (tabs(q) + bx2)) {
+    if (le_nn(tabs(D), Eps<T>::degen * (tabs(q) + bx2))) {
       vsR = R.v; wsR = R.w; b1sR = R.b1; b2sR = R.b2;
     } else {
       const T iD = T(1) / D;
@@ -135,7 +174,7 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   const T SsR = SM + abx * rqR;
 
   // the side that contains x/t = 0
-  const bool left = SM >= T(0);
+  const bool left = ge0(SM);
   const Side<T>& s = left ? L : R;
   const T S = left ? SL : SR;
   const T su = left ? sLu : sRu;
@@ -168,9 +207,9 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
 #pragma unroll
   for (int q = 0; q < 7; ++q) F[q] = Fs[q] + S * (Ustar[q] - Us[q]);
 
-  const bool dbl = left ? (SsL < T(0)) : (SsR >= T(0));
-  if (dbl && !(T(0.5) * bx2 < Eps<T>::hllc * pTs)) {
-    const T sgn = bx < T(0) ? T(-1) : T(1);
+  const bool dbl = left ? lt0(SsL) : ge0(SsR);
+  if (dbl && !lt_nn(T(0.5) * bx2, Eps<T>::hllc * pTs)) {
+    const T sgn = lt0(bx) ? T(-1) : T(1);
     const T isum = T(1) / (sqL + sqR);
     const T v2 = (sqL * vsL + sqR * vsR + (b1sR - b1sL) * sgn) * isum;
     const T w2 = (sqL * wsL + sqR * wsR + (b2sR - b2sL) * sgn) * isum;
@@ -219,8 +258,8 @@ __device__ __forceinline__ void fast_speeds(const Side<T>& L, const Side<T>& R, 
   const T gpL = gamma * L.p, gpR = gamma * R.p;
   const T aL = gpL + bx2 + L.b1 * L.b1 + L.b2 * L.b2;
   const T aR = gpR + bx2 + R.b1 * R.b1 + R.b2 * R.b2;
-  const T dL = tmax(aL * aL - T(4) * gpL * bx2, T(0));
-  const T dR = tmax(aR * aR - T(4) * gpR * bx2, T(0));
+  const T dL = pos_part(aL * aL - T(4) * gpL * bx2);
+  const T dR = pos_part(aR * aR - T(4) * gpR * bx2);
   cfL = tsqrt((aL + tsqrt(dL)) * (T(0.5) / L.r));
   cfR = tsqrt((aR + tsqrt(dR)) * (T(0.5) / R.r));
 }
@@ -230,9 +269,9 @@ __device__ __forceinline__ void rusanov(const Side<T>& L, const Side<T>& R, T bx
                                         T gm1inv, T F[7], T& c) {
   T cfL, cfR;
   fast_speeds(L, R, bx, gamma, cfL, cfR);
-  const T cfm = tmax(cfL, cfR);
-  c = tmax(tabs(tmin(L.u, R.u) - cfm), tabs(tmax(L.u, R.u) + cfm));
-  const T smax = tmax(tabs(L.u) + cfL, tabs(R.u) + cfR);
+  const T cfm = max_nn(cfL, cfR);
+  c = max_nn(tabs(imin(L.u, R.u) - cfm), tabs(imax(L.u, R.u) + cfm));
+  const T smax = max_nn(tabs(L.u) + cfL, tabs(R.u) + cfR);
   T FL[7], UL[7], FR[7], UR[7];
   side_flux(L, bx, gm1inv, FL, UL);
   side_flux(R, bx, gm1inv, FR, UR);
@@ -245,17 +284,17 @@ __device__ __forceinline__ void hll(const Side<T>& L, const Side<T>& R, T bx, T 
                                     T F[7], T& c) {
   T cfL, cfR;
   fast_speeds(L, R, bx, gamma, cfL, cfR);
-  const T cfm = tmax(cfL, cfR);
-  const T SL = tmin(L.u, R.u) - cfm;
-  const T SR = tmax(L.u, R.u) + cfm;
-  c = tmax(tabs(SL), tabs(SR));
+  const T cfm = max_nn(cfL, cfR);
+  const T SL = imin(L.u, R.u) - cfm;
+  const T SR = imax(L.u, R.u) + cfm;
+  c = max_nn(tabs(SL), tabs(SR));
   T FL[7], UL[7], FR[7], UR[7];
   side_flux(L, bx, gm1inv, FL, UL);
   side_flux(R, bx, gm1inv, FR, UR);
-  if (SL > T(0)) {
+  if (gt0(SL)) {
 #pragma unroll
     for (int q = 0; q < 7; ++q) F[q] = FL[q];
-  } else if (SR < T(0)) {
+  } else if (lt0(SR)) {
 #pragma unroll
     for (int q = 0; q < 7; ++q) F[q] = FR[q];
   } else {
@@ -285,7 +324,7 @@ template <typename T>
 __device__ __forceinline__ T emf_ec(T X0, T X1, T Y0, T Y1, T C00, T C01, T C10, T C11, T Fa0,
                                     T Fa1, T Fb0, T Fb1) {
   auto pick = [](T f, T up, T dn) {
-    return f > T(0) ? up : (f < T(0) ? dn : T(0.5) * (up + dn));
+    return gt0(f) ? up : (lt0(f) ? dn : T(0.5) * (up + dn));
   };
   const T dB1 = pick(Fa0, C10 - Y1, C00 - Y0);
   const T dB3 = pick(Fa1, Y1 - C11, Y0 - C01);
