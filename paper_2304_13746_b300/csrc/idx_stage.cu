@@ -120,7 +120,7 @@ __device__ __forceinline__ void prims_body(const Geo& g, const Ptr8<const double
     const double kin = 0.5 * rho * (vx * vx + vy * vy + vz * vz);
     const double mag = 0.5 * (bx * bx + by * by + bz * bz);
     const double P = (g.gamma - 1.0) * (U.f[4][c] - kin - mag);
-    if (!gt0(rho) || !gt0(P) || !isfinite(rho) || !isfinite(P) || !isfinite(vx) ||
+    if (!(rho > 0.0) || !(P > 0.0) || !isfinite(rho) || !isfinite(P) || !isfinite(vx) ||
         !isfinite(vy) || !isfinite(vz))
       flag_bad(ctrl, c);
     W.f[0][c] = rho; W.f[1][c] = vx; W.f[2][c] = vy; W.f[3][c] = vz;
@@ -137,7 +137,7 @@ __device__ __forceinline__ void prims_body(const Geo& g, const Ptr8<const double
     const double P = (g.gamma - 1.0) * (U.f[4][c] - kin - mag);
     const float irf = (float)ir;
     const float vx = (float)mx * irf, vy = (float)my * irf, vz = (float)mz * irf;
-    if (!gt0(rho) || !gt0(P) || !isfinite(rho) || !isfinite(P) || !isfinite(vx) ||
+    if (!(rho > 0.0) || !(P > 0.0) || !isfinite(rho) || !isfinite(P) || !isfinite(vx) ||
         !isfinite(vy) || !isfinite(vz))
       flag_bad(ctrl, c);
     W.f[0][c] = (float)rho; W.f[1][c] = vx; W.f[2][c] = vy; W.f[3][c] = vz;

@@ -24,40 +24,49 @@ template <> struct Eps<float> {
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a < b ? b : a; }
 template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return b < a ? b : a; }
 
-// Sign and order tests on the bit pattern, run by the integer pipe.  On this part an
-// FP64 compare or min/max takes an FP64-pipe slot, like an FMA, and the FP64 stage is
-// bound by that pipe; the integer forms below cost a fraction of one.  For non-NaN
-// arguments each equals the IEEE comparison in its name, signed zeros included.
+// Sign and order tests.  On this part an FP64 compare or min/max takes an FP64-pipe slot,
+// like an FMA, and the FP64 stage is bound by that pipe, so for doubles the tests run on
+// the bit pattern in the integer pipe.  FP32 compares are cheap and stay native.  For
+// non-NaN arguments each equals the IEEE comparison in its name, signed zeros included.
 __device__ __forceinline__ long long ibits(double x) { return __double_as_longlong(x); }
-__device__ __forceinline__ int ibits(float x) { return __float_as_int(x); }
-template <typename T> __device__ __forceinline__ bool gt0(T x) { return ibits(x) > 0; }  // x > 0
-template <typename T> __device__ __forceinline__ bool lt0(T x) {                        // x < 0
-  const auto b = ibits(x);
+__device__ __forceinline__ bool gt0(double x) { return ibits(x) > 0; }  // x > 0
+__device__ __forceinline__ bool gt0(float x) { return x > 0.f; }
+__device__ __forceinline__ bool lt0(double x) {                         // x < 0
+  const long long b = ibits(x);
   return b < 0 && (b << 1) != 0;  // -0 is not < 0
 }
-template <typename T> __device__ __forceinline__ bool ge0(T x) { return !lt0(x); }    // x >= 0
-// Larger / smaller of two values that are >= 0 (non-negative doubles and floats order
-// like their bit patterns); a <= b for two such values.
-template <typename T> __device__ __forceinline__ T max_nn(T a, T b) {
-  return ibits(a) < ibits(b) ? b : a;
-}
-template <typename T> __device__ __forceinline__ bool le_nn(T a, T b) {
+__device__ __forceinline__ bool lt0(float x) { return x < 0.f; }
+template <typename T> __device__ __forceinline__ bool ge0(T x) { return !lt0(x); }  // x >= 0
+// Larger of two values that are >= 0 (non-negative doubles order like their bit
+// patterns); a <= b and a < b for two such values.
+__device__ __forceinline__ double max_nn(double a, double b) { return ibits(a) < ibits(b) ? b : a; }
+__device__ __forceinline__ float max_nn(float a, float b) { return a < b ? b : a; }
+__device__ __forceinline__ bool le_nn(double a, double b) {
   return ibits(a) <= ibits(b) || (ibits(a) << 1) == 0;  // +0 <= -0 too
 }
-template <typename T> __device__ __forceinline__ bool lt_nn(T a, T b) {
+__device__ __forceinline__ bool le_nn(float a, float b) { return a <= b; }
+__device__ __forceinline__ bool lt_nn(double a, double b) {
   return ibits(a) < ibits(b) && (ibits(b) << 1) != 0;
 }
+__device__ __forceinline__ bool lt_nn(float a, float b) { return a < b; }
 // max(x, 0) for any x (a negative value or -0 gives +0)
-template <typename T> __device__ __forceinline__ T pos_part(T x) { return ibits(x) > 0 ? x : T(0); }
-// min / max of two values of any sign: integer keys that order like the values
-template <typename T> __device__ __forceinline__ auto okey(T x) {
-  const auto b = ibits(x);
-  using I = decltype(b);
-  constexpr I mag = ~(I(1) << (8 * sizeof(I) - 1));
-  return b < 0 ? I(b ^ mag) : b;  // negative values: reverse the magnitude order
+__device__ __forceinline__ double pos_part(double x) { return ibits(x) > 0 ? x : 0.0; }
+__device__ __forceinline__ float pos_part(float x) { return x > 0.f ? x : 0.f; }
+// min / max of two doubles of any sign through integer keys that order like the values
+__device__ __forceinline__ long long okey(double x) {
+  const long long b = ibits(x);
+  return b < 0 ? (b ^ 0x7fffffffffffffffll) : b;  // negative values: reverse the magnitude order
 }
-template <typename T> __device__ __forceinline__ T imin(T a, T b) { return okey(b) < okey(a) ? b : a; }
-template <typename T> __device__ __forceinline__ T imax(T a, T b) { return okey(a) < okey(b) ? b : a; }
+__device__ __forceinline__ double imin(double a, double b) { return okey(b) < okey(a) ? b : a; }
+__device__ __forceinline__ double imax(double a, double b) { return okey(a) < okey(b) ? b : a; }
+__device__ __forceinline__ float imin(float a, float b) { return b < a ? b : a; }
+__device__ __forceinline__ float imax(float a, float b) { return a < b ? b : a; }
+// dl * dr > 0: same sign and both non-zero
+__device__ __forceinline__ bool same_sign_nz(double dl, double dr, double) {
+  const long long a = ibits(dl), b = ibits(dr);
+  return (a ^ b) >= 0 && (a << 1) != 0 && (b << 1) != 0;
+}
+__device__ __forceinline__ bool same_sign_nz(float, float, float prod) { return prod > 0.f; }
 __device__ __forceinline__ double tsqrt(double a) { return sqrt(a); }
 __device__ __forceinline__ float tsqrt(float a) { return sqrtf(a); }
 __device__ __forceinline__ double tabs(double a) { return fabs(a); }
@@ -68,10 +77,7 @@ __device__ __forceinline__ float trsqrt(float a) { return rsqrtf(a); }
 // van Leer (harmonic) limited slope from the two one-sided differences (Sec. 2.3).
 template <typename T> __device__ __forceinline__ T vanleer(T dl, T dr) {
   const T prod = dl * dr;
-  // dl * dr > 0: same sign and both non-zero (tested on the bit patterns)
-  const auto a = ibits(dl), b = ibits(dr);
-  const bool same = (a ^ b) >= 0 && (a << 1) != 0 && (b << 1) != 0;
-  return same ? T(2) * prod / (dl + dr) : T(0);
+  return same_sign_nz(dl, dr, prod) ? T(2) * prod / (dl + dr) : T(0);
 }
 
 // Primitive state on one side of a face, rotated so that "u" is the normal velocity.
