@@ -68,9 +68,29 @@ struct Geo {
   int active[3];   // n_d > 1
   double inv_dl[3];
   double gamma;
+  double gm1;        // gamma - 1
+  double gm1inv;     // 1 / (gamma - 1)
   float inv_dlf[3];  // 1/dl in FP32 for the FP32-bulk arithmetic
+  float gammaf, gm1invf;
   int riemann;       // 1 Rusanov, 2 HLL, 4 HLLD
 };
+
+// gamma and 1/(gamma - 1) in the bulk type, formed once on the host
+template <typename T> __device__ __forceinline__ T geo_gamma(const Geo& g);
+template <> __device__ __forceinline__ double geo_gamma<double>(const Geo& g) { return g.gamma; }
+template <> __device__ __forceinline__ float geo_gamma<float>(const Geo& g) { return g.gammaf; }
+template <typename T> __device__ __forceinline__ T geo_gm1inv(const Geo& g);
+template <> __device__ __forceinline__ double geo_gm1inv<double>(const Geo& g) { return g.gm1inv; }
+template <> __device__ __forceinline__ float geo_gm1inv<float>(const Geo& g) { return g.gm1invf; }
+
+// The derived constants of Geo.
+inline void geo_set_gamma(Geo& geo, double gamma) {
+  geo.gamma = gamma;
+  geo.gm1 = gamma - 1.0;
+  geo.gm1inv = 1.0 / (gamma - 1.0);
+  geo.gammaf = (float)gamma;
+  geo.gm1invf = (float)geo.gm1inv;
+}
 
 template <typename T> struct Ptr8 {
   T* f[8];
@@ -111,15 +131,15 @@ __device__ __forceinline__ void prims_body(const Geo& g, const Ptr8<const double
   int i, j, k;
   coords(g, c, i, j, k);
   const double rho = U.f[0][c];
-  const double ir = 1.0 / rho;
   if constexpr (std::is_same<T, double>::value) {
+    const double ir = 1.0 / rho;
     const double vx = U.f[1][c] * ir, vy = U.f[2][c] * ir, vz = U.f[3][c] * ir;
     const double bx = 0.5 * (U.f[5][c] + U.f[5][shifted(g, c, i, 0, 1)]);
     const double by = 0.5 * (U.f[6][c] + U.f[6][shifted(g, c, j, 1, 1)]);
     const double bz = 0.5 * (U.f[7][c] + U.f[7][shifted(g, c, k, 2, 1)]);
     const double kin = 0.5 * rho * (vx * vx + vy * vy + vz * vz);
     const double mag = 0.5 * (bx * bx + by * by + bz * bz);
-    const double P = (g.gamma - 1.0) * (U.f[4][c] - kin - mag);
+    const double P = g.gm1 * (U.f[4][c] - kin - mag);
     if (!(rho > 0.0) || !(P > 0.0) || !isfinite(rho) || !isfinite(P) || !isfinite(vx) ||
         !isfinite(vy) || !isfinite(vz))
       flag_bad(ctrl, c);
@@ -128,13 +148,19 @@ __device__ __forceinline__ void prims_body(const Geo& g, const Ptr8<const double
   } else {
     // FP32 bulk: the energy-to-pressure recovery stays FP64 (kinetic and magnetic
     // energies from the FP64 state); the velocities and cell-centre B go out in FP32.
+    // 1/rho only scales the kinetic energy: an FP32 seed refined by one Newton-Raphson
+    // step y1 = y0 + y0 (1 - rho y0), which squares the seed's relative error (~1e-14
+    // after the step), in place of an FP64 division (densities inside the FP32 range,
+    // which the FP32 sweeps need anyway).
+    const double y0 = (double)__frcp_rn((float)rho);
+    const double ir = fma(y0, fma(-rho, y0, 1.0), y0);
     const double mx = U.f[1][c], my = U.f[2][c], mz = U.f[3][c];
     const double sx = U.f[5][c] + U.f[5][shifted(g, c, i, 0, 1)];  // 2 B_c
     const double sy = U.f[6][c] + U.f[6][shifted(g, c, j, 1, 1)];
     const double sz = U.f[7][c] + U.f[7][shifted(g, c, k, 2, 1)];
     const double kin = 0.5 * (mx * mx + my * my + mz * mz) * ir;
     const double mag = 0.125 * (sx * sx + sy * sy + sz * sz);
-    const double P = (g.gamma - 1.0) * (U.f[4][c] - kin - mag);
+    const double P = g.gm1 * (U.f[4][c] - kin - mag);
     const float irf = (float)ir;
     const float vx = (float)mx * irf, vy = (float)my * irf, vz = (float)mz * irf;
     if (!(rho > 0.0) || !(P > 0.0) || !isfinite(rho) || !isfinite(P) || !isfinite(vx) ||
@@ -169,7 +195,7 @@ __global__ void __launch_bounds__(kThreads) k_cons_from_prims(Geo g, Ptr8<const 
   U.f[1][c] = rho * vx;
   U.f[2][c] = rho * vy;
   U.f[3][c] = rho * vz;
-  U.f[4][c] = P.f[4][c] / (g.gamma - 1.0) + 0.5 * rho * (vx * vx + vy * vy + vz * vz) +
+  U.f[4][c] = P.f[4][c] / g.gm1 + 0.5 * rho * (vx * vx + vy * vy + vz * vz) +
               0.5 * (bx * bx + by * by + bz * bz);
   U.f[5][c] = P.f[5][c];
   U.f[6][c] = P.f[6][c];
@@ -219,8 +245,8 @@ __device__ __forceinline__ void sweep_body(const Geo& g, const Ptr8<const T>& W,
   };
   // rotated variable slots in W: rho, v_n, v_t1, v_t2, P, B_t1, B_t2
   constexpr int var[7] = {0, 1 + D, 1 + A, 1 + B, 4, 5 + A, 5 + B};
-  const T gamma = T(g.gamma);
-  const T gm1inv = T(1.0 / (g.gamma - 1.0));
+  const T gamma = geo_gamma<T>(g);
+  const T gm1inv = geo_gm1inv<T>(g);
 
   // cells f-1, f, f+1 in registers, cell f+2 prefetched one face ahead so that its
   // loads overlap the current face's Riemann solve
@@ -355,8 +381,8 @@ __global__ void __launch_bounds__(8 * L, sizeof(T) == 4 ? 96 / L : 1)
     mbar_wait(&bar, 0, kWaitNs);  // let copies in flight land before the block leaves
     return;
   }
-  const T gamma = T(g.gamma);
-  const T gm1inv = T(1.0 / (g.gamma - 1.0));
+  const T gamma = geo_gamma<T>(g);
+  const T gm1inv = geo_gm1inv<T>(g);
   auto ld = [&](int q, int row) { return tile[q * PLANE + row * 32 + lane]; };
   // face f uses tile rows f .. f+3 (cells f-2 .. f+1)
   T wm[7], w0[7], wp[7], slope_m[7];
@@ -430,8 +456,8 @@ __device__ __forceinline__ void sweep_x_body(const Geo& g, const Ptr8<const T>& 
   const int i = base + lane;
   const int c = at_x(i);
   constexpr int var[7] = {0, 1, 2, 3, 4, 6, 7};  // rho, v_n = vx, vy, vz, P, B_t1 = By, B_t2 = Bz
-  const T gamma = T(g.gamma);
-  const T gm1inv = T(1.0 / (g.gamma - 1.0));
+  const T gamma = geo_gamma<T>(g);
+  const T gm1inv = geo_gm1inv<T>(g);
   T w0[7], wm1[7], wm2[7], wp32[7];
 #pragma unroll
   for (int q = 0; q < 7; ++q) w0[q] = W.f[var[q]][c];
@@ -1280,7 +1306,7 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
     g.inv_dl[d] = (double)g.n[d] / l[d];
     g.inv_dlf[d] = (float)g.inv_dl[d];
   }
-  g.gamma = gamma;
+  geo_set_gamma(g, gamma);
   g.riemann = solver->riemann;
 
   // memory plan: U, U1 (16 doubles/cell) + W, F (3 x 8), E (3) in the bulk type
@@ -1726,7 +1752,7 @@ extern "C" int idx_step_noalloc(const idx_grid* grid, double gamma, double cfl,
     g.inv_dl[d] = (double)g.n[d] / l[d];
     g.inv_dlf[d] = (float)g.inv_dl[d];
   }
-  g.gamma = gamma;
+  geo_set_gamma(g, gamma);
   g.riemann = 4;
   const size_t arr = align256(sizeof(double) * (size_t)ncell);
   char* p = (char*)base;
