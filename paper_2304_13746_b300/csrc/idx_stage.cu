@@ -96,6 +96,13 @@ template <typename T> struct Ptr8 {
   T* f[8];
 };
 
+// FP64 value into the bulk type and back, through the integer-pipe conversions for FP32.
+template <typename T> __device__ __forceinline__ T to_bulk(double x);
+template <> __device__ __forceinline__ double to_bulk<double>(double x) { return x; }
+template <> __device__ __forceinline__ float to_bulk<float>(double x) { return d2f(x); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f2d(x); }
+
 __device__ __forceinline__ void coords(const Geo& g, int c, int& i, int& j, int& k) {
   const int nxy = g.n[0] * g.n[1];
   k = c / nxy;
@@ -152,7 +159,7 @@ __device__ __forceinline__ void prims_body(const Geo& g, const Ptr8<const double
     // step y1 = y0 + y0 (1 - rho y0), which squares the seed's relative error (~1e-14
     // after the step), in place of an FP64 division (densities inside the FP32 range,
     // which the FP32 sweeps need anyway).
-    const double y0 = (double)__frcp_rn((float)rho);
+    const double y0 = f2d(__frcp_rn(d2f(rho)));
     const double ir = fma(y0, fma(-rho, y0, 1.0), y0);
     const double mx = U.f[1][c], my = U.f[2][c], mz = U.f[3][c];
     const double sx = U.f[5][c] + U.f[5][shifted(g, c, i, 0, 1)];  // 2 B_c
@@ -161,14 +168,14 @@ __device__ __forceinline__ void prims_body(const Geo& g, const Ptr8<const double
     const double kin = 0.5 * (mx * mx + my * my + mz * mz) * ir;
     const double mag = 0.125 * (sx * sx + sy * sy + sz * sz);
     const double P = g.gm1 * (U.f[4][c] - kin - mag);
-    const float irf = (float)ir;
-    const float vx = (float)mx * irf, vy = (float)my * irf, vz = (float)mz * irf;
+    const float irf = d2f(ir);
+    const float vx = d2f(mx) * irf, vy = d2f(my) * irf, vz = d2f(mz) * irf;
     if (!(rho > 0.0) || !(P > 0.0) || !isfinite(rho) || !isfinite(P) || !isfinite(vx) ||
         !isfinite(vy) || !isfinite(vz))
       flag_bad(ctrl, c);
-    W.f[0][c] = (float)rho; W.f[1][c] = vx; W.f[2][c] = vy; W.f[3][c] = vz;
-    W.f[4][c] = (float)P;
-    W.f[5][c] = 0.5f * (float)sx; W.f[6][c] = 0.5f * (float)sy; W.f[7][c] = 0.5f * (float)sz;
+    W.f[0][c] = d2f(rho); W.f[1][c] = vx; W.f[2][c] = vy; W.f[3][c] = vz;
+    W.f[4][c] = d2f(P);
+    W.f[5][c] = 0.5f * d2f(sx); W.f[6][c] = 0.5f * d2f(sy); W.f[7][c] = 0.5f * d2f(sz);
   }
 }
 
@@ -280,7 +287,7 @@ __device__ __forceinline__ void sweep_body(const Geo& g, const Ptr8<const T>& W,
     L.p = wm[4] + T(0.5) * slope_m[4]; R.p = w0[4] - T(0.5) * slope0[4];
     L.b1 = wm[5] + T(0.5) * slope_m[5]; R.b1 = w0[5] - T(0.5) * slope0[5];
     L.b2 = wm[6] + T(0.5) * slope_m[6]; R.b2 = w0[6] - T(0.5) * slope0[6];
-    const T bn = T(bface[cf]);
+    const T bn = to_bulk<T>(bface[cf]);
     T flux[7], cmax;
     riemann_flux(g.riemann, L, R, bn, gamma, gm1inv, flux, cmax);
 #pragma unroll
@@ -375,7 +382,7 @@ __global__ void __launch_bounds__(8 * L, sizeof(T) == 4 ? 96 / L : 1)
   const int cbase = x0 + lane + co * g.stride[O];
   T bn[4];  // the Riemann solves take the normal field in the bulk type
 #pragma unroll
-  for (int q = 0; q < 4; ++q) bn[q] = T(bface[cbase + (t0 + f0 + q) * g.stride[D]]);
+  for (int q = 0; q < 4; ++q) bn[q] = to_bulk<T>(bface[cbase + (t0 + f0 + q) * g.stride[D]]);
   if (!mbar_wait(&bar, 0, kWaitNs)) {
     if (threadIdx.x == 0) flag_timeout(ctrl);
     mbar_wait(&bar, 0, kWaitNs);  // let copies in flight land before the block leaves
@@ -492,7 +499,7 @@ __device__ __forceinline__ void sweep_x_body(const Geo& g, const Ptr8<const T>& 
   L.r = Lq[0]; L.u = Lq[1]; L.v = Lq[2]; L.w = Lq[3]; L.p = Lq[4]; L.b1 = Lq[5]; L.b2 = Lq[6];
   R.r = Rq[0]; R.u = Rq[1]; R.v = Rq[2]; R.w = Rq[3]; R.p = Rq[4]; R.b1 = Rq[5]; R.b2 = Rq[6];
   T flux[7], cmax;
-  riemann_flux(g.riemann, L, R, T(bface[c]), gamma, gm1inv, flux, cmax);
+  riemann_flux(g.riemann, L, R, to_bulk<T>(bface[c]), gamma, gm1inv, flux, cmax);
 #pragma unroll
   for (int q = 0; q < 7; ++q) F.f[q][c] = flux[q];
   F.f[7][c] = cmax;
@@ -600,9 +607,9 @@ __global__ void __launch_bounds__(kThreads) k_emf_pot(Geo g, Ptr8<const T> W, Pt
   for (int e = 0; e < 3; ++e) {
     const int a = (e + 1) % 3, b = (e + 2) % 3;
     double E = 0.0;  // neither transverse direction integrated: A_e enters no face field
-    if (g.active[a] && g.active[b]) E = (double)edge_emf(g, e, c, ijk, W, F);
-    else if (g.active[a]) E = -(double)F[a].f[slot(5 + b, a)][c];
-    else if (g.active[b]) E = (double)F[b].f[slot(5 + a, b)][c];
+    if (g.active[a] && g.active[b]) E = to_f64(edge_emf(g, e, c, ijk, W, F));
+    else if (g.active[a]) E = -to_f64(F[a].f[slot(5 + b, a)][c]);
+    else if (g.active[b]) E = to_f64(F[b].f[slot(5 + a, b)][c]);
     const double As = P.in[e][c] - dt * E;
     P.out[e][c] = COMBINE ? fma(w, As, w0 * P.a0[e][c]) : As;
   }
@@ -679,17 +686,17 @@ __device__ __forceinline__ T update_body(const Geo& g, const Ptr8<const double>&
       if constexpr (std::is_same<T, double>::value) return g.inv_dl[d];
       else return g.inv_dlf[d];
     };
-    const float dtf = (float)dt;
+    const float dtf = d2f(dt);
     auto accumulate = [&](int f, T div) -> double {
       if constexpr (std::is_same<T, double>::value) {
         return Uin.f[f][c] - dt * div;
       } else {
         if (COMBINE) {
-          const float wdt = (float)(w * dt);
-          if (w == w0) return fma(w, U0.f[f][c] + Uin.f[f][c], (double)(-wdt * div));
-          return fma(w0, U0.f[f][c], w * Uin.f[f][c]) + (double)(-wdt * div);
+          const float wdt = d2f(w * dt);
+          if (w == w0) return fma(w, U0.f[f][c] + Uin.f[f][c], f2d(-wdt * div));
+          return fma(w0, U0.f[f][c], w * Uin.f[f][c]) + f2d(-wdt * div);
         }
-        return Uin.f[f][c] + (double)(-dtf * div);
+        return Uin.f[f][c] + f2d(-dtf * div);
       }
     };
     double out[8];

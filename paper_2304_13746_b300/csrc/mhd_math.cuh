@@ -74,6 +74,42 @@ __device__ __forceinline__ float tabs(float a) { return fabsf(a); }
 __device__ __forceinline__ double trsqrt(double a) { return rsqrt(a); }
 __device__ __forceinline__ float trsqrt(float a) { return rsqrtf(a); }
 
+// float <-> double conversions rebuilt from the IEEE-754 bit layouts in the integer pipe.
+// On this part the converters run on the FP64 pipe at its rate, which the FP32-bulk
+// kernels otherwise spend on format changes.  Results equal the round-to-nearest-even
+// conversions; inputs outside the fast ranges (subnormals, infinities, NaNs, doubles
+// outside the normal float range) go to the converter.
+//
+// binary32 -> binary64 is exact: same sign, exponent rebiased by 1023 - 127 = 896,
+// mantissa shifted left by 29.
+__host__ __device__ __forceinline__ unsigned long long f2d_bits(unsigned u, bool* slow) {
+  const unsigned a = u & 0x7fffffffu;
+  *slow = (a - 1u) < 0x007fffffu || a >= 0x7f800000u;  // subnormal, infinity, NaN
+  const unsigned hi = (u & 0x80000000u) | (a == 0u ? 0u : (a >> 3) + 0x38000000u);
+  return ((unsigned long long)hi << 32) | (unsigned long long)(u << 29);
+}
+// binary64 -> binary32 for |x| in [2^-126, 2^128) (and zeros): rebias the exponent, then
+// round the 29 dropped mantissa bits to nearest, ties to even; a carry out of the
+// mantissa steps the exponent (up to infinity, as overflow under rounding to nearest).
+__host__ __device__ __forceinline__ unsigned d2f_bits(unsigned long long b, bool* slow) {
+  const unsigned long long a = b & 0x7fffffffffffffffull;
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  *slow = a != 0ull && (a - 0x3810000000000000ull) >= 0x0fe0000000000000ull;
+  const unsigned long long r = a - 0x3800000000000000ull;
+  const unsigned q = (unsigned)((r + 0x0fffffffull + ((r >> 29) & 1ull)) >> 29);
+  return sign | (a == 0ull ? 0u : q);
+}
+__device__ __forceinline__ double f2d(float x) {
+  bool slow;
+  const unsigned long long b = f2d_bits(__float_as_uint(x), &slow);
+  return slow ? (double)x : __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ float d2f(double x) {
+  bool slow;
+  const unsigned u = d2f_bits((unsigned long long)__double_as_longlong(x), &slow);
+  return slow ? (float)x : __uint_as_float(u);
+}
+
 // van Leer (harmonic) limited slope from the two one-sided differences (Sec. 2.3).
 template <typename T> __device__ __forceinline__ T vanleer(T dl, T dr) {
   const T prod = dl * dr;
