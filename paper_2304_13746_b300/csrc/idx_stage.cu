@@ -158,20 +158,25 @@ __device__ __forceinline__ void prims_body(const Geo& g, const Ptr8<const double
     // 1/rho only scales the kinetic energy: an FP32 seed refined by one Newton-Raphson
     // step y1 = y0 + y0 (1 - rho y0), which squares the seed's relative error (~1e-14
     // after the step), in place of an FP64 division (densities inside the FP32 range,
-    // which the FP32 sweeps need anyway).
-    const double y0 = f2d(__frcp_rn(d2f(rho)));
-    const double ir = fma(y0, fma(-rho, y0, 1.0), y0);
+    // which the FP32 sweeps need anyway).  The step is taken on y0/2, giving 1/(2 rho).
+    const float y0f = __frcp_rn(d2f(rho));
+    const double y0h = f2d(0.5f * y0f);
+    const double irh = fma(y0h, fma(-rho, f2d(y0f), 1.0), y0h);
     const double mx = U.f[1][c], my = U.f[2][c], mz = U.f[3][c];
     const double sx = U.f[5][c] + U.f[5][shifted(g, c, i, 0, 1)];  // 2 B_c
     const double sy = U.f[6][c] + U.f[6][shifted(g, c, j, 1, 1)];
     const double sz = U.f[7][c] + U.f[7][shifted(g, c, k, 2, 1)];
-    const double kin = 0.5 * (mx * mx + my * my + mz * mz) * ir;
-    const double mag = 0.125 * (sx * sx + sy * sy + sz * sz);
-    const double P = g.gm1 * (U.f[4][c] - kin - mag);
-    const float irf = d2f(ir);
+    // P = (gamma - 1) (E - |m|^2 / (2 rho) - |2 B_c|^2 / 8), FP64 with fused steps
+    const double msq = fma(mx, mx, fma(my, my, mz * mz));
+    const double ssq = fma(sx, sx, fma(sy, sy, sz * sz));
+    const double P = g.gm1 * fma(-0.125, ssq, fma(-msq, irh, U.f[4][c]));
+    const float irf = 2.0f * d2f(irh);
     const float vx = d2f(mx) * irf, vy = d2f(my) * irf, vz = d2f(mz) * irf;
-    if (!(rho > 0.0) || !(P > 0.0) || !isfinite(rho) || !isfinite(P) || !isfinite(vx) ||
-        !isfinite(vy) || !isfinite(vz))
+    // 0 < rho, P < infinity, tested on the bit patterns (FP64 compares take FP64 slots)
+    auto pos_finite = [](double x) {
+      return (unsigned long long)__double_as_longlong(x) - 1ull < 0x7fefffffffffffffull;
+    };
+    if (!pos_finite(rho) || !pos_finite(P) || !isfinite(vx) || !isfinite(vy) || !isfinite(vz))
       flag_bad(ctrl, c);
     W.f[0][c] = d2f(rho); W.f[1][c] = vx; W.f[2][c] = vy; W.f[3][c] = vz;
     W.f[4][c] = d2f(P);

@@ -88,16 +88,18 @@ __host__ __device__ __forceinline__ unsigned long long f2d_bits(unsigned u, bool
   const unsigned hi = (u & 0x80000000u) | (a == 0u ? 0u : (a >> 3) + 0x38000000u);
   return ((unsigned long long)hi << 32) | (unsigned long long)(u << 29);
 }
-// binary64 -> binary32 for |x| in [2^-126, 2^128) (and zeros): rebias the exponent, then
-// round the 29 dropped mantissa bits to nearest, ties to even; a carry out of the
-// mantissa steps the exponent (up to infinity, as overflow under rounding to nearest).
-__host__ __device__ __forceinline__ unsigned d2f_bits(unsigned long long b, bool* slow) {
-  const unsigned long long a = b & 0x7fffffffffffffffull;
-  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  *slow = a != 0ull && (a - 0x3810000000000000ull) >= 0x0fe0000000000000ull;
-  const unsigned long long r = a - 0x3800000000000000ull;
-  const unsigned q = (unsigned)((r + 0x0fffffffull + ((r >> 29) & 1ull)) >> 29);
-  return sign | (a == 0ull ? 0u : q);
+// binary64 -> binary32 for |x| in [2^-126, 2^128) (and zeros), on the two 32-bit words:
+// the float's exponent and mantissa are the rebiased high word shifted left by 3 with
+// the top 3 bits of the low word; the low word's other 29 bits round it to nearest, ties
+// to even.  A carry out of the mantissa steps the exponent (up to infinity, as overflow
+// under rounding to nearest).
+__host__ __device__ __forceinline__ unsigned d2f_bits(unsigned hi, unsigned lo, bool* slow) {
+  const unsigned ahi = hi & 0x7fffffffu;
+  const bool zero = (ahi | lo) == 0u;
+  *slow = !zero && (ahi - 0x38100000u) >= 0x0fe00000u;
+  const unsigned q = ((ahi - 0x38000000u) << 3) | (lo >> 29);
+  const unsigned up = ((lo & 0x1fffffffu) + (q & 1u)) > 0x10000000u ? 1u : 0u;
+  return (hi & 0x80000000u) | (zero ? 0u : q + up);
 }
 __device__ __forceinline__ double f2d(float x) {
   bool slow;
@@ -106,7 +108,7 @@ __device__ __forceinline__ double f2d(float x) {
 }
 __device__ __forceinline__ float d2f(double x) {
   bool slow;
-  const unsigned u = d2f_bits((unsigned long long)__double_as_longlong(x), &slow);
+  const unsigned u = d2f_bits((unsigned)__double2hiint(x), (unsigned)__double2loint(x), &slow);
   return slow ? (float)x : __uint_as_float(u);
 }
 

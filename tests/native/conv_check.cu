@@ -71,7 +71,7 @@ int main(int argc, char** argv) {
       double d;
       memcpy(&d, &db, 8);
       bool slow;
-      const uint32_t q = d2f_bits(db, &slow);
+      const uint32_t q = d2f_bits((uint32_t)(db >> 32), (uint32_t)db, &slow);
       if (!slow) {
         const float ref = (float)d;
         uint32_t rb;
