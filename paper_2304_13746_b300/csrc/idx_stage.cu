@@ -99,7 +99,7 @@ template <typename T> struct Ptr8 {
 // FP64 value into the bulk type and back, through the integer-pipe conversions for FP32.
 template <typename T> __device__ __forceinline__ T to_bulk(double x);
 template <> __device__ __forceinline__ double to_bulk<double>(double x) { return x; }
-template <> __device__ __forceinline__ float to_bulk<float>(double x) { return d2f(x); }
+template <> __device__ __forceinline__ float to_bulk<float>(double x) { return d2f_warp(x); }
 __device__ __forceinline__ double to_f64(double x) { return x; }
 __device__ __forceinline__ double to_f64(float x) { return f2d(x); }
 
@@ -159,7 +159,8 @@ __device__ __forceinline__ void prims_body(const Geo& g, const Ptr8<const double
     // step y1 = y0 + y0 (1 - rho y0), which squares the seed's relative error (~1e-14
     // after the step), in place of an FP64 division (densities inside the FP32 range,
     // which the FP32 sweeps need anyway).  The step is taken on y0/2, giving 1/(2 rho).
-    const float y0f = __frcp_rn(d2f(rho));
+    const float rhof = d2f(rho);
+    const float y0f = __frcp_rn(rhof);
     const double y0h = f2d(0.5f * y0f);
     const double irh = fma(y0h, fma(-rho, f2d(y0f), 1.0), y0h);
     const double mx = U.f[1][c], my = U.f[2][c], mz = U.f[3][c];
@@ -178,7 +179,7 @@ __device__ __forceinline__ void prims_body(const Geo& g, const Ptr8<const double
     };
     if (!pos_finite(rho) || !pos_finite(P) || !isfinite(vx) || !isfinite(vy) || !isfinite(vz))
       flag_bad(ctrl, c);
-    W.f[0][c] = d2f(rho); W.f[1][c] = vx; W.f[2][c] = vy; W.f[3][c] = vz;
+    W.f[0][c] = rhof; W.f[1][c] = vx; W.f[2][c] = vy; W.f[3][c] = vz;
     W.f[4][c] = d2f(P);
     W.f[5][c] = 0.5f * d2f(sx); W.f[6][c] = 0.5f * d2f(sy); W.f[7][c] = 0.5f * d2f(sz);
   }
@@ -691,13 +692,13 @@ __device__ __forceinline__ T update_body(const Geo& g, const Ptr8<const double>&
       if constexpr (std::is_same<T, double>::value) return g.inv_dl[d];
       else return g.inv_dlf[d];
     };
-    const float dtf = d2f(dt);
+    const float dtf = d2f_warp(dt);
     auto accumulate = [&](int f, T div) -> double {
       if constexpr (std::is_same<T, double>::value) {
         return Uin.f[f][c] - dt * div;
       } else {
         if (COMBINE) {
-          const float wdt = d2f(w * dt);
+          const float wdt = d2f_warp(w * dt);
           if (w == w0) return fma(w, U0.f[f][c] + Uin.f[f][c], f2d(-wdt * div));
           return fma(w0, U0.f[f][c], w * Uin.f[f][c]) + f2d(-wdt * div);
         }

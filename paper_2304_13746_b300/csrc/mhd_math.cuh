@@ -101,6 +101,13 @@ __host__ __device__ __forceinline__ unsigned d2f_bits(unsigned hi, unsigned lo, 
   const unsigned up = ((lo & 0x1fffffffu) + (q & 1u)) > 0x10000000u ? 1u : 0u;
   return (hi & 0x80000000u) | (zero ? 0u : q + up);
 }
+// Where the fallback converter runs decides the cost, and the compiler may execute a
+// guarded conversion on every lane and select afterwards.  Three forms, each used where
+// it measured fastest: f2d selects (its guard compiles to a branch), d2f calls an
+// out-of-line converter (a real branch; for kernels with registers to spare), d2f_warp
+// runs the converter only in warps with a lane outside the fast range (no call, so no
+// spills in the register-heavy sweeps).
+__device__ __noinline__ float d2f_slow(double x) { return (float)x; }
 __device__ __forceinline__ double f2d(float x) {
   bool slow;
   const unsigned long long b = f2d_bits(__float_as_uint(x), &slow);
@@ -109,7 +116,18 @@ __device__ __forceinline__ double f2d(float x) {
 __device__ __forceinline__ float d2f(double x) {
   bool slow;
   const unsigned u = d2f_bits((unsigned)__double2hiint(x), (unsigned)__double2loint(x), &slow);
-  return slow ? (float)x : __uint_as_float(u);
+  float r = __uint_as_float(u);
+  if (__builtin_expect(slow, 0)) r = d2f_slow(x);
+  return r;
+}
+// The vote names only the lanes executing it (__activemask): callers may sit behind an
+// early return or a bounds test, where the rest of the warp never gets here.
+__device__ __forceinline__ float d2f_warp(double x) {
+  bool slow;
+  const unsigned u = d2f_bits((unsigned)__double2hiint(x), (unsigned)__double2loint(x), &slow);
+  float r = __uint_as_float(u);
+  if (__any_sync(__activemask(), slow)) r = slow ? (float)x : r;
+  return r;
 }
 
 // van Leer (harmonic) limited slope from the two one-sided differences (Sec. 2.3).
