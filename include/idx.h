@@ -219,6 +219,12 @@ int idx_batch_poll(idx_batch* batch, idx_sim** finished, int cap, int* n_finishe
 /* Sweep shapes chosen by the batch's autotuner (as idx_sweep_shapes). */
 int idx_batch_shapes(const idx_batch* batch, int shapes[3]);
 
+/* Fix the batch's sweep shapes instead of autotuning them (values as idx_sweep_shapes; a
+ * staged shape 116 / 132 applies to the members whose grids fit its tiles, the others
+ * march 16 faces per thread).  IDX_EINVAL for an unknown shape.  A measurement and
+ * testing aid, not part of the method. */
+int idx_batch_set_shapes(idx_batch* batch, const int shapes[3]);
+
 void idx_batch_destroy(idx_batch* batch);
 
 /* ---- Allocation-free cycle (no counterpart in the paper) -------------------------

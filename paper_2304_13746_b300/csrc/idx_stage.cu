@@ -335,22 +335,21 @@ __device__ __forceinline__ void flag_timeout(Ctrl* ctrl) {
   atomicCAS(&ctrl->err, 0, IDX_ETIMEOUT);
 }
 
+// One staged tile: tile index -> (x tile, D tile, coordinate along the third direction),
+// copies issued by thread 0 onto `bar`, bounded wait for the phase of parity `parity`,
+// then the march.  Returns false (the same on every thread of the block) if the copies
+// did not land in time; the caller then records the timeout and leaves.
 template <typename T, int D, int L>
-__global__ void __launch_bounds__(8 * L, sizeof(T) == 4 ? 96 / L : 1)
-    k_sweep_tma(Geo g, const __grid_constant__ CUtensorMap tm_body,
-                const __grid_constant__ CUtensorMap tm_halo, const double* bface, Ptr8<T> F,
-                Ctrl* ctrl, int check_dt) {
+__device__ __forceinline__ bool tma_tile(const Geo& g, const CUtensorMap* tm_body,
+                                         const CUtensorMap* tm_halo, const double* bface,
+                                         const Ptr8<T>& F, int tile_index, T* tile,
+                                         uint64_t* bar, uint32_t parity) {
   static_assert(D == 1 || D == 2, "staged sweeps run along y or z");
-  if (check_dt && !(ctrl->dt > 0.0)) return;
   constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
   constexpr int ROWS = L + 4, PLANE = ROWS * 32;
   constexpr int O = (D == 1) ? 2 : 1;  // the transverse direction that is not x
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  T* tile = reinterpret_cast<T*>(smem_raw);  // [7][ROWS][32]: variable, row along D, x
-  __shared__ __align__(8) uint64_t bar;
-
   const int ntx = g.n[0] >> 5, ntd = g.n[D] / L;
-  int b = blockIdx.x;
+  int b = tile_index;
   const int x0 = (b % ntx) * 32;
   b /= ntx;
   const int t0 = (b % ntd) * L;
@@ -359,12 +358,7 @@ __global__ void __launch_bounds__(8 * L, sizeof(T) == 4 ? 96 / L : 1)
   constexpr int var[7] = {0, 1 + D, 1 + A, 1 + B, 4, 5 + A, 5 + B};
 
   if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
-    mbar_fence_init();
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    mbar_arrive_expect_tx(&bar, 7u * PLANE * sizeof(T));
+    mbar_arrive_expect_tx(bar, 7u * PLANE * sizeof(T));
     int lo = t0 - 2;
     if (lo < 0) lo += g.n[D];
     int hi = t0 + L;
@@ -373,13 +367,13 @@ __global__ void __launch_bounds__(8 * L, sizeof(T) == 4 ? 96 / L : 1)
     for (int q = 0; q < 7; ++q) {
       T* dst = tile + q * PLANE;
       if (D == 1) {
-        tma_load_4d(dst, &tm_halo, x0, lo, co, var[q], &bar);
-        tma_load_4d(dst + 2 * 32, &tm_body, x0, t0, co, var[q], &bar);
-        tma_load_4d(dst + (L + 2) * 32, &tm_halo, x0, hi, co, var[q], &bar);
+        tma_load_4d(dst, tm_halo, x0, lo, co, var[q], bar);
+        tma_load_4d(dst + 2 * 32, tm_body, x0, t0, co, var[q], bar);
+        tma_load_4d(dst + (L + 2) * 32, tm_halo, x0, hi, co, var[q], bar);
       } else {
-        tma_load_4d(dst, &tm_halo, x0, co, lo, var[q], &bar);
-        tma_load_4d(dst + 2 * 32, &tm_body, x0, co, t0, var[q], &bar);
-        tma_load_4d(dst + (L + 2) * 32, &tm_halo, x0, co, hi, var[q], &bar);
+        tma_load_4d(dst, tm_halo, x0, co, lo, var[q], bar);
+        tma_load_4d(dst + 2 * 32, tm_body, x0, co, t0, var[q], bar);
+        tma_load_4d(dst + (L + 2) * 32, tm_halo, x0, co, hi, var[q], bar);
       }
     }
   }
@@ -389,11 +383,8 @@ __global__ void __launch_bounds__(8 * L, sizeof(T) == 4 ? 96 / L : 1)
   T bn[4];  // the Riemann solves take the normal field in the bulk type
 #pragma unroll
   for (int q = 0; q < 4; ++q) bn[q] = to_bulk<T>(bface[cbase + (t0 + f0 + q) * g.stride[D]]);
-  if (!mbar_wait(&bar, 0, kWaitNs)) {
-    if (threadIdx.x == 0) flag_timeout(ctrl);
-    mbar_wait(&bar, 0, kWaitNs);  // let copies in flight land before the block leaves
-    return;
-  }
+  const bool landed = mbar_wait(bar, parity, kWaitNs);
+  if (__syncthreads_or(!landed)) return false;
   const T gamma = geo_gamma<T>(g);
   const T gm1inv = geo_gm1inv<T>(g);
   auto ld = [&](int q, int row) { return tile[q * PLANE + row * 32 + lane]; };
@@ -436,6 +427,32 @@ __global__ void __launch_bounds__(8 * L, sizeof(T) == 4 ? 96 / L : 1)
       }
     }
   }
+  return true;
+}
+
+// After a timeout: record it, give the copies in flight a bounded time to land in
+// shared memory, and let the block leave.
+__device__ __forceinline__ void tma_give_up(Ctrl* ctrl, uint64_t* bar, uint32_t parity) {
+  if (threadIdx.x == 0) flag_timeout(ctrl);
+  mbar_wait(bar, parity, kWaitNs);
+}
+
+template <typename T, int D, int L>
+__global__ void __launch_bounds__(8 * L, sizeof(T) == 4 ? 96 / L : 1)
+    k_sweep_tma(Geo g, const __grid_constant__ CUtensorMap tm_body,
+                const __grid_constant__ CUtensorMap tm_halo, const double* bface, Ptr8<T> F,
+                Ctrl* ctrl, int check_dt) {
+  if (check_dt && !(ctrl->dt > 0.0)) return;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* tile = reinterpret_cast<T*>(smem_raw);  // [7][L + 4][32]: variable, row along D, x
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (!tma_tile<T, D, L>(g, &tm_body, &tm_halo, bface, F, blockIdx.x, tile, &bar, 0))
+    tma_give_up(ctrl, &bar, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -1818,6 +1835,8 @@ extern "C" int idx_step_noalloc(const idx_grid* grid, double gamma, double cfl,
 namespace {
 
 template <typename T> struct InstT {
+  CUtensorMap tm_body[3][2];  // the member's staged-sweep maps (global memory copies)
+  CUtensorMap tm_halo[3];
   Geo g;
   Ptr8<double> U, U1;
   Ptr8<T> W;
@@ -1834,11 +1853,13 @@ struct Item {
 template <typename T> struct BatchDev {
   InstT<T>* inst;
   Item* cell;      // items of kThreads cells
-  Item* sweep[3];  // items of kThreads sweep threads, per direction
+  Item* sweep[3];  // items of kThreads marching/warp sweep threads, per direction
+  Item* tile[3];   // items of one staged tile (begin = tile index), per direction
   Ctrl* gather;    // poll buffer, one Ctrl per instance
   int n_inst;
   int n_cell;
   int n_sweep[3];
+  int n_tile[3];
 };
 
 template <typename T> __device__ __forceinline__ Ptr8<const T> dconst(const Ptr8<T>& p) {
@@ -1874,6 +1895,39 @@ __global__ void __launch_bounds__(kThreads) kb_sweep(const BatchDev<T>* B, int s
       sweep_body<T, D, (SEG > 0 ? SEG : 1)>(g, dconst(I->W), bface, I->F[D], w.begin + threadIdx.x);
     else
       sweep_x_body<T>(g, dconst(I->W), bface, I->F[D], w.begin + threadIdx.x);
+  }
+}
+
+// Staged sweep over the batch's tile items (members whose grids fit the tiles): a
+// persistent block refills its shared-memory tile item after item, the mbarrier's phase
+// parity flipping with each completed copy.
+template <typename T, int D, int L>
+__global__ void __launch_bounds__(8 * L, sizeof(T) == 4 ? 96 / L : 1)
+    kb_sweep_tma(const BatchDev<T>* B, int stage, int check) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* tile = reinterpret_cast<T*>(smem_raw);
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const int n = B->n_tile[D];
+  uint32_t parity = 0;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const Item w = B->tile[D][it];
+    const InstT<T>* I = &B->inst[w.inst];
+    if (check && !(I->ctrl->dt > 0.0)) continue;  // uniform over the block
+    const Geo g = I->g;
+    const double* bface = (stage ? I->U1 : I->U).f[5 + D];
+    if (!tma_tile<T, D, L>(g, &I->tm_body[D][L == 32 ? 1 : 0], &I->tm_halo[D], bface, I->F[D],
+                           w.begin, tile, &bar, parity)) {
+      tma_give_up(I->ctrl, &bar, parity);
+      return;
+    }
+    parity ^= 1u;
+    __syncthreads();  // every thread is done with the tile before it is refilled
+    if (threadIdx.x == 0) fence_proxy_async();
   }
 }
 
@@ -1940,8 +1994,11 @@ struct idx_batch {
   size_t host_cap;
   bool dirty;
   bool tuned;
-  int shape[3];        // sweep shape per direction (marching segment, or -1 warp x sweep)
-  int graph_shape[3];
+  int shape[3];        // sweep shape per direction (marching segment, -1 warp x sweep,
+                       // 116 / 132 staged tiles for the members that fit them)
+  int fallback[3];     // marching shape of the other members when shape[d] is staged
+  int graph_shape[3], graph_fallback[3];
+  int grid_tma[2];     // persistent blocks of the staged sweep, L = 16 / 32
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   int grid_cell, grid_sweep;
@@ -1950,8 +2007,16 @@ struct idx_batch {
 namespace {
 
 template <typename T> InstT<T> inst_of(idx_sim* s);
+template <typename T> void copy_maps(InstT<T>& I, const idx_sim* s) {
+  for (int d = 0; d < 3; ++d) {
+    I.tm_body[d][0] = s->tm_body[d][0];
+    I.tm_body[d][1] = s->tm_body[d][1];
+    I.tm_halo[d] = s->tm_halo[d];
+  }
+}
 template <> InstT<double> inst_of<double>(idx_sim* s) {
   InstT<double> I;
+  copy_maps(I, s);
   I.g = s->geo; I.U = s->U; I.U1 = s->U1; I.W = s->Wd;
   for (int d = 0; d < 3; ++d) { I.F[d] = s->Fd[d]; I.E[d] = s->Ed[d]; }
   I.ctrl = s->ctrl;
@@ -1959,6 +2024,7 @@ template <> InstT<double> inst_of<double>(idx_sim* s) {
 }
 template <> InstT<float> inst_of<float>(idx_sim* s) {
   InstT<float> I;
+  copy_maps(I, s);
   I.g = s->geo; I.U = s->U; I.U1 = s->U1; I.W = s->Wf;
   for (int d = 0; d < 3; ++d) { I.F[d] = s->Ff[d]; I.E[d] = s->Ef[d]; }
   I.ctrl = s->ctrl;
@@ -1974,22 +2040,30 @@ int sweep_threads(const Geo& g, int d, int shape) {
 template <typename T> int batch_upload(idx_batch* b) {
   const int n = (int)b->sims.size();
   std::vector<InstT<T>> inst(n);
-  std::vector<Item> cell, sweep[3];
+  std::vector<Item> cell, sweep[3], tile[3];
   for (int i = 0; i < n; ++i) {
     idx_sim* s = b->sims[i];
     inst[i] = inst_of<T>(s);
     for (int c0 = 0; c0 < s->geo.ncell; c0 += kThreads) cell.push_back({i, c0});
     for (int d = 0; d < 3; ++d) {
       if (!s->geo.active[d]) continue;
-      const int nt = sweep_threads(s->geo, d, b->shape[d]);
+      const int sd = b->shape[d];
+      const bool staged = d != 0 && (sd == 116 || sd == 132);
+      if (staged && tma_shape_ok(s, d, sd)) {
+        const Geo& g = s->geo;
+        const int ntiles = (g.n[0] / 32) * (g.n[d] / (sd - 100)) * g.n[d == 1 ? 2 : 1];
+        for (int t = 0; t < ntiles; ++t) tile[d].push_back({i, t});
+        continue;
+      }
+      const int nt = sweep_threads(s->geo, d, staged ? b->fallback[d] : sd);
       for (int t0 = 0; t0 < nt; t0 += kThreads) sweep[d].push_back({i, t0});
     }
   }
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-  const size_t need = al(sizeof(InstT<T>) * (n + 1)) + al(sizeof(Item) * (cell.size() + 1)) +
-                      al(sizeof(Item) * (sweep[0].size() + 1)) +
-                      al(sizeof(Item) * (sweep[1].size() + 1)) +
-                      al(sizeof(Item) * (sweep[2].size() + 1)) + al(sizeof(Ctrl) * (n + 1));
+  size_t need = al(sizeof(InstT<T>) * (n + 1)) + al(sizeof(Item) * (cell.size() + 1)) +
+                al(sizeof(Ctrl) * (n + 1));
+  for (int d = 0; d < 3; ++d)
+    need += al(sizeof(Item) * (sweep[d].size() + 1)) + al(sizeof(Item) * (tile[d].size() + 1));
   if (need > b->lists_cap) {
     IDX_TRY(cudaStreamSynchronize(b->stream));
     if (b->lists) cudaFree(b->lists);
@@ -2014,16 +2088,21 @@ template <typename T> int batch_upload(idx_batch* b) {
   h.inst = (InstT<T>*)p; p += al(sizeof(InstT<T>) * (n + 1));
   h.cell = (Item*)p; p += al(sizeof(Item) * (cell.size() + 1));
   for (int d = 0; d < 3; ++d) { h.sweep[d] = (Item*)p; p += al(sizeof(Item) * (sweep[d].size() + 1)); }
+  for (int d = 0; d < 3; ++d) { h.tile[d] = (Item*)p; p += al(sizeof(Item) * (tile[d].size() + 1)); }
   h.gather = (Ctrl*)p;
   h.n_inst = n;
   h.n_cell = (int)cell.size();
   for (int d = 0; d < 3; ++d) h.n_sweep[d] = (int)sweep[d].size();
+  for (int d = 0; d < 3; ++d) h.n_tile[d] = (int)tile[d].size();
   // pageable sources: each copy is staged before the call returns
   if (n) IDX_TRY(cudaMemcpyAsync(h.inst, inst.data(), sizeof(InstT<T>) * n, cudaMemcpyHostToDevice, b->stream));
   if (!cell.empty()) IDX_TRY(cudaMemcpyAsync(h.cell, cell.data(), sizeof(Item) * cell.size(), cudaMemcpyHostToDevice, b->stream));
-  for (int d = 0; d < 3; ++d)
+  for (int d = 0; d < 3; ++d) {
     if (!sweep[d].empty())
       IDX_TRY(cudaMemcpyAsync(h.sweep[d], sweep[d].data(), sizeof(Item) * sweep[d].size(), cudaMemcpyHostToDevice, b->stream));
+    if (!tile[d].empty())
+      IDX_TRY(cudaMemcpyAsync(h.tile[d], tile[d].data(), sizeof(Item) * tile[d].size(), cudaMemcpyHostToDevice, b->stream));
+  }
   IDX_TRY(cudaMemcpyAsync(b->header, &h, sizeof(h), cudaMemcpyHostToDevice, b->stream));
   IDX_TRY(cudaStreamSynchronize(b->stream));
   return IDX_OK;
@@ -2044,10 +2123,31 @@ void launch_batch_sweep_d(idx_batch* b, int shape, int stage, int check) {
   kb_sweep<T, D, kSegDefault><<<grid, kThreads, 0, b->stream>>>(B, stage, check);
 }
 
+template <typename T, int D, int L> void launch_batch_tma(idx_batch* b, int stage, int check) {
+  const BatchDev<T>* B = (const BatchDev<T>*)b->header;
+  const size_t smem = 7 * (L + 4) * 32 * sizeof(T);
+  kb_sweep_tma<T, D, L><<<b->grid_tma[L == 32 ? 1 : 0], 8 * L, smem, b->stream>>>(B, stage, check);
+}
+
+// A staged shape launches the tile kernel for the members that fit the tiles and the
+// marching fallback for the others (each loops over an empty list when it has none).
 template <typename T> void launch_batch_sweep(idx_batch* b, int d, int stage, int check) {
-  if (d == 0) launch_batch_sweep_d<T, 0>(b, b->shape[0], stage, check);
-  else if (d == 1) launch_batch_sweep_d<T, 1>(b, b->shape[1], stage, check);
-  else launch_batch_sweep_d<T, 2>(b, b->shape[2], stage, check);
+  const int sd = b->shape[d];
+  if (d != 0 && (sd == 116 || sd == 132)) {
+    if (d == 1) {
+      if (sd == 116) launch_batch_tma<T, 1, 16>(b, stage, check);
+      else launch_batch_tma<T, 1, 32>(b, stage, check);
+      launch_batch_sweep_d<T, 1>(b, b->fallback[1], stage, check);
+    } else {
+      if (sd == 116) launch_batch_tma<T, 2, 16>(b, stage, check);
+      else launch_batch_tma<T, 2, 32>(b, stage, check);
+      launch_batch_sweep_d<T, 2>(b, b->fallback[2], stage, check);
+    }
+    return;
+  }
+  if (d == 0) launch_batch_sweep_d<T, 0>(b, sd, stage, check);
+  else if (d == 1) launch_batch_sweep_d<T, 1>(b, sd, stage, check);
+  else launch_batch_sweep_d<T, 2>(b, sd, stage, check);
 }
 
 template <typename T> void launch_batch_cycle(idx_batch* b) {
@@ -2095,6 +2195,28 @@ template <typename T> int batch_tune(idx_batch* b) {
       if (ms < best) { best = ms; best_shape = cand[q]; }
     }
     b->shape[d] = best_shape;
+    // staged tiles for the members that fit them, the best marching shape for the rest
+    if (d == 0 || rc != IDX_OK) continue;
+    const int march = best_shape;
+    for (const int staged : {116, 132}) {
+      bool fits = false;
+      for (idx_sim* s : b->sims) fits = fits || (s->geo.active[d] && tma_shape_ok(s, d, staged));
+      if (!fits) continue;
+      b->shape[d] = staged;
+      b->fallback[d] = march;
+      rc = batch_upload<T>(b);
+      if (rc != IDX_OK) break;
+      launch_batch_sweep<T>(b, d, 0, 0);
+      cudaEventRecord(e0, b->stream);
+      for (int r = 0; r < 3; ++r) launch_batch_sweep<T>(b, d, 0, 0);
+      cudaEventRecord(e1, b->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = IDX_ECUDA; break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; best_shape = staged; }
+    }
+    b->shape[d] = best_shape;
+    b->fallback[d] = march;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -2110,8 +2232,9 @@ template <typename T> int batch_prepare(idx_batch* b) {
     if (rc != IDX_OK) return rc;
     b->dirty = false;
   }
-  const bool same = b->exec && b->graph_shape[0] == b->shape[0] &&
-                    b->graph_shape[1] == b->shape[1] && b->graph_shape[2] == b->shape[2];
+  bool same = b->exec != nullptr;
+  for (int d = 0; d < 3; ++d)
+    same = same && b->graph_shape[d] == b->shape[d] && b->graph_fallback[d] == b->fallback[d];
   if (same) return IDX_OK;
   if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
   if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
@@ -2119,16 +2242,35 @@ template <typename T> int batch_prepare(idx_batch* b) {
   launch_batch_cycle<T>(b);
   IDX_TRY(cudaStreamEndCapture(b->stream, &b->graph));
   IDX_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
-  for (int d = 0; d < 3; ++d) b->graph_shape[d] = b->shape[d];
+  for (int d = 0; d < 3; ++d) {
+    b->graph_shape[d] = b->shape[d];
+    b->graph_fallback[d] = b->fallback[d];
+  }
   return IDX_OK;
 }
 
+// The FP64 tiles of 32 rows take 63 KB of shared memory, above the 48 KB default.
+void allow_batch_tma_smem() {
+  const int big = 7 * (32 + 4) * 32 * (int)sizeof(double);
+  cudaFuncSetAttribute(kb_sweep_tma<double, 1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(kb_sweep_tma<double, 2, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaGetLastError();
+}
+
 template <typename T> int batch_occupancy(idx_batch* b) {
+  allow_batch_tma_smem();
   int per_sm_cell = 0, per_sm_sweep = 0;
   IDX_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_cell, kb_update<T, true>, kThreads, 0));
   IDX_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_sweep, kb_sweep<T, 1, kSegDefault>, kThreads, 0));
   b->grid_cell = b->sms * (per_sm_cell > 0 ? per_sm_cell : 1);
   b->grid_sweep = b->sms * (per_sm_sweep > 0 ? per_sm_sweep : 1);
+  int per16 = 0, per32 = 0;
+  IDX_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per16, kb_sweep_tma<T, 1, 16>, 8 * 16,
+                                                        7 * 20 * 32 * sizeof(T)));
+  IDX_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per32, kb_sweep_tma<T, 1, 32>, 8 * 32,
+                                                        7 * 36 * 32 * sizeof(T)));
+  b->grid_tma[0] = b->sms * (per16 > 0 ? per16 : 1);
+  b->grid_tma[1] = b->sms * (per32 > 0 ? per32 : 1);
   return IDX_OK;
 }
 
@@ -2154,7 +2296,10 @@ int idx_batch_create(int precision, void* stream, idx_batch** out) {
   idx_batch* b = new idx_batch();
   b->precision = precision;
   b->dirty = true;
-  for (int d = 0; d < 3; ++d) { b->shape[d] = kSegDefault; b->graph_shape[d] = 0; }
+  for (int d = 0; d < 3; ++d) {
+    b->shape[d] = b->fallback[d] = kSegDefault;
+    b->graph_shape[d] = b->graph_fallback[d] = 0;
+  }
   int rc = IDX_OK;
   if (cudaGetDevice(&b->device) != cudaSuccess) rc = IDX_ECUDA;
   if (rc == IDX_OK && cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) rc = IDX_ECUDA;
@@ -2265,6 +2410,23 @@ int idx_batch_poll(idx_batch* b, idx_sim** finished, int cap, int* n_finished, i
 int idx_batch_shapes(const idx_batch* b, int shapes[3]) {
   if (!b || !shapes) return IDX_EINVAL;
   for (int d = 0; d < 3; ++d) shapes[d] = b->shape[d];
+  return IDX_OK;
+}
+
+int idx_batch_set_shapes(idx_batch* b, const int shapes[3]) {
+  if (!b || !shapes) return IDX_EINVAL;
+  for (int d = 0; d < 3; ++d) {
+    const int x = shapes[d];
+    const bool march = x == 2 || x == 4 || x == 8 || x == 16 || x == 32;
+    if (!march && !(x == -1 && d == 0) && !((x == 116 || x == 132) && d != 0)) return IDX_EINVAL;
+  }
+  IDX_TRY(cudaStreamSynchronize(b->stream));
+  for (int d = 0; d < 3; ++d) {
+    b->shape[d] = shapes[d];
+    b->fallback[d] = kSegDefault;
+  }
+  b->tuned = true;
+  b->dirty = true;  // rebuild the work-lists for the new shapes
   return IDX_OK;
 }
 

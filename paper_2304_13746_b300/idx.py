@@ -86,6 +86,7 @@ def lib(path=LIB_PATH):
     L.idx_batch_poll.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(ctypes.c_int)]
     L.idx_batch_shapes.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.idx_batch_set_shapes.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.idx_batch_destroy.argtypes = [vp]
     L.idx_batch_destroy.restype = None
     _lib = L
@@ -322,6 +323,11 @@ class Batch:
         out = (ctypes.c_int * 3)()
         self._check(lib().idx_batch_shapes(self._h, out), "idx_batch_shapes")
         return list(out)
+
+    def set_shapes(self, shapes):
+        """Fix the batch's sweep shapes (x, y, z) instead of autotuning them."""
+        arr = (ctypes.c_int * 3)(*[int(v) for v in shapes])
+        self._check(lib().idx_batch_set_shapes(self._h, arr), "idx_batch_set_shapes")
 
     def close(self):
         if getattr(self, "_h", None):

@@ -104,6 +104,37 @@ def test_alone_equals_mix(precision):
     assert all(t == 0.0 for t, _ in n0)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("shapes", [(-1, 116, 116), (16, 132, 132)])
+def test_staged_batch_sweeps(precision, shapes):
+    # staged tiles for the members that fit them (nx % 32 == 0, n_d a multiple of the
+    # tile), marching for the others, in one batched cycle
+    cases = [
+        (inputs.turbulent_box(32, seed=5), 0.01),             # fits 16 and 32
+        (inputs.random_smooth((16, 32, 64), seed=8), 0.02),   # z fits 16 only
+        (inputs.orszag_tang_2d(64), 0.03),                     # 2D: y only
+        (inputs.turbulent_box(24, seed=2), 0.01),             # nx = 24: marches
+        (inputs.sod_double_tube(40, axis=2), 0.03),           # 1D along z: marches
+    ]
+    alone = run_alone(cases, precision)
+    b = idx.Batch(precision)
+    b.set_shapes(shapes)
+    sims = [new_sim(ic, precision) for ic, _ in cases]
+    for s, (_, t_end) in zip(sims, cases):
+        b.add(s, t_end)
+    run_batch_until_done(b, sims)
+    assert b.shapes() == list(shapes)
+    for s, (ic, t_end), (ref, n_ref, t_ref) in zip(sims, cases, alone):
+        assert s.time()[0] == t_ref == t_end
+        err = scaled_error(s.get_state(), ref)
+        print(f"{precision} {shapes} {ic.name}: alone vs staged batch {err:.2e}")
+        assert err <= TOL[precision], (ic.name, err)
+    for s in sims:
+        b.remove(s)
+        s.close()
+    b.close()
+
+
 def test_members_join_and_leave():
     cases = mix()
     alone = run_alone(cases, "fp64")
