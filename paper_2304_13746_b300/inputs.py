@@ -296,6 +296,53 @@ def sod_double_tube(n_per_unit=200, axis=0, gamma=1.4):
               tuple(lengths), gamma, "sod_double_tube", {"n_per_unit": n_per_unit, "axis": axis})
 
 
+def brio_wu_double_tube(n_per_unit=200, axis=0, gamma=5.0 / 3.0):
+    """Brio-Wu MHD shock tube (Sec. 4.1; gamma = 5/3 as the paper runs it): (rho, P, B_t) =
+    (1, 1, 1) | (0.125, 0.1, -1), v = 0, normal field 0.75, as a periodic double tube of
+    length 2 along ``axis`` like ``sod_double_tube`` (left state in [0.5, 1.5)).  The normal
+    field is the component along ``axis``, the transverse one the next component in cyclic
+    order, so the three orientations are the same problem rotated."""
+    n = 2 * n_per_unit
+    c = _centres(n, 2.0)
+    left = (c >= 0.5) & (c < 1.5)
+    shape = [1, 1, 1]
+    shape[2 - axis] = n
+    shape = tuple(shape)
+    rho = np.where(left, 1.0, 0.125).reshape(shape).copy()
+    P = np.where(left, 1.0, 0.1).reshape(shape).copy()
+    bt = np.where(left, 1.0, -1.0).reshape(shape).copy()
+    z = np.zeros(shape)
+    B = [z.copy(), z.copy(), z.copy()]
+    B[axis] = _full(shape, 0.75)
+    B[(axis + 1) % 3] = bt
+    lengths = [1.0, 1.0, 1.0]
+    lengths[axis] = 2.0
+    return IC([rho, z.copy(), z.copy(), z.copy(), P] + B, tuple(lengths), gamma,
+              "brio_wu_double_tube", {"n_per_unit": n_per_unit, "axis": axis})
+
+
+def sedov_blast(n=64, energy=1.0, r_in=None, rho0=1.0, P0=1e-2, gamma=5.0 / 3.0):
+    """Sedov-Taylor blast (Sec. 4.1): a uniform gas at rest, rho = 1, P = 1e-2, on the periodic
+    unit cube, with the thermal energy E = sum over cells with centre inside r < r_in of
+    P dV / (gamma - 1) = energy deposited at the centre (0.5, 0.5, 0.5).  r_in defaults to 3.5
+    cells; no magnetic field."""
+    h = 1.0 / n
+    if r_in is None:
+        r_in = 3.5 * h
+    xc = _centres(n, 1.0)
+    X, Y, Z = _mesh(xc, xc, xc)
+    r2 = (X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2
+    inside = np.broadcast_to(r2 < r_in * r_in, (n, n, n))
+    n_in = int(inside.sum())
+    P_in = (gamma - 1.0) * energy / (n_in * h ** 3)
+    shape = (n, n, n)
+    P = np.where(inside, P_in, P0).astype(np.float64)
+    z = np.zeros(shape)
+    return IC([_full(shape, rho0), z.copy(), z.copy(), z.copy(), P, z.copy(), z.copy(), z.copy()],
+              (1.0, 1.0, 1.0), gamma, "sedov_blast",
+              {"n": n, "energy": energy, "r_in": r_in, "cells_in": n_in, "P0": P0, "rho0": rho0})
+
+
 def uniform(shape=(4, 4, 4), lengths=(1.0, 1.0, 1.0), gamma=5.0 / 3.0,
             rho=1.3, v=(0.3, -0.2, 0.1), P=0.7, B=(0.4, -0.5, 0.25)):
     p = [_full(shape, rho), _full(shape, v[0]), _full(shape, v[1]), _full(shape, v[2]),

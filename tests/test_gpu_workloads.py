@@ -1,0 +1,82 @@
+"""Brio-Wu and Sedov-Taylor on the GPU (Sec. 4.1 problems): parity with the oracle over
+whole runs, and the blast radius against the self-similar solution at a resolution the
+oracle cannot reach in a test."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2304_13746_b300 import build as idx_build
+from paper_2304_13746_b300 import idx, inputs
+
+sys.path.insert(0, os.path.dirname(__file__))
+import sedov_taylor  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    idx_build.build()
+    idx.lib()
+
+
+def field_errors(g, o):
+    rho, E = np.abs(o[0]), np.abs(o[4])
+    msc = float(np.max(np.sqrt(2.0 * rho * E)))
+    bsc = float(np.max(np.sqrt(2.0 * E)))
+    own = [float(np.max(np.abs(o[f]))) for f in range(8)]
+    sc = [own[0], max(own[1], msc), max(own[2], msc), max(own[3], msc), own[4],
+          max(own[5], bsc), max(own[6], bsc), max(own[7], bsc)]
+    return [float(np.max(np.abs(np.asarray(g[f]) - o[f]))) / max(sc[f], 1e-300) for f in range(8)]
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_brio_wu_run_matches_oracle(axis):
+    ic = inputs.brio_wu_double_tube(100, axis=axis)
+    o = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, 0.4)
+    s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, "fp64")
+    s.set_primitive(ic.prim)
+    n_o = o.advance(0.1)
+    n_g = s.advance(0.1)
+    assert n_g == n_o
+    err = field_errors(s.get_state(), o.u)
+    print(f"brio-wu axis {axis}: {n_g} cycles, max err {max(err):.2e}")
+    assert max(err) <= 1e-10, err
+    s.close()
+
+
+def test_sedov_blast_matches_oracle():
+    ic = inputs.sedov_blast(32)
+    o = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, 0.4)
+    s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, "fp64")
+    s.set_primitive(ic.prim)
+    for _ in range(30):
+        dt = o.step()
+        assert s.step(want_dt=True) == pytest.approx(dt, rel=1e-12)
+    err = field_errors(s.get_state(), o.u)
+    print(f"sedov 32^3, 30 cycles: max err {max(err):.2e}")
+    assert max(err) <= 1e-10, err
+    s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 0.02), ("fp32", 0.02)])
+def test_sedov_blast_radius_at_128(precision, tol):
+    ic = inputs.sedov_blast(128)
+    s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, precision)
+    s.set_primitive(ic.prim)
+    t_end = 0.05
+    n = s.advance(t_end)
+    u = s.get_state()
+    s.close()
+    R = sedov_taylor.density_peak_radius(u[0])
+    R_th = sedov_taylor.shock_radius(1.0, 1.0, t_end, ic.gamma)
+    print(f"sedov 128^3 {precision}: {n} cycles, R {R:.4f} vs {R_th:.4f}")
+    assert R == pytest.approx(R_th, rel=tol)
+    assert abs(u[4].sum() - sum(ic.prim[4].ravel()) / (ic.gamma - 1)) <= 1e-12 * u[4].sum()
+    # the set-up is symmetric under axis swaps; the sweeps differ only by rounding
+    scale = np.abs(u[0]).max()
+    for axes in ((0, 2, 1), (1, 0, 2), (2, 1, 0)):
+        assert np.abs(u[0] - u[0].transpose(axes)).max() <= (1e-9 if precision == "fp64" else 1e-3) * scale
