@@ -75,8 +75,10 @@ def test_sedov_blast_radius_at_128(precision, tol):
     R_th = sedov_taylor.shock_radius(1.0, 1.0, t_end, ic.gamma)
     print(f"sedov 128^3 {precision}: {n} cycles, R {R:.4f} vs {R_th:.4f}")
     assert R == pytest.approx(R_th, rel=tol)
-    # total energy: conserved to the rounding of ~1500 cycles of 2M-cell sums
-    assert abs(u[4].sum() - ic.prim[4].sum() / (ic.gamma - 1)) <= 1e-10 * u[4].sum()
+    # total energy: conserved to the rounding of ~1500 cycles of 2M-cell sums; the FP32
+    # bulk forms each cell's flux difference in FP32, so its sums telescope to FP32 rounding
+    etol = 1e-10 if precision == "fp64" else 1e-7
+    assert abs(u[4].sum() - ic.prim[4].sum() / (ic.gamma - 1)) <= etol * u[4].sum()
     # the set-up is symmetric under axis swaps; the sweeps differ only by rounding
     scale = np.abs(u[0]).max()
     for axes in ((0, 2, 1), (1, 0, 2), (2, 1, 0)):
