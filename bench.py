@@ -481,10 +481,12 @@ def main():
                    "idx_step, idx_get_state to pinned host"}
     sim.close()
 
-    def time_variant(precision, **kw):
-        # another configuration on the same box, same timing rules
-        sv = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, precision, stream=stream.cuda_stream, **kw)
-        sv.set_primitive(ic.prim)
+    def time_variant(precision, ic_v=None, **kw):
+        # another configuration (same box unless given), same timing rules
+        ic_v = ic if ic_v is None else ic_v
+        sv = idx.Sim(ic_v.shape, ic_v.lengths, ic_v.gamma, 0.4, precision, stream=stream.cuda_stream,
+                     **kw)
+        sv.set_primitive(ic_v.prim)
         for _ in range(args.warmup):
             sv.step()
         torch.cuda.synchronize()
@@ -505,6 +507,12 @@ def main():
         variants["fp32_bulk"] = time_variant("fp32")
         variants["fp64_vector_potential"] = time_variant("fp64", induction="potential")
         variants["fp64_vector_potential"]["note"] = "Eqs. 7-8: edge potential stepped, B = Bref + curl A"
+        # the paper's own performance problem (Sec. 5): 3D Orszag-Tang, FP64, at this box size
+        ot = inputs.orszag_tang_3d(args.n)
+        variants["fp64_orszag_tang_3d"] = time_variant("fp64", ot)
+        variants["fp64_orszag_tang_3d"]["note"] = (
+            f"3D Orszag-Tang {args.n}^3 (Sec. 5 performance problem); the paper reports ~121 Mcell/s "
+            "per V100 at 256^3 per GPU (4-GPU node, 484 Mcell/s): context, another machine")
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

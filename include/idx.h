@@ -132,8 +132,8 @@ int idx_time(const idx_sim* sim, double* t, double* next_dt);
 /* RK2 cycles taken since the last idx_set_state / idx_set_primitive.  Synchronises. */
 int idx_step_count(const idx_sim* sim, int64_t* nsteps);
 
-/* Device bytes idx_create allocates for this grid and precision with RK2 (FP64 408 B per
- * cell, FP32 bulk 268 B per cell, plus alignment; RK3 adds 64 B per cell); no device
+/* Device bytes idx_create allocates for this grid and precision with RK2 (FP64 432 B per
+ * cell, FP32 bulk 280 B per cell, plus alignment; RK3 adds 64 B per cell); no device
  * call.  For admission control. */
 int idx_footprint(const idx_grid* grid, int precision, uint64_t* bytes);
 

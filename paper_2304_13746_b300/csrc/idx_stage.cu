@@ -96,6 +96,13 @@ template <typename T> struct Ptr8 {
   T* f[8];
 };
 
+// Cell-centre EMF components -(v x B)_e of every cell, formed once per stage by the
+// primitive recovery for the E^c kernel (each cell's value serves the 4 edges around it
+// in each of 3 directions).  Null pointers: the E^c kernel forms them itself.
+template <typename T> struct CellEmf {
+  T* f[3];
+};
+
 // FP64 value into the bulk type and back, through the integer-pipe conversions for FP32.
 template <typename T> __device__ __forceinline__ T to_bulk(double x);
 template <> __device__ __forceinline__ double to_bulk<double>(double x) { return x; }
@@ -134,7 +141,8 @@ __device__ __forceinline__ void flag_bad(Ctrl* ctrl, int c) {
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void prims_body(const Geo& g, const Ptr8<const double>& U,
-                                           const Ptr8<T>& W, Ctrl* ctrl, int c) {
+                                           const Ptr8<T>& W, const CellEmf<T>& cc, Ctrl* ctrl,
+                                           int c) {
   int i, j, k;
   coords(g, c, i, j, k);
   const double rho = U.f[0][c];
@@ -152,6 +160,11 @@ __device__ __forceinline__ void prims_body(const Geo& g, const Ptr8<const double
       flag_bad(ctrl, c);
     W.f[0][c] = rho; W.f[1][c] = vx; W.f[2][c] = vy; W.f[3][c] = vz;
     W.f[4][c] = P;   W.f[5][c] = bx; W.f[6][c] = by; W.f[7][c] = bz;
+    if (cc.f[0]) {
+      cc.f[0][c] = -(vy * bz - vz * by);
+      cc.f[1][c] = -(vz * bx - vx * bz);
+      cc.f[2][c] = -(vx * by - vy * bx);
+    }
   } else {
     // FP32 bulk: the energy-to-pressure recovery stays FP64 (kinetic and magnetic
     // energies from the FP64 state); the velocities and cell-centre B go out in FP32.
@@ -181,16 +194,22 @@ __device__ __forceinline__ void prims_body(const Geo& g, const Ptr8<const double
       flag_bad(ctrl, c);
     W.f[0][c] = rhof; W.f[1][c] = vx; W.f[2][c] = vy; W.f[3][c] = vz;
     W.f[4][c] = d2f(P);
-    W.f[5][c] = 0.5f * d2f(sx); W.f[6][c] = 0.5f * d2f(sy); W.f[7][c] = 0.5f * d2f(sz);
+    const float bx = 0.5f * d2f(sx), by = 0.5f * d2f(sy), bz = 0.5f * d2f(sz);
+    W.f[5][c] = bx; W.f[6][c] = by; W.f[7][c] = bz;
+    if (cc.f[0]) {
+      cc.f[0][c] = -(vy * bz - vz * by);
+      cc.f[1][c] = -(vz * bx - vx * bz);
+      cc.f[2][c] = -(vx * by - vy * bx);
+    }
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_prims(Geo g, Ptr8<const double> U, Ptr8<T> W,
-                                                    Ctrl* ctrl, int check_dt) {
+                                                    CellEmf<T> cc, Ctrl* ctrl, int check_dt) {
   if (check_dt && !(ctrl->dt > 0.0)) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < g.ncell) prims_body<T>(g, U, W, ctrl, c);
+  if (c < g.ncell) prims_body<T>(g, U, W, cc, ctrl, c);
 }
 
 // Conserved state from primitives (cell-centre rho, v, P; face B).
@@ -542,7 +561,8 @@ __global__ void __launch_bounds__(kThreads) k_sweep_x(Geo g, Ptr8<const T> W, co
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ T edge_emf(const Geo& g, int e, int c, const int ijk[3],
-                                      const Ptr8<const T>& W, const Ptr8<const T>* F) {
+                                      const Ptr8<const T>& W, const Ptr8<const T>* F,
+                                      const T* cce) {
   const int a = (e + 1) % 3, b = (e + 2) % 3;
   const Ptr8<const T>& Fa = F[a];
   const Ptr8<const T>& Fb = F[b];
@@ -553,7 +573,9 @@ __device__ __forceinline__ T edge_emf(const Geo& g, int e, int c, const int ijk[
   const T Y0 = Fb.f[6][c], Y1 = Fb.f[6][ca];
   const T Fa0 = Fa.f[0][c], Fa1 = Fa.f[0][cb];
   const T Fb0 = Fb.f[0][c], Fb1 = Fb.f[0][ca];
-  auto cc = [&](int q) { return -(W.f[1 + a][q] * W.f[5 + b][q] - W.f[1 + b][q] * W.f[5 + a][q]); };
+  auto cc = [&](int q) {
+    return cce ? cce[q] : -(W.f[1 + a][q] * W.f[5 + b][q] - W.f[1 + b][q] * W.f[5 + a][q]);
+  };
   const T C00 = cc(c), C01 = cc(cb), C10 = cc(ca), C11 = cc(cab);
   return emf_ec(X0, X1, Y0, Y1, C00, C01, C10, C11, Fa0, Fa1, Fb0, Fb1);
 }
@@ -561,7 +583,8 @@ __device__ __forceinline__ T edge_emf(const Geo& g, int e, int c, const int ijk[
 template <typename T>
 __device__ __forceinline__ void emf_body(const Geo& g, const Ptr8<const T>& W,
                                          const Ptr8<const T>& Fx, const Ptr8<const T>& Fy,
-                                         const Ptr8<const T>& Fz, T* Ex, T* Ey, T* Ez, int c) {
+                                         const Ptr8<const T>& Fz, const CellEmf<T>& cc, T* Ex,
+                                         T* Ey, T* Ez, int c) {
   int ijk[3];
   coords(g, c, ijk[0], ijk[1], ijk[2]);
   const Ptr8<const T> F[3] = {Fx, Fy, Fz};
@@ -569,17 +592,18 @@ __device__ __forceinline__ void emf_body(const Geo& g, const Ptr8<const T>& W,
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
     const int a = (e + 1) % 3, b = (e + 2) % 3;
-    if (g.active[a] && g.active[b]) out[e][c] = edge_emf(g, e, c, ijk, W, F);
+    if (g.active[a] && g.active[b]) out[e][c] = edge_emf<T>(g, e, c, ijk, W, F, cc.f[e]);
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_emf(Geo g, Ptr8<const T> W, Ptr8<const T> Fx,
-                                                  Ptr8<const T> Fy, Ptr8<const T> Fz, T* Ex,
-                                                  T* Ey, T* Ez, const Ctrl* ctrl) {
+                                                  Ptr8<const T> Fy, Ptr8<const T> Fz,
+                                                  CellEmf<T> cc, T* Ex, T* Ey, T* Ez,
+                                                  const Ctrl* ctrl) {
   if (!(ctrl->dt > 0.0)) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < g.ncell) emf_body<T>(g, W, Fx, Fy, Fz, Ex, Ey, Ez, c);
+  if (c < g.ncell) emf_body<T>(g, W, Fx, Fy, Fz, cc, Ex, Ey, Ez, c);
 }
 
 // Rotated flux slot of conserved field f (0..4) or face field 5+m for direction d.
@@ -617,8 +641,8 @@ struct PotStage {
 template <typename T, bool COMBINE>
 __global__ void __launch_bounds__(kThreads) k_emf_pot(Geo g, Ptr8<const T> W, Ptr8<const T> Fx,
                                                       Ptr8<const T> Fy, Ptr8<const T> Fz,
-                                                      PotStage P, const Ctrl* ctrl, double w,
-                                                      double w0) {
+                                                      CellEmf<T> cc, PotStage P, const Ctrl* ctrl,
+                                                      double w, double w0) {
   const double dt = ctrl->dt;
   if (!(dt > 0.0)) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -630,7 +654,7 @@ __global__ void __launch_bounds__(kThreads) k_emf_pot(Geo g, Ptr8<const T> W, Pt
   for (int e = 0; e < 3; ++e) {
     const int a = (e + 1) % 3, b = (e + 2) % 3;
     double E = 0.0;  // neither transverse direction integrated: A_e enters no face field
-    if (g.active[a] && g.active[b]) E = to_f64(edge_emf(g, e, c, ijk, W, F));
+    if (g.active[a] && g.active[b]) E = to_f64(edge_emf<T>(g, e, c, ijk, W, F, cc.f[e]));
     else if (g.active[a]) E = -to_f64(F[a].f[slot(5 + b, a)][c]);
     else if (g.active[b]) E = to_f64(F[b].f[slot(5 + a, b)][c]);
     const double As = P.in[e][c] - dt * E;
@@ -876,6 +900,8 @@ struct idx_sim {
   Ptr8<float> Wf, Ff[3];
   double* Ed[3];
   float* Ef[3];
+  CellEmf<double> Cd;   // cell-centre EMFs (null in the no-allocation path)
+  CellEmf<float> Cf;
   bool pot;             // vector-potential induction (Eqs. 7-8)
   Ptr3 A, A1, A2;       // edge potential of the state and of the stage results
   Ptr3 Bref;            // fixed face field: B = Bref + curl A
@@ -907,6 +933,10 @@ unsigned blocks_x(const Geo& g) {
   const long warps = (long)g.n[1] * g.n[2] * ((g.n[0] + 31) / 32);
   return blocks_for(warps * 32);
 }
+
+template <typename T> CellEmf<T> cell_emf(const idx_sim* s);
+template <> CellEmf<double> cell_emf<double>(const idx_sim* s) { return s->Cd; }
+template <> CellEmf<float> cell_emf<float>(const idx_sim* s) { return s->Cf; }
 
 template <typename T> Ptr8<const T> cst(const Ptr8<T>& p) {
   Ptr8<const T> q;
@@ -1024,7 +1054,8 @@ template <typename T>
 void launch_fluxes(idx_sim* s, const Ptr8<double>& Uin, const Ptr8<T>& W, Ptr8<T>* F,
                    int check_dt) {
   const Geo& g = s->geo;
-  k_prims<T><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), W, s->ctrl, check_dt);
+  k_prims<T><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), W, cell_emf<T>(s),
+                                                              s->ctrl, check_dt);
   for (int d = 0; d < 3; ++d)
     if (g.active[d]) launch_sweep<T>(s, d, W, Uin.f[5 + d], F[d], check_dt);
 }
@@ -1080,16 +1111,18 @@ void launch_emf(idx_sim* s, const StagePlan& p, int st, const Ptr8<T>& W, Ptr8<T
   const Geo& g = s->geo;
   if (!s->pot) {
     k_emf<T><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
-        g, cst(W), cst(F[0]), cst(F[1]), cst(F[2]), E[0], E[1], E[2], s->ctrl);
+        g, cst(W), cst(F[0]), cst(F[1]), cst(F[2]), cell_emf<T>(s), E[0], E[1], E[2], s->ctrl);
     return;
   }
   const PotStage P = pot_stage(s, p, st);
   if (st > 0)
     k_emf_pot<T, true><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
-        g, cst(W), cst(F[0]), cst(F[1]), cst(F[2]), P, s->ctrl, p.w[st], p.w0[st]);
+        g, cst(W), cst(F[0]), cst(F[1]), cst(F[2]), cell_emf<T>(s), P, s->ctrl, p.w[st],
+        p.w0[st]);
   else
     k_emf_pot<T, false><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
-        g, cst(W), cst(F[0]), cst(F[1]), cst(F[2]), P, s->ctrl, p.w[st], p.w0[st]);
+        g, cst(W), cst(F[0]), cst(F[1]), cst(F[2]), cell_emf<T>(s), P, s->ctrl, p.w[st],
+        p.w0[st]);
 }
 
 template <typename T, bool COMBINE, bool POT>
@@ -1231,7 +1264,7 @@ size_t sim_bytes(long long ncell, bool f32, bool rk3 = false, bool pot = false) 
   const size_t arr_d = align(sizeof(double) * ncell);
   const size_t arr_t = align((f32 ? sizeof(float) : sizeof(double)) * ncell);
   const size_t pot_arrays = pot ? (rk3 ? 12 : 9) : 0;
-  return ((rk3 ? 24 : 16) + pot_arrays) * arr_d + (8 + 24 + 3) * arr_t + align(sizeof(Ctrl));
+  return ((rk3 ? 24 : 16) + pot_arrays) * arr_d + (8 + 24 + 3 + 3) * arr_t + align(sizeof(Ctrl));
 }
 
 using EncodeTiled = PFN_cuTensorMapEncodeTiled_v12000;
@@ -1382,11 +1415,13 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
     for (int d = 0; d < 3; ++d)
       for (int f = 0; f < 8; ++f) { s->Ff[d].f[f] = (float*)p; p += arr_t; }
     for (int d = 0; d < 3; ++d) { s->Ef[d] = (float*)p; p += arr_t; }
+    for (int e = 0; e < 3; ++e) { s->Cf.f[e] = (float*)p; p += arr_t; }
   } else {
     for (int f = 0; f < 8; ++f) { s->Wd.f[f] = (double*)p; p += arr_t; }
     for (int d = 0; d < 3; ++d)
       for (int f = 0; f < 8; ++f) { s->Fd[d].f[f] = (double*)p; p += arr_t; }
     for (int d = 0; d < 3; ++d) { s->Ed[d] = (double*)p; p += arr_t; }
+    for (int e = 0; e < 3; ++e) { s->Cd.f[e] = (double*)p; p += arr_t; }
   }
   s->ctrl = (Ctrl*)p;
   if (f32) encode_sweep_maps(s, s->Wf.f[0], sizeof(float), arr_t);
@@ -1606,9 +1641,9 @@ int idx_kernel_times(idx_sim* s, int reps, double ms[6]) {
       const Ptr8<double>& Uin = *plan.in[st];
       IDX_TRY(cudaEventRecord(ev[0], s->stream));
       if (f32) {
-        k_prims<float><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), s->Wf, s->ctrl, 1);
+        k_prims<float><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), s->Wf, s->Cf, s->ctrl, 1);
       } else {
-        k_prims<double><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), s->Wd, s->ctrl, 1);
+        k_prims<double><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), s->Wd, s->Cd, s->ctrl, 1);
       }
       IDX_TRY(cudaEventRecord(ev[1], s->stream));
       for (int d = 0; d < 3; ++d) {
@@ -1842,6 +1877,7 @@ template <typename T> struct InstT {
   Ptr8<T> W;
   Ptr8<T> F[3];
   T* E[3];
+  CellEmf<T> cc;
   Ctrl* ctrl;
 };
 
@@ -1878,7 +1914,7 @@ __global__ void __launch_bounds__(kThreads) kb_prims(const BatchDev<T>* B, int s
     if (check && !(I->ctrl->dt > 0.0)) continue;
     const Geo g = I->g;
     const int c = w.begin + threadIdx.x;
-    if (c < g.ncell) prims_body<T>(g, dconst(stage ? I->U1 : I->U), I->W, I->ctrl, c);
+    if (c < g.ncell) prims_body<T>(g, dconst(stage ? I->U1 : I->U), I->W, I->cc, I->ctrl, c);
   }
 }
 
@@ -1941,7 +1977,7 @@ __global__ void __launch_bounds__(kThreads) kb_emf(const BatchDev<T>* B) {
     const Geo g = I->g;
     const int c = w.begin + threadIdx.x;
     if (c < g.ncell)
-      emf_body<T>(g, dconst(I->W), dconst(I->F[0]), dconst(I->F[1]), dconst(I->F[2]), I->E[0],
+      emf_body<T>(g, dconst(I->W), dconst(I->F[0]), dconst(I->F[1]), dconst(I->F[2]), I->cc, I->E[0],
                   I->E[1], I->E[2], c);
   }
 }
@@ -2019,6 +2055,7 @@ template <> InstT<double> inst_of<double>(idx_sim* s) {
   copy_maps(I, s);
   I.g = s->geo; I.U = s->U; I.U1 = s->U1; I.W = s->Wd;
   for (int d = 0; d < 3; ++d) { I.F[d] = s->Fd[d]; I.E[d] = s->Ed[d]; }
+  I.cc = s->Cd;
   I.ctrl = s->ctrl;
   return I;
 }
@@ -2027,6 +2064,7 @@ template <> InstT<float> inst_of<float>(idx_sim* s) {
   copy_maps(I, s);
   I.g = s->geo; I.U = s->U; I.U1 = s->U1; I.W = s->Wf;
   for (int d = 0; d < 3; ++d) { I.F[d] = s->Ff[d]; I.E[d] = s->Ef[d]; }
+  I.cc = s->Cf;
   I.ctrl = s->ctrl;
   return I;
 }

@@ -80,9 +80,9 @@ def test_null_arguments(L):
 
 
 @pytest.mark.parametrize("precision,rk,induction,per_cell", [
-    ("fp64", 2, "field", 408), ("fp32", 2, "field", 268),
-    ("fp64", 3, "field", 472), ("fp64", 2, "potential", 480),
-    ("fp64", 3, "potential", 568), ("fp32", 2, "potential", 340),
+    ("fp64", 2, "field", 432), ("fp32", 2, "field", 280),
+    ("fp64", 3, "field", 496), ("fp64", 2, "potential", 504),
+    ("fp64", 3, "potential", 592), ("fp32", 2, "potential", 352),
 ])
 def test_footprint_per_cell(L, precision, rk, induction, per_cell):
     # 64^3 cells: every array is a multiple of 256 B, so the count is exact bar the
