@@ -281,7 +281,7 @@ __device__ __forceinline__ void sweep_body(const Geo& g, const Ptr8<const T>& W,
   const T gm1inv = geo_gm1inv<T>(g);
 
   // cells f-1, f, f+1 in registers, cell f+2 prefetched one face ahead so that its
-  // loads overlap the current face's Riemann solve
+  // loads overlap the current face's Riemann solve; slope_m / slope0 hold half slopes
   T wm[7], w0[7], wp[7], wn[7], slope_m[7];
   {
     const int cm2 = cell(f0 - 2), cm1 = cell(f0 - 1), c0 = cell(f0), cp = cell(f0 + 1);
@@ -291,7 +291,7 @@ __device__ __forceinline__ void sweep_body(const Geo& g, const Ptr8<const T>& W,
       wm[q] = W.f[var[q]][cm1];
       w0[q] = W.f[var[q]][c0];
       wp[q] = W.f[var[q]][cp];
-      slope_m[q] = vanleer(wm[q] - a, w0[q] - wm[q]);
+      slope_m[q] = vanleer_half(wm[q] - a, w0[q] - wm[q]);
     }
   }
   for (int f = f0; f < f1; ++f) {
@@ -304,14 +304,14 @@ __device__ __forceinline__ void sweep_body(const Geo& g, const Ptr8<const T>& W,
     Side<T> L, R;
     T slope0[7];
 #pragma unroll
-    for (int q = 0; q < 7; ++q) slope0[q] = vanleer(w0[q] - wm[q], wp[q] - w0[q]);
-    L.r = wm[0] + T(0.5) * slope_m[0]; R.r = w0[0] - T(0.5) * slope0[0];
-    L.u = wm[1] + T(0.5) * slope_m[1]; R.u = w0[1] - T(0.5) * slope0[1];
-    L.v = wm[2] + T(0.5) * slope_m[2]; R.v = w0[2] - T(0.5) * slope0[2];
-    L.w = wm[3] + T(0.5) * slope_m[3]; R.w = w0[3] - T(0.5) * slope0[3];
-    L.p = wm[4] + T(0.5) * slope_m[4]; R.p = w0[4] - T(0.5) * slope0[4];
-    L.b1 = wm[5] + T(0.5) * slope_m[5]; R.b1 = w0[5] - T(0.5) * slope0[5];
-    L.b2 = wm[6] + T(0.5) * slope_m[6]; R.b2 = w0[6] - T(0.5) * slope0[6];
+    for (int q = 0; q < 7; ++q) slope0[q] = vanleer_half(w0[q] - wm[q], wp[q] - w0[q]);
+    L.r = wm[0] + slope_m[0]; R.r = w0[0] - slope0[0];
+    L.u = wm[1] + slope_m[1]; R.u = w0[1] - slope0[1];
+    L.v = wm[2] + slope_m[2]; R.v = w0[2] - slope0[2];
+    L.w = wm[3] + slope_m[3]; R.w = w0[3] - slope0[3];
+    L.p = wm[4] + slope_m[4]; R.p = w0[4] - slope0[4];
+    L.b1 = wm[5] + slope_m[5]; R.b1 = w0[5] - slope0[5];
+    L.b2 = wm[6] + slope_m[6]; R.b2 = w0[6] - slope0[6];
     const T bn = to_bulk<T>(bface[cf]);
     T flux[7], cmax;
     riemann_flux(g.riemann, L, R, bn, gamma, gm1inv, flux, cmax);
@@ -407,7 +407,7 @@ __device__ __forceinline__ bool tma_tile(const Geo& g, const CUtensorMap* tm_bod
   const T gamma = geo_gamma<T>(g);
   const T gm1inv = geo_gm1inv<T>(g);
   auto ld = [&](int q, int row) { return tile[q * PLANE + row * 32 + lane]; };
-  // face f uses tile rows f .. f+3 (cells f-2 .. f+1)
+  // face f uses tile rows f .. f+3 (cells f-2 .. f+1); slope_m / slope0 hold half slopes
   T wm[7], w0[7], wp[7], slope_m[7];
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
@@ -415,21 +415,21 @@ __device__ __forceinline__ bool tma_tile(const Geo& g, const CUtensorMap* tm_bod
     wm[q] = ld(q, f0 + 1);
     w0[q] = ld(q, f0 + 2);
     wp[q] = ld(q, f0 + 3);
-    slope_m[q] = vanleer(wm[q] - a, w0[q] - wm[q]);
+    slope_m[q] = vanleer_half(wm[q] - a, w0[q] - wm[q]);
   }
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     Side<T> Ls, Rs;
     T slope0[7];
 #pragma unroll
-    for (int q = 0; q < 7; ++q) slope0[q] = vanleer(w0[q] - wm[q], wp[q] - w0[q]);
-    Ls.r = wm[0] + T(0.5) * slope_m[0]; Rs.r = w0[0] - T(0.5) * slope0[0];
-    Ls.u = wm[1] + T(0.5) * slope_m[1]; Rs.u = w0[1] - T(0.5) * slope0[1];
-    Ls.v = wm[2] + T(0.5) * slope_m[2]; Rs.v = w0[2] - T(0.5) * slope0[2];
-    Ls.w = wm[3] + T(0.5) * slope_m[3]; Rs.w = w0[3] - T(0.5) * slope0[3];
-    Ls.p = wm[4] + T(0.5) * slope_m[4]; Rs.p = w0[4] - T(0.5) * slope0[4];
-    Ls.b1 = wm[5] + T(0.5) * slope_m[5]; Rs.b1 = w0[5] - T(0.5) * slope0[5];
-    Ls.b2 = wm[6] + T(0.5) * slope_m[6]; Rs.b2 = w0[6] - T(0.5) * slope0[6];
+    for (int q = 0; q < 7; ++q) slope0[q] = vanleer_half(w0[q] - wm[q], wp[q] - w0[q]);
+    Ls.r = wm[0] + slope_m[0]; Rs.r = w0[0] - slope0[0];
+    Ls.u = wm[1] + slope_m[1]; Rs.u = w0[1] - slope0[1];
+    Ls.v = wm[2] + slope_m[2]; Rs.v = w0[2] - slope0[2];
+    Ls.w = wm[3] + slope_m[3]; Rs.w = w0[3] - slope0[3];
+    Ls.p = wm[4] + slope_m[4]; Rs.p = w0[4] - slope0[4];
+    Ls.b1 = wm[5] + slope_m[5]; Rs.b1 = w0[5] - slope0[5];
+    Ls.b2 = wm[6] + slope_m[6]; Rs.b2 = w0[6] - slope0[6];
     T flux[7], cmax;
     riemann_flux(g.riemann, Ls, Rs, bn[k], gamma, gm1inv, flux, cmax);
     const int cf = cbase + (t0 + f0 + k) * g.stride[D];
@@ -531,11 +531,11 @@ __device__ __forceinline__ void sweep_x_body(const Geo& g, const Ptr8<const T>& 
     T dn = __shfl_down_sync(0xffffffffu, w0[q], 1);  // cell c+1
     if (lane == 0) up = wm1[q];
     if (lane == 31) dn = wp32[q];
-    const T slope0 = vanleer(w0[q] - up, dn - w0[q]);
+    const T slope0 = vanleer_half(w0[q] - up, dn - w0[q]);
     T slope_m = __shfl_up_sync(0xffffffffu, slope0, 1);  // slope of cell c-1
-    if (lane == 0) slope_m = vanleer(wm1[q] - wm2[q], w0[q] - wm1[q]);
-    Lq[q] = up + T(0.5) * slope_m;
-    Rq[q] = w0[q] - T(0.5) * slope0;
+    if (lane == 0) slope_m = vanleer_half(wm1[q] - wm2[q], w0[q] - wm1[q]);
+    Lq[q] = up + slope_m;
+    Rq[q] = w0[q] - slope0;
   }
   if (i >= nx) return;
   L.r = Lq[0]; L.u = Lq[1]; L.v = Lq[2]; L.w = Lq[3]; L.p = Lq[4]; L.b1 = Lq[5]; L.b2 = Lq[6];

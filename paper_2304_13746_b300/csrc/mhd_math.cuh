@@ -131,9 +131,12 @@ __device__ __forceinline__ float d2f_warp(double x) {
 }
 
 // van Leer (harmonic) limited slope from the two one-sided differences (Sec. 2.3).
-template <typename T> __device__ __forceinline__ T vanleer(T dl, T dr) {
+// The kernels use half the slope, dl dr / (dl + dr) (the slope is 2 dl dr / (dl + dr)): the
+// face states take w -/+ slope / 2, and forming the half directly gives the same bits (the
+// factors 2 and 1/2 are exact) with two multiplies fewer per variable and face.
+template <typename T> __device__ __forceinline__ T vanleer_half(T dl, T dr) {
   const T prod = dl * dr;
-  return same_sign_nz(dl, dr, prod) ? T(2) * prod / (dl + dr) : T(0);
+  return same_sign_nz(dl, dr, prod) ? prod / (dl + dr) : T(0);
 }
 
 // Primitive state on one side of a face, rotated so that "u" is the normal velocity.
@@ -147,13 +150,13 @@ template <typename T>
 __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T gamma,
                                      T gm1inv, T F[7], T& c) {
   const T bx2 = bx * bx;
-  const T magL = T(0.5) * (bx2 + L.b1 * L.b1 + L.b2 * L.b2);
-  const T magR = T(0.5) * (bx2 + R.b1 * R.b1 + R.b2 * R.b2);
+  const T b2L = bx2 + L.b1 * L.b1 + L.b2 * L.b2, b2R = bx2 + R.b1 * R.b1 + R.b2 * R.b2;
+  const T magL = T(0.5) * b2L, magR = T(0.5) * b2R;
   const T pTL = L.p + magL, pTR = R.p + magR;
 
   // outer speeds from the fast magnetosonic speeds (MK05 eq. 67)
   const T gpL = gamma * L.p, gpR = gamma * R.p;
-  const T aL = gpL + T(2) * magL, aR = gpR + T(2) * magR;
+  const T aL = gpL + b2L, aR = gpR + b2R;  // 2 magL is b2L exactly
   const T dL = pos_part(aL * aL - T(4) * gpL * bx2);
   const T dR = pos_part(aR * aR - T(4) * gpR * bx2);
   // 0.5/rho_L and 0.5/rho_R from one division
