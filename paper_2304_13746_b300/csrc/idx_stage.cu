@@ -155,8 +155,9 @@ __device__ __forceinline__ void prims_body(const Geo& g, const Ptr8<const double
     const double kin = 0.5 * rho * (vx * vx + vy * vy + vz * vz);
     const double mag = 0.5 * (bx * bx + by * by + bz * bz);
     const double P = g.gm1 * (U.f[4][c] - kin - mag);
-    if (!(rho > 0.0) || !(P > 0.0) || !isfinite(rho) || !isfinite(P) || !isfinite(vx) ||
-        !isfinite(vy) || !isfinite(vz))
+    // 0 < rho, P < infinity and finite velocities, on the bit patterns
+    if (!pos_finite(rho) || !pos_finite(P) || !finite_bits(vx) || !finite_bits(vy) ||
+        !finite_bits(vz))
       flag_bad(ctrl, c);
     W.f[0][c] = rho; W.f[1][c] = vx; W.f[2][c] = vy; W.f[3][c] = vz;
     W.f[4][c] = P;   W.f[5][c] = bx; W.f[6][c] = by; W.f[7][c] = bz;
@@ -187,9 +188,6 @@ __device__ __forceinline__ void prims_body(const Geo& g, const Ptr8<const double
     const float irf = 2.0f * d2f(irh);
     const float vx = d2f(mx) * irf, vy = d2f(my) * irf, vz = d2f(mz) * irf;
     // 0 < rho, P < infinity, tested on the bit patterns (FP64 compares take FP64 slots)
-    auto pos_finite = [](double x) {
-      return (unsigned long long)__double_as_longlong(x) - 1ull < 0x7fefffffffffffffull;
-    };
     if (!pos_finite(rho) || !pos_finite(P) || !isfinite(vx) || !isfinite(vy) || !isfinite(vz))
       flag_bad(ctrl, c);
     W.f[0][c] = rhof; W.f[1][c] = vx; W.f[2][c] = vy; W.f[3][c] = vz;
@@ -746,17 +744,32 @@ __device__ __forceinline__ T update_body(const Geo& g, const Ptr8<const double>&
         return Uin.f[f][c] + f2d(-dtf * div);
       }
     };
+    // FP64: dt folded into the inverse cell sizes, each difference accumulated by one FMA
+    double kdt[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) kdt[d] = dt * g.inv_dl[d];
     double out[8];
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
-      T div = T(0);
+      if constexpr (std::is_same<T, double>::value) {
+        double acc = Uin.f[f][c];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        if (!g.active[d]) continue;
-        const int s = slot(f, d);
-        div += (F[d].f[s][up[d]] - F[d].f[s][c]) * idl(d);
+        for (int d = 0; d < 3; ++d) {
+          if (!g.active[d]) continue;
+          const int s = slot(f, d);
+          acc = fma(F[d].f[s][c] - F[d].f[s][up[d]], kdt[d], acc);
+        }
+        out[f] = acc;
+      } else {
+        T div = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          if (!g.active[d]) continue;
+          const int s = slot(f, d);
+          div += (F[d].f[s][up[d]] - F[d].f[s][c]) * idl(d);
+        }
+        out[f] = accumulate(f, div);
       }
-      out[f] = accumulate(f, div);
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -767,6 +780,22 @@ __device__ __forceinline__ T update_body(const Geo& g, const Ptr8<const double>&
         if (g.active[t1]) b += (pot->out[t2][up[t1]] - pot->out[t2][c]) * g.inv_dl[t1];
         if (g.active[t2]) b -= (pot->out[t1][up[t2]] - pot->out[t1][c]) * g.inv_dl[t2];
         out[5 + d] = b;
+        continue;
+      }
+      if constexpr (std::is_same<T, double>::value) {
+        double acc = Uin.f[5 + d][c];
+        if (g.active[d]) {
+          if (g.active[t1]) acc = fma(E[t2][c] - E[t2][up[t1]], kdt[t1], acc);
+          if (g.active[t2]) acc = fma(E[t1][up[t2]] - E[t1][c], kdt[t2], acc);
+        } else {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            if (a == d || !g.active[a]) continue;
+            const int s = slot(5 + d, a);
+            acc = fma(F[a].f[s][c] - F[a].f[s][up[a]], kdt[a], acc);
+          }
+        }
+        out[5 + d] = acc;
         continue;
       }
       T curl = T(0);

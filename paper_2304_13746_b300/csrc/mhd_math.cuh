@@ -61,6 +61,13 @@ __device__ __forceinline__ double imin(double a, double b) { return okey(b) < ok
 __device__ __forceinline__ double imax(double a, double b) { return okey(a) < okey(b) ? b : a; }
 __device__ __forceinline__ float imin(float a, float b) { return b < a ? b : a; }
 __device__ __forceinline__ float imax(float a, float b) { return a < b ? b : a; }
+// 0 < x < infinity, and x finite, for doubles on the bit patterns
+__device__ __forceinline__ bool pos_finite(double x) {
+  return (unsigned long long)ibits(x) - 1ull < 0x7fefffffffffffffull;
+}
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((unsigned long long)ibits(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
 // dl * dr > 0: same sign and both non-zero
 __device__ __forceinline__ bool same_sign_nz(double dl, double dr, double) {
   const long long a = ibits(dl), b = ibits(dr);
