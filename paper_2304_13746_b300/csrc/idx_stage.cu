@@ -731,7 +731,7 @@ __device__ __forceinline__ T update_body(const Geo& g, const Ptr8<const double>&
       if constexpr (std::is_same<T, double>::value) return g.inv_dl[d];
       else return g.inv_dlf[d];
     };
-    const float dtf = d2f_warp(dt);
+    [[maybe_unused]] const float dtf = std::is_same<T, float>::value ? d2f_warp(dt) : 0.f;
     auto accumulate = [&](int f, T div) -> double {
       if constexpr (std::is_same<T, double>::value) {
         return Uin.f[f][c] - dt * div;
