@@ -28,7 +28,6 @@
 #include <mutex>
 #include <type_traits>
 #include <vector>
-#include <algorithm>
 #include <array>
 #include <map>
 #include <tuple>
@@ -2053,9 +2052,7 @@ struct idx_batch {
   int device;
   int sms;
   std::vector<idx_sim*> sims;
-  void* header;        // BatchDev<T> headers at fixed addresses (captured by the graph), one
-                       // per 256 bytes: [0] the whole batch, [1 + g] member group g
-  int n_groups, graph_groups;
+  void* header;        // BatchDev<T>, fixed address (captured by the graph)
   void* lists;         // instances, items, poll buffer (reallocated as the batch grows)
   size_t lists_cap;
   Ctrl* host_gather;   // pinned
@@ -2106,80 +2103,28 @@ int sweep_threads(const Geo& g, int d, int shape) {
   return march_threads(g, d, shape > 0 ? shape : kSegDefault);
 }
 
-// Member groups of a batched cycle.  A group runs both stages of its members before the
-// next group starts, so a group whose device buffers fit in L2 keeps its working set there
-// from one kernel to the next, as a sim stepped alone does; members too large for that
-// share one streaming group.  First-fit decreasing by device bytes.
-constexpr int kMaxGroups = 32;
-constexpr size_t kGroupBytes = 48ull << 20;
-
-std::vector<std::vector<int>> member_groups(const idx_batch* b) {
-  const int n = (int)b->sims.size();
-  std::vector<int> order(n);
-  for (int i = 0; i < n; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    return b->sims[x]->mem_bytes > b->sims[y]->mem_bytes;
-  });
-  std::vector<std::vector<int>> groups;
-  std::vector<size_t> load;
-  std::vector<int> big;
-  for (int i : order) {
-    const size_t m = b->sims[i]->mem_bytes;
-    if (m > kGroupBytes) { big.push_back(i); continue; }
-    size_t g = 0;
-    while (g < groups.size() && load[g] + m > kGroupBytes) ++g;
-    if (g == groups.size()) {
-      if ((int)groups.size() + 1 >= kMaxGroups) { big.push_back(i); continue; }
-      groups.emplace_back();
-      load.push_back(0);
-    }
-    groups[g].push_back(i);
-    load[g] += m;
-  }
-  if (!big.empty()) groups.push_back(big);
-  for (auto& g : groups) std::sort(g.begin(), g.end());  // members in batch order
-  return groups;
-}
-
-// Build the work-lists on the host, group by group, and upload them with the headers:
-// every group's items are one contiguous range of each list.
+// Build the work-lists on the host and upload them with the header.
 template <typename T> int batch_upload(idx_batch* b) {
   const int n = (int)b->sims.size();
-  const std::vector<std::vector<int>> groups = member_groups(b);
-  const int G = (int)groups.size();
   std::vector<InstT<T>> inst(n);
-  for (int i = 0; i < n; ++i) inst[i] = inst_of<T>(b->sims[i]);
   std::vector<Item> cell, sweep[3], tile[3];
-  std::vector<int> off_cell(G + 1), off_sweep[3], off_tile[3];
-  for (int d = 0; d < 3; ++d) { off_sweep[d].resize(G + 1); off_tile[d].resize(G + 1); }
-  for (int gi = 0; gi < G; ++gi) {
-    off_cell[gi] = (int)cell.size();
+  for (int i = 0; i < n; ++i) {
+    idx_sim* s = b->sims[i];
+    inst[i] = inst_of<T>(s);
+    for (int c0 = 0; c0 < s->geo.ncell; c0 += kThreads) cell.push_back({i, c0});
     for (int d = 0; d < 3; ++d) {
-      off_sweep[d][gi] = (int)sweep[d].size();
-      off_tile[d][gi] = (int)tile[d].size();
-    }
-    for (int i : groups[gi]) {
-      idx_sim* s = b->sims[i];
-      for (int c0 = 0; c0 < s->geo.ncell; c0 += kThreads) cell.push_back({i, c0});
-      for (int d = 0; d < 3; ++d) {
-        if (!s->geo.active[d]) continue;
-        const int sd = b->shape[d];
-        const bool staged = d != 0 && (sd == 116 || sd == 132);
-        if (staged && tma_shape_ok(s, d, sd)) {
-          const Geo& g = s->geo;
-          const int ntiles = (g.n[0] / 32) * (g.n[d] / (sd - 100)) * g.n[d == 1 ? 2 : 1];
-          for (int t = 0; t < ntiles; ++t) tile[d].push_back({i, t});
-          continue;
-        }
-        const int nt = sweep_threads(s->geo, d, staged ? b->fallback[d] : sd);
-        for (int t0 = 0; t0 < nt; t0 += kThreads) sweep[d].push_back({i, t0});
+      if (!s->geo.active[d]) continue;
+      const int sd = b->shape[d];
+      const bool staged = d != 0 && (sd == 116 || sd == 132);
+      if (staged && tma_shape_ok(s, d, sd)) {
+        const Geo& g = s->geo;
+        const int ntiles = (g.n[0] / 32) * (g.n[d] / (sd - 100)) * g.n[d == 1 ? 2 : 1];
+        for (int t = 0; t < ntiles; ++t) tile[d].push_back({i, t});
+        continue;
       }
+      const int nt = sweep_threads(s->geo, d, staged ? b->fallback[d] : sd);
+      for (int t0 = 0; t0 < nt; t0 += kThreads) sweep[d].push_back({i, t0});
     }
-  }
-  off_cell[G] = (int)cell.size();
-  for (int d = 0; d < 3; ++d) {
-    off_sweep[d][G] = (int)sweep[d].size();
-    off_tile[d][G] = (int)tile[d].size();
   }
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   size_t need = al(sizeof(InstT<T>) * (n + 1)) + al(sizeof(Item) * (cell.size() + 1)) +
@@ -2225,34 +2170,14 @@ template <typename T> int batch_upload(idx_batch* b) {
     if (!tile[d].empty())
       IDX_TRY(cudaMemcpyAsync(h.tile[d], tile[d].data(), sizeof(Item) * tile[d].size(), cudaMemcpyHostToDevice, b->stream));
   }
-  // headers: the whole batch, then each group's subranges of the same lists
-  std::vector<BatchDev<T>> hdr(G + 1, h);
-  for (int gi = 0; gi < G; ++gi) {
-    BatchDev<T>& q = hdr[gi + 1];
-    q.cell = h.cell + off_cell[gi];
-    q.n_cell = off_cell[gi + 1] - off_cell[gi];
-    for (int d = 0; d < 3; ++d) {
-      q.sweep[d] = h.sweep[d] + off_sweep[d][gi];
-      q.n_sweep[d] = off_sweep[d][gi + 1] - off_sweep[d][gi];
-      q.tile[d] = h.tile[d] + off_tile[d][gi];
-      q.n_tile[d] = off_tile[d][gi + 1] - off_tile[d][gi];
-    }
-  }
-  static_assert(sizeof(BatchDev<T>) <= 256, "a batch header fits its 256-byte slot");
-  for (int k = 0; k <= G; ++k)
-    IDX_TRY(cudaMemcpyAsync((char*)b->header + 256 * k, &hdr[k], sizeof(BatchDev<T>),
-                            cudaMemcpyHostToDevice, b->stream));
-  b->n_groups = G;
+  IDX_TRY(cudaMemcpyAsync(b->header, &h, sizeof(h), cudaMemcpyHostToDevice, b->stream));
   IDX_TRY(cudaStreamSynchronize(b->stream));
   return IDX_OK;
 }
 
-template <typename T> const BatchDev<T>* batch_header(const idx_batch* b, int k) {
-  return (const BatchDev<T>*)((const char*)b->header + 256 * k);
-}
-
 template <typename T, int D>
-void launch_batch_sweep_d(idx_batch* b, const BatchDev<T>* B, int shape, int stage, int check) {
+void launch_batch_sweep_d(idx_batch* b, int shape, int stage, int check) {
+  const BatchDev<T>* B = (const BatchDev<T>*)b->header;
   const int grid = b->grid_sweep;
   switch (shape) {
     case -1: if (D == 0) { kb_sweep<T, D, -1><<<grid, kThreads, 0, b->stream>>>(B, stage, check); return; } break;
@@ -2265,56 +2190,50 @@ void launch_batch_sweep_d(idx_batch* b, const BatchDev<T>* B, int shape, int sta
   kb_sweep<T, D, kSegDefault><<<grid, kThreads, 0, b->stream>>>(B, stage, check);
 }
 
-template <typename T, int D, int L>
-void launch_batch_tma(idx_batch* b, const BatchDev<T>* B, int stage, int check) {
+template <typename T, int D, int L> void launch_batch_tma(idx_batch* b, int stage, int check) {
+  const BatchDev<T>* B = (const BatchDev<T>*)b->header;
   const size_t smem = 7 * (L + 4) * 32 * sizeof(T);
   kb_sweep_tma<T, D, L><<<b->grid_tma[L == 32 ? 1 : 0], 8 * L, smem, b->stream>>>(B, stage, check);
 }
 
 // A staged shape launches the tile kernel for the members that fit the tiles and the
 // marching fallback for the others (each loops over an empty list when it has none).
-template <typename T>
-void launch_batch_sweep(idx_batch* b, const BatchDev<T>* B, int d, int stage, int check) {
+template <typename T> void launch_batch_sweep(idx_batch* b, int d, int stage, int check) {
   const int sd = b->shape[d];
   if (d != 0 && (sd == 116 || sd == 132)) {
     if (d == 1) {
-      if (sd == 116) launch_batch_tma<T, 1, 16>(b, B, stage, check);
-      else launch_batch_tma<T, 1, 32>(b, B, stage, check);
-      launch_batch_sweep_d<T, 1>(b, B, b->fallback[1], stage, check);
+      if (sd == 116) launch_batch_tma<T, 1, 16>(b, stage, check);
+      else launch_batch_tma<T, 1, 32>(b, stage, check);
+      launch_batch_sweep_d<T, 1>(b, b->fallback[1], stage, check);
     } else {
-      if (sd == 116) launch_batch_tma<T, 2, 16>(b, B, stage, check);
-      else launch_batch_tma<T, 2, 32>(b, B, stage, check);
-      launch_batch_sweep_d<T, 2>(b, B, b->fallback[2], stage, check);
+      if (sd == 116) launch_batch_tma<T, 2, 16>(b, stage, check);
+      else launch_batch_tma<T, 2, 32>(b, stage, check);
+      launch_batch_sweep_d<T, 2>(b, b->fallback[2], stage, check);
     }
     return;
   }
-  if (d == 0) launch_batch_sweep_d<T, 0>(b, B, sd, stage, check);
-  else if (d == 1) launch_batch_sweep_d<T, 1>(b, B, sd, stage, check);
-  else launch_batch_sweep_d<T, 2>(b, B, sd, stage, check);
+  if (d == 0) launch_batch_sweep_d<T, 0>(b, sd, stage, check);
+  else if (d == 1) launch_batch_sweep_d<T, 1>(b, sd, stage, check);
+  else launch_batch_sweep_d<T, 2>(b, sd, stage, check);
 }
 
-// One batched cycle: dt of every member, then group by group both stages, then the
-// members' time and speeds.
 template <typename T> void launch_batch_cycle(idx_batch* b) {
-  const BatchDev<T>* all = batch_header<T>(b, 0);
-  kb_begin<T><<<b->sms, kThreads, 0, b->stream>>>(all);
-  for (int gi = 0; gi < b->n_groups; ++gi) {
-    const BatchDev<T>* B = batch_header<T>(b, gi + 1);
-    for (int st = 0; st < 2; ++st) {
-      kb_prims<T><<<b->grid_cell, kThreads, 0, b->stream>>>(B, st, 1);
-      for (int d = 0; d < 3; ++d) launch_batch_sweep<T>(b, B, d, st, 1);
-      kb_emf<T><<<b->grid_cell, kThreads, 0, b->stream>>>(B);
-      if (st == 0) kb_update<T, false><<<b->grid_cell, kThreads, 0, b->stream>>>(B);
-      else kb_update<T, true><<<b->grid_cell, kThreads, 0, b->stream>>>(B);
-    }
+  const BatchDev<T>* B = (const BatchDev<T>*)b->header;
+  kb_begin<T><<<b->sms, kThreads, 0, b->stream>>>(B);
+  for (int st = 0; st < 2; ++st) {
+    kb_prims<T><<<b->grid_cell, kThreads, 0, b->stream>>>(B, st, 1);
+    for (int d = 0; d < 3; ++d) launch_batch_sweep<T>(b, d, st, 1);
+    kb_emf<T><<<b->grid_cell, kThreads, 0, b->stream>>>(B);
+    if (st == 0) kb_update<T, false><<<b->grid_cell, kThreads, 0, b->stream>>>(B);
+    else kb_update<T, true><<<b->grid_cell, kThreads, 0, b->stream>>>(B);
   }
-  kb_end<T><<<b->sms, kThreads, 0, b->stream>>>(all);
+  kb_end<T><<<b->sms, kThreads, 0, b->stream>>>(B);
 }
 
 // Tile-shape autotuner of the batch: per direction, every candidate sweep shape is timed
 // on the whole batch (primitives of the current states, three launches each).
 template <typename T> int batch_tune(idx_batch* b) {
-  const BatchDev<T>* B = batch_header<T>(b, 0);
+  const BatchDev<T>* B = (const BatchDev<T>*)b->header;
   int rc = batch_upload<T>(b);
   if (rc != IDX_OK) return rc;
   kb_prims<T><<<b->grid_cell, kThreads, 0, b->stream>>>(B, 0, 0);
@@ -2333,9 +2252,9 @@ template <typename T> int batch_tune(idx_batch* b) {
       b->shape[d] = cand[q];
       rc = batch_upload<T>(b);
       if (rc != IDX_OK) break;
-      launch_batch_sweep<T>(b, B, d, 0, 0);
+      launch_batch_sweep<T>(b, d, 0, 0);
       cudaEventRecord(e0, b->stream);
-      for (int r = 0; r < 3; ++r) launch_batch_sweep<T>(b, B, d, 0, 0);
+      for (int r = 0; r < 3; ++r) launch_batch_sweep<T>(b, d, 0, 0);
       cudaEventRecord(e1, b->stream);
       if (cudaEventSynchronize(e1) != cudaSuccess) { rc = IDX_ECUDA; break; }
       float ms = 0.f;
@@ -2354,9 +2273,9 @@ template <typename T> int batch_tune(idx_batch* b) {
       b->fallback[d] = march;
       rc = batch_upload<T>(b);
       if (rc != IDX_OK) break;
-      launch_batch_sweep<T>(b, B, d, 0, 0);
+      launch_batch_sweep<T>(b, d, 0, 0);
       cudaEventRecord(e0, b->stream);
-      for (int r = 0; r < 3; ++r) launch_batch_sweep<T>(b, B, d, 0, 0);
+      for (int r = 0; r < 3; ++r) launch_batch_sweep<T>(b, d, 0, 0);
       cudaEventRecord(e1, b->stream);
       if (cudaEventSynchronize(e1) != cudaSuccess) { rc = IDX_ECUDA; break; }
       float ms = 0.f;
@@ -2380,7 +2299,7 @@ template <typename T> int batch_prepare(idx_batch* b) {
     if (rc != IDX_OK) return rc;
     b->dirty = false;
   }
-  bool same = b->exec != nullptr && b->graph_groups == b->n_groups;
+  bool same = b->exec != nullptr;
   for (int d = 0; d < 3; ++d)
     same = same && b->graph_shape[d] == b->shape[d] && b->graph_fallback[d] == b->fallback[d];
   if (same) return IDX_OK;
@@ -2394,7 +2313,6 @@ template <typename T> int batch_prepare(idx_batch* b) {
     b->graph_shape[d] = b->shape[d];
     b->graph_fallback[d] = b->fallback[d];
   }
-  b->graph_groups = b->n_groups;
   return IDX_OK;
 }
 
@@ -2460,7 +2378,7 @@ int idx_batch_create(int precision, void* stream, idx_batch** out) {
       if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) rc = IDX_ECUDA;
     }
   }
-  if (rc == IDX_OK && cudaMalloc(&b->header, 256 * (kMaxGroups + 1)) != cudaSuccess) rc = IDX_ENOMEM;
+  if (rc == IDX_OK && cudaMalloc(&b->header, 256) != cudaSuccess) rc = IDX_ENOMEM;
   if (rc == IDX_OK) rc = precision == IDX_FP32_BULK ? batch_occupancy<float>(b) : batch_occupancy<double>(b);
   if (rc != IDX_OK) {
     idx_batch_destroy(b);
