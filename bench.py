@@ -314,10 +314,10 @@ def run_serve(args):
             out.append(q)
         return out
 
-    def served(precision, rate, cap=None):
+    def served(precision, rate, cap=None, order="oldest"):
         be = serve.IdxBackend(precision, stream=stream.cuda_stream)
         st = serve.Server(be, budget, cycles_per_poll=4, chunk_s=0.01,
-                          max_active_cells=cap).run(clone(base, rate))
+                          max_active_cells=cap, order=order).run(clone(base, rate))
         be.close()
         return st
 
@@ -336,6 +336,8 @@ def run_serve(args):
         for cap in [int(float(c)) for c in args.serve_caps.split(",") if float(c) > 0]:
             r[f"served_70pct_cap{cap}"] = dict(served(precision, rate70, cap), rate=rate70,
                                                max_active_cells=cap)
+        r["served_70pct_least_work"] = dict(served(precision, rate70, order="least_work"),
+                                            rate=rate70, order="least_work")
         r["sequential_70pct"] = dict(serve.serve_sequential(
             serve.IdxSequential(precision, stream=stream.cuda_stream), clone(base, rate70),
             budget_bytes=budget), rate=rate70)

@@ -1,7 +1,8 @@
 """Serving many ideal-MHD simulations on one GPU with continuous batching.
 
 Requests (an initial state, a grid, an end time) arrive over time.  The server admits
-them, oldest first, as device memory frees up under a fixed HBM budget; every admitted
+them (oldest first, or least estimated work first) as device memory frees up under a
+fixed HBM budget; every admitted
 request joins the running batch (idx_batch_*), where all of them advance together, each
 with its own CFL dt, until its end time; a finished request's state is copied back to
 the host and its memory released, which lets the next ones in.  Latency is arrival to
@@ -174,22 +175,35 @@ def _stats(requests, t_first, t_last):
             "cell_updates": work, "makespan_s": span, "cell_updates_per_s": work / span}
 
 
+def estimated_work(r):
+    """Cell-updates a request needs, up to a constant: cells x cycles, with cycles
+    proportional to t_end / dt and dt to the cell size (CFL), i.e. to t_end * n."""
+    return r.cells * r.n * r.t_end
+
+
 class Server:
-    """Continuous batching under an HBM budget (oldest request first)."""
+    """Continuous batching under an HBM budget."""
+
+    ORDERS = ("oldest", "least_work")
 
     def __init__(self, backend, budget_bytes, clock=None, cycles_per_poll=8, chunk_s=None,
-                 max_active_cells=None):
+                 max_active_cells=None, order="oldest"):
         """cycles_per_poll: batched cycles between polls; with chunk_s set, that number
         adapts so that one chunk takes about chunk_s seconds (new arrivals and finished
         requests are handled at chunk boundaries).  max_active_cells: when set, a request
         waits while the running ones already hold that many cells (enough work to keep
-        the device busy), so late arrivals do not slow down large running requests."""
+        the device busy), so late arrivals do not slow down large running requests.
+        order: which waiting request is admitted next -- the oldest, or the one with the
+        least estimated work (shortest-job-first among those waiting)."""
+        if order not in self.ORDERS:
+            raise ValueError(order)
         self.backend = backend
         self.budget = int(budget_bytes)
         self.clock = clock or WallClock()
         self.k = int(cycles_per_poll)
         self.chunk_s = chunk_s
         self.max_cells = max_active_cells
+        self.order = order
         self.used = 0
         self.peak = 0
 
@@ -212,6 +226,8 @@ class Server:
             now = self.clock.now()
             while pending and pending[0].arrival <= now:
                 queue.append(pending.popleft())
+            if self.order == "least_work" and len(queue) > 1:
+                queue = deque(sorted(queue, key=lambda q: (estimated_work(q), q.arrival)))
             in_batch = [rid for rid in running if rid not in to_read]
             t0 = self.clock.now()
             stepped = bool(in_batch)
@@ -231,7 +247,7 @@ class Server:
                 r.finished = self.clock.now()
                 phase["finish_s"] += r.finished - tf
                 t_last = max(t_last, r.finished)
-            # overlapped with the chunk: admissions, oldest first, while the budget allows
+            # overlapped with the chunk: admissions in the server's order, while the budget allows
             while queue:
                 r = queue[0]
                 need = self.backend.footprint(r)

@@ -160,3 +160,21 @@ def test_active_cell_cap_limits_concurrency():
     assert st["done"] == len(reqs)
     biggest = max(r.cells for r in reqs)
     assert max(seen) <= max(cap, biggest)
+
+
+def test_least_work_order_admits_small_requests_first():
+    clock = FakeClock()
+    be = FakeBackend(clock)
+    reqs = stream(12)
+    for r in reqs:
+        r.arrival = 0.0                               # all arrive at once
+    budget = 64 * 64 * 100                            # one large request's worth
+    st = serve.Server(be, budget, clock, cycles_per_poll=2, order="least_work").run(reqs)
+    assert st["done"] == len(reqs)
+    work = {r.rid: serve.estimated_work(r) for r in reqs}
+    started = [work[rid] for rid in be.started]
+    # whenever the device frees up, the smallest waiting request goes next: the start
+    # order is the work order
+    assert started == sorted(started)
+    with pytest.raises(ValueError):
+        serve.Server(be, budget, clock, order="largest")
