@@ -1915,10 +1915,6 @@ struct Item {
   int begin;
 };
 
-// A cell item is kItemChunks consecutive chunks of kThreads cells: the item -> instance ->
-// buffer lookups before a block's first load are paid once per chunk group, not per chunk.
-constexpr int kItemChunks = 4;
-
 template <typename T> struct BatchDev {
   InstT<T>* inst;
   Item* cell;      // items of kThreads cells
@@ -1946,14 +1942,8 @@ __global__ void __launch_bounds__(kThreads) kb_prims(const BatchDev<T>* B, int s
     const InstT<T>* I = &B->inst[w.inst];
     if (check && !(I->ctrl->dt > 0.0)) continue;
     const Geo g = I->g;
-    const Ptr8<const double> U = dconst(stage ? I->U1 : I->U);
-    const Ptr8<T> W = I->W;
-    const CellEmf<T> cc = I->cc;
-#pragma unroll
-    for (int k = 0; k < kItemChunks; ++k) {
-      const int c = w.begin + k * kThreads + threadIdx.x;
-      if (c < g.ncell) prims_body<T>(g, U, W, cc, I->ctrl, c);
-    }
+    const int c = w.begin + threadIdx.x;
+    if (c < g.ncell) prims_body<T>(g, dconst(stage ? I->U1 : I->U), I->W, I->cc, I->ctrl, c);
   }
 }
 
@@ -2014,17 +2004,10 @@ __global__ void __launch_bounds__(kThreads) kb_emf(const BatchDev<T>* B) {
     const InstT<T>* I = &B->inst[w.inst];
     if (!(I->ctrl->dt > 0.0)) continue;
     const Geo g = I->g;
-    const Ptr8<const T> W = dconst(I->W);
-    const Ptr8<const T> F0 = dconst(I->F[0]), F1 = dconst(I->F[1]), F2 = dconst(I->F[2]);
-    const CellEmf<T> cc = I->cc;
-    T* const E0 = I->E[0];
-    T* const E1 = I->E[1];
-    T* const E2 = I->E[2];
-#pragma unroll
-    for (int k = 0; k < kItemChunks; ++k) {
-      const int c = w.begin + k * kThreads + threadIdx.x;
-      if (c < g.ncell) emf_body<T>(g, W, F0, F1, F2, cc, E0, E1, E2, c);
-    }
+    const int c = w.begin + threadIdx.x;
+    if (c < g.ncell)
+      emf_body<T>(g, dconst(I->W), dconst(I->F[0]), dconst(I->F[1]), dconst(I->F[2]), I->cc, I->E[0],
+                  I->E[1], I->E[2], c);
   }
 }
 
@@ -2037,15 +2020,10 @@ __global__ void __launch_bounds__(kThreads) kb_update(const BatchDev<T>* B) {
     const double dt = I->ctrl->dt;
     if (!(dt > 0.0)) continue;  // uniform over the block: one item per block
     const Geo g = I->g;
-    const Ptr8<const double> Uin = dconst(COMBINE ? I->U1 : I->U), U0 = dconst(I->U);
-    const Ptr8<const T> F0 = dconst(I->F[0]), F1 = dconst(I->F[1]), F2 = dconst(I->F[2]);
-    const Ptr8<double> Uout = COMBINE ? I->U : I->U1;
-    T inv = T(0);
-#pragma unroll
-    for (int k = 0; k < kItemChunks; ++k)
-      inv = max_nn(inv, update_body<T, COMBINE>(g, Uin, U0, F0, F1, F2, I->E[0], I->E[1],
-                                                I->E[2], Uout, dt,
-                                                w.begin + k * kThreads + threadIdx.x));
+    const T inv = update_body<T, COMBINE>(
+        g, dconst(COMBINE ? I->U1 : I->U), dconst(I->U), dconst(I->F[0]), dconst(I->F[1]),
+        dconst(I->F[2]), I->E[0], I->E[1], I->E[2], COMBINE ? I->U : I->U1, dt,
+        w.begin + threadIdx.x);
     block_max_to(&I->ctrl->inv_acc, inv);
   }
 }
@@ -2133,7 +2111,7 @@ template <typename T> int batch_upload(idx_batch* b) {
   for (int i = 0; i < n; ++i) {
     idx_sim* s = b->sims[i];
     inst[i] = inst_of<T>(s);
-    for (int c0 = 0; c0 < s->geo.ncell; c0 += kThreads * kItemChunks) cell.push_back({i, c0});
+    for (int c0 = 0; c0 < s->geo.ncell; c0 += kThreads) cell.push_back({i, c0});
     for (int d = 0; d < 3; ++d) {
       if (!s->geo.active[d]) continue;
       const int sd = b->shape[d];
