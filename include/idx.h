@@ -192,6 +192,8 @@ int idx_pipe_rates(double rates[6]);
  * the same result, to rounding, alone and in a batch.  The work-list is read at run time, so
  * sims join and leave between steps without re-capturing the batch's CUDA graph.  The
  * sweep shapes are autotuned on the batch when its membership first changes.
+ * Members of at least 2^18 cells run their own (single-sim) kernels inside the batch's
+ * cycle; the smaller ones share the work-list kernels.
  * Members must share the batch's precision and device and use RK2 in the field form
  * (IDX_INDUCTION_FIELD; IDX_EINVAL otherwise); a member must not be stepped by
  * idx_step/idx_advance, nor read with idx_get_state/idx_time, until idx_batch_poll or

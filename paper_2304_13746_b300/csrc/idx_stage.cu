@@ -2064,6 +2064,8 @@ struct idx_batch {
   int fallback[3];     // marching shape of the other members when shape[d] is staged
   int graph_shape[3], graph_fallback[3];
   int grid_tma[2];     // persistent blocks of the staged sweep, L = 16 / 32
+  std::vector<idx_sim*> solo;        // members stepped by their own kernels in the cycle
+  std::vector<idx_sim*> graph_solo;  // the solo members the captured cycle was built with
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   int grid_cell, grid_sweep;
@@ -2072,6 +2074,12 @@ struct idx_batch {
 namespace {
 
 template <typename T> InstT<T> inst_of(idx_sim* s);
+
+// Members of at least this many cells run the single-sim kernels inside the batched cycle:
+// their own launch parameters and tuned shapes beat the work-list kernels once a member
+// fills the GPU by itself (measured on the FP32-bulk boxes of 32^3 .. 128^3), while the
+// small members gain most from sharing launches.
+constexpr int kSoloCells = 1 << 18;
 template <typename T> void copy_maps(InstT<T>& I, const idx_sim* s) {
   for (int d = 0; d < 3; ++d) {
     I.tm_body[d][0] = s->tm_body[d][0];
@@ -2108,9 +2116,14 @@ template <typename T> int batch_upload(idx_batch* b) {
   const int n = (int)b->sims.size();
   std::vector<InstT<T>> inst(n);
   std::vector<Item> cell, sweep[3], tile[3];
+  b->solo.clear();
   for (int i = 0; i < n; ++i) {
     idx_sim* s = b->sims[i];
     inst[i] = inst_of<T>(s);
+    if (s->geo.ncell >= kSoloCells) {  // stepped by its own kernels: no work-list items
+      b->solo.push_back(s);
+      continue;
+    }
     for (int c0 = 0; c0 < s->geo.ncell; c0 += kThreads) cell.push_back({i, c0});
     for (int d = 0; d < 3; ++d) {
       if (!s->geo.active[d]) continue;
@@ -2217,6 +2230,26 @@ template <typename T> void launch_batch_sweep(idx_batch* b, int d, int stage, in
   else launch_batch_sweep_d<T, 2>(b, sd, stage, check);
 }
 
+template <typename T> void launch_solo_stage(idx_batch* b, int st);
+template <> void launch_solo_stage<double>(idx_batch* b, int st) {
+  for (idx_sim* s : b->solo) {
+    const cudaStream_t own = s->stream;
+    s->stream = b->stream;  // the member's kernels go into the batch's stream (and graph)
+    launch_stage<double>(s, stage_plan(s), st, s->Wd, s->Fd, s->Ed);
+    s->stream = own;
+  }
+}
+template <> void launch_solo_stage<float>(idx_batch* b, int st) {
+  for (idx_sim* s : b->solo) {
+    const cudaStream_t own = s->stream;
+    s->stream = b->stream;
+    launch_stage<float>(s, stage_plan(s), st, s->Wf, s->Ff, s->Ef);
+    s->stream = own;
+  }
+}
+
+// One batched cycle: every member's dt, both stages (work-list kernels for the small
+// members, each solo member's own kernels), then every member's time and speeds.
 template <typename T> void launch_batch_cycle(idx_batch* b) {
   const BatchDev<T>* B = (const BatchDev<T>*)b->header;
   kb_begin<T><<<b->sms, kThreads, 0, b->stream>>>(B);
@@ -2226,6 +2259,7 @@ template <typename T> void launch_batch_cycle(idx_batch* b) {
     kb_emf<T><<<b->grid_cell, kThreads, 0, b->stream>>>(B);
     if (st == 0) kb_update<T, false><<<b->grid_cell, kThreads, 0, b->stream>>>(B);
     else kb_update<T, true><<<b->grid_cell, kThreads, 0, b->stream>>>(B);
+    launch_solo_stage<T>(b, st);
   }
   kb_end<T><<<b->sms, kThreads, 0, b->stream>>>(B);
 }
@@ -2299,7 +2333,12 @@ template <typename T> int batch_prepare(idx_batch* b) {
     if (rc != IDX_OK) return rc;
     b->dirty = false;
   }
-  bool same = b->exec != nullptr;
+  // solo members' own shapes, tuned before the capture (cached per grid)
+  for (idx_sim* s : b->solo) {
+    const int trc = tune_once(s);
+    if (trc != IDX_OK) return trc;
+  }
+  bool same = b->exec != nullptr && b->graph_solo == b->solo;
   for (int d = 0; d < 3; ++d)
     same = same && b->graph_shape[d] == b->shape[d] && b->graph_fallback[d] == b->fallback[d];
   if (same) return IDX_OK;
@@ -2313,6 +2352,7 @@ template <typename T> int batch_prepare(idx_batch* b) {
     b->graph_shape[d] = b->shape[d];
     b->graph_fallback[d] = b->fallback[d];
   }
+  b->graph_solo = b->solo;
   return IDX_OK;
 }
 

@@ -35,6 +35,7 @@ def mix():
         (inputs.orszag_tang_3d(16), 0.03),
         (inputs.linear_wave(8, "alfven"), 0.06),
         (inputs.turbulent_box(40, seed=7), 0.015),   # large enough to be tuned alone
+        (inputs.turbulent_box(64, seed=9), 0.008),   # 2^18 cells: stepped by its own kernels
     ]
 
 
