@@ -192,10 +192,10 @@ int idx_pipe_rates(double rates[6]);
  * the same result, to rounding, alone and in a batch.  The work-list is read at run time, so
  * sims join and leave between steps without re-capturing the batch's CUDA graph.  The
  * sweep shapes are autotuned on the batch when its membership first changes.
- * Members of at least 2^18 cells run their own (single-sim) kernels inside the batch's
- * cycle; the smaller ones share the work-list kernels.
- * Members must share the batch's precision and device and use RK2 in the field form
- * (IDX_INDUCTION_FIELD; IDX_EINVAL otherwise); a member must not be stepped by
+ * Members of at least 2^18 cells, and members with RK3 or the vector-potential form, run
+ * their own (single-sim) kernels inside the batch's cycle; the smaller RK2 field-form
+ * members share the work-list kernels.
+ * Members must share the batch's precision and device; a member must not be stepped by
  * idx_step/idx_advance, nor read with idx_get_state/idx_time, until idx_batch_poll or
  * idx_batch_remove has synchronised the batch. */
 typedef struct idx_batch idx_batch; /* opaque */
@@ -210,7 +210,7 @@ int idx_batch_add(idx_batch* batch, idx_sim* sim, double t_end);
 /* Remove a member (waits for the batch's work); it goes back to unclamped idx_step. */
 int idx_batch_remove(idx_batch* batch, idx_sim* sim);
 
-/* Enqueue ncycles batched RK2 cycles (asynchronous); finished members idle. */
+/* Enqueue ncycles batched cycles (asynchronous); finished members idle. */
 int idx_batch_step(idx_batch* batch, int ncycles);
 
 /* Synchronise the batch and list the members that reached their end time or failed

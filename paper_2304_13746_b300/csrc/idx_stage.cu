@@ -2120,7 +2120,9 @@ template <typename T> int batch_upload(idx_batch* b) {
   for (int i = 0; i < n; ++i) {
     idx_sim* s = b->sims[i];
     inst[i] = inst_of<T>(s);
-    if (s->geo.ncell >= kSoloCells) {  // stepped by its own kernels: no work-list items
+    // stepped by its own kernels, no work-list items: large members, and members whose
+    // cycle the work-list kernels do not run (RK3, vector-potential form)
+    if (s->geo.ncell >= kSoloCells || s->solver.rk_order != 2 || s->pot) {
       b->solo.push_back(s);
       continue;
     }
@@ -2230,26 +2232,23 @@ template <typename T> void launch_batch_sweep(idx_batch* b, int d, int stage, in
   else launch_batch_sweep_d<T, 2>(b, sd, stage, check);
 }
 
-template <typename T> void launch_solo_stage(idx_batch* b, int st);
-template <> void launch_solo_stage<double>(idx_batch* b, int st) {
-  for (idx_sim* s : b->solo) {
-    const cudaStream_t own = s->stream;
-    s->stream = b->stream;  // the member's kernels go into the batch's stream (and graph)
-    launch_stage<double>(s, stage_plan(s), st, s->Wd, s->Fd, s->Ed);
-    s->stream = own;
-  }
-}
-template <> void launch_solo_stage<float>(idx_batch* b, int st) {
+// The stages of every solo member's own cycle (its RK order and induction form), on the
+// batch's stream (and into its graph).
+void launch_solo_stages(idx_batch* b) {
   for (idx_sim* s : b->solo) {
     const cudaStream_t own = s->stream;
     s->stream = b->stream;
-    launch_stage<float>(s, stage_plan(s), st, s->Wf, s->Ff, s->Ef);
+    const StagePlan p = stage_plan(s);
+    for (int st = 0; st < p.n; ++st) {
+      if (s->solver.precision == IDX_FP32_BULK) launch_stage<float>(s, p, st, s->Wf, s->Ff, s->Ef);
+      else launch_stage<double>(s, p, st, s->Wd, s->Fd, s->Ed);
+    }
     s->stream = own;
   }
 }
 
-// One batched cycle: every member's dt, both stages (work-list kernels for the small
-// members, each solo member's own kernels), then every member's time and speeds.
+// One batched cycle: every member's dt, both RK2 stages of the work-list members, each
+// solo member's own stages, then every member's time and speeds.
 template <typename T> void launch_batch_cycle(idx_batch* b) {
   const BatchDev<T>* B = (const BatchDev<T>*)b->header;
   kb_begin<T><<<b->sms, kThreads, 0, b->stream>>>(B);
@@ -2259,8 +2258,8 @@ template <typename T> void launch_batch_cycle(idx_batch* b) {
     kb_emf<T><<<b->grid_cell, kThreads, 0, b->stream>>>(B);
     if (st == 0) kb_update<T, false><<<b->grid_cell, kThreads, 0, b->stream>>>(B);
     else kb_update<T, true><<<b->grid_cell, kThreads, 0, b->stream>>>(B);
-    launch_solo_stage<T>(b, st);
   }
+  launch_solo_stages(b);
   kb_end<T><<<b->sms, kThreads, 0, b->stream>>>(B);
 }
 
@@ -2443,8 +2442,6 @@ void idx_batch_destroy(idx_batch* b) {
 int idx_batch_add(idx_batch* b, idx_sim* s, double t_end) {
   if (!b || !s || !(t_end >= 0.0)) return IDX_EINVAL;
   if (s->solver.precision != b->precision || s->device != b->device) return IDX_EINVAL;
-  // batched cycles are RK2 in the field form
-  if (s->solver.rk_order != 2 || s->pot) return IDX_EINVAL;
   for (idx_sim* m : b->sims)
     if (m == s) return IDX_EINVAL;
   IDX_TRY(cudaStreamSynchronize(b->stream));

@@ -182,13 +182,33 @@ def test_batched_result_matches_oracle():
     s.close()
 
 
-def test_batch_refuses_rk3_members():
-    ic = inputs.orszag_tang_2d(16)
-    s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, "fp64", rk_order=3)
-    s.set_primitive(ic.prim)
-    b = idx.Batch("fp64")
-    with pytest.raises(idx.IdxError) as e:
-        b.add(s)
-    assert e.value.code == idx.IDX_EINVAL
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_rk3_and_potential_members_match_alone(precision):
+    # members whose cycle the work-list kernels do not run step with their own kernels
+    # inside the batched cycle, next to ordinary members
+    ics = [(inputs.orszag_tang_2d(32), dict(rk_order=3), 0.02),
+           (inputs.random_smooth((8, 8, 8), seed=4), dict(induction="potential"), 0.02),
+           (inputs.turbulent_box(16, seed=3), dict(), 0.02)]
+    alone = []
+    for ic, kw, t_end in ics:
+        s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, precision, **kw)
+        s.set_primitive(ic.prim)
+        s.advance(t_end)
+        alone.append(s.get_state())
+        s.close()
+    b = idx.Batch(precision)
+    sims = []
+    for ic, kw, t_end in ics:
+        s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, precision, **kw)
+        s.set_primitive(ic.prim)
+        b.add(s, t_end)
+        sims.append(s)
+    run_batch_until_done(b, sims)
+    for s, (ic, kw, t_end), ref in zip(sims, ics, alone):
+        assert s.time()[0] == t_end
+        err = scaled_error(s.get_state(), ref)
+        assert err <= TOL[precision], (ic.name, kw, err)
+    for s in sims:
+        b.remove(s)
+        s.close()
     b.close()
-    s.close()

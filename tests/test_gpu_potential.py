@@ -230,12 +230,21 @@ def test_device_tensors_and_field_form_from_potential():
     s.close()
 
 
-def test_batch_refuses_potential_form():
+def test_potential_member_in_a_batch():
     ic = POTENTIAL_CASES["smooth_8cube"]()
     o, s = pair_from_potential(ic)
     b = idx.Batch("fp64")
-    with pytest.raises(idx.IdxError) as e:
-        b.add(s, 1.0)
-    assert e.value.code == idx.IDX_EINVAL
+    b.add(s, 0.02)
+    for _ in range(100):
+        b.step(2)
+        fin, active = b.poll()
+        if active == 0:
+            break
+    assert s.time()[0] == 0.02
+    o.advance(0.02)
+    err = field_errors(s.get_state(), o.u)
+    assert max(err) <= 1e-10, err
+    assert potential_error(s.get_potential(), o.A) <= 1e-10
+    b.remove(s)
     b.close()
     s.close()
