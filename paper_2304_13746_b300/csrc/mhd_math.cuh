@@ -164,8 +164,9 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   // outer speeds from the fast magnetosonic speeds (MK05 eq. 67)
   const T gpL = gamma * L.p, gpR = gamma * R.p;
   const T aL = gpL + b2L, aR = gpR + b2R;  // 2 magL is b2L exactly
-  const T dL = pos_part(aL * aL - T(4) * gpL * bx2);
-  const T dR = pos_part(aR * aR - T(4) * gpR * bx2);
+  const T bx2x4 = T(4) * bx2;               // exact scaling, shared by both sides
+  const T dL = pos_part(aL * aL - gpL * bx2x4);
+  const T dR = pos_part(aR * aR - gpR * bx2x4);
   // 0.5/rho_L and 0.5/rho_R from one division
   const T hLR = T(0.5) / (L.r * R.r);
   const T cfL = tsqrt((aL + tsqrt(dL)) * (R.r * hLR));
@@ -207,7 +208,7 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   const T rsL = qL * iL, rsR = qR * iR;  // rho*
   T vsL, wsL, b1sL, b2sL, vsR, wsR, b1sR, b2sR;
   {
-    const T q = qL * (SL - SM);
+    const T q = qL * eL;  // rho_L (S_L - u_L)(S_L - S_M)
     const T D = q - bx2;
     if (le_nn(tabs(D), Eps<T>::degen * (tabs(q) + bx2))) {
       vsL = L.v; wsL = L.w; b1sL = L.b1; b2sL = L.b2;
@@ -222,7 +223,7 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
     }
   }
   {
-    const T q = qR * (SR - SM);
+    const T q = qR * eR;
     const T D = q - bx2;
     if (le_nn(tabs(D), Eps<T>::degen * (tabs(q) + bx2))) {
       vsR = R.v; wsR = R.w; b1sR = R.b1; b2sR = R.b2;
