@@ -295,3 +295,56 @@ def count_faces(cons, lengths, gamma, d):
 
 def threads():
     return lib().ora_threads()
+
+
+class SimBC:
+    """Oracle simulation with non-periodic boundaries (oracle/boundaries.py): the padded
+    grid is stepped stage by stage with ora_stage (HLLD, E^c), the ghosts refilled before
+    every stage.  bc = (kind_x, kind_y, kind_z) of boundaries.PERIODIC / OUTFLOW /
+    REFLECTING.  Fields in the user layout (normal field n + 1 faces along a non-periodic
+    direction); every array numpy float64 of shape (nz, ny, nx) (+1 along that axis)."""
+
+    def __init__(self, prim, lengths, gamma, cfl, bc, rk_order=2):
+        from . import boundaries as bd
+        self.bd = bd
+        self.bc = tuple(int(b) for b in bc)
+        self.cell_shape = prim[0].shape
+        self.lengths = tuple(float(x) for x in lengths)
+        self.plengths = bd.padded_lengths(self.lengths, self.cell_shape, self.bc)
+        self.gamma = float(gamma)
+        self.cfl = float(cfl)
+        self.rk_order = int(rk_order)
+        w = bd.fill_ghosts(bd.pad([_c(a) for a in prim], self.bc), self.bc)
+        self.u = bd.fill_ghosts(cons_from_prims(w, self.plengths, self.gamma), self.bc)
+        self.t = 0.0
+        self.nsteps = 0
+        self.inv_dt = speed_pass(self.u, self.plengths, self.gamma)
+
+    def state(self):
+        return self.bd.unpad(self.u, self.bc, self.cell_shape)
+
+    def step(self, dt_max=math.inf):
+        dt = min(self.cfl / self.inv_dt, dt_max)
+        weights = [(1.0, 0.0), (0.5, 0.5)] if self.rk_order == 2 else \
+            [(1.0, 0.0), (0.25, 0.75), (2.0 / 3.0, 1.0 / 3.0)]
+        u0 = self.u
+        prev = u0
+        inv = 0.0
+        for w, w0 in weights:
+            out, inv_s = stage(prev, self.plengths, self.gamma, dt, u0=u0 if w0 else None, w=w,
+                               w0=w0)
+            prev = self.bd.fill_ghosts(out, self.bc)
+            inv = max(inv, inv_s)
+        self.u = prev
+        self.inv_dt = inv
+        self.nsteps += 1
+        return dt
+
+    def advance(self, t_end, max_steps=10**7):
+        n = 0
+        while self.t < t_end and n < max_steps:
+            remaining = t_end - self.t
+            dt = self.step(dt_max=remaining)
+            self.t = t_end if dt >= remaining else self.t + dt
+            n += 1
+        return n
