@@ -13,11 +13,13 @@
  *   Sec. 2.7      RK2 stages U_s = w_s U* + w0_s U_0 (Eq. 9, Table 1: w = 1, 0; 1/2, 1/2)
  *                 and the CFL step dt = sigma / max_V sum_d c_max,d / dl_d (Eq. 10).
  *
- * Layout (every field): double[nz][ny][nx], x fastest, periodic in x, y and z.
- * The 8 state fields, in this order: rho, mx, my, mz, E (cell averages), then
- * Bx, By, Bz (face averages: Bx[k][j][i] on the x-face at i-1/2, By[k][j][i] on the
- * y-face at j-1/2, Bz[k][j][i] on the z-face at k-1/2).  A direction with a single
- * cell is not integrated (nz == 1 is the 2D case).
+ * Layout (every field): double[nz][ny][nx], x fastest, periodic in x, y and z unless
+ * idx_grid.bc says otherwise.  The 8 state fields, in this order: rho, mx, my, mz, E
+ * (cell averages), then Bx, By, Bz (face averages: Bx[k][j][i] on the x-face at i-1/2,
+ * By[k][j][i] on the y-face at j-1/2, Bz[k][j][i] on the z-face at k-1/2).  Along a
+ * non-periodic direction the normal field has one more face: Bx is double[nz][ny][nx+1]
+ * when x is not periodic (face i = nx is the upper boundary face), and likewise for By, Bz.
+ * A direction with a single cell is not integrated (nz == 1 is the 2D case).
  *
  * Time step: the first cycle after idx_set_state / idx_set_primitive takes its dt
  * from a signal-speed pass on the new state; every later cycle takes
@@ -46,9 +48,21 @@ extern "C" {
 #define IDX_ECUDA (-4)     /* a CUDA runtime call failed                                      */
 #define IDX_ETIMEOUT (-5)  /* a bounded wait expired                                          */
 
+typedef enum {
+  IDX_BC_PERIODIC = 0,    /* the default                                                   */
+  IDX_BC_OUTFLOW = 1,     /* zero gradient: ghost cells copy the nearest interior cell (the
+                             paper's outflow boundary, Sec. 4.1)                           */
+  IDX_BC_REFLECTING = 2   /* mirror image about the boundary face with the normal velocity and
+                             the normal field reversed (a rigid, perfectly conducting wall) */
+} idx_bc;
+
 typedef struct {
   int nx, ny, nz;      /* cells per direction, each >= 1, nx*ny*nz < 2^31 */
   double lx, ly, lz;   /* box [0,lx) x [0,ly) x [0,lz); cell size l/n      */
+  int bc[3];           /* boundary kind per direction (idx_bc); a direction with one cell is
+                          not integrated and takes none.  A non-periodic direction needs at
+                          least 2 cells; it is stepped with 2 ghost cells per side that are
+                          refilled from the interior before every stage. */
 } idx_grid;
 
 typedef enum {
@@ -104,7 +118,9 @@ int idx_set_primitive(idx_sim* sim, const double* const fields[8], int on_device
  * curl A (circulation over each face / its area; differences along a direction with one
  * cell are dropped), so its discrete divergence vanishes to rounding.  Then as
  * idx_set_primitive.  In the vector-potential form A is kept and Bref = bmean; in the
- * field form A only shapes the initial field.  IDX_EINVAL for NULL or non-finite bmean. */
+ * field form A only shapes the initial field.  IDX_EINVAL for NULL or non-finite bmean,
+ * and on a grid with a non-periodic direction (the vector-potential form, too, takes
+ * periodic grids only: idx_create refuses the combination). */
 int idx_set_potential(idx_sim* sim, const double* const fields[8], const double bmean[3],
                       int on_device);
 
@@ -239,7 +255,8 @@ void idx_batch_destroy(idx_batch* batch);
  * device array inside the library (IDX_NOALLOC_SCRATCH_BYTES), which every GPU that
  * loads the library holds until the process exits.
  *
- *   grid, gamma, cfl  as for idx_create (precision is FP64).
+ *   grid, gamma, cfl  as for idx_create (precision is FP64); periodic in every direction
+ *                     (IDX_EINVAL otherwise).
  *   state             8 device pointers on the current device, layout as above, updated
  *                     in place.
  *   inv_dt            host double, in/out: the inverse CFL time carried between calls.

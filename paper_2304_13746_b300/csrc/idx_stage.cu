@@ -233,6 +233,75 @@ __global__ void __launch_bounds__(kThreads) k_cons_from_prims(Geo g, Ptr8<const 
 }
 
 // ---------------------------------------------------------------------------
+// Non-periodic boundaries.  Along a non-periodic direction the grid carries two ghost
+// cells per side (interior cell i is cell i + 2; the normal field's n + 1 faces are faces
+// 2 .. n + 2) and is stepped as a periodic one: the wrap-around only touches ghost cells,
+// which k_fill_ghosts refills from the interior before every stage, direction by
+// direction (x, y, z, each over the full padded extent of the others, so edge and corner
+// ghosts are consistent).  Outflow: copies of the nearest interior cell (cell fields and
+// the transverse face fields stored with it) and of the boundary face (normal field).
+// Reflecting: the mirror image about the boundary face with the normal momentum and
+// normal field reversed.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_fill_ghosts(Geo g, int d, int kind,
+                                                          Ptr8<double> U) {
+  const int a = (d + 1) % 3, b = (d + 2) % 3;
+  const long long total = 4ll * g.n[a] * g.n[b];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int slot = (int)(t & 3);
+  const long long r = t >> 2;
+  const int oa = (int)(r % g.n[a]), ob = (int)(r / g.n[a]);
+  const int n = g.n[d] - 4;  // interior cells
+  const int base = oa * g.stride[a] + ob * g.stride[b];
+  const int sd = g.stride[d];
+  const int gp = slot < 2 ? slot : n + slot;  // ghost cells 0, 1, n + 2, n + 3
+  const bool reflect = kind == IDX_BC_REFLECTING;
+  const int src = reflect ? (slot < 2 ? 3 - gp : 2 * n + 3 - gp) : (slot < 2 ? 2 : n + 1);
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    if (f == 5 + d) continue;
+    const double v = U.f[f][base + src * sd];
+    U.f[f][base + gp * sd] = (reflect && f == 1 + d) ? -v : v;
+  }
+  // normal field on the ghost faces 0, 1 and n + 3 (face n + 2 is the boundary face)
+  if (slot == 2) return;
+  const int fsrc = reflect ? (slot == 0 ? 4 : (slot == 1 ? 3 : n + 1)) : (slot < 2 ? 2 : n + 2);
+  const double v = U.f[5 + d][base + fsrc * sd];
+  U.f[5 + d][base + gp * sd] = reflect ? -v : v;
+}
+
+// User layout <-> padded layout of the 8 fields (user layout: cells n_d, the normal field
+// n_d + 1 faces along a non-periodic d).  One thread per point of the user box extended
+// by one along each non-periodic direction.
+struct Pad {
+  int un[3];    // user cells per direction
+  int off[3];   // 2 along a non-periodic direction, else 0
+  int ext[3];   // 1 along a non-periodic direction, else 0
+};
+__global__ void __launch_bounds__(kThreads) k_pad(Geo g, Pad pd, Ptr8<const double> src,
+                                                  Ptr8<double> dst, int unpad) {
+  const int ex = pd.un[0] + pd.ext[0], ey = pd.un[1] + pd.ext[1], ez = pd.un[2] + pd.ext[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)ex * ey * ez) return;
+  const int i = (int)(t % ex);
+  const long long r = t / ex;
+  const int j = (int)(r % ey), k = (int)(r / ey);
+  const int p = (i + pd.off[0]) + (j + pd.off[1]) * g.stride[1] + (k + pd.off[2]) * g.stride[2];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    // this field's user extent: the normal field of a non-periodic direction has n + 1
+    const int ux = pd.un[0] + (f == 5 ? pd.ext[0] : 0);
+    const int uy = pd.un[1] + (f == 6 ? pd.ext[1] : 0);
+    const int uz = pd.un[2] + (f == 7 ? pd.ext[2] : 0);
+    if (i >= ux || j >= uy || k >= uz) continue;
+    const long long u = i + (long long)ux * (j + (long long)uy * k);
+    if (unpad) dst.f[f][u] = src.f[f][p];
+    else dst.f[f][p] = src.f[f][u];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Sweep along direction D: a thread owns a segment of up to SEG faces of one pencil,
 // marches along D keeping three cells' primitives and one slope in registers, and
 // computes each cell's van Leer slopes once and each face's HLLD flux once.
@@ -934,6 +1003,8 @@ struct idx_sim {
   bool pot;             // vector-potential induction (Eqs. 7-8)
   Ptr3 A, A1, A2;       // edge potential of the state and of the stage results
   Ptr3 Bref;            // fixed face field: B = Bref + curl A
+  int bc[3];            // boundary kind per direction (periodic along a one-cell direction)
+  bool bounded;         // some direction is not periodic: the grid is padded
   Ctrl* ctrl;           // device
   Ctrl* host_ctrl;      // pinned mirror
   cudaGraph_t graph;
@@ -1174,8 +1245,21 @@ void launch_update(idx_sim* s, const StagePlan& p, int st, Ptr8<T>* F, T** E) {
   }
 }
 
+// Ghost refill of a padded state, direction by direction.
+void launch_fill_ghosts(idx_sim* s, const Ptr8<double>& U) {
+  if (!s->bounded) return;
+  const Geo& g = s->geo;
+  for (int d = 0; d < 3; ++d) {
+    if (s->bc[d] == IDX_BC_PERIODIC) continue;
+    const long long total = 4ll * g.n[(d + 1) % 3] * g.n[(d + 2) % 3];
+    k_fill_ghosts<<<(unsigned)((total + kThreads - 1) / kThreads), kThreads, 0, s->stream>>>(
+        g, d, s->bc[d], U);
+  }
+}
+
 template <typename T>
 void launch_stage(idx_sim* s, const StagePlan& p, int st, const Ptr8<T>& W, Ptr8<T>* F, T** E) {
+  launch_fill_ghosts(s, *p.in[st]);
   launch_fluxes<T>(s, *p.in[st], W, F, 1);
   launch_emf<T>(s, p, st, W, F, E);
   launch_update<T>(s, p, st, F, E);
@@ -1210,7 +1294,7 @@ int tune_once(idx_sim* s) {
   if (s->tuned) return IDX_OK;
   s->tuned = true;
   if (s->geo.ncell < kTuneMinCells) return IDX_OK;
-  const TuneKey key{s->grid.nx, s->grid.ny, s->grid.nz, s->solver.precision, s->device};
+  const TuneKey key{s->geo.n[0], s->geo.n[1], s->geo.n[2], s->solver.precision, s->device};
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tune_cache.find(key);
@@ -1251,9 +1335,21 @@ int sync_ctrl(const idx_sim* s) {
   return IDX_OK;
 }
 
+// Flat index of a cell of the (possibly padded) grid in the user's layout; a ghost cell
+// maps to the interior cell it was filled from along each non-periodic direction.
+int64_t user_cell(const idx_sim* s, unsigned long long c) {
+  if (!s->bounded) return (int64_t)c;
+  const Geo& g = s->geo;
+  int ijk[3] = {(int)(c % g.n[0]), (int)((c / g.n[0]) % g.n[1]), (int)(c / ((unsigned long long)g.n[0] * g.n[1]))};
+  const int un[3] = {s->grid.nx, s->grid.ny, s->grid.nz};
+  for (int d = 0; d < 3; ++d)
+    if (s->bc[d]) ijk[d] = std::min(std::max(ijk[d] - 2, 0), un[d] - 1);
+  return ijk[0] + (int64_t)un[0] * (ijk[1] + (int64_t)un[1] * ijk[2]);
+}
+
 int pending_error(idx_sim* s) {
   if (s->host_ctrl->err != 0) {
-    s->last_bad = (int64_t)s->host_ctrl->bad_cell;
+    s->last_bad = user_cell(s, s->host_ctrl->bad_cell);
     return s->host_ctrl->err;
   }
   return IDX_OK;
@@ -1346,6 +1442,19 @@ void encode_sweep_maps(idx_sim* s, void* wbase, size_t elem, size_t field_stride
   }
 }
 
+// Boundary kinds of a grid (periodic along a one-cell direction) and the padded cell
+// counts; false for an unknown kind or a non-periodic direction of fewer than 2 cells.
+bool grid_bc(const idx_grid* grid, int bc[3], int pn[3]) {
+  const int n[3] = {grid->nx, grid->ny, grid->nz};
+  for (int d = 0; d < 3; ++d) {
+    const int k = grid->bc[d];
+    if (k != IDX_BC_PERIODIC && k != IDX_BC_OUTFLOW && k != IDX_BC_REFLECTING) return false;
+    bc[d] = n[d] > 1 ? k : IDX_BC_PERIODIC;
+    pn[d] = n[d] + (bc[d] ? 4 : 0);
+  }
+  return true;
+}
+
 bool valid_solver(const idx_solver* v) {
   return v && v->recon == 1 && (v->riemann == 1 || v->riemann == 2 || v->riemann == 4) &&
          v->emf == 2 && (v->rk_order == 2 || v->rk_order == 3) &&
@@ -1378,7 +1487,11 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
   if (!grid || !valid_solver(solver) || !(gamma > 1.0) || !std::isfinite(gamma)) return IDX_EINVAL;
   if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return IDX_EINVAL;
   if (!(grid->lx > 0) || !(grid->ly > 0) || !(grid->lz > 0)) return IDX_EINVAL;
-  const long long ncell = (long long)grid->nx * grid->ny * grid->nz;
+  int bc[3], pn[3];
+  if (!grid_bc(grid, bc, pn)) return IDX_EINVAL;
+  const bool bounded = bc[0] || bc[1] || bc[2];
+  if (bounded && solver->induction == IDX_INDUCTION_POTENTIAL) return IDX_EINVAL;
+  const long long ncell = (long long)pn[0] * pn[1] * pn[2];
   if (ncell >= (1ll << 31)) return IDX_EINVAL;
 
   idx_sim* s = new idx_sim();
@@ -1388,14 +1501,17 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
   s->solver = *solver;
   s->last_bad = -1;
   if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return IDX_ECUDA; }
-  Geo& g = s->geo;
-  g.n[0] = grid->nx; g.n[1] = grid->ny; g.n[2] = grid->nz;
-  g.stride[0] = 1; g.stride[1] = grid->nx; g.stride[2] = grid->nx * grid->ny;
+  for (int d = 0; d < 3; ++d) s->bc[d] = bc[d];
+  s->bounded = bounded;
+  Geo& g = s->geo;  // the padded grid along non-periodic directions
+  g.n[0] = pn[0]; g.n[1] = pn[1]; g.n[2] = pn[2];
+  g.stride[0] = 1; g.stride[1] = pn[0]; g.stride[2] = pn[0] * pn[1];
   g.ncell = (int)ncell;
   const double l[3] = {grid->lx, grid->ly, grid->lz};
+  const int un[3] = {grid->nx, grid->ny, grid->nz};
   for (int d = 0; d < 3; ++d) {
     g.active[d] = g.n[d] > 1;
-    g.inv_dl[d] = (double)g.n[d] / l[d];
+    g.inv_dl[d] = (double)un[d] / l[d];
     g.inv_dlf[d] = (float)g.inv_dl[d];
   }
   geo_set_gamma(g, gamma);
@@ -1509,8 +1625,98 @@ static int potential_from_field(idx_sim* s) {
   return IDX_OK;
 }
 
+// Padded sims: the user layout of field f (cells, or n + 1 normal faces along a
+// non-periodic direction), as a pad descriptor and per-field element counts.
+static Pad pad_of(const idx_sim* s, size_t count[8]) {
+  Pad pd;
+  const int un[3] = {s->grid.nx, s->grid.ny, s->grid.nz};
+  for (int d = 0; d < 3; ++d) {
+    pd.un[d] = un[d];
+    pd.off[d] = s->bc[d] ? 2 : 0;
+    pd.ext[d] = s->bc[d] ? 1 : 0;
+  }
+  for (int f = 0; f < 8; ++f) {
+    size_t c = 1;
+    for (int d = 0; d < 3; ++d) c *= (size_t)(un[d] + (f == 5 + d ? pd.ext[d] : 0));
+    count[f] = c;
+  }
+  return pd;
+}
+
+static unsigned pad_blocks(const Pad& pd) {
+  const long long t = (long long)(pd.un[0] + pd.ext[0]) * (pd.un[1] + pd.ext[1]) *
+                      (pd.un[2] + pd.ext[2]);
+  return (unsigned)((t + kThreads - 1) / kThreads);
+}
+
+// User fields (host or device) into the interior of a padded state.  Host fields pass
+// through a stream-ordered device staging buffer.
+static int pad_in(idx_sim* s, const double* const fields[8], int on_device, Ptr8<double> dst) {
+  size_t count[8], total = 0;
+  const Pad pd = pad_of(s, count);
+  for (int f = 0; f < 8; ++f) total += count[f];
+  Ptr8<const double> src;
+  double* staging = nullptr;
+  if (on_device) {
+    for (int f = 0; f < 8; ++f) src.f[f] = fields[f];
+  } else {
+    if (cudaMallocAsync(&staging, sizeof(double) * total, s->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return IDX_ENOMEM;
+    }
+    double* q = staging;
+    for (int f = 0; f < 8; ++f) {
+      IDX_TRY(cudaMemcpyAsync(q, fields[f], sizeof(double) * count[f], cudaMemcpyHostToDevice,
+                              s->stream));
+      src.f[f] = q;
+      q += count[f];
+    }
+  }
+  k_pad<<<pad_blocks(pd), kThreads, 0, s->stream>>>(s->geo, pd, src, dst, 0);
+  IDX_TRY(cudaGetLastError());
+  if (staging) IDX_TRY(cudaFreeAsync(staging, s->stream));
+  return IDX_OK;
+}
+
+// The interior of the padded state U out to user fields (host or device).
+static int pad_out(idx_sim* s, double* const fields[8], int on_device) {
+  size_t count[8], total = 0;
+  const Pad pd = pad_of(s, count);
+  for (int f = 0; f < 8; ++f) total += count[f];
+  Ptr8<double> dst;
+  double* staging = nullptr;
+  if (on_device) {
+    for (int f = 0; f < 8; ++f) dst.f[f] = fields[f];
+  } else {
+    if (cudaMallocAsync(&staging, sizeof(double) * total, s->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return IDX_ENOMEM;
+    }
+    double* q = staging;
+    for (int f = 0; f < 8; ++f) { dst.f[f] = q; q += count[f]; }
+  }
+  k_pad<<<pad_blocks(pd), kThreads, 0, s->stream>>>(s->geo, pd, cst(s->U), dst, 1);
+  IDX_TRY(cudaGetLastError());
+  if (staging) {
+    for (int f = 0; f < 8; ++f)
+      IDX_TRY(cudaMemcpyAsync(fields[f], dst.f[f], sizeof(double) * count[f],
+                              cudaMemcpyDeviceToHost, s->stream));
+    IDX_TRY(cudaFreeAsync(staging, s->stream));
+  }
+  return IDX_OK;
+}
+
 int idx_set_state(idx_sim* s, const double* const fields[8], int on_device) {
   if (!s || !fields) return IDX_EINVAL;
+  if (s->bounded) {
+    for (int f = 0; f < 8; ++f)
+      if (!fields[f]) return IDX_EINVAL;
+    int rc = pad_in(s, fields, on_device, s->U);
+    if (rc != IDX_OK) return rc;
+    launch_fill_ghosts(s, s->U);
+    IDX_TRY(cudaGetLastError());
+    return after_new_state(s);
+  }
   int rc = copy_fields_in(s, s->U, fields, on_device);
   if (rc == IDX_OK) rc = potential_from_field(s);
   if (rc != IDX_OK) return rc;
@@ -1519,6 +1725,19 @@ int idx_set_state(idx_sim* s, const double* const fields[8], int on_device) {
 
 int idx_set_primitive(idx_sim* s, const double* const fields[8], int on_device) {
   if (!s || !fields) return IDX_EINVAL;
+  if (s->bounded) {
+    // primitives padded into U1 (scratch here), ghosts filled (the velocity flips like the
+    // momentum), converted into U, whose ghosts are filled again
+    for (int f = 0; f < 8; ++f)
+      if (!fields[f]) return IDX_EINVAL;
+    int rc = pad_in(s, fields, on_device, s->U1);
+    if (rc != IDX_OK) return rc;
+    launch_fill_ghosts(s, s->U1);
+    k_cons_from_prims<<<blocks_for(s->geo.ncell), kThreads, 0, s->stream>>>(s->geo, cst(s->U1), s->U);
+    launch_fill_ghosts(s, s->U);
+    IDX_TRY(cudaGetLastError());
+    return after_new_state(s);
+  }
   // stage the primitives in U1 (scratch at this point), convert into U
   int rc = copy_fields_in(s, s->U1, fields, on_device);
   if (rc != IDX_OK) return rc;
@@ -1531,7 +1750,7 @@ int idx_set_primitive(idx_sim* s, const double* const fields[8], int on_device) 
 
 int idx_set_potential(idx_sim* s, const double* const fields[8], const double bmean[3],
                       int on_device) {
-  if (!s || !fields || !bmean) return IDX_EINVAL;
+  if (!s || !fields || !bmean || s->bounded) return IDX_EINVAL;
   for (int f = 0; f < 8; ++f)
     if (!fields[f]) return IDX_EINVAL;
   for (int d = 0; d < 3; ++d)
@@ -1578,6 +1797,13 @@ int idx_get_state(const idx_sim* cs, double* const fields[8], int on_device) {
   if (!s || !fields) return IDX_EINVAL;
   for (int f = 0; f < 8; ++f)
     if (!fields[f]) return IDX_EINVAL;
+  if (s->bounded) {
+    int rc = pad_out(s, fields, on_device);
+    if (rc != IDX_OK) return rc;
+    rc = sync_ctrl(s);
+    if (rc != IDX_OK) return rc;
+    return pending_error(s);
+  }
   const size_t bytes = sizeof(double) * (size_t)s->geo.ncell;
   for (int f = 0; f < 8; ++f)
     IDX_TRY(cudaMemcpyAsync(fields[f], s->U.f[f], bytes,
@@ -1668,6 +1894,7 @@ int idx_kernel_times(idx_sim* s, int reps, double ms[6]) {
     const StagePlan plan = stage_plan(s);
     for (int st = 0; st < plan.n; ++st) {
       const Ptr8<double>& Uin = *plan.in[st];
+      launch_fill_ghosts(s, Uin);
       IDX_TRY(cudaEventRecord(ev[0], s->stream));
       if (f32) {
         k_prims<float><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), s->Wf, s->Cf, s->ctrl, 1);
@@ -1746,7 +1973,9 @@ int idx_step_count(const idx_sim* cs, int64_t* nsteps) {
 int idx_footprint(const idx_grid* grid, int precision, uint64_t* bytes) {
   if (!grid || !bytes || grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return IDX_EINVAL;
   if (precision != IDX_FP64 && precision != IDX_FP32_BULK) return IDX_EINVAL;
-  const long long ncell = (long long)grid->nx * grid->ny * grid->nz;
+  int bc[3], pn[3];
+  if (!grid_bc(grid, bc, pn)) return IDX_EINVAL;
+  const long long ncell = (long long)pn[0] * pn[1] * pn[2];
   if (ncell >= (1ll << 31)) return IDX_EINVAL;
   *bytes = (uint64_t)sim_bytes(ncell, precision == IDX_FP32_BULK);
   return IDX_OK;
@@ -1755,7 +1984,9 @@ int idx_footprint(const idx_grid* grid, int precision, uint64_t* bytes) {
 int idx_footprint_solver(const idx_grid* grid, const idx_solver* solver, uint64_t* bytes) {
   if (!grid || !bytes || !valid_solver(solver) || grid->nx < 1 || grid->ny < 1 || grid->nz < 1)
     return IDX_EINVAL;
-  const long long ncell = (long long)grid->nx * grid->ny * grid->nz;
+  int bc[3], pn[3];
+  if (!grid_bc(grid, bc, pn)) return IDX_EINVAL;
+  const long long ncell = (long long)pn[0] * pn[1] * pn[2];
   if (ncell >= (1ll << 31)) return IDX_EINVAL;
   *bytes = (uint64_t)sim_bytes(ncell, solver->precision == IDX_FP32_BULK, solver->rk_order == 3,
                                solver->induction == IDX_INDUCTION_POTENTIAL);
@@ -1818,6 +2049,10 @@ extern "C" int idx_step_noalloc(const idx_grid* grid, double gamma, double cfl,
     if (!state[f]) return IDX_EINVAL;
   if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return IDX_EINVAL;
   if (!(grid->lx > 0) || !(grid->ly > 0) || !(grid->lz > 0)) return IDX_EINVAL;
+  {
+    int bc[3], pn[3];
+    if (!grid_bc(grid, bc, pn) || bc[0] || bc[1] || bc[2]) return IDX_EINVAL;
+  }
   const long long ncell = (long long)grid->nx * grid->ny * grid->nz;
   if (ncell > IDX_NOALLOC_MAX_CELLS) return IDX_ETOOLARGE;
 
@@ -2122,7 +2357,7 @@ template <typename T> int batch_upload(idx_batch* b) {
     inst[i] = inst_of<T>(s);
     // stepped by its own kernels, no work-list items: large members, and members whose
     // cycle the work-list kernels do not run (RK3, vector-potential form)
-    if (s->geo.ncell >= kSoloCells || s->solver.rk_order != 2 || s->pot) {
+    if (s->geo.ncell >= kSoloCells || s->solver.rk_order != 2 || s->pot || s->bounded) {
       b->solo.push_back(s);
       continue;
     }

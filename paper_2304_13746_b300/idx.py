@@ -32,7 +32,15 @@ class IdxError(RuntimeError):
 
 class Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
-                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double)]
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+                ("bc", ctypes.c_int * 3)]
+
+
+BC = {"periodic": 0, "outflow": 1, "reflecting": 2}
+
+
+def _bc_codes(bc):
+    return [BC[b] if isinstance(b, str) else int(b) for b in bc]
 
 
 class Solver(ctypes.Structure):
@@ -107,14 +115,15 @@ def pipe_rates():
     return dict(zip(keys, out[:]))
 
 
-def footprint(shape, precision="fp64", rk_order=2, induction="field", riemann="hlld"):
+def footprint(shape, precision="fp64", rk_order=2, induction="field", riemann="hlld",
+              bc=(0, 0, 0)):
     """Device bytes a sim of this shape (nz, ny, nx) and configuration allocates."""
     nz, ny, nx = (int(v) for v in shape)
     out = ctypes.c_uint64()
     s = Solver(1, RIEMANN[riemann], 2, int(rk_order), 0.4, PRECISIONS[precision],
                INDUCTION[induction])
-    rc = lib().idx_footprint_solver(ctypes.byref(Grid(nx, ny, nz, 1.0, 1.0, 1.0)), ctypes.byref(s),
-                                    ctypes.byref(out))
+    g = Grid(nx, ny, nz, 1.0, 1.0, 1.0, (ctypes.c_int * 3)(*_bc_codes(bc)))
+    rc = lib().idx_footprint_solver(ctypes.byref(g), ctypes.byref(s), ctypes.byref(out))
     if rc != IDX_OK:
         raise IdxError(rc, "idx_footprint_solver")
     return int(out.value)
@@ -137,15 +146,26 @@ class Sim:
     """
 
     def __init__(self, shape, lengths, gamma=5.0 / 3.0, cfl=0.4, precision="fp64", stream=None,
-                 riemann="hlld", rk_order=2, induction="field"):
+                 riemann="hlld", rk_order=2, induction="field", bc=(0, 0, 0)):
+        """bc: boundary kind per direction x, y, z ("periodic", "outflow", "reflecting" or
+        0/1/2); along a non-periodic direction of more than one cell the normal face field
+        has one more face than cells (see include/idx.h)."""
         L = lib()
         nz, ny, nx = (int(s) for s in shape)
         self.shape = (nz, ny, nx)
+        self.bc = _bc_codes(bc)
+        # per-field shapes in the user layout
+        self.field_shapes = [self.shape] * 5
+        for d, ax in ((0, 2), (1, 1), (2, 0)):
+            fs = list(self.shape)
+            if self.bc[d] and self.shape[ax] > 1:
+                fs[ax] += 1
+            self.field_shapes.append(tuple(fs))
         self.lengths = tuple(float(x) for x in lengths)
         self.gamma = float(gamma)
         self.cfl = float(cfl)
         self.precision = precision
-        g = Grid(nx, ny, nz, *self.lengths)
+        g = Grid(nx, ny, nz, *self.lengths, (ctypes.c_int * 3)(*self.bc))
         self.induction = induction
         s = Solver(1, RIEMANN[riemann], 2, int(rk_order), self.cfl, PRECISIONS[precision],
                    INDUCTION[induction])
@@ -180,18 +200,19 @@ class Sim:
     def _ptrs(self, fields, writable=False):
         assert len(fields) in (3, 8)
         P = P8 if len(fields) == 8 else P3
+        shapes = self.field_shapes if len(fields) == 8 else [self.shape] * 3
         if all(_is_torch(a) for a in fields):
             import torch
-            for a in fields:
+            for a, sh in zip(fields, shapes):
                 assert a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()
-                assert tuple(a.shape) == self.shape
+                assert tuple(a.shape) == sh
             _torch_sync()
             return P(*[a.data_ptr() for a in fields]), 1, fields
         arrs = []
-        for a in fields:
+        for a, sh in zip(fields, shapes):
             a = np.asarray(a)
-            assert a.dtype == np.float64 and a.flags.c_contiguous and a.shape == self.shape, \
-                (a.dtype, a.shape)
+            assert a.dtype == np.float64 and a.flags.c_contiguous and a.shape == sh, \
+                (a.dtype, a.shape, sh)
             if writable:
                 assert a.flags.writeable
             arrs.append(a)
@@ -232,10 +253,10 @@ class Sim:
         if out is None:
             if device:
                 import torch
-                out = [torch.empty(self.shape, dtype=torch.float64, device="cuda")
-                       for _ in range(8)]
+                out = [torch.empty(sh, dtype=torch.float64, device="cuda")
+                       for sh in self.field_shapes]
             else:
-                out = [np.empty(self.shape, dtype=np.float64) for _ in range(8)]
+                out = [np.empty(sh, dtype=np.float64) for sh in self.field_shapes]
         p, dev, keep = self._ptrs(out, writable=True)
         self._check(lib().idx_get_state(self._h, p, dev), "idx_get_state")
         return out

@@ -59,6 +59,9 @@ def _create(L, grid, gamma=5 / 3, solver=None):
     (idx.Grid(4, 4, 4, 1, 1, 1), 5 / 3, idx.Solver(1, 4, 2, 2, 1.0, 0)),  # cfl
     (idx.Grid(4, 4, 4, 1, 1, 1), 5 / 3, idx.Solver(1, 4, 2, 2, 0.4, 7)),  # precision
     (idx.Grid(4, 4, 4, 1, 1, 1), 5 / 3, idx.Solver(1, 4, 2, 2, 0.4, 0, 2)),  # induction
+    (idx.Grid(4, 4, 4, 1, 1, 1, (ctypes.c_int * 3)(3, 0, 0)), 5 / 3, None),   # boundary kind
+    (idx.Grid(4, 4, 4, 1, 1, 1, (ctypes.c_int * 3)(0, 1, 0)), 5 / 3,
+     idx.Solver(1, 4, 2, 2, 0.4, 0, 1)),                                      # potential + walls
 ])
 def test_create_rejects_invalid_arguments(L, grid, gamma, solver):
     rc, h = _create(L, grid, gamma, solver)
@@ -112,3 +115,14 @@ def test_binding_refuses_to_run_without_library(tmp_path):
             idx.lib(str(tmp_path / "missing.so"))
     finally:
         idx._lib = saved
+
+
+def test_footprint_of_a_padded_grid(L):
+    # two ghost cells per side along each non-periodic direction; a one-cell direction
+    # takes no boundary
+    base = idx.footprint((8, 16, 32))
+    per_cell = (base - 256) / (8 * 16 * 32)
+    got = idx.footprint((8, 16, 32), bc=("outflow", "reflecting", "periodic"))
+    padded = 8 * 20 * 36
+    assert got == pytest.approx(per_cell * padded + 256, rel=1e-3)
+    assert idx.footprint((1, 16, 32), bc=(0, 0, 1)) == idx.footprint((1, 16, 32))
