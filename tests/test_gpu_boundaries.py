@@ -51,14 +51,15 @@ def run_pair(prim, lengths, gamma, bc, cycles, precision="fp64", t_end=None):
     nz, ny, nx = prim[0].shape
     s = idx.Sim((nz, ny, nx), lengths, gamma, 0.4, precision, bc=bc)
     s.set_primitive(prim)
-    assert s.time()[1] == pytest.approx(o.cfl / o.inv_dt, rel=1e-13)
+    rel = 1e-12 if precision == "fp64" else 1e-5   # FP32 bulk: signal speeds in FP32
+    assert s.time()[1] == pytest.approx(o.cfl / o.inv_dt, rel=rel)
     if t_end is not None:
         n_o, n_g = o.advance(t_end), s.advance(t_end)
         assert n_o == n_g
     else:
         for _ in range(cycles):
             dt = o.step()
-            assert s.step(want_dt=True) == pytest.approx(dt, rel=1e-12)
+            assert s.step(want_dt=True) == pytest.approx(dt, rel=rel)
     return o, s
 
 
