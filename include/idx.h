@@ -173,6 +173,9 @@ int idx_kernel_times(idx_sim* sim, int reps, double ms[6]);
  * results are cached per grid, precision and device for the process):
  *   2, 4, 8, 16, 32   one thread marches that many faces of a pencil (loads from HBM);
  *   -1                x only: one warp per 32 cells of an x-row, neighbours by shuffle;
+ *   -2                x only: a block stages 32 x-faces of 8 rows (plus periodic halos)
+ *                     into shared memory with bulk tensor copies (TMA), one face per
+ *                     thread; needs nx % 32 == 0 and ny % 8 == 0;
  *   116, 132          y or z only: a block stages a tile of 32 x-cells by 16 / 32 faces
  *                     (plus a 2-cell periodic halo) into shared memory with bulk tensor
  *                     copies (TMA) and marches it there; needs nx % 32 == 0 and n_d a

@@ -542,6 +542,85 @@ __global__ void __launch_bounds__(8 * L, sizeof(T) == 4 ? 96 / L : 1)
 }
 
 // ---------------------------------------------------------------------------
+// TMA-staged sweep along x.  A block owns 32 x-faces of 8 consecutive y-rows at one z.
+// The 7 rotated variables arrive by bulk tensor copies: the body (32 cells) and the two
+// halos of 4 cells (the start of a copy must sit on a 16-byte boundary, so a 2-cell halo
+// is fetched as 4), each wrapped periodically by hand.  Warp r takes row r, lane f face f,
+// and forms its face from cells f-2 .. f+1 in shared memory (each cell's slope is formed
+// by the two faces that use it).  Needs nx % 32 == 0 and ny % 8 == 0.
+// ---------------------------------------------------------------------------
+constexpr int kXRows = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kXRows)
+    k_sweep_tma_x(Geo g, const __grid_constant__ CUtensorMap tm_body,
+                  const __grid_constant__ CUtensorMap tm_halo, const double* bface, Ptr8<T> F,
+                  Ctrl* ctrl, int check_dt) {
+  if (check_dt && !(ctrl->dt > 0.0)) return;
+  constexpr int R = kXRows;
+  constexpr int PB = 32 * R, PH = 4 * R;          // body / halo plane sizes (elements)
+  constexpr int PLANE = PB + 2 * PH;
+  __shared__ __align__(128) T tile[7 * PLANE];     // [var]{lo [R][4], body [R][32], hi [R][4]}
+  __shared__ __align__(8) uint64_t bar;
+  const int ntx = g.n[0] >> 5, nty = g.n[1] / R;
+  int b = blockIdx.x;
+  const int x0 = (b % ntx) * 32;
+  b /= ntx;
+  const int y0 = (b % nty) * R;
+  const int z = b / nty;
+  constexpr int var[7] = {0, 1, 2, 3, 4, 6, 7};  // rho, v_n = vx, vy, vz, P, B_t1 = By, B_t2 = Bz
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(&bar, 7u * PLANE * sizeof(T));
+    int lo = x0 - 4;
+    if (lo < 0) lo += g.n[0];
+    int hi = x0 + 32;
+    if (hi >= g.n[0]) hi -= g.n[0];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      T* dst = tile + q * PLANE;
+      tma_load_4d(dst, &tm_halo, lo, y0, z, var[q], &bar);
+      tma_load_4d(dst + PH, &tm_body, x0, y0, z, var[q], &bar);
+      tma_load_4d(dst + PH + PB, &tm_halo, hi, y0, z, var[q], &bar);
+    }
+  }
+  const int f = threadIdx.x & 31, r = threadIdx.x >> 5;
+  const int c = (x0 + f) + (y0 + r) * g.stride[1] + z * g.stride[2];
+  const T bn = to_bulk<T>(bface[c]);
+  const bool landed = mbar_wait(&bar, 0, kWaitNs);
+  if (__syncthreads_or(!landed)) {
+    tma_give_up(ctrl, &bar, 0);
+    return;
+  }
+  // cell at column col (-4 .. 35) of row r of variable q
+  auto ld = [&](int q, int col) {
+    const T* base = tile + q * PLANE;
+    if (col < 0) return base[r * 4 + col + 4];
+    if (col < 32) return base[PH + r * 32 + col];
+    return base[PH + PB + r * 4 + col - 32];
+  };
+  Side<T> Ls, Rs;
+  T Lq[7], Rq[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    const T wmm = ld(q, f - 2), wm = ld(q, f - 1), w0 = ld(q, f), wp = ld(q, f + 1);
+    Lq[q] = wm + vanleer_half(wm - wmm, w0 - wm);
+    Rq[q] = w0 - vanleer_half(w0 - wm, wp - w0);
+  }
+  Ls.r = Lq[0]; Ls.u = Lq[1]; Ls.v = Lq[2]; Ls.w = Lq[3]; Ls.p = Lq[4]; Ls.b1 = Lq[5]; Ls.b2 = Lq[6];
+  Rs.r = Rq[0]; Rs.u = Rq[1]; Rs.v = Rq[2]; Rs.w = Rq[3]; Rs.p = Rq[4]; Rs.b1 = Rq[5]; Rs.b2 = Rq[6];
+  T flux[7], cmax;
+  riemann_flux(g.riemann, Ls, Rs, bn, geo_gamma<T>(g), geo_gm1inv<T>(g), flux, cmax);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) F.f[q][c] = flux[q];
+  F.f[7][c] = cmax;
+}
+
+// ---------------------------------------------------------------------------
 // Sweep along x: one warp per run of 32 consecutive cells of an x-row, lane l holding
 // cell base + l (mod nx), so every load is coalesced.  A lane gets its neighbours'
 // primitives and slopes by warp shuffle; lane 0 also loads cells base-1, base-2 and
@@ -1075,13 +1154,26 @@ void allow_tma_smem() {
 
 // Shapes a direction can take: 100 + L only where the staged tiles fit the grid.
 bool tma_shape_ok(const idx_sim* s, int d, int shape) {
+  if (shape == -2) return d == 0 && s->tma_ok[0][0];
   if (shape != 116 && shape != 132) return true;
   return d != 0 && s->tma_ok[d][shape == 132 ? 1 : 0] && s->geo.n[d] % (shape - 100) == 0;
+}
+
+template <typename T> void launch_tma_x(idx_sim* s, const double* bface, const Ptr8<T>& F,
+                                        int check_dt) {
+  const Geo& g = s->geo;
+  const unsigned blocks = (unsigned)((g.n[0] / 32) * (g.n[1] / kXRows) * g.n[2]);
+  k_sweep_tma_x<T><<<blocks, 32 * kXRows, 0, s->stream>>>(g, s->tm_body[0][0], s->tm_halo[0],
+                                                          bface, F, s->ctrl, check_dt);
 }
 
 template <typename T, int D>
 void launch_sweep_d(idx_sim* s, int shape, const Ptr8<T>& W, const double* bface,
                     const Ptr8<T>& F, int check_dt) {
+  if (D == 0 && shape == -2 && tma_shape_ok(s, 0, -2)) {
+    launch_tma_x<T>(s, bface, F, check_dt);
+    return;
+  }
   if (D != 0 && tma_shape_ok(s, D, shape)) {
     if (shape == 116) { launch_tma<T, (D == 0 ? 1 : D), 16>(s, bface, F, check_dt); return; }
     if (shape == 132) { launch_tma<T, (D == 0 ? 1 : D), 32>(s, bface, F, check_dt); return; }
@@ -1121,16 +1213,16 @@ int tune_sweeps(idx_sim* s, const Ptr8<double>& U, const Ptr8<T>& W, Ptr8<T>* F)
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return IDX_ECUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return IDX_ECUDA; }
-  const int cand[8] = {-1, 2, 4, 8, 16, 32, 116, 132};
+  const int cand[9] = {-1, -2, 2, 4, 8, 16, 32, 116, 132};
   int rc = IDX_OK;
   for (int d = 0; d < 3 && rc == IDX_OK; ++d) {
     if (!g.active[d]) continue;
     float best = 1e30f;
     int best_shape = kSegDefault;
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < 9; ++q) {
       const int shape = cand[q];
-      if (shape == -1 && d != 0) continue;
-      if (shape > 100 && !tma_shape_ok(s, d, shape)) continue;
+      if (shape < 0 && d != 0) continue;
+      if ((shape > 100 || shape == -2) && !tma_shape_ok(s, d, shape)) continue;
       if (shape > 0 && shape < 100 && shape > 2 * g.n[d]) continue;
       s->sweep_shape[d] = shape;
       launch_sweep<T>(s, d, W, U.f[5 + d], F[d], 0);
@@ -1426,6 +1518,16 @@ void encode_sweep_maps(idx_sim* s, void* wbase, size_t elem, size_t field_stride
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   const CUtensorMapDataType dt =
       elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  // x: body of 32 cells and halos of 4, 8 rows deep
+  if (g.active[0] && g.n[1] % kXRows == 0) {
+    auto encode_x = [&](unsigned width, CUtensorMap* m) {
+      const cuuint32_t box[4] = {width, (cuuint32_t)kXRows, 1, 1};
+      return enc(m, dt, 4, wbase, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                 CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    s->tma_ok[0][0] = encode_x(4, &s->tm_halo[0]) && encode_x(32, &s->tm_body[0][0]);
+  }
   for (int d = 1; d <= 2; ++d) {
     if (!g.active[d]) continue;
     auto encode = [&](unsigned rows, CUtensorMap* m) {
@@ -1950,7 +2052,7 @@ int idx_set_sweep_shapes(idx_sim* s, const int shapes[3]) {
     const int x = v[d];
     const bool march = x == 2 || x == 4 || x == 8 || x == 16 || x == 32;
     const bool warpx = x == -1 && d == 0;
-    const bool staged = (x == 116 || x == 132) && tma_shape_ok(s, d, x);
+    const bool staged = (x == 116 || x == 132 || x == -2) && tma_shape_ok(s, d, x);
     if (!march && !warpx && !staged) return IDX_EINVAL;
   }
   for (int d = 0; d < 3; ++d) s->sweep_shape[d] = v[d];

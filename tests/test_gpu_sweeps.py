@@ -39,6 +39,9 @@ CASES = [
     ((16, 16, 32), (-1, 116, 116)),   # one tile per pencil: both halos wrap
     ((64, 32, 32), (32, 132, 132)),
     ((1, 64, 32), (-1, 132, 0)),      # 2D
+    ((32, 48, 64), (-2, 116, 132)),   # staged x tiles too
+    ((16, 16, 32), (-2, 116, 116)),   # one x tile per row: both x halos wrap
+    ((1, 64, 32), (-2, 132, 0)),
 ]
 
 
@@ -64,7 +67,7 @@ def test_staged_sweeps_match_oracle(shape, sweeps):
 def test_staged_and_marching_agree_on_turbulent_box(precision, tol):
     ic = inputs.turbulent_box(64, seed=6)
     out = []
-    for sweeps in ((16, 16, 16), (-1, 132, 132), (32, 116, 116)):
+    for sweeps in ((16, 16, 16), (-1, 132, 132), (32, 116, 116), (-2, 116, 116)):
         s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, precision)
         s.set_primitive(ic.prim)
         s.set_sweep_shapes(sweeps)
@@ -81,14 +84,20 @@ def test_invalid_shapes_are_refused():
     ic = inputs.random_smooth((32, 48, 64), seed=1)
     s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, "fp64")
     s.set_primitive(ic.prim)
-    for bad in ((116, 116, 116), (-1, -1, 16), (16, 132, 16), (7, 16, 16), (16, 16, 0)):
+    for bad in ((116, 116, 116), (-1, -1, 16), (16, 132, 16), (7, 16, 16), (16, 16, 0),
+                (16, -2, 16)):
         with pytest.raises(idx.IdxError) as e:
             s.set_sweep_shapes(bad)
         assert e.value.code == idx.IDX_EINVAL
     s.close()
-    # staged tiles need nx % 32 == 0
+    # staged tiles need nx % 32 == 0; staged x tiles also ny % 8 == 0
     ic = inputs.random_smooth((16, 16, 40), seed=2)
     s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, "fp64")
     with pytest.raises(idx.IdxError):
         s.set_sweep_shapes((16, 116, 16))
+    s.close()
+    ic = inputs.random_smooth((16, 12, 32), seed=2)
+    s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, "fp64")
+    with pytest.raises(idx.IdxError):
+        s.set_sweep_shapes((-2, 16, 16))
     s.close()
