@@ -509,6 +509,8 @@ def main():
         variants["fp32_bulk"] = time_variant("fp32")
         variants["fp64_vector_potential"] = time_variant("fp64", induction="potential")
         variants["fp64_vector_potential"]["note"] = "Eqs. 7-8: edge potential stepped, B = Bref + curl A"
+        variants["fp64_rk3"] = time_variant("fp64", rk_order=3)
+        variants["fp64_rk3"]["note"] = "RK3 (Table 1): three stages per cycle instead of two"
         # the paper's own performance problem (Sec. 5): 3D Orszag-Tang, FP64, at this box size
         ot = inputs.orszag_tang_3d(args.n)
         variants["fp64_orszag_tang_3d"] = time_variant("fp64", ot)
