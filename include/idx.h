@@ -1,17 +1,20 @@
 /*
- * idx.h -- C ABI of the B300 (sm_103a) ideal-MHD RK2 stage library (libidx.so).
+ * idx.h -- C ABI of the B300 (sm_103a) ideal-MHD Runge-Kutta stage library (libidx.so).
  *
- * One simulation ("sim") is one periodic Cartesian box of ideal MHD advanced by the
- * Godunov scheme of the IDEFIX paper (Lesur et al. 2023):
+ * One simulation ("sim") is one Cartesian box of ideal MHD (periodic, or with outflow or
+ * reflecting boundaries per direction) advanced by the Godunov scheme of the IDEFIX paper
+ * (Lesur et al. 2023):
  *   Eqs. (1)-(4)  ideal-MHD conservation laws (units without 4*pi),
  *   Eq. (5)       finite-volume update of cell averages,
  *   Sec. 2.3      PLM reconstruction of the primitives with the van Leer limiter,
- *                 HLLD Riemann solver (Miyoshi & Kusano 2005), pressure in the flux,
+ *                 HLLD Riemann solver (Miyoshi & Kusano 2005), pressure in the flux;
+ *                 HLL or Rusanov selectable,
  *   Sec. 2.4      constrained transport of face-centred B with the E^c edge EMF
  *                 (Gardiner & Stone 2005), Eq. (6); or its vector-potential form,
  *                 Eqs. (7)-(8): an edge potential A stepped with -E, B = curl A,
- *   Sec. 2.7      RK2 stages U_s = w_s U* + w0_s U_0 (Eq. 9, Table 1: w = 1, 0; 1/2, 1/2)
- *                 and the CFL step dt = sigma / max_V sum_d c_max,d / dl_d (Eq. 10).
+ *   Sec. 2.7      Runge-Kutta stages U_s = w_s U* + w0_s U_0 (Eq. 9, Table 1: RK2 w = 1, 0;
+ *                 1/2, 1/2 -- the default; RK3 w = 1, 0; 1/4, 3/4; 2/3, 1/3) and the CFL
+ *                 step dt = sigma / max_V sum_d c_max,d / dl_d (Eq. 10).
  *
  * Layout (every field): double[nz][ny][nx], x fastest, periodic in x, y and z unless
  * idx_grid.bc says otherwise.  The 8 state fields, in this order: rho, mx, my, mz, E
@@ -134,7 +137,7 @@ int idx_get_potential(const idx_sim* sim, double* const A[3], int on_device);
  * device error (IDX_ENONPHYS) of earlier asynchronous steps. */
 int idx_get_state(const idx_sim* sim, double* const fields[8], int on_device);
 
-/* One RK2 cycle (two stages with the same dt).  Asynchronous when dt_taken is NULL
+/* One RK cycle (its two or three stages with the same dt).  Asynchronous when dt_taken is NULL
  * (errors surface at the next synchronising call); otherwise waits and writes dt. */
 int idx_step(idx_sim* sim, double* dt_taken);
 
@@ -145,7 +148,7 @@ int idx_advance(idx_sim* sim, double t_end, int64_t* nsteps);
 /* Current time and the dt the next cycle will take (before any clamp).  Synchronises. */
 int idx_time(const idx_sim* sim, double* t, double* next_dt);
 
-/* RK2 cycles taken since the last idx_set_state / idx_set_primitive.  Synchronises. */
+/* Cycles taken since the last idx_set_state / idx_set_primitive.  Synchronises. */
 int idx_step_count(const idx_sim* sim, int64_t* nsteps);
 
 /* Device bytes idx_create allocates for this grid and precision with RK2 (FP64 432 B per
