@@ -313,7 +313,8 @@ __host__ __device__ __forceinline__ int march_threads(const Geo& g, int d, int s
   return g.n[(d + 1) % 3] * g.n[(d + 2) % 3] * ((g.n[d] + seg - 1) / seg);
 }
 
-template <typename T, int D, int SEG>
+// SPEEDS: the signal-speed pass -- reconstruct and form only the face's c (slot 7).
+template <typename T, int D, int SEG, bool SPEEDS = false>
 __device__ __forceinline__ void sweep_body(const Geo& g, const Ptr8<const T>& W,
                                            const double* bface, const Ptr8<T>& F, int t) {
   constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
@@ -380,11 +381,15 @@ __device__ __forceinline__ void sweep_body(const Geo& g, const Ptr8<const T>& W,
     L.b1 = wm[5] + slope_m[5]; R.b1 = w0[5] - slope0[5];
     L.b2 = wm[6] + slope_m[6]; R.b2 = w0[6] - slope0[6];
     const T bn = to_bulk<T>(bface[cf]);
-    T flux[7], cmax;
-    riemann_flux(g.riemann, L, R, bn, gamma, gm1inv, flux, cmax);
+    if constexpr (SPEEDS) {
+      F.f[7][cf] = outer_speed(g.riemann, L, R, bn, gamma);
+    } else {
+      T flux[7], cmax;
+      riemann_flux(g.riemann, L, R, bn, gamma, gm1inv, flux, cmax);
 #pragma unroll
-    for (int q = 0; q < 7; ++q) F.f[q][cf] = flux[q];
-    F.f[7][cf] = cmax;
+      for (int q = 0; q < 7; ++q) F.f[q][cf] = flux[q];
+      F.f[7][cf] = cmax;
+    }
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
       wm[q] = w0[q];
@@ -401,6 +406,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
                                                     Ptr8<T> F, const Ctrl* ctrl, int check_dt) {
   if (check_dt && !(ctrl->dt > 0.0)) return;
   sweep_body<T, D, SEG>(g, W, bface, F, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// Signal speeds of one direction for the first dt of a new state (16-face segments).
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads) k_sweep_speeds(Geo g, Ptr8<const T> W,
+                                                           const double* bface, Ptr8<T> F) {
+  sweep_body<T, D, 16, true>(g, W, bface, F, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1447,6 +1459,24 @@ int pending_error(idx_sim* s) {
   return IDX_OK;
 }
 
+// Signal-speed pass on a state: primitives, each direction's face speeds only, and the
+// inverse CFL time into ctrl->inv_prev.
+template <typename T>
+void launch_speed_pass(idx_sim* s, const Ptr8<double>& U, const Ptr8<T>& W, Ptr8<T>* F) {
+  const Geo& g = s->geo;
+  k_prims<T><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(U), W, cell_emf<T>(s),
+                                                              s->ctrl, 0);
+  for (int d = 0; d < 3; ++d) {
+    if (!g.active[d]) continue;
+    const long nthr = (long)g.n[(d + 1) % 3] * g.n[(d + 2) % 3] * ((g.n[d] + 15) / 16);
+    if (d == 0) k_sweep_speeds<T, 0><<<blocks_for(nthr), kThreads, 0, s->stream>>>(g, cst(W), U.f[5], F[0]);
+    else if (d == 1) k_sweep_speeds<T, 1><<<blocks_for(nthr), kThreads, 0, s->stream>>>(g, cst(W), U.f[6], F[1]);
+    else k_sweep_speeds<T, 2><<<blocks_for(nthr), kThreads, 0, s->stream>>>(g, cst(W), U.f[7], F[2]);
+  }
+  k_inv_only<T><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(F[0]), cst(F[1]),
+                                                                 cst(F[2]), s->ctrl);
+}
+
 // Reset time/flags and run the signal-speed pass on the current state U.
 int after_new_state(idx_sim* s) {
   Ctrl c;
@@ -1456,17 +1486,9 @@ int after_new_state(idx_sim* s) {
   c.cfl = s->solver.cfl;
   c.bad_cell = ~0ull;
   IDX_TRY(cudaMemcpyAsync(s->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s->stream));
-  const Geo& g = s->geo;
   // the speed pass of the first cycle
-  if (s->solver.precision == IDX_FP32_BULK) {
-    launch_fluxes<float>(s, s->U, s->Wf, s->Ff, 0);
-    k_inv_only<float><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
-        g, cst(s->Ff[0]), cst(s->Ff[1]), cst(s->Ff[2]), s->ctrl);
-  } else {
-    launch_fluxes<double>(s, s->U, s->Wd, s->Fd, 0);
-    k_inv_only<double><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
-        g, cst(s->Fd[0]), cst(s->Fd[1]), cst(s->Fd[2]), s->ctrl);
-  }
+  if (s->solver.precision == IDX_FP32_BULK) launch_speed_pass<float>(s, s->U, s->Wf, s->Ff);
+  else launch_speed_pass<double>(s, s->U, s->Wd, s->Fd);
   IDX_TRY(cudaGetLastError());
   int rc = sync_ctrl(s);
   if (rc != IDX_OK) return rc;
@@ -2207,9 +2229,7 @@ extern "C" int idx_step_noalloc(const idx_grid* grid, double gamma, double cfl,
   IDX_TRY(cudaMemcpyAsync(s.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s.stream));
   if (!(*inv_dt > 0.0)) {
     // no bound carried in: the signal-speed pass of a first cycle
-    launch_fluxes<double>(&s, s.U, s.Wd, s.Fd, 0);
-    k_inv_only<double><<<blocks_for(g.ncell), kThreads, 0, s.stream>>>(
-        g, cst(s.Fd[0]), cst(s.Fd[1]), cst(s.Fd[2]), s.ctrl);
+    launch_speed_pass<double>(&s, s.U, s.Wd, s.Fd);
   }
   launch_cycle(&s);
   IDX_TRY(cudaGetLastError());

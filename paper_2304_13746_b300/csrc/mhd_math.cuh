@@ -378,6 +378,31 @@ __device__ __forceinline__ void hll(const Side<T>& L, const Side<T>& R, T bx, T 
   }
 }
 
+// The CFL signal speed c = max(|S_L|, |S_R|) of a face alone, as each solver forms it (the
+// same outer speed estimates and operations), for the signal-speed pass that fixes the
+// first dt of a new state: no star states, no fluxes.
+template <typename T>
+__device__ __forceinline__ T outer_speed(int solver, const Side<T>& L, const Side<T>& R, T bx,
+                                         T gamma) {
+  T cfL, cfR;
+  if (solver == 4) {
+    const T bx2 = bx * bx;
+    const T b2L = bx2 + L.b1 * L.b1 + L.b2 * L.b2, b2R = bx2 + R.b1 * R.b1 + R.b2 * R.b2;
+    const T gpL = gamma * L.p, gpR = gamma * R.p;
+    const T aL = gpL + b2L, aR = gpR + b2R;
+    const T bx2x4 = T(4) * bx2;
+    const T dL = pos_part(aL * aL - gpL * bx2x4);
+    const T dR = pos_part(aR * aR - gpR * bx2x4);
+    const T hLR = T(0.5) / (L.r * R.r);
+    cfL = tsqrt((aL + tsqrt(dL)) * (R.r * hLR));
+    cfR = tsqrt((aR + tsqrt(dR)) * (L.r * hLR));
+  } else {
+    fast_speeds(L, R, bx, gamma, cfL, cfR);
+  }
+  const T cfm = max_nn(cfL, cfR);
+  return max_nn(tabs(imin(L.u, R.u) - cfm), tabs(imax(L.u, R.u) + cfm));
+}
+
 // Riemann solver by code: 1 Rusanov, 2 HLL, 4 HLLD (uniform over a sim, so warp-uniform).
 template <typename T>
 __device__ __forceinline__ void riemann_flux(int solver, const Side<T>& L, const Side<T>& R, T bx,
