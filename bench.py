@@ -511,6 +511,10 @@ def main():
         variants["fp64_vector_potential"]["note"] = "Eqs. 7-8: edge potential stepped, B = Bref + curl A"
         variants["fp64_rk3"] = time_variant("fp64", rk_order=3)
         variants["fp64_rk3"]["note"] = "RK3 (Table 1): three stages per cycle instead of two"
+        variants["fp64_limo3"] = time_variant("fp64", recon="limo3")
+        variants["fp64_limo3"]["note"] = "LimO3 reconstruction (Sec. 2.3) instead of van Leer PLM"
+        variants["fp64_limo3_rk3"] = time_variant("fp64", recon="limo3", rk_order=3)
+        variants["fp64_limo3_rk3"]["note"] = "LimO3 + RK3, the paper's higher-accuracy pairing"
         # the paper's own performance problem (Sec. 5): 3D Orszag-Tang, FP64, at this box size
         ot = inputs.orszag_tang_3d(args.n)
         variants["fp64_orszag_tang_3d"] = time_variant("fp64", ot)

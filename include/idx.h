@@ -6,7 +6,8 @@
  * (Lesur et al. 2023):
  *   Eqs. (1)-(4)  ideal-MHD conservation laws (units without 4*pi),
  *   Eq. (5)       finite-volume update of cell averages,
- *   Sec. 2.3      PLM reconstruction of the primitives with the van Leer limiter,
+ *   Sec. 2.3      PLM reconstruction of the primitives with the van Leer limiter, or the
+ *                 compact third-order LimO3 (Cada & Torrilhon 2009);
  *                 HLLD Riemann solver (Miyoshi & Kusano 2005), pressure in the flux;
  *                 HLL or Rusanov selectable,
  *   Sec. 2.4      constrained transport of face-centred B with the E^c edge EMF
@@ -84,7 +85,12 @@ typedef enum {
 } idx_induction;
 
 typedef struct {
-  int recon;       /* 1 = PLM with the van Leer limiter (Sec. 2.3); the only value accepted */
+  int recon;       /* reconstruction of the primitives (Sec. 2.3): 1 = PLM with the van Leer
+                      limiter; 3 = LimO3, face value w + phi(t) dw / 2 toward each face with
+                      phi(t) = max(0, min(P3, max(-t/2, min(2t, P3, 3/2)))), P3 = (2 + t)/3,
+                      t the ratio of the difference behind the cell to the one toward the
+                      face (no switch to P3 near smooth extrema).  Both read two cells on
+                      each side of a face.                                                  */
   int riemann;     /* Riemann solver (Sec. 2.3): 4 = HLLD, 2 = HLL, 1 = Rusanov (Lax-
                       Friedrichs).  All use the HLLD outer speed estimates for the CFL dt. */
   int emf;         /* 2 = E^c (Sec. 2.4); the only value accepted                          */
@@ -184,13 +190,15 @@ int idx_kernel_times(idx_sim* sim, int reps, double ms[6]);
  *                     copies (TMA) and marches it there; needs nx % 32 == 0 and n_d a
  *                     multiple of the tile length;
  *   0                 a direction that is not integrated.
+ * With LimO3 (idx_solver.recon = 3) only 16 and 32 are used.
  * Every shape does the same arithmetic per face; results differ between shapes at most by
  * rounding (the compiler may contract products into FMAs differently in each kernel
  * instantiation). */
 int idx_sweep_shapes(const idx_sim* sim, int shapes[3]);
 
 /* Fix the sweep shapes (values as above; ignored for a direction that is not integrated)
- * instead of autotuning them.  IDX_EINVAL if a shape is unknown or does not fit the grid.
+ * instead of autotuning them.  IDX_EINVAL if a shape is unknown or does not fit the grid
+ * (with LimO3, anything but 16 or 32).
  * A measurement and testing aid, not part of the method; call it before stepping. */
 int idx_set_sweep_shapes(idx_sim* sim, const int shapes[3]);
 
@@ -214,9 +222,9 @@ int idx_pipe_rates(double rates[6]);
  * the same result, to rounding, alone and in a batch.  The work-list is read at run time, so
  * sims join and leave between steps without re-capturing the batch's CUDA graph.  The
  * sweep shapes are autotuned on the batch when its membership first changes.
- * Members of at least 2^18 cells, and members with RK3 or the vector-potential form, run
- * their own (single-sim) kernels inside the batch's cycle; the smaller RK2 field-form
- * members share the work-list kernels.
+ * Members of at least 2^18 cells, and members with RK3, LimO3, the vector-potential form or
+ * non-periodic boundaries, run their own (single-sim) kernels inside the batch's cycle; the
+ * smaller periodic RK2 PLM field-form members share the work-list kernels.
  * Members must share the batch's precision and device; a member must not be stepped by
  * idx_step/idx_advance, nor read with idx_get_state/idx_time, until idx_batch_poll or
  * idx_batch_remove has synchronised the batch. */

@@ -6,7 +6,7 @@ inputs of ``paper_2304_13746_b300.inputs`` and nothing else.
 
 Method: IDEFIX paper (Lesur et al. 2023), Eqs. (1)-(6), (9), (10), Table 1,
 Secs. 2.3, 2.4, 2.7; HLLD of Miyoshi & Kusano (2005); E^c EMF of Gardiner &
-Stone (2005).  Every array is numpy float64 with shape (nz, ny, nx), periodic.
+Stone (2005); LimO3 reconstruction of Cada & Torrilhon (2009).  Every array is numpy float64 with shape (nz, ny, nx), periodic.
 """
 import ctypes
 import math
@@ -69,6 +69,17 @@ def lib():
         L.ora_cycle_vp.argtypes = [G, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                    _P8, _P3, _P3, _D, ctypes.c_double, _D,
                                    ctypes.POINTER(ctypes.c_long)]
+        L.ora_limo3_face.argtypes = [ctypes.c_double] * 3
+        L.ora_limo3_face.restype = ctypes.c_double
+        L.ora_speed_pass_recon.argtypes = [G, ctypes.c_double, ctypes.c_int, _P8, _D,
+                                           ctypes.POINTER(ctypes.c_long)]
+        L.ora_stage_scheme.argtypes = [G, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                       ctypes.c_int, _P8, _P8, ctypes.c_double, ctypes.c_double,
+                                       _P8, _D, ctypes.POINTER(ctypes.c_long)]
+        L.ora_cycle_scheme.argtypes = [G, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int, _P8, ctypes.c_void_p,
+                                       ctypes.c_void_p, _D, ctypes.c_double, _D,
+                                       ctypes.POINTER(ctypes.c_long)]
         L.ora_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -121,6 +132,14 @@ def vanleer(wm, w0, wp):
     return lib().ora_vanleer(float(wm), float(w0), float(wp))
 
 
+RECONS = {"plm": 1, "limo3": 3}
+
+
+def limo3_face(w_back, w0, w_face):
+    """LimO3 value of a cell (value w0) at its face toward w_face (Sec. 2.3)."""
+    return lib().ora_limo3_face(float(w_back), float(w0), float(w_face))
+
+
 def _arr(x, n):
     return (ctypes.c_double * n)(*[float(v) for v in x])
 
@@ -159,24 +178,26 @@ def emf_ec(X, Y, C, Fa, Fb, da, db):
                             float(db))
 
 
-def speed_pass(cons, lengths, gamma):
+def speed_pass(cons, lengths, gamma, recon="plm"):
     cons = [_c(a) for a in cons]
     inv = ctypes.c_double()
     bad = ctypes.c_long(-1)
-    _check(lib().ora_speed_pass(ctypes.byref(_grid(cons[0].shape, lengths)), gamma, _ptrs(cons),
-                                ctypes.byref(inv), ctypes.byref(bad)), bad)
+    _check(lib().ora_speed_pass_recon(ctypes.byref(_grid(cons[0].shape, lengths)), gamma,
+                                      RECONS[recon], _ptrs(cons), ctypes.byref(inv),
+                                      ctypes.byref(bad)), bad)
     return inv.value
 
 
-def stage(uin, lengths, gamma, dt, u0=None, w=1.0, w0=0.0):
+def stage(uin, lengths, gamma, dt, u0=None, w=1.0, w0=0.0, recon="plm", solver="hlld"):
     uin = [_c(a) for a in uin]
     out = _new(uin[0].shape)
     keep = [_c(a) for a in u0] if u0 is not None else None
     p0 = _ptrs(keep) if keep is not None else _P8()
     inv = ctypes.c_double()
     bad = ctypes.c_long(-1)
-    _check(lib().ora_stage(ctypes.byref(_grid(uin[0].shape, lengths)), gamma, dt, _ptrs(uin), p0,
-                           w, w0, _ptrs(out), ctypes.byref(inv), ctypes.byref(bad)), bad)
+    _check(lib().ora_stage_scheme(ctypes.byref(_grid(uin[0].shape, lengths)), gamma, dt,
+                                  RECONS[recon], SOLVERS[solver], _ptrs(uin), p0, w, w0,
+                                  _ptrs(out), ctypes.byref(inv), ctypes.byref(bad)), bad)
     return out, inv.value
 
 
@@ -202,10 +223,12 @@ class Sim:
     """
 
     def __init__(self, cons, lengths, gamma, cfl, solver="hlld", rk_order=2, induction="field",
-                 A=None, bref=None):
+                 A=None, bref=None, recon="plm"):
         if induction not in INDUCTION:
             raise ValueError(induction)
         self.solver = SOLVERS[solver]
+        self.recon_name = recon
+        self.recon = RECONS[recon]
         self.rk_order = int(rk_order)
         self.u = [_c(a).copy() for a in cons]
         self.lengths = tuple(float(x) for x in lengths)
@@ -219,23 +242,24 @@ class Sim:
             self.A = [np.zeros(shape) for _ in range(3)] if A is None else [_c(a).copy() for a in A]
             self.bref = [self.u[5 + d].copy() for d in range(3)] if bref is None else \
                 [_c(b).copy() for b in bref]
-        self.inv_dt = speed_pass(self.u, self.lengths, self.gamma)
+        self.inv_dt = speed_pass(self.u, self.lengths, self.gamma, recon)
 
     @classmethod
-    def from_prims(cls, prim, lengths, gamma, cfl, solver="hlld", rk_order=2, induction="field"):
+    def from_prims(cls, prim, lengths, gamma, cfl, solver="hlld", rk_order=2, induction="field",
+                   recon="plm"):
         return cls(cons_from_prims(prim, lengths, gamma), lengths, gamma, cfl, solver, rk_order,
-                   induction)
+                   induction, recon=recon)
 
     @classmethod
     def from_potential(cls, prim5, A, bmean, lengths, gamma, cfl, solver="hlld", rk_order=2,
-                       induction="potential"):
+                       induction="potential", recon="plm"):
         """Cells from (rho, vx, vy, vz, P), faces from bmean + curl A."""
         B = b_from_potential(A, bmean, lengths)
         cons = cons_from_prims(list(prim5) + B, lengths, gamma)
         if induction == "field":
-            return cls(cons, lengths, gamma, cfl, solver, rk_order)
+            return cls(cons, lengths, gamma, cfl, solver, rk_order, recon=recon)
         bref = [np.full(B[0].shape, float(bmean[d])) for d in range(3)]
-        return cls(cons, lengths, gamma, cfl, solver, rk_order, "potential", A, bref)
+        return cls(cons, lengths, gamma, cfl, solver, rk_order, "potential", A, bref, recon)
 
     def step(self, dt_max=math.inf):
         inv = ctypes.c_double(self.inv_dt)
@@ -243,14 +267,13 @@ class Sim:
         bad = ctypes.c_long(-1)
         g = ctypes.byref(_grid(self.u[0].shape, self.lengths))
         if self.induction == "potential":
-            rc = lib().ora_cycle_vp(g, self.gamma, self.cfl, self.solver, self.rk_order,
-                                    _ptrs(self.u), _ptrs(self.A), _ptrs(self.bref),
-                                    ctypes.byref(inv), float(dt_max), ctypes.byref(dt),
-                                    ctypes.byref(bad))
+            pa, pb = _ptrs(self.A), _ptrs(self.bref)
+            A, bref = ctypes.cast(pa, ctypes.c_void_p), ctypes.cast(pb, ctypes.c_void_p)
         else:
-            rc = lib().ora_cycle_rk(g, self.gamma, self.cfl, self.solver, self.rk_order,
-                                    _ptrs(self.u), ctypes.byref(inv), float(dt_max),
-                                    ctypes.byref(dt), ctypes.byref(bad))
+            A = bref = None
+        rc = lib().ora_cycle_scheme(g, self.gamma, self.cfl, self.recon, self.solver,
+                                    self.rk_order, _ptrs(self.u), A, bref, ctypes.byref(inv),
+                                    float(dt_max), ctypes.byref(dt), ctypes.byref(bad))
         _check(rc, bad)
         self.inv_dt = inv.value
         self.nsteps += 1
@@ -299,12 +322,12 @@ def threads():
 
 class SimBC:
     """Oracle simulation with non-periodic boundaries (oracle/boundaries.py): the padded
-    grid is stepped stage by stage with ora_stage (HLLD, E^c), the ghosts refilled before
+    grid is stepped stage by stage with ora_stage_scheme (E^c), the ghosts refilled before
     every stage.  bc = (kind_x, kind_y, kind_z) of boundaries.PERIODIC / OUTFLOW /
     REFLECTING.  Fields in the user layout (normal field n + 1 faces along a non-periodic
     direction); every array numpy float64 of shape (nz, ny, nx) (+1 along that axis)."""
 
-    def __init__(self, prim, lengths, gamma, cfl, bc, rk_order=2):
+    def __init__(self, prim, lengths, gamma, cfl, bc, rk_order=2, recon="plm", solver="hlld"):
         from . import boundaries as bd
         self.bd = bd
         self.bc = tuple(int(b) for b in bc)
@@ -314,11 +337,12 @@ class SimBC:
         self.gamma = float(gamma)
         self.cfl = float(cfl)
         self.rk_order = int(rk_order)
+        self.recon_name, self.solver_name = recon, solver
         w = bd.fill_ghosts(bd.pad([_c(a) for a in prim], self.bc), self.bc)
         self.u = bd.fill_ghosts(cons_from_prims(w, self.plengths, self.gamma), self.bc)
         self.t = 0.0
         self.nsteps = 0
-        self.inv_dt = speed_pass(self.u, self.plengths, self.gamma)
+        self.inv_dt = speed_pass(self.u, self.plengths, self.gamma, recon)
 
     def state(self):
         return self.bd.unpad(self.u, self.bc, self.cell_shape)
@@ -332,7 +356,7 @@ class SimBC:
         inv = 0.0
         for w, w0 in weights:
             out, inv_s = stage(prev, self.plengths, self.gamma, dt, u0=u0 if w0 else None, w=w,
-                               w0=w0)
+                               w0=w0, recon=self.recon_name, solver=self.solver_name)
             prev = self.bd.fill_ghosts(out, self.bc)
             inv = max(inv, inv_s)
         self.u = prev

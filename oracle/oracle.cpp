@@ -159,6 +159,30 @@ template <class R> R vanleer(R wm, R w0, R wp) {
 }
 
 // ---------------------------------------------------------------------------
+// Compact third-order reconstruction "LimO3" (Cada & Torrilhon 2009), the third scheme
+// listed in Sec. 2.3.  With t the ratio of the difference on the far side of the cell to
+// the difference toward the face, the face value is w0 + phi(t) (w_face - w0) / 2 where
+//   phi(t) = max(0, min(P3(t), max(-t/2, min(2t, P3(t), 3/2)))),  P3(t) = (2 + t)/3.
+// P3 alone is the unlimited third-order (parabolic) face value; the min/max chain keeps
+// the face value between the neighbours (phi <= 2t, phi <= 3/2 < 2) and turns it off
+// beyond a jump of the opposite sign.  The switch to P3 near smooth extrema, which the
+// limiter's authors tie to a length scale, is not applied.
+// ---------------------------------------------------------------------------
+template <class R> R limo3_phi(R t) {
+  const R p3 = (R(2.0) + t) / R(3.0);
+  const R inner = rmin(rmin(R(2.0) * t, p3), R(1.5));
+  return rmax(R(0.0), rmin(p3, rmax(-t / R(2.0), inner)));
+}
+
+// Face value of cell w0 on the side of w_face, with w_back its neighbour on the other side.
+template <class R> R limo3_face(R w_back, R w0, R w_face) {
+  const R toward = w_face - w0;
+  if (value(toward) == 0.0) return w0;  // t infinite: the limit of phi(t) (w_face - w0) is 0
+  const R t = (w0 - w_back) / toward;
+  return w0 + limo3_phi(t) * toward / R(2.0);
+}
+
+// ---------------------------------------------------------------------------
 // HLLD (Miyoshi & Kusano 2005), the magnetised HLLC counterpart named in Sec. 2.3.
 // Normal = "x": state w = (rho, u, v, w, P, By, Bz), normal field bx.
 // Flux ordering: (rho, m_n, m_t1, m_t2, E, Bt1, Bt2).  Pressure inside the
@@ -448,9 +472,10 @@ R emf_ec(const R X[2], const R Y[2], const R C[2][2], const R Fa[2], const R Fb[
 // the global conserved ordering (slot 5 + d, the normal field, stays 0), plus
 // the face signal speed max(|S_L|, |S_R|).
 // ---------------------------------------------------------------------------
+// recon: 1 PLM with the van Leer limiter, 3 LimO3 (both Sec. 2.3)
 template <class R>
 void face_state(const Grid& G, const std::vector<R>* W, int i, int j, int k, int d, int side,
-                State<R>* s) {
+                State<R>* s, int recon = 1) {
   // side = -1: "left" state of face p, i.e. the +1/2 extrapolation of cell p - e_d
   // side = +1: "right" state of face p, the -1/2 extrapolation of cell p
   const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
@@ -462,6 +487,10 @@ void face_state(const Grid& G, const std::vector<R>* W, int i, int j, int k, int
   R out[7];
   for (int q = 0; q < 7; ++q) {
     const std::vector<R>& f = W[var[q]];
+    if (recon == 3) {
+      out[q] = (side < 0) ? limo3_face(f[pm], f[p0], f[pp]) : limo3_face(f[pp], f[p0], f[pm]);
+      continue;
+    }
     const R slope = vanleer(f[pm], f[p0], f[pp]);
     out[q] = (side < 0) ? f[p0] + R(0.5) * slope : f[p0] - R(0.5) * slope;
   }
@@ -471,7 +500,8 @@ void face_state(const Grid& G, const std::vector<R>* W, int i, int j, int k, int
 
 template <class R>
 void face_fluxes(const Grid& G, double gamma, const std::vector<R>* U, const std::vector<R>* W,
-                 int d, std::vector<R>* F /*8*/, std::vector<R>& cface, int solver) {
+                 int d, std::vector<R>* F /*8*/, std::vector<R>& cface, int solver,
+                 int recon = 1) {
   const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
 #pragma omp parallel for if (kPar<R>)
   for (int k = 0; k < G.n[2]; ++k)
@@ -479,8 +509,8 @@ void face_fluxes(const Grid& G, double gamma, const std::vector<R>* U, const std
       for (int i = 0; i < G.n[0]; ++i) {
         const long p = at(G, i, j, k);
         State<R> L, Rr;
-        face_state(G, W, i, j, k, d, -1, &L);
-        face_state(G, W, i, j, k, d, +1, &Rr);
+        face_state(G, W, i, j, k, d, -1, &L, recon);
+        face_state(G, W, i, j, k, d, +1, &Rr, recon);
         const R bn = U[5 + d][p];
         R f[7], sL, sR;
         riemann(solver, L, Rr, bn, gamma, f, &sL, &sR);
@@ -498,15 +528,15 @@ void face_fluxes(const Grid& G, double gamma, const std::vector<R>* U, const std
 
 template <class R>
 void face_speeds(const Grid& G, double gamma, const std::vector<R>* U, const std::vector<R>* W,
-                 int d, std::vector<R>& cface) {
+                 int d, std::vector<R>& cface, int recon = 1) {
 #pragma omp parallel for if (kPar<R>)
   for (int k = 0; k < G.n[2]; ++k)
     for (int j = 0; j < G.n[1]; ++j)
       for (int i = 0; i < G.n[0]; ++i) {
         const long p = at(G, i, j, k);
         State<R> L, Rr;
-        face_state(G, W, i, j, k, d, -1, &L);
-        face_state(G, W, i, j, k, d, +1, &Rr);
+        face_state(G, W, i, j, k, d, -1, &L, recon);
+        face_state(G, W, i, j, k, d, +1, &Rr, recon);
         const R bn = U[5 + d][p];
         const R cfL = fast_speed(L, bn, gamma);
         const R cfR = fast_speed(Rr, bn, gamma);
@@ -627,7 +657,7 @@ template <class R>
 int stage(const Grid& G, double gamma, R dt, const std::vector<R>* Uin, const std::vector<R>* U0,
           double w, double w0, std::vector<R>* Uout, R* inv_dt, long* bad, int solver = 4,
           const std::vector<R>* Ain = nullptr, const std::vector<R>* A0 = nullptr,
-          std::vector<R>* Aout = nullptr, const std::vector<R>* Bref = nullptr) {
+          std::vector<R>* Aout = nullptr, const std::vector<R>* Bref = nullptr, int recon = 1) {
   const long N = G.ncell;
   std::vector<R> W[8];
   for (int f = 0; f < 8; ++f) W[f].assign(N, R(0.0));
@@ -639,7 +669,7 @@ int stage(const Grid& G, double gamma, R dt, const std::vector<R>* Uin, const st
   for (int q = 0; q < 24; ++q) F[q].assign(N, R(0.0));
   for (int d = 0; d < 3; ++d) {
     cface[d].assign(N, R(0.0));
-    if (G.active[d]) face_fluxes(G, gamma, Uin, W, d, &F[8 * d], cface[d], solver);
+    if (G.active[d]) face_fluxes(G, gamma, Uin, W, d, &F[8 * d], cface[d], solver, recon);
   }
   *inv_dt = inverse_dt(G, cface);
 
@@ -719,7 +749,7 @@ int stage(const Grid& G, double gamma, R dt, const std::vector<R>* Uin, const st
 template <class R>
 int cycle(const Grid& G, double gamma, double cfl, std::vector<R>* U, R* inv_dt, double dt_max,
           R* dt_taken, long* bad, int solver = 4, int rk_order = 2, std::vector<R>* A = nullptr,
-          const std::vector<R>* Bref = nullptr) {
+          const std::vector<R>* Bref = nullptr, int recon = 1) {
   R dt = R(cfl) / *inv_dt;
   if (value(dt) > dt_max) dt = R(dt_max);
   const long N = G.ncell;
@@ -740,7 +770,7 @@ int cycle(const Grid& G, double gamma, double cfl, std::vector<R>* U, R* inv_dt,
     R inv_s;
     const int rc = stage(G, gamma, dt, prev, st == 0 ? (const std::vector<R>*)nullptr : U, w, w0,
                          next, &inv_s, bad, solver, A ? prevA : nullptr,
-                         (A && st > 0) ? A : nullptr, A ? nextA : nullptr, Bref);
+                         (A && st > 0) ? A : nullptr, A ? nextA : nullptr, Bref, recon);
     if (rc != ORA_OK) return rc;
     inv = rmax(inv, inv_s);
     for (int f = 0; f < 8; ++f) prev[f].swap(next[f]);
@@ -847,7 +877,17 @@ double ora_emf_ec(const double X[2], const double Y[2], const double C[2][2], co
 
 int ora_speed_pass(const ora_grid* g, double gamma, const double* const cons[8], double* inv_dt,
                    long* bad_cell) {
-  if (!grid_ok(g) || !(gamma > 1.0) || !ptrs_ok((const void* const*)cons) || !inv_dt)
+  return ora_speed_pass_recon(g, gamma, 1, cons, inv_dt, bad_cell);
+}
+
+double ora_limo3_face(double w_back, double w0, double w_face) {
+  return limo3_face<double>(w_back, w0, w_face);
+}
+
+int ora_speed_pass_recon(const ora_grid* g, double gamma, int recon, const double* const cons[8],
+                         double* inv_dt, long* bad_cell) {
+  if (!grid_ok(g) || !(gamma > 1.0) || !ptrs_ok((const void* const*)cons) || !inv_dt ||
+      (recon != 1 && recon != 3))
     return ORA_EINVAL;
   const Grid G = make_grid(g);
   std::vector<double> U[8], W[8], cface[3];
@@ -857,7 +897,7 @@ int ora_speed_pass(const ora_grid* g, double gamma, const double* const cons[8],
   if (st != ORA_OK) return st;
   for (int d = 0; d < 3; ++d) {
     cface[d].assign(G.ncell, 0.0);
-    if (G.active[d]) face_speeds(G, gamma, U, W, d, cface[d]);
+    if (G.active[d]) face_speeds(G, gamma, U, W, d, cface[d], recon);
   }
   *inv_dt = inverse_dt(G, cface);
   return ORA_OK;
@@ -866,8 +906,15 @@ int ora_speed_pass(const ora_grid* g, double gamma, const double* const cons[8],
 int ora_stage(const ora_grid* g, double gamma, double dt, const double* const uin[8],
               const double* const u0[8], double w, double w0, double* const uout[8],
               double* inv_dt, long* bad_cell) {
+  return ora_stage_scheme(g, gamma, dt, 1, 4, uin, u0, w, w0, uout, inv_dt, bad_cell);
+}
+
+int ora_stage_scheme(const ora_grid* g, double gamma, double dt, int recon, int solver,
+                     const double* const uin[8], const double* const u0[8], double w, double w0,
+                     double* const uout[8], double* inv_dt, long* bad_cell) {
   if (!grid_ok(g) || !(gamma > 1.0) || !ptrs_ok((const void* const*)uin) ||
-      !ptrs_ok((const void* const*)uout) || !inv_dt || !(dt >= 0.0))
+      !ptrs_ok((const void* const*)uout) || !inv_dt || !(dt >= 0.0) ||
+      (recon != 1 && recon != 3) || (solver != 1 && solver != 2 && solver != 4))
     return ORA_EINVAL;
   if (w0 != 0.0 && !ptrs_ok((const void* const*)u0)) return ORA_EINVAL;
   const Grid G = make_grid(g);
@@ -876,7 +923,8 @@ int ora_stage(const ora_grid* g, double gamma, double dt, const double* const ui
   if (w0 != 0.0) load(G, u0, U0);
   for (int f = 0; f < 8; ++f) Uo[f].assign(G.ncell, 0.0);
   double inv = 0.0;
-  const int st = stage(G, gamma, dt, Ui, U0, w, w0, Uo, &inv, bad_cell);
+  const int st = stage<double>(G, gamma, dt, Ui, U0, w, w0, Uo, &inv, bad_cell, solver, nullptr,
+                               nullptr, nullptr, nullptr, recon);
   if (st != ORA_OK) return st;
   store(G, Uo, uout);
   *inv_dt = inv;
@@ -989,6 +1037,39 @@ int ora_cycle_vp(const ora_grid* g, double gamma, double cfl, int solver, int rk
   if (st != ORA_OK) return st;
   store(G, U, u);
   for (int e = 0; e < 3; ++e) std::memcpy(A[e], Av[e].data(), sizeof(double) * G.ncell);
+  *inv_dt = inv;
+  if (dt_taken) *dt_taken = dt;
+  return ORA_OK;
+}
+
+int ora_cycle_scheme(const ora_grid* g, double gamma, double cfl, int recon, int solver,
+                     int rk_order, double* const u[8], double* const A[3],
+                     const double* const Bref[3], double* inv_dt, double dt_max,
+                     double* dt_taken, long* bad_cell) {
+  if (!grid_ok(g) || !(gamma > 1.0) || !(cfl > 0.0 && cfl < 1.0) ||
+      !ptrs_ok((const void* const*)u) || !inv_dt || !(*inv_dt > 0.0) || !(dt_max >= 0.0))
+    return ORA_EINVAL;
+  if ((recon != 1 && recon != 3) || (solver != 1 && solver != 2 && solver != 4) ||
+      (rk_order != 2 && rk_order != 3) || (!A) != (!Bref))
+    return ORA_EINVAL;
+  if (A)
+    for (int e = 0; e < 3; ++e)
+      if (!A[e] || !Bref[e]) return ORA_EINVAL;
+  const Grid G = make_grid(g);
+  std::vector<double> U[8], Av[3], Br[3];
+  load(G, (const double* const*)u, U);
+  if (A)
+    for (int e = 0; e < 3; ++e) {
+      Av[e].assign(A[e], A[e] + G.ncell);
+      Br[e].assign(Bref[e], Bref[e] + G.ncell);
+    }
+  double inv = *inv_dt, dt = 0.0;
+  const int st = cycle(G, gamma, cfl, U, &inv, dt_max, &dt, bad_cell, solver, rk_order,
+                       A ? Av : nullptr, A ? Br : nullptr, recon);
+  if (st != ORA_OK) return st;
+  store(G, U, u);
+  if (A)
+    for (int e = 0; e < 3; ++e) std::memcpy(A[e], Av[e].data(), sizeof(double) * G.ncell);
   *inv_dt = inv;
   if (dt_taken) *dt_taken = dt;
   return ORA_OK;

@@ -9,7 +9,8 @@
  * Method (IDEFIX paper, Lesur et al. 2023):
  *   Eq. (1)-(4)  ideal-MHD conservation laws (no 4*pi in the units),
  *   Eq. (5)      Godunov finite-volume form,
- *   Sec. 2.3     reconstruction on primitives (PLM, van Leer), HLLD Riemann solver,
+ *   Sec. 2.3     reconstruction on primitives (PLM with van Leer, or the compact
+ *                third-order LimO3), HLLD / HLL / Rusanov Riemann solvers,
  *                pressure kept inside the momentum flux,
  *   Sec. 2.4     constrained transport on face-centred B, E^c edge EMF (Eq. 6),
  *   Sec. 2.7     method-of-lines RK2 (Eq. 9, Table 1) and the CFL time step (Eq. 10).
@@ -50,6 +51,10 @@ int ora_prims(const ora_grid* g, double gamma, const double* const cons[8], doub
 
 /* van Leer limited slope of one variable from the values at i-1, i, i+1. */
 double ora_vanleer(double wm, double w0, double wp);
+
+/* LimO3 face value (Sec. 2.3, the compact third-order scheme of Cada & Torrilhon 2009) of a
+ * cell with value w0 on its side toward w_face, w_back the neighbour on the other side. */
+double ora_limo3_face(double w_back, double w0, double w_face);
 
 /* HLLD flux at one interface whose normal is "x".  wL, wR = (rho, u, v, w, P, Bt1, Bt2);
  * bn = normal field.  F = fluxes of (rho, m_n, m_t1, m_t2, E, Bt1, Bt2).  sL, sR = the
@@ -100,6 +105,23 @@ double ora_emf_ec(const double X[2], const double Y[2], const double C[2][2], co
  * sum_d max(c_face(i-1/2), c_face(i+1/2)) / dl_d  (the inverse CFL time). */
 int ora_speed_pass(const ora_grid* g, double gamma, const double* const cons[8], double* inv_dt,
                    long* bad_cell);
+
+/* ora_speed_pass with a chosen reconstruction: recon 1 PLM (van Leer), 3 LimO3. */
+int ora_speed_pass_recon(const ora_grid* g, double gamma, int recon, const double* const cons[8],
+                         double* inv_dt, long* bad_cell);
+
+/* ora_stage with a chosen reconstruction (1, 3) and Riemann solver (1, 2, 4). */
+int ora_stage_scheme(const ora_grid* g, double gamma, double dt, int recon, int solver,
+                     const double* const uin[8], const double* const u0[8], double w, double w0,
+                     double* const uout[8], double* inv_dt, long* bad_cell);
+
+/* One cycle with every choice: reconstruction (1 PLM, 3 LimO3), Riemann solver (1, 2, 4),
+ * RK order (2, 3) and induction form (A and Bref both NULL: face field stepped; both given:
+ * vector potential as in ora_cycle_vp). */
+int ora_cycle_scheme(const ora_grid* g, double gamma, double cfl, int recon, int solver,
+                     int rk_order, double* const u[8], double* const A[3],
+                     const double* const Bref[3], double* inv_dt, double dt_max,
+                     double* dt_taken, long* bad_cell);
 
 /* One stage: uout = w * S_dt(uin) + w0 * u0 (u0 may be NULL when w0 == 0).
  * *inv_dt receives the stage's inverse CFL time. */

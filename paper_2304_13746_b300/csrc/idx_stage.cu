@@ -73,6 +73,7 @@ struct Geo {
   float inv_dlf[3];  // 1/dl in FP32 for the FP32-bulk arithmetic
   float gammaf, gm1invf;
   int riemann;       // 1 Rusanov, 2 HLL, 4 HLLD
+  int recon;         // 1 PLM (van Leer), 3 LimO3
 };
 
 // gamma and 1/(gamma - 1) in the bulk type, formed once on the host
@@ -314,7 +315,8 @@ __host__ __device__ __forceinline__ int march_threads(const Geo& g, int d, int s
 }
 
 // SPEEDS: the signal-speed pass -- reconstruct and form only the face's c (slot 7).
-template <typename T, int D, int SEG, bool SPEEDS = false>
+// RECON: 1 PLM with the van Leer limiter, 3 LimO3 (Sec. 2.3); both read cells f-2 .. f+1.
+template <typename T, int D, int SEG, bool SPEEDS = false, int RECON = 1>
 __device__ __forceinline__ void sweep_body(const Geo& g, const Ptr8<const T>& W,
                                            const double* bface, const Ptr8<T>& F, int t) {
   constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
@@ -349,7 +351,9 @@ __device__ __forceinline__ void sweep_body(const Geo& g, const Ptr8<const T>& W,
   const T gm1inv = geo_gm1inv<T>(g);
 
   // cells f-1, f, f+1 in registers, cell f+2 prefetched one face ahead so that its
-  // loads overlap the current face's Riemann solve; slope_m / slope0 hold half slopes
+  // loads overlap the current face's Riemann solve.  slope_m: the change of cell f-1 at
+  // its upper face (face f); slope0: the change of cell f at its lower face, subtracted.
+  // PLM uses one half slope for both faces of a cell; LimO3 has one per face.
   T wm[7], w0[7], wp[7], wn[7], slope_m[7];
   {
     const int cm2 = cell(f0 - 2), cm1 = cell(f0 - 1), c0 = cell(f0), cp = cell(f0 + 1);
@@ -359,7 +363,8 @@ __device__ __forceinline__ void sweep_body(const Geo& g, const Ptr8<const T>& W,
       wm[q] = W.f[var[q]][cm1];
       w0[q] = W.f[var[q]][c0];
       wp[q] = W.f[var[q]][cp];
-      slope_m[q] = vanleer_half(wm[q] - a, w0[q] - wm[q]);
+      slope_m[q] = RECON == 3 ? limo3_half(wm[q] - a, w0[q] - wm[q])
+                              : vanleer_half(wm[q] - a, w0[q] - wm[q]);
     }
   }
   for (int f = f0; f < f1; ++f) {
@@ -370,9 +375,18 @@ __device__ __forceinline__ void sweep_body(const Geo& g, const Ptr8<const T>& W,
       for (int q = 0; q < 7; ++q) wn[q] = W.f[var[q]][cn];
     }
     Side<T> L, R;
-    T slope0[7];
+    T slope0[7], up0[7];
 #pragma unroll
-    for (int q = 0; q < 7; ++q) slope0[q] = vanleer_half(w0[q] - wm[q], wp[q] - w0[q]);
+    for (int q = 0; q < 7; ++q) {
+      const T dl = w0[q] - wm[q], dr = wp[q] - w0[q];
+      if constexpr (RECON == 3) {
+        slope0[q] = limo3_half(dr, dl);
+        up0[q] = limo3_half(dl, dr);
+      } else {
+        slope0[q] = vanleer_half(dl, dr);
+        up0[q] = slope0[q];
+      }
+    }
     L.r = wm[0] + slope_m[0]; R.r = w0[0] - slope0[0];
     L.u = wm[1] + slope_m[1]; R.u = w0[1] - slope0[1];
     L.v = wm[2] + slope_m[2]; R.v = w0[2] - slope0[2];
@@ -395,24 +409,24 @@ __device__ __forceinline__ void sweep_body(const Geo& g, const Ptr8<const T>& W,
       wm[q] = w0[q];
       w0[q] = wp[q];
       wp[q] = wn[q];
-      slope_m[q] = slope0[q];
+      slope_m[q] = up0[q];
     }
   }
 }
 
-template <typename T, int D, int SEG>
+template <typename T, int D, int SEG, int RECON = 1>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
     k_sweep(Geo g, Ptr8<const T> W, const double* bface,
                                                     Ptr8<T> F, const Ctrl* ctrl, int check_dt) {
   if (check_dt && !(ctrl->dt > 0.0)) return;
-  sweep_body<T, D, SEG>(g, W, bface, F, blockIdx.x * blockDim.x + threadIdx.x);
+  sweep_body<T, D, SEG, false, RECON>(g, W, bface, F, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Signal speeds of one direction for the first dt of a new state (16-face segments).
-template <typename T, int D>
+template <typename T, int D, int RECON>
 __global__ void __launch_bounds__(kThreads) k_sweep_speeds(Geo g, Ptr8<const T> W,
                                                            const double* bface, Ptr8<T> F) {
-  sweep_body<T, D, 16, true>(g, W, bface, F, blockIdx.x * blockDim.x + threadIdx.x);
+  sweep_body<T, D, 16, true, RECON>(g, W, bface, F, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1136,14 +1150,14 @@ template <typename T> Ptr8<const T> cst(const Ptr8<T>& p) {
 }
 
 // One sweep launch in the given shape (see idx_sim::sweep_shape).
-template <typename T, int D, int SEG>
+template <typename T, int D, int SEG, int RECON = 1>
 void launch_march(idx_sim* s, const Ptr8<T>& W, const double* bface, const Ptr8<T>& F,
                   int check_dt) {
   const Geo& g = s->geo;
   const int a = (D + 1) % 3, b = (D + 2) % 3;
   const long nthr = (long)g.n[a] * g.n[b] * ((g.n[D] + SEG - 1) / SEG);
-  k_sweep<T, D, SEG><<<blocks_for(nthr), kThreads, 0, s->stream>>>(g, cst(W), bface, F, s->ctrl,
-                                                                    check_dt);
+  k_sweep<T, D, SEG, RECON><<<blocks_for(nthr), kThreads, 0, s->stream>>>(g, cst(W), bface, F,
+                                                                           s->ctrl, check_dt);
 }
 
 template <typename T, int D, int L>
@@ -1182,6 +1196,11 @@ template <typename T> void launch_tma_x(idx_sim* s, const double* bface, const P
 template <typename T, int D>
 void launch_sweep_d(idx_sim* s, int shape, const Ptr8<T>& W, const double* bface,
                     const Ptr8<T>& F, int check_dt) {
+  if (s->geo.recon == 3) {  // LimO3: marching sweeps of 16 or 32 faces
+    if (shape == 32) launch_march<T, D, 32, 3>(s, W, bface, F, check_dt);
+    else launch_march<T, D, 16, 3>(s, W, bface, F, check_dt);
+    return;
+  }
   if (D == 0 && shape == -2 && tma_shape_ok(s, 0, -2)) {
     launch_tma_x<T>(s, bface, F, check_dt);
     return;
@@ -1233,6 +1252,7 @@ int tune_sweeps(idx_sim* s, const Ptr8<double>& U, const Ptr8<T>& W, Ptr8<T>* F)
     int best_shape = kSegDefault;
     for (int q = 0; q < 9; ++q) {
       const int shape = cand[q];
+      if (g.recon == 3 && shape != 16 && shape != 32) continue;  // LimO3: marching 16 / 32
       if (shape < 0 && d != 0) continue;
       if ((shape > 100 || shape == -2) && !tma_shape_ok(s, d, shape)) continue;
       if (shape > 0 && shape < 100 && shape > 2 * g.n[d]) continue;
@@ -1383,9 +1403,10 @@ void launch_cycle(idx_sim* s) {
 
 // Sweep shapes already tuned in this process, by grid, precision and device.
 struct TuneKey {
-  int nx, ny, nz, precision, device;
+  int nx, ny, nz, precision, recon, device;
   bool operator<(const TuneKey& o) const {
-    return std::tie(nx, ny, nz, precision, device) < std::tie(o.nx, o.ny, o.nz, o.precision, o.device);
+    return std::tie(nx, ny, nz, precision, recon, device) <
+           std::tie(o.nx, o.ny, o.nz, o.precision, o.recon, o.device);
   }
 };
 std::map<TuneKey, std::array<int, 3>> g_tune_cache;
@@ -1398,7 +1419,8 @@ int tune_once(idx_sim* s) {
   if (s->tuned) return IDX_OK;
   s->tuned = true;
   if (s->geo.ncell < kTuneMinCells) return IDX_OK;
-  const TuneKey key{s->geo.n[0], s->geo.n[1], s->geo.n[2], s->solver.precision, s->device};
+  const TuneKey key{s->geo.n[0], s->geo.n[1], s->geo.n[2], s->solver.precision, s->geo.recon,
+                   s->device};
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tune_cache.find(key);
@@ -1469,9 +1491,16 @@ void launch_speed_pass(idx_sim* s, const Ptr8<double>& U, const Ptr8<T>& W, Ptr8
   for (int d = 0; d < 3; ++d) {
     if (!g.active[d]) continue;
     const long nthr = (long)g.n[(d + 1) % 3] * g.n[(d + 2) % 3] * ((g.n[d] + 15) / 16);
-    if (d == 0) k_sweep_speeds<T, 0><<<blocks_for(nthr), kThreads, 0, s->stream>>>(g, cst(W), U.f[5], F[0]);
-    else if (d == 1) k_sweep_speeds<T, 1><<<blocks_for(nthr), kThreads, 0, s->stream>>>(g, cst(W), U.f[6], F[1]);
-    else k_sweep_speeds<T, 2><<<blocks_for(nthr), kThreads, 0, s->stream>>>(g, cst(W), U.f[7], F[2]);
+    const int nb = blocks_for(nthr);
+    if (g.recon == 3) {
+      if (d == 0) k_sweep_speeds<T, 0, 3><<<nb, kThreads, 0, s->stream>>>(g, cst(W), U.f[5], F[0]);
+      else if (d == 1) k_sweep_speeds<T, 1, 3><<<nb, kThreads, 0, s->stream>>>(g, cst(W), U.f[6], F[1]);
+      else k_sweep_speeds<T, 2, 3><<<nb, kThreads, 0, s->stream>>>(g, cst(W), U.f[7], F[2]);
+    } else {
+      if (d == 0) k_sweep_speeds<T, 0, 1><<<nb, kThreads, 0, s->stream>>>(g, cst(W), U.f[5], F[0]);
+      else if (d == 1) k_sweep_speeds<T, 1, 1><<<nb, kThreads, 0, s->stream>>>(g, cst(W), U.f[6], F[1]);
+      else k_sweep_speeds<T, 2, 1><<<nb, kThreads, 0, s->stream>>>(g, cst(W), U.f[7], F[2]);
+    }
   }
   k_inv_only<T><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(F[0]), cst(F[1]),
                                                                  cst(F[2]), s->ctrl);
@@ -1580,7 +1609,8 @@ bool grid_bc(const idx_grid* grid, int bc[3], int pn[3]) {
 }
 
 bool valid_solver(const idx_solver* v) {
-  return v && v->recon == 1 && (v->riemann == 1 || v->riemann == 2 || v->riemann == 4) &&
+  return v && (v->recon == 1 || v->recon == 3) &&
+         (v->riemann == 1 || v->riemann == 2 || v->riemann == 4) &&
          v->emf == 2 && (v->rk_order == 2 || v->rk_order == 3) &&
          (v->induction == IDX_INDUCTION_FIELD || v->induction == IDX_INDUCTION_POTENTIAL) &&
          v->cfl > 0.0 && v->cfl < 1.0 &&
@@ -1640,6 +1670,7 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
   }
   geo_set_gamma(g, gamma);
   g.riemann = solver->riemann;
+  g.recon = solver->recon;
 
   // memory plan: U, U1 (16 doubles/cell) + W, F (3 x 8), E (3) in the bulk type
   const bool f32 = solver->precision == IDX_FP32_BULK;
@@ -2072,6 +2103,10 @@ int idx_set_sweep_shapes(idx_sim* s, const int shapes[3]) {
     v[d] = g.active[d] ? shapes[d] : 0;
     if (!g.active[d]) continue;
     const int x = v[d];
+    if (g.recon == 3) {  // LimO3 runs the marching sweeps of 16 or 32 faces only
+      if (x != 16 && x != 32) return IDX_EINVAL;
+      continue;
+    }
     const bool march = x == 2 || x == 4 || x == 8 || x == 16 || x == 32;
     const bool warpx = x == -1 && d == 0;
     const bool staged = (x == 116 || x == 132 || x == -2) && tma_shape_ok(s, d, x);
@@ -2207,6 +2242,7 @@ extern "C" int idx_step_noalloc(const idx_grid* grid, double gamma, double cfl,
   }
   geo_set_gamma(g, gamma);
   g.riemann = 4;
+  g.recon = 1;
   const size_t arr = align256(sizeof(double) * (size_t)ncell);
   char* p = (char*)base;
   s.ctrl = (Ctrl*)p;
@@ -2478,8 +2514,9 @@ template <typename T> int batch_upload(idx_batch* b) {
     idx_sim* s = b->sims[i];
     inst[i] = inst_of<T>(s);
     // stepped by its own kernels, no work-list items: large members, and members whose
-    // cycle the work-list kernels do not run (RK3, vector-potential form)
-    if (s->geo.ncell >= kSoloCells || s->solver.rk_order != 2 || s->pot || s->bounded) {
+    // cycle the work-list kernels do not run (RK3, vector-potential form, LimO3, boundaries)
+    if (s->geo.ncell >= kSoloCells || s->solver.rk_order != 2 || s->pot || s->bounded ||
+        s->geo.recon != 1) {
       b->solo.push_back(s);
       continue;
     }

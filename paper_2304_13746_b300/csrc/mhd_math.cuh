@@ -146,6 +146,31 @@ template <typename T> __device__ __forceinline__ T vanleer_half(T dl, T dr) {
   return same_sign_nz(dl, dr, prod) ? prod / (dl + dr) : T(0);
 }
 
+// x with its sign flipped where y is negative (x * sign(y), signed zeros included), on the
+// bit patterns.
+__device__ __forceinline__ double xsign(double x, double y) {
+  return __longlong_as_double(ibits(x) ^ (ibits(y) & (long long)0x8000000000000000ull));
+}
+__device__ __forceinline__ float xsign(float x, float y) {
+  return __int_as_float(__float_as_int(x) ^ (__float_as_int(y) & (int)0x80000000u));
+}
+
+// LimO3, the compact third-order reconstruction of Sec. 2.3 (Cada & Torrilhon 2009), as the
+// change of a cell's value at one face: with dt the difference toward that face's
+// neighbour and db the difference from the neighbour behind, the face value is
+// w + phi(db / dt) dt / 2 with
+//   phi(t) = max(0, min(P3, max(-t/2, min(2t, P3, 3/2)))),   P3 = (2 + t) / 3
+// (P3 alone: the unlimited third-order value).  Every piece of phi is linear in t, so
+// phi(db/dt) dt / 2 is the same chain in a = sign(dt) db / 2 and b = |dt| / 2 (b >= 0 keeps
+// each min and max in place), formed without a division; dt = 0 gives 0, the limit.
+template <typename T> __device__ __forceinline__ T limo3_half(T db, T dt) {
+  const T b = T(0.5) * tabs(dt);
+  const T a = T(0.5) * xsign(db, dt);
+  const T p3 = (T(2) * b + a) * T(1.0 / 3.0);
+  const T chain = imin(imin(T(2) * a, p3), T(1.5) * b);
+  return xsign(pos_part(imin(p3, imax(T(-0.5) * a, chain))), dt);
+}
+
 // Primitive state on one side of a face, rotated so that "u" is the normal velocity.
 template <typename T> struct Side {
   T r, u, v, w, p, b1, b2;  // rho, v_n, v_t1, v_t2, P, B_t1, B_t2

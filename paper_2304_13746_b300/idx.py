@@ -52,6 +52,7 @@ class Solver(ctypes.Structure):
 P8 = ctypes.c_void_p * 8
 P3 = ctypes.c_void_p * 3
 INDUCTION = {"field": 0, "potential": 1}
+RECON = {"plm": 1, "limo3": 3}
 
 
 def lib(path=LIB_PATH):
@@ -116,11 +117,11 @@ def pipe_rates():
 
 
 def footprint(shape, precision="fp64", rk_order=2, induction="field", riemann="hlld",
-              bc=(0, 0, 0)):
+              bc=(0, 0, 0), recon="plm"):
     """Device bytes a sim of this shape (nz, ny, nx) and configuration allocates."""
     nz, ny, nx = (int(v) for v in shape)
     out = ctypes.c_uint64()
-    s = Solver(1, RIEMANN[riemann], 2, int(rk_order), 0.4, PRECISIONS[precision],
+    s = Solver(RECON[recon], RIEMANN[riemann], 2, int(rk_order), 0.4, PRECISIONS[precision],
                INDUCTION[induction])
     g = Grid(nx, ny, nz, 1.0, 1.0, 1.0, (ctypes.c_int * 3)(*_bc_codes(bc)))
     rc = lib().idx_footprint_solver(ctypes.byref(g), ctypes.byref(s), ctypes.byref(out))
@@ -146,7 +147,7 @@ class Sim:
     """
 
     def __init__(self, shape, lengths, gamma=5.0 / 3.0, cfl=0.4, precision="fp64", stream=None,
-                 riemann="hlld", rk_order=2, induction="field", bc=(0, 0, 0)):
+                 riemann="hlld", rk_order=2, induction="field", bc=(0, 0, 0), recon="plm"):
         """bc: boundary kind per direction x, y, z ("periodic", "outflow", "reflecting" or
         0/1/2); along a non-periodic direction of more than one cell the normal face field
         has one more face than cells (see include/idx.h)."""
@@ -167,8 +168,8 @@ class Sim:
         self.precision = precision
         g = Grid(nx, ny, nz, *self.lengths, (ctypes.c_int * 3)(*self.bc))
         self.induction = induction
-        s = Solver(1, RIEMANN[riemann], 2, int(rk_order), self.cfl, PRECISIONS[precision],
-                   INDUCTION[induction])
+        s = Solver(RECON[recon], RIEMANN[riemann], 2, int(rk_order), self.cfl,
+                   PRECISIONS[precision], INDUCTION[induction])
         h = ctypes.c_void_p()
         rc = L.idx_create(ctypes.byref(g), self.gamma, ctypes.byref(s),
                           ctypes.c_void_p(stream) if stream else None, ctypes.byref(h))

@@ -105,6 +105,17 @@ def test_footprint_rejects_invalid_solver(L):
     s = idx.Solver(1, 4, 2, 2, 0.4, 0, 5)
     assert L.idx_footprint_solver(ctypes.byref(idx.Grid(8, 8, 8, 1, 1, 1)), ctypes.byref(s),
                                   ctypes.byref(out)) == idx.IDX_EINVAL
+    for recon in (0, 2, 4):  # 1 PLM and 3 LimO3 are the reconstructions
+        s = idx.Solver(recon, 4, 2, 2, 0.4, 0, 0)
+        assert L.idx_footprint_solver(ctypes.byref(idx.Grid(8, 8, 8, 1, 1, 1)), ctypes.byref(s),
+                                      ctypes.byref(out)) == idx.IDX_EINVAL
+
+
+def test_limo3_needs_no_extra_memory(L):
+    for precision in ("fp64", "fp32"):
+        for rk in (2, 3):
+            assert idx.footprint((64, 64, 64), precision, rk_order=rk, recon="limo3") == \
+                idx.footprint((64, 64, 64), precision, rk_order=rk)
 
 
 def test_binding_refuses_to_run_without_library(tmp_path):

@@ -183,11 +183,12 @@ def test_batched_result_matches_oracle():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_rk3_and_potential_members_match_alone(precision):
-    # members whose cycle the work-list kernels do not run step with their own kernels
-    # inside the batched cycle, next to ordinary members
+def test_solo_members_match_alone(precision):
+    # members whose cycle the work-list kernels do not run (RK3, potential, LimO3) step with
+    # their own kernels inside the batched cycle, next to ordinary members
     ics = [(inputs.orszag_tang_2d(32), dict(rk_order=3), 0.02),
            (inputs.random_smooth((8, 8, 8), seed=4), dict(induction="potential"), 0.02),
+           (inputs.random_smooth((6, 5, 7), seed=8), dict(recon="limo3"), 0.02),
            (inputs.turbulent_box(16, seed=3), dict(), 0.02)]
     alone = []
     for ic, kw, t_end in ics:

@@ -46,10 +46,12 @@ def with_faces(prim, bc):
     return out
 
 
-def run_pair(prim, lengths, gamma, bc, cycles, precision="fp64", t_end=None):
-    o = oracle.SimBC(prim, lengths, gamma, 0.4, bc)
+def run_pair(prim, lengths, gamma, bc, cycles, precision="fp64", t_end=None, recon="plm",
+             rk_order=2):
+    o = oracle.SimBC(prim, lengths, gamma, 0.4, bc, rk_order=rk_order, recon=recon)
     nz, ny, nx = prim[0].shape
-    s = idx.Sim((nz, ny, nx), lengths, gamma, 0.4, precision, bc=bc)
+    s = idx.Sim((nz, ny, nx), lengths, gamma, 0.4, precision, bc=bc, recon=recon,
+                rk_order=rk_order)
     s.set_primitive(prim)
     rel = 1e-12 if precision == "fp64" else 1e-5   # FP32 bulk: signal speeds in FP32
     assert s.time()[1] == pytest.approx(o.cfl / o.inv_dt, rel=rel)
@@ -95,6 +97,18 @@ def test_mixed_boundaries_3d(bc):
     o, s = run_pair(prim, ic.lengths, ic.gamma, bc, 12)
     err = field_errors(s.get_state(), o.state())
     print(bc, f"{max(err):.2e}")
+    assert max(err) <= 1e-12, err
+    s.close()
+
+
+@pytest.mark.parametrize("rk_order", [2, 3])
+def test_limo3_with_boundaries(rk_order):
+    bc = (bd.OUTFLOW, bd.REFLECTING, bd.PERIODIC)
+    ic = inputs.random_smooth((10, 12, 14), seed=7)
+    prim = with_faces(ic.prim, bc)
+    o, s = run_pair(prim, ic.lengths, ic.gamma, bc, 10, recon="limo3", rk_order=rk_order)
+    err = field_errors(s.get_state(), o.state())
+    print(bc, rk_order, f"{max(err):.2e}")
     assert max(err) <= 1e-12, err
     s.close()
 

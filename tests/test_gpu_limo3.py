@@ -1,0 +1,178 @@
+"""LimO3 reconstruction (Sec. 2.3; Cada & Torrilhon 2009) on the GPU against the oracle.
+
+The marching sweeps form each cell's two face changes without a division (the limiter's
+min/max chain scaled by the differences); the oracle divides for the ratio t.  They differ
+by rounding, so the bar is the periodic path's: 1e-12 of each field's scale per cycle,
+1e-10 after 100 cycles, with the per-cell relaxation near ill-conditioned HLLD star states
+of the parity tests.  Cases: ragged multi-segment grids, 1D/2D, both sweep segments (16,
+32), RK2 and RK3, HLL and Rusanov, the vector-potential form, FP32 bulk, and windows of
+the 256^3 turbulent box in the benchmark's launch configuration.
+"""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2304_13746_b300 import build as idx_build
+from paper_2304_13746_b300 import idx, inputs
+
+sys.path.insert(0, os.path.dirname(__file__))
+from test_gpu_parity import CASES, TOL_100, TOL_STEP, check_cycle, field_errors  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    idx_build.build()
+    idx.lib()
+
+
+def pair(ic, rk_order=2, riemann="hlld", precision="fp64", shapes=None):
+    o = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, 0.4, solver=riemann,
+                              rk_order=rk_order, recon="limo3")
+    s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, precision, riemann=riemann,
+                rk_order=rk_order, recon="limo3")
+    if shapes is not None:
+        s.set_sweep_shapes(shapes)
+    s.set_primitive(ic.prim)
+    return o, s
+
+
+@pytest.mark.parametrize("name", ["smooth_6x5x7", "smooth_33x17x40", "smooth_2d_1x12x10",
+                                  "smooth_1x24x1", "turb_40cube", "ot2d_64", "sod_x", "sod_z"])
+def test_one_cycle_matches_oracle(name):
+    ic = CASES[name]()
+    o, s = pair(ic)
+    assert s.time()[1] == pytest.approx(o.next_dt(), rel=1e-14)  # LimO3 speed pass
+    u0 = [a.copy() for a in o.u]
+    dt_o = o.step()
+    assert s.step(want_dt=True) == pytest.approx(dt_o, rel=1e-14)
+    u1, _ = oracle.stage(u0, ic.lengths, ic.gamma, dt_o, recon="limo3")
+    worst, relaxed = check_cycle(s.get_state(), o.u, [u0, u1], ic.lengths, ic.gamma,
+                                 recon="limo3")
+    print(f"limo3 {name}: max err {worst:.2e}, relaxed cells {relaxed}")
+    assert s.time()[1] == pytest.approx(o.next_dt(), rel=1e-12)
+    s.close()
+
+
+@pytest.mark.parametrize("seg", [16, 32])
+@pytest.mark.parametrize("rk_order", [2, 3])
+def test_segments_and_rk_orders(seg, rk_order):
+    ic = inputs.random_smooth((17, 33, 40), seed=31)
+    o, s = pair(ic, rk_order=rk_order, shapes=(seg, seg, seg))
+    assert s.sweep_shapes() == [seg, seg, seg]
+    for _ in range(3):
+        dt_o = o.step()
+        assert s.step(want_dt=True) == pytest.approx(dt_o, rel=1e-12)
+    err = field_errors(s.get_state(), o.u)
+    print(seg, rk_order, f"{max(err):.2e}")
+    assert max(err) <= 3 * TOL_STEP, err
+    s.close()
+
+
+def test_only_marching_shapes_are_accepted():
+    ic = inputs.random_smooth((8, 8, 32), seed=1)
+    s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, "fp64", recon="limo3")
+    for bad in ((-1, 16, 16), (16, 116, 16), (8, 16, 16), (-2, 16, 16)):
+        with pytest.raises(idx.IdxError) as e:
+            s.set_sweep_shapes(bad)
+        assert e.value.code == idx.IDX_EINVAL
+    s.set_sweep_shapes((32, 16, 32))
+    s.close()
+
+
+@pytest.mark.parametrize("riemann", ["hll", "rusanov"])
+def test_other_solvers(riemann):
+    ic = CASES["turb_40cube"]()
+    o, s = pair(ic, riemann=riemann)
+    assert s.time()[1] == pytest.approx(o.next_dt(), rel=1e-14)
+    for _ in range(3):
+        o.step()
+        s.step()
+    err = field_errors(s.get_state(), o.u)
+    assert max(err) <= 3 * TOL_STEP, err
+    s.close()
+
+
+def test_vector_potential_form():
+    ic = inputs.random_smooth((10, 12, 14), seed=9)
+    A = ic.meta["A"]
+    bmean = ic.meta["bmean"]
+    o = oracle.Sim.from_potential(ic.prim[:5], A, bmean, ic.lengths, ic.gamma, 0.4,
+                                  induction="potential", recon="limo3")
+    s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, "fp64", induction="potential",
+                recon="limo3")
+    s.set_potential(ic.prim[:5], A, bmean)
+    for _ in range(4):
+        dt_o = o.step()
+        assert s.step(want_dt=True) == pytest.approx(dt_o, rel=1e-12)
+    err = field_errors(s.get_state(), o.u)
+    assert max(err) <= 3 * TOL_STEP, err
+    gA = s.get_potential()
+    scale = max(float(np.max(np.abs(a))) for a in o.A)
+    assert max(float(np.max(np.abs(np.asarray(g) - a))) for g, a in zip(gA, o.A)) \
+        <= 3 * TOL_STEP * scale
+    s.close()
+
+
+def test_fp32_bulk_tracks_the_oracle():
+    # FP32 reconstruction and solver: rounding of ~1e-7 relative per cycle
+    ic = CASES["turb_40cube"]()
+    o, s = pair(ic, precision="fp32")
+    assert s.time()[1] == pytest.approx(o.next_dt(), rel=1e-5)
+    for _ in range(3):
+        o.step()
+        s.step()
+    err = field_errors(s.get_state(), o.u)
+    print(f"fp32 limo3: {max(err):.2e}")
+    assert max(err) <= 3e-6, err
+    s.close()
+
+
+def test_hundred_cycles_orszag_tang_rk3():
+    ic = inputs.orszag_tang_2d(128)
+    o, s = pair(ic, rk_order=3)
+    for _ in range(100):
+        o.step()
+        s.step()
+    err = field_errors(s.get_state(), o.u)
+    print(f"100 cycles: {max(err):.2e}")
+    assert max(err) <= TOL_100, err
+    s.close()
+
+
+def test_full_size_turbulent_box_256_windows():
+    # The 256^3 box in the benchmark's launch configuration (autotuned LimO3 sweeps, CUDA
+    # graph), one RK3 cycle.  A stage reaches at most 3 stored cells away in any direction
+    # (two cells of reconstruction, the upper face field of the outermost cell, the EMF's
+    # transverse neighbour), so a cycle reaches 9: the oracle steps windows of its own
+    # initial state as if periodic, with the dt of its own speed pass over the whole box, and
+    # cells more than 12 from a window's edge must match.
+    n, m, core = 256, 12, 32
+    ic = inputs.turbulent_box(n, seed=0)
+    s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, "fp64", rk_order=3, recon="limo3")
+    s.set_primitive(ic.prim)
+    dt_g = s.step(want_dt=True)
+    g = s.get_state()
+    s.close()
+    u0 = oracle.cons_from_prims(ic.prim, ic.lengths, ic.gamma)
+    dt = 0.4 / oracle.speed_pass(u0, ic.lengths, ic.gamma, "limo3")
+    assert dt_g == pytest.approx(dt, rel=1e-14)
+    w = core + 2 * m
+    wl = (w * ic.lengths[0] / n,) * 3
+    for c in ((0, 0, 0), (100, 37, 211), (240, 128, 64)):
+        win = np.ix_(*(np.arange(c[a] - m, c[a] - m + w) % n for a in range(3)))
+        uw = [np.ascontiguousarray(a[win]) for a in u0]
+        o = oracle.Sim(uw, wl, ic.gamma, 0.4, rk_order=3, recon="limo3")
+        o.inv_dt = 0.2 / dt          # a dt above the box's: dt_max then gives it exactly
+        assert o.step(dt_max=dt) == dt
+        u1, _ = oracle.stage(uw, wl, ic.gamma, dt, recon="limo3")
+        u2, _ = oracle.stage(u1, wl, ic.gamma, dt, u0=uw, w=0.25, w0=0.75, recon="limo3")
+        keep = (slice(m, m + core),) * 3
+        worst, relaxed = check_cycle([a[win] for a in g], o.u, [uw, u1, u2], wl, ic.gamma,
+                                     recon="limo3", keep=keep)
+        print(f"window {c}: max err {worst:.2e}, relaxed {relaxed} of {core ** 3}")
+        assert relaxed < 1e-2 * core ** 3

@@ -62,10 +62,21 @@ def gpu_sim(ic, cfl=0.4, precision="fp64"):
     return s
 
 
-def degeneracy_ratio(u, lengths, gamma):
+def limo3_face_np(back, w0, face):
+    """LimO3 face value (Sec. 2.3), vectorised, for the tolerance map only."""
+    toward = face - w0
+    safe = np.where(toward == 0, 1.0, toward)
+    t = (w0 - back) / safe
+    p3 = (2.0 + t) / 3.0
+    phi = np.maximum(0.0, np.minimum(p3, np.maximum(-t / 2, np.minimum(np.minimum(2 * t, p3),
+                                                                        1.5))))
+    return np.where(toward == 0, w0, w0 + 0.5 * phi * toward)
+
+
+def degeneracy_ratio(u, lengths, gamma, recon="plm"):
     """Per cell: min over the cell's faces (integrated directions) of the HLLD single-star
     degeneracy ratio |D| / (|rho (S-u)(S-S_M)| + Bx^2) of each side with B_t != 0, from
-    the oracle's face states (van Leer PLM of the oracle's primitives)."""
+    the oracle's face states (van Leer PLM, or LimO3, of the oracle's primitives)."""
     w = oracle.prims(u, lengths, gamma)
     out = np.full(u[0].shape, np.inf)
     for d, ax in ((0, 2), (1, 1), (2, 0)):
@@ -82,8 +93,12 @@ def degeneracy_ratio(u, lengths, gamma):
         for q in var:
             f = w[q]
             fm, fmm, fp = np.roll(f, 1, ax), np.roll(f, 2, ax), np.roll(f, -1, ax)
-            L.append(fm + 0.5 * vl(fmm, fm, f))
-            R.append(f - 0.5 * vl(fm, f, fp))
+            if recon == "limo3":
+                L.append(limo3_face_np(fmm, fm, f))
+                R.append(limo3_face_np(fp, f, fm))
+            else:
+                L.append(fm + 0.5 * vl(fmm, fm, f))
+                R.append(f - 0.5 * vl(fm, f, fp))
         bx = u[5 + d]
 
         def cf(st):
@@ -111,20 +126,25 @@ def degeneracy_ratio(u, lengths, gamma):
     return out
 
 
-def cell_tolerance(o_states, lengths, gamma, tol):
+def cell_tolerance(o_states, lengths, gamma, tol, recon="plm"):
     """1e-12 (tol) scaled by R0 / r_min near ill-conditioned HLLD star states."""
     from scipy.ndimage import minimum_filter
     r = np.full(o_states[0][0].shape, np.inf)
     for u in o_states:
-        r = np.minimum(r, degeneracy_ratio(u, lengths, gamma))
+        r = np.minimum(r, degeneracy_ratio(u, lengths, gamma, recon))
     r = minimum_filter(r, size=5, mode="wrap")
     return tol * np.maximum(1.0, R0 / np.maximum(r, 1e-300))
 
 
-def check_cycle(g, o_after, o_states, lengths, gamma, tol=TOL_STEP):
-    """Per field and cell |g - o| / scale_f <= cell tolerance; returns (max err, cells relaxed)."""
+def check_cycle(g, o_after, o_states, lengths, gamma, tol=TOL_STEP, recon="plm", keep=None):
+    """Per field and cell |g - o| / scale_f <= cell tolerance; returns (max err, cells relaxed).
+    keep: an index (tuple of slices) restricting the comparison to part of the grid."""
     sc = field_scales(o_after)
-    tcell = cell_tolerance(o_states, lengths, gamma, tol)
+    tcell = cell_tolerance(o_states, lengths, gamma, tol, recon)
+    if keep is not None:
+        g = [np.asarray(a)[keep] for a in g]
+        o_after = [a[keep] for a in o_after]
+        tcell = tcell[keep]
     worst = 0.0
     for f in range(8):
         e = np.abs(np.asarray(g[f]) - o_after[f]) / max(sc[f], 1e-300)
