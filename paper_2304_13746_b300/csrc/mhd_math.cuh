@@ -194,9 +194,11 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   const T dR = pos_part(aR * aR - gpR * bx2x4);
   // 0.5/rho_L and 0.5/rho_R from one division
   const T hLR = T(0.5) / (L.r * R.r);
-  const T cfL = tsqrt((aL + tsqrt(dL)) * (R.r * hLR));
-  const T cfR = tsqrt((aR + tsqrt(dR)) * (L.r * hLR));
-  const T cfm = max_nn(cfL, cfR);
+  // only the larger fast speed enters: sqrt is correctly rounded and monotone, so the root
+  // of the larger square equals the larger root, bit for bit, at one square root fewer
+  const T cf2L = (aL + tsqrt(dL)) * (R.r * hLR);
+  const T cf2R = (aR + tsqrt(dR)) * (L.r * hLR);
+  const T cfm = tsqrt(max_nn(cf2L, cf2R));
   const T SL = imin(L.u, R.u) - cfm;
   const T SR = imax(L.u, R.u) + cfm;
   c = max_nn(tabs(SL), tabs(SR));
@@ -225,20 +227,29 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   const T SM = (qR * R.u - qL * L.u - pTR + pTL) / (qR - qL);
   const T pTs = pTL + qL * (SM - L.u);
 
-  // single-star transverse states, both sides (needed by the double-star average)
-  // 1/(S_L - S_M) and 1/(S_R - S_M) from one division (S_L < S_M < S_R: both O(c_f))
+  // single-star transverse states, both sides (needed by the double-star average), with
+  // D = rho (S - u)(S - S_M) - Bx^2 per side (MK05 eqs. 44-47); a side where D vanishes
+  // against its terms keeps its transverse state (the HLLC limit)
   const T eL = SL - SM, eR = SR - SM;
-  const T iLR = T(1) / (eL * eR);
+  const T qeL = qL * eL, qeR = qR * eR;
+  const T DL = qeL - bx2, DR = qeR - bx2;
+  const bool degL = le_nn(tabs(DL), Eps<T>::degen * (tabs(qeL) + bx2));
+  const bool degR = le_nn(tabs(DR), Eps<T>::degen * (tabs(qeR) + bx2));
+  // 1/(S_L - S_M), 1/(S_R - S_M), 1/D_L and 1/D_R from one division of their product
+  // (S_L < S_M < S_R: the e's are O(c_f); a degenerate side's D stays out of it)
+  const T kL = degL ? T(1) : DL, kR = degR ? T(1) : DR;
+  const T eLR = eL * eR, kLR = kL * kR;
+  const T inv = T(1) / (eLR * kLR);
+  const T iLR = kLR * inv, eLRinv = eLR * inv;
   const T iL = eR * iLR, iR = eL * iLR;
+  const T iDL = kR * eLRinv, iDR = kL * eLRinv;
   const T rsL = qL * iL, rsR = qR * iR;  // rho*
   T vsL, wsL, b1sL, b2sL, vsR, wsR, b1sR, b2sR;
   {
-    const T q = qL * eL;  // rho_L (S_L - u_L)(S_L - S_M)
-    const T D = q - bx2;
-    if (le_nn(tabs(D), Eps<T>::degen * (tabs(q) + bx2))) {
+    if (degL) {
       vsL = L.v; wsL = L.w; b1sL = L.b1; b2sL = L.b2;
     } else {
-      const T iD = T(1) / D;
+      const T iD = iDL;
       const T t = bx * (SM - L.u) * iD;
       vsL = L.v - L.b1 * t;
       wsL = L.w - L.b2 * t;
@@ -248,12 +259,10 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
     }
   }
   {
-    const T q = qR * eR;
-    const T D = q - bx2;
-    if (le_nn(tabs(D), Eps<T>::degen * (tabs(q) + bx2))) {
+    if (degR) {
       vsR = R.v; wsR = R.w; b1sR = R.b1; b2sR = R.b2;
     } else {
-      const T iD = T(1) / D;
+      const T iD = iDR;
       const T t = bx * (SM - R.u) * iD;
       vsR = R.v - R.b1 * t;
       wsR = R.w - R.b2 * t;
@@ -362,6 +371,18 @@ __device__ __forceinline__ void fast_speeds(const Side<T>& L, const Side<T>& R, 
   cfR = tsqrt((aR + tsqrt(dR)) * (T(0.5) / R.r));
 }
 
+// The larger of the two fast speeds, from one outer square root (see hlld).
+template <typename T>
+__device__ __forceinline__ T fast_speed_max(const Side<T>& L, const Side<T>& R, T bx, T gamma) {
+  const T bx2 = bx * bx;
+  const T gpL = gamma * L.p, gpR = gamma * R.p;
+  const T aL = gpL + bx2 + L.b1 * L.b1 + L.b2 * L.b2;
+  const T aR = gpR + bx2 + R.b1 * R.b1 + R.b2 * R.b2;
+  const T dL = pos_part(aL * aL - T(4) * gpL * bx2);
+  const T dR = pos_part(aR * aR - T(4) * gpR * bx2);
+  return tsqrt(max_nn((aL + tsqrt(dL)) * (T(0.5) / L.r), (aR + tsqrt(dR)) * (T(0.5) / R.r)));
+}
+
 template <typename T>
 __device__ __forceinline__ void rusanov(const Side<T>& L, const Side<T>& R, T bx, T gamma,
                                         T gm1inv, T F[7], T& c) {
@@ -380,9 +401,7 @@ __device__ __forceinline__ void rusanov(const Side<T>& L, const Side<T>& R, T bx
 template <typename T>
 __device__ __forceinline__ void hll(const Side<T>& L, const Side<T>& R, T bx, T gamma, T gm1inv,
                                     T F[7], T& c) {
-  T cfL, cfR;
-  fast_speeds(L, R, bx, gamma, cfL, cfR);
-  const T cfm = max_nn(cfL, cfR);
+  const T cfm = fast_speed_max(L, R, bx, gamma);
   const T SL = imin(L.u, R.u) - cfm;
   const T SR = imax(L.u, R.u) + cfm;
   c = max_nn(tabs(SL), tabs(SR));
@@ -409,7 +428,7 @@ __device__ __forceinline__ void hll(const Side<T>& L, const Side<T>& R, T bx, T 
 template <typename T>
 __device__ __forceinline__ T outer_speed(int solver, const Side<T>& L, const Side<T>& R, T bx,
                                          T gamma) {
-  T cfL, cfR;
+  T cfm;
   if (solver == 4) {
     const T bx2 = bx * bx;
     const T b2L = bx2 + L.b1 * L.b1 + L.b2 * L.b2, b2R = bx2 + R.b1 * R.b1 + R.b2 * R.b2;
@@ -419,12 +438,14 @@ __device__ __forceinline__ T outer_speed(int solver, const Side<T>& L, const Sid
     const T dL = pos_part(aL * aL - gpL * bx2x4);
     const T dR = pos_part(aR * aR - gpR * bx2x4);
     const T hLR = T(0.5) / (L.r * R.r);
-    cfL = tsqrt((aL + tsqrt(dL)) * (R.r * hLR));
-    cfR = tsqrt((aR + tsqrt(dR)) * (L.r * hLR));
+    cfm = tsqrt(max_nn((aL + tsqrt(dL)) * (R.r * hLR), (aR + tsqrt(dR)) * (L.r * hLR)));
+  } else if (solver == 2) {
+    cfm = fast_speed_max(L, R, bx, gamma);
   } else {
+    T cfL, cfR;
     fast_speeds(L, R, bx, gamma, cfL, cfR);
+    cfm = max_nn(cfL, cfR);
   }
-  const T cfm = max_nn(cfL, cfR);
   return max_nn(tabs(imin(L.u, R.u) - cfm), tabs(imax(L.u, R.u) + cfm));
 }
 
