@@ -1997,14 +1997,25 @@ int idx_advance(idx_sim* s, double t_end, int64_t* nsteps) {
   c.t_end = t_end;
   c.done = (c.t >= t_end) ? 1 : 0;
   IDX_TRY(cudaMemcpyAsync(s->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s->stream));
-  int chunk = 4;
+  // Graph replays between host checks: the cycles left at the current dt, plus one for the
+  // clamped last cycle (at most 256).  Cycles launched past the end exit at once (the
+  // device clamps and flags the end), so a growing dt only wastes empty launches and a
+  // shrinking one costs another round.
+  auto chunk_for = [&](const Ctrl& h) {
+    double inv;
+    std::memcpy(&inv, &h.inv_prev, sizeof(double));
+    const double left = (t_end - h.t) * inv / s->solver.cfl;
+    if (!(left >= 0.0) || !(left < 256.0)) return 256;
+    return std::max(1, (int)std::ceil(left) + 1);
+  };
+  int chunk = chunk_for(c);
   while (true) {
     for (int q = 0; q < chunk; ++q) IDX_TRY(cudaGraphLaunch(s->exec, s->stream));
     rc = sync_ctrl(s);
     if (rc != IDX_OK) return rc;
     if (s->host_ctrl->err) break;
     if (s->host_ctrl->done) break;
-    if (chunk < 256) chunk *= 2;
+    chunk = chunk_for(*s->host_ctrl);
   }
   // disarm: later idx_step calls run unclamped
   c = *s->host_ctrl;

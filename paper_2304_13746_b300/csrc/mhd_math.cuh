@@ -145,6 +145,15 @@ template <typename T> __device__ __forceinline__ T vanleer_half(T dl, T dr) {
   const T prod = dl * dr;
   return same_sign_nz(dl, dr, prod) ? prod / (dl + dr) : T(0);
 }
+// In FP64 the quotient is a product with the reciprocal: a reciprocal costs fewer FP64-pipe
+// slots than a general division, for one more rounding (within an ulp of the quotient).  The
+// test is on the rounded product itself: where dl * dr underflows to 0 (both differences
+// near the subnormal range, as ahead of a blast into gas at rest) 1/(dl + dr) could overflow
+// and 0 * inf give NaN; a positive product bounds |dl + dr| >= 2 sqrt(dl dr) > 4e-162.
+template <> __device__ __forceinline__ double vanleer_half<double>(double dl, double dr) {
+  const double prod = dl * dr;
+  return gt0(prod) ? prod * (1.0 / (dl + dr)) : 0.0;
+}
 
 // x with its sign flipped where y is negative (x * sign(y), signed zeros included), on the
 // bit patterns.
@@ -224,7 +233,7 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   // contact speed and star total pressure
   const T sLu = SL - L.u, sRu = SR - R.u;
   const T qL = sLu * L.r, qR = sRu * R.r;
-  const T SM = (qR * R.u - qL * L.u - pTR + pTL) / (qR - qL);
+  const T SM = (qR * R.u - qL * L.u - pTR + pTL) * (T(1) / (qR - qL));
   const T pTs = pTL + qL * (SM - L.u);
 
   // single-star transverse states, both sides (needed by the double-star average), with

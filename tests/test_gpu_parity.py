@@ -349,3 +349,20 @@ def test_pipe_rates_and_kernel_times():
     t, _ = s.time()
     assert t > 0
     s.close()
+
+
+def test_grid_beyond_device_memory_reports_enomem():
+    # 1200^3 cells pass the argument checks (fewer than 2^31) but need ~750 GB: the one
+    # allocation of the sim fails, idx_create returns IDX_ENOMEM, and the device stays usable
+    n = 1200
+    assert idx.footprint((n, n, n)) > 300e9
+    with pytest.raises(idx.IdxError) as e:
+        idx.Sim((n, n, n), (1.0, 1.0, 1.0), 5.0 / 3.0, 0.4, "fp64")
+    assert e.value.code == idx.IDX_ENOMEM
+    ic = inputs.random_smooth((6, 5, 7), seed=1)
+    o = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, 0.4)
+    s = gpu_sim(ic)
+    o.step()
+    s.step()
+    assert max(field_errors(s.get_state(), o.u)) <= TOL_STEP
+    s.close()
