@@ -178,8 +178,10 @@ int idx_last_error_cell(const idx_sim* sim, int64_t* cell);
 int idx_kernel_times(idx_sim* sim, int reps, double ms[6]);
 
 /* Sweep shape per direction chosen by the autotuner, which runs before a sim's first
- * idx_step / idx_advance (grids of at least 32768 cells; smaller ones keep the default;
- * results are cached per grid, precision and device for the process):
+ * idx_step / idx_advance (grids of at least 32768 cells; smaller ones march 2 faces per
+ * thread, LimO3 16; results are cached per grid, precision and device for the process).
+ * A marching sweep too small to give two 256-thread blocks per SM runs smaller blocks
+ * (down to 32 threads), so that a small grid spreads over the SMs.  Shapes:
  *   2, 4, 8, 16, 32   one thread marches that many faces of a pencil (loads from HBM);
  *   -1                x only: one warp per 32 cells of an x-row, neighbours by shuffle;
  *   -2                x only: a block stages 32 x-faces of 8 rows (plus periodic halos)

@@ -1095,6 +1095,7 @@ struct idx_sim {
   cudaStream_t stream;
   bool own_stream;
   int device;
+  int nsm = 0;          // SMs of the device (0: not known, full-size blocks)
   void* mem;            // single device allocation
   size_t mem_bytes;
   Ptr8<double> U, U1;   // state and first-stage result (FP64)
@@ -1149,6 +1150,15 @@ template <typename T> Ptr8<const T> cst(const Ptr8<T>& p) {
   return q;
 }
 
+// Block size of a marching sweep of nthr threads: full blocks, halved (down to one warp)
+// while the launch would give fewer than two blocks per SM -- a small grid then spreads
+// over the GPU instead of running a few full blocks on a few SMs.
+int march_block(const idx_sim* s, long nthr) {
+  int nt = kThreads;
+  while (s->nsm > 0 && nt > 32 && (nthr + nt - 1) / nt < 2L * s->nsm) nt >>= 1;
+  return nt;
+}
+
 // One sweep launch in the given shape (see idx_sim::sweep_shape).
 template <typename T, int D, int SEG, int RECON = 1>
 void launch_march(idx_sim* s, const Ptr8<T>& W, const double* bface, const Ptr8<T>& F,
@@ -1156,8 +1166,9 @@ void launch_march(idx_sim* s, const Ptr8<T>& W, const double* bface, const Ptr8<
   const Geo& g = s->geo;
   const int a = (D + 1) % 3, b = (D + 2) % 3;
   const long nthr = (long)g.n[a] * g.n[b] * ((g.n[D] + SEG - 1) / SEG);
-  k_sweep<T, D, SEG, RECON><<<blocks_for(nthr), kThreads, 0, s->stream>>>(g, cst(W), bface, F,
-                                                                           s->ctrl, check_dt);
+  const int nt = march_block(s, nthr);
+  k_sweep<T, D, SEG, RECON><<<(unsigned)((nthr + nt - 1) / nt), nt, 0, s->stream>>>(
+      g, cst(W), bface, F, s->ctrl, check_dt);
 }
 
 template <typename T, int D, int L>
@@ -1220,10 +1231,14 @@ void launch_sweep_d(idx_sim* s, int shape, const Ptr8<T>& W, const double* bface
     case 2: launch_march<T, D, 2>(s, W, bface, F, check_dt); return;
     case 4: launch_march<T, D, 4>(s, W, bface, F, check_dt); return;
     case 8: launch_march<T, D, 8>(s, W, bface, F, check_dt); return;
+    case 16: launch_march<T, D, 16>(s, W, bface, F, check_dt); return;
     case 32: launch_march<T, D, 32>(s, W, bface, F, check_dt); return;
     default: break;
   }
-  launch_march<T, D, kSegDefault>(s, W, bface, F, check_dt);
+  // not tuned: grids below the tuning size take 2-face segments, which give them 8x the
+  // threads of the default at one extra cell slope per 2 faces
+  if (s->geo.ncell < kTuneMinCells) launch_march<T, D, 2>(s, W, bface, F, check_dt);
+  else launch_march<T, D, kSegDefault>(s, W, bface, F, check_dt);
 }
 
 template <typename T>
@@ -1491,15 +1506,16 @@ void launch_speed_pass(idx_sim* s, const Ptr8<double>& U, const Ptr8<T>& W, Ptr8
   for (int d = 0; d < 3; ++d) {
     if (!g.active[d]) continue;
     const long nthr = (long)g.n[(d + 1) % 3] * g.n[(d + 2) % 3] * ((g.n[d] + 15) / 16);
-    const int nb = blocks_for(nthr);
+    const int nt = march_block(s, nthr);
+    const unsigned nb = (unsigned)((nthr + nt - 1) / nt);
     if (g.recon == 3) {
-      if (d == 0) k_sweep_speeds<T, 0, 3><<<nb, kThreads, 0, s->stream>>>(g, cst(W), U.f[5], F[0]);
-      else if (d == 1) k_sweep_speeds<T, 1, 3><<<nb, kThreads, 0, s->stream>>>(g, cst(W), U.f[6], F[1]);
-      else k_sweep_speeds<T, 2, 3><<<nb, kThreads, 0, s->stream>>>(g, cst(W), U.f[7], F[2]);
+      if (d == 0) k_sweep_speeds<T, 0, 3><<<nb, nt, 0, s->stream>>>(g, cst(W), U.f[5], F[0]);
+      else if (d == 1) k_sweep_speeds<T, 1, 3><<<nb, nt, 0, s->stream>>>(g, cst(W), U.f[6], F[1]);
+      else k_sweep_speeds<T, 2, 3><<<nb, nt, 0, s->stream>>>(g, cst(W), U.f[7], F[2]);
     } else {
-      if (d == 0) k_sweep_speeds<T, 0, 1><<<nb, kThreads, 0, s->stream>>>(g, cst(W), U.f[5], F[0]);
-      else if (d == 1) k_sweep_speeds<T, 1, 1><<<nb, kThreads, 0, s->stream>>>(g, cst(W), U.f[6], F[1]);
-      else k_sweep_speeds<T, 2, 1><<<nb, kThreads, 0, s->stream>>>(g, cst(W), U.f[7], F[2]);
+      if (d == 0) k_sweep_speeds<T, 0, 1><<<nb, nt, 0, s->stream>>>(g, cst(W), U.f[5], F[0]);
+      else if (d == 1) k_sweep_speeds<T, 1, 1><<<nb, nt, 0, s->stream>>>(g, cst(W), U.f[6], F[1]);
+      else k_sweep_speeds<T, 2, 1><<<nb, nt, 0, s->stream>>>(g, cst(W), U.f[7], F[2]);
     }
   }
   k_inv_only<T><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(F[0]), cst(F[1]),
@@ -1655,6 +1671,8 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
   s->solver = *solver;
   s->last_bad = -1;
   if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return IDX_ECUDA; }
+  if (cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess)
+    s->nsm = 0;
   for (int d = 0; d < 3; ++d) s->bc[d] = bc[d];
   s->bounded = bounded;
   Geo& g = s->geo;  // the padded grid along non-periodic directions
@@ -2101,7 +2119,8 @@ int idx_sweep_shapes(const idx_sim* s, int shapes[3]) {
   if (!s || !shapes) return IDX_EINVAL;
   for (int d = 0; d < 3; ++d) {
     const int v = s->sweep_shape[d];
-    shapes[d] = s->geo.active[d] ? (v == 0 ? kSegDefault : v) : 0;
+    const int dflt = (s->geo.recon == 1 && s->geo.ncell < kTuneMinCells) ? 2 : kSegDefault;
+    shapes[d] = s->geo.active[d] ? (v == 0 ? dflt : v) : 0;
   }
   return IDX_OK;
 }
