@@ -201,8 +201,9 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   const T bx2x4 = T(4) * bx2;               // exact scaling, shared by both sides
   const T dL = pos_part(aL * aL - gpL * bx2x4);
   const T dR = pos_part(aR * aR - gpR * bx2x4);
-  // 0.5/rho_L and 0.5/rho_R from one division
-  const T hLR = T(0.5) / (L.r * R.r);
+  // 0.5/rho_L and 0.5/rho_R from one reciprocal (cheaper than a division; the factor 1/2
+  // is exact)
+  const T hLR = T(0.5) * (T(1) / (L.r * R.r));
   // only the larger fast speed enters: sqrt is correctly rounded and monotone, so the root
   // of the larger square equals the larger root, bit for bit, at one square root fewer
   const T cf2L = (aL + tsqrt(dL)) * (R.r * hLR);
@@ -376,8 +377,9 @@ __device__ __forceinline__ void fast_speeds(const Side<T>& L, const Side<T>& R, 
   const T aR = gpR + bx2 + R.b1 * R.b1 + R.b2 * R.b2;
   const T dL = pos_part(aL * aL - T(4) * gpL * bx2);
   const T dR = pos_part(aR * aR - T(4) * gpR * bx2);
-  cfL = tsqrt((aL + tsqrt(dL)) * (T(0.5) / L.r));
-  cfR = tsqrt((aR + tsqrt(dR)) * (T(0.5) / R.r));
+  const T hLR = T(0.5) * (T(1) / (L.r * R.r));  // 0.5/rho_L, 0.5/rho_R from one reciprocal
+  cfL = tsqrt((aL + tsqrt(dL)) * (R.r * hLR));
+  cfR = tsqrt((aR + tsqrt(dR)) * (L.r * hLR));
 }
 
 // The larger of the two fast speeds, from one outer square root (see hlld).
@@ -389,7 +391,8 @@ __device__ __forceinline__ T fast_speed_max(const Side<T>& L, const Side<T>& R, 
   const T aR = gpR + bx2 + R.b1 * R.b1 + R.b2 * R.b2;
   const T dL = pos_part(aL * aL - T(4) * gpL * bx2);
   const T dR = pos_part(aR * aR - T(4) * gpR * bx2);
-  return tsqrt(max_nn((aL + tsqrt(dL)) * (T(0.5) / L.r), (aR + tsqrt(dR)) * (T(0.5) / R.r)));
+  const T hLR = T(0.5) * (T(1) / (L.r * R.r));
+  return tsqrt(max_nn((aL + tsqrt(dL)) * (R.r * hLR), (aR + tsqrt(dR)) * (L.r * hLR)));
 }
 
 template <typename T>
@@ -446,7 +449,7 @@ __device__ __forceinline__ T outer_speed(int solver, const Side<T>& L, const Sid
     const T bx2x4 = T(4) * bx2;
     const T dL = pos_part(aL * aL - gpL * bx2x4);
     const T dR = pos_part(aR * aR - gpR * bx2x4);
-    const T hLR = T(0.5) / (L.r * R.r);
+    const T hLR = T(0.5) * (T(1) / (L.r * R.r));
     cfm = tsqrt(max_nn((aL + tsqrt(dL)) * (R.r * hLR), (aR + tsqrt(dR)) * (L.r * hLR)));
   } else if (solver == 2) {
     cfm = fast_speed_max(L, R, bx, gamma);
