@@ -80,6 +80,11 @@ __device__ __forceinline__ double tabs(double a) { return fabs(a); }
 __device__ __forceinline__ float tabs(float a) { return fabsf(a); }
 __device__ __forceinline__ double trsqrt(double a) { return rsqrt(a); }
 __device__ __forceinline__ float trsqrt(float a) { return rsqrtf(a); }
+// 1/a: the correctly rounded reciprocal in FP64; in the FP32 bulk the fast one (within 2 ulp
+// of 1/a for |a| < 2^126), far below the variant's own FP32 rounding budget, where the
+// correctly rounded FP32 division takes about 11 FMA slots.
+__device__ __forceinline__ double trcp(double a) { return 1.0 / a; }
+__device__ __forceinline__ float trcp(float a) { return __fdividef(1.0f, a); }
 
 // float <-> double conversions rebuilt from the IEEE-754 bit layouts in the integer pipe.
 // On this part the converters run on the FP64 pipe at its rate, which the FP32-bulk
@@ -143,7 +148,7 @@ __device__ __forceinline__ float d2f_warp(double x) {
 // factors 2 and 1/2 are exact) with two multiplies fewer per variable and face.
 template <typename T> __device__ __forceinline__ T vanleer_half(T dl, T dr) {
   const T prod = dl * dr;
-  return same_sign_nz(dl, dr, prod) ? prod / (dl + dr) : T(0);
+  return same_sign_nz(dl, dr, prod) ? __fdividef(prod, dl + dr) : T(0);
 }
 // In FP64 the quotient is a product with the reciprocal: a reciprocal costs fewer FP64-pipe
 // slots than a general division, for one more rounding (within an ulp of the quotient).  The
@@ -203,7 +208,7 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   const T dR = pos_part(aR * aR - gpR * bx2x4);
   // 0.5/rho_L and 0.5/rho_R from one reciprocal (cheaper than a division; the factor 1/2
   // is exact)
-  const T hLR = T(0.5) * (T(1) / (L.r * R.r));
+  const T hLR = T(0.5) * trcp(L.r * R.r);
   // only the larger fast speed enters: sqrt is correctly rounded and monotone, so the root
   // of the larger square equals the larger root, bit for bit, at one square root fewer
   const T cf2L = (aL + tsqrt(dL)) * (R.r * hLR);
@@ -234,7 +239,7 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   // contact speed and star total pressure
   const T sLu = SL - L.u, sRu = SR - R.u;
   const T qL = sLu * L.r, qR = sRu * R.r;
-  const T SM = (qR * R.u - qL * L.u - pTR + pTL) * (T(1) / (qR - qL));
+  const T SM = (qR * R.u - qL * L.u - pTR + pTL) * trcp(qR - qL);
   const T pTs = pTL + qL * (SM - L.u);
 
   // single-star transverse states, both sides (needed by the double-star average), with
@@ -249,7 +254,7 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   // (S_L < S_M < S_R: the e's are O(c_f); a degenerate side's D stays out of it)
   const T kL = degL ? T(1) : DL, kR = degR ? T(1) : DR;
   const T eLR = eL * eR, kLR = kL * kR;
-  const T inv = T(1) / (eLR * kLR);
+  const T inv = trcp(eLR * kLR);
   const T iLR = kLR * inv, eLRinv = eLR * inv;
   const T iL = eR * iLR, iR = eL * iLR;
   const T iDL = kR * eLRinv, iDR = kL * eLRinv;
@@ -327,7 +332,7 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   const bool dbl = left ? lt0(SsL) : ge0(SsR);
   if (dbl && !lt_nn(T(0.5) * bx2, Eps<T>::hllc * pTs)) {
     const T sgn = lt0(bx) ? T(-1) : T(1);
-    const T isum = T(1) / (sqL + sqR);
+    const T isum = trcp(sqL + sqR);
     const T v2 = (sqL * vsL + sqR * vsR + (b1sR - b1sL) * sgn) * isum;
     const T w2 = (sqL * wsL + sqR * wsR + (b2sR - b2sL) * sgn) * isum;
     const T sLR = sqL * sqR;
@@ -377,7 +382,7 @@ __device__ __forceinline__ void fast_speeds(const Side<T>& L, const Side<T>& R, 
   const T aR = gpR + bx2 + R.b1 * R.b1 + R.b2 * R.b2;
   const T dL = pos_part(aL * aL - T(4) * gpL * bx2);
   const T dR = pos_part(aR * aR - T(4) * gpR * bx2);
-  const T hLR = T(0.5) * (T(1) / (L.r * R.r));  // 0.5/rho_L, 0.5/rho_R from one reciprocal
+  const T hLR = T(0.5) * trcp(L.r * R.r);  // 0.5/rho_L, 0.5/rho_R from one reciprocal
   cfL = tsqrt((aL + tsqrt(dL)) * (R.r * hLR));
   cfR = tsqrt((aR + tsqrt(dR)) * (L.r * hLR));
 }
@@ -391,7 +396,7 @@ __device__ __forceinline__ T fast_speed_max(const Side<T>& L, const Side<T>& R, 
   const T aR = gpR + bx2 + R.b1 * R.b1 + R.b2 * R.b2;
   const T dL = pos_part(aL * aL - T(4) * gpL * bx2);
   const T dR = pos_part(aR * aR - T(4) * gpR * bx2);
-  const T hLR = T(0.5) * (T(1) / (L.r * R.r));
+  const T hLR = T(0.5) * trcp(L.r * R.r);
   return tsqrt(max_nn((aL + tsqrt(dL)) * (R.r * hLR), (aR + tsqrt(dR)) * (L.r * hLR)));
 }
 
@@ -427,7 +432,7 @@ __device__ __forceinline__ void hll(const Side<T>& L, const Side<T>& R, T bx, T 
 #pragma unroll
     for (int q = 0; q < 7; ++q) F[q] = FR[q];
   } else {
-    const T inv = T(1) / (SR - SL);
+    const T inv = trcp(SR - SL);
     const T sLR = SL * SR;
 #pragma unroll
     for (int q = 0; q < 7; ++q) F[q] = (SR * FL[q] - SL * FR[q] + sLR * (UR[q] - UL[q])) * inv;
@@ -449,7 +454,7 @@ __device__ __forceinline__ T outer_speed(int solver, const Side<T>& L, const Sid
     const T bx2x4 = T(4) * bx2;
     const T dL = pos_part(aL * aL - gpL * bx2x4);
     const T dR = pos_part(aR * aR - gpR * bx2x4);
-    const T hLR = T(0.5) * (T(1) / (L.r * R.r));
+    const T hLR = T(0.5) * trcp(L.r * R.r);
     cfm = tsqrt(max_nn((aL + tsqrt(dL)) * (R.r * hLR), (aR + tsqrt(dR)) * (L.r * hLR)));
   } else if (solver == 2) {
     cfm = fast_speed_max(L, R, bx, gamma);
