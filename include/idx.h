@@ -192,7 +192,7 @@ int idx_kernel_times(idx_sim* sim, int reps, double ms[6]);
  *                     copies (TMA) and marches it there; needs nx % 32 == 0 and n_d a
  *                     multiple of the tile length;
  *   0                 a direction that is not integrated.
- * With LimO3 (idx_solver.recon = 3) only 16 and 32 are used.
+ * With LimO3 (idx_solver.recon = 3) only 16, 32 and the staged y/z tiles 116, 132 are used.
  * Every shape does the same arithmetic per face; results differ between shapes at most by
  * rounding (the compiler may contract products into FMAs differently in each kernel
  * instantiation). */
@@ -200,7 +200,7 @@ int idx_sweep_shapes(const idx_sim* sim, int shapes[3]);
 
 /* Fix the sweep shapes (values as above; ignored for a direction that is not integrated)
  * instead of autotuning them.  IDX_EINVAL if a shape is unknown or does not fit the grid
- * (with LimO3, anything but 16 or 32).
+ * (with LimO3, anything but 16, 32, 116 or 132).
  * A measurement and testing aid, not part of the method; call it before stepping. */
 int idx_set_sweep_shapes(idx_sim* sim, const int shapes[3]);
 

@@ -450,8 +450,9 @@ __device__ __forceinline__ void flag_timeout(Ctrl* ctrl) {
 // One staged tile: tile index -> (x tile, D tile, coordinate along the third direction),
 // copies issued by thread 0 onto `bar`, bounded wait for the phase of parity `parity`,
 // then the march.  Returns false (the same on every thread of the block) if the copies
-// did not land in time; the caller then records the timeout and leaves.
-template <typename T, int D, int L>
+// did not land in time; the caller then records the timeout and leaves.  RECON as in
+// sweep_body (1 PLM, 3 LimO3).
+template <typename T, int D, int L, int RECON = 1>
 __device__ __forceinline__ bool tma_tile(const Geo& g, const CUtensorMap* tm_body,
                                          const CUtensorMap* tm_halo, const double* bface,
                                          const Ptr8<T>& F, int tile_index, T* tile,
@@ -500,7 +501,8 @@ __device__ __forceinline__ bool tma_tile(const Geo& g, const CUtensorMap* tm_bod
   const T gamma = geo_gamma<T>(g);
   const T gm1inv = geo_gm1inv<T>(g);
   auto ld = [&](int q, int row) { return tile[q * PLANE + row * 32 + lane]; };
-  // face f uses tile rows f .. f+3 (cells f-2 .. f+1); slope_m / slope0 hold half slopes
+  // face f uses tile rows f .. f+3 (cells f-2 .. f+1); slope_m: the change of cell f-1 at
+  // face f, slope0: the change of cell f at face f (subtracted), up0: at face f+1
   T wm[7], w0[7], wp[7], slope_m[7];
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
@@ -508,14 +510,24 @@ __device__ __forceinline__ bool tma_tile(const Geo& g, const CUtensorMap* tm_bod
     wm[q] = ld(q, f0 + 1);
     w0[q] = ld(q, f0 + 2);
     wp[q] = ld(q, f0 + 3);
-    slope_m[q] = vanleer_half(wm[q] - a, w0[q] - wm[q]);
+    slope_m[q] = RECON == 3 ? limo3_half(wm[q] - a, w0[q] - wm[q])
+                            : vanleer_half(wm[q] - a, w0[q] - wm[q]);
   }
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     Side<T> Ls, Rs;
-    T slope0[7];
+    T slope0[7], up0[7];
 #pragma unroll
-    for (int q = 0; q < 7; ++q) slope0[q] = vanleer_half(w0[q] - wm[q], wp[q] - w0[q]);
+    for (int q = 0; q < 7; ++q) {
+      const T dl = w0[q] - wm[q], dr = wp[q] - w0[q];
+      if constexpr (RECON == 3) {
+        slope0[q] = limo3_half(dr, dl);
+        up0[q] = limo3_half(dl, dr);
+      } else {
+        slope0[q] = vanleer_half(dl, dr);
+        up0[q] = slope0[q];
+      }
+    }
     Ls.r = wm[0] + slope_m[0]; Rs.r = w0[0] - slope0[0];
     Ls.u = wm[1] + slope_m[1]; Rs.u = w0[1] - slope0[1];
     Ls.v = wm[2] + slope_m[2]; Rs.v = w0[2] - slope0[2];
@@ -535,7 +547,7 @@ __device__ __forceinline__ bool tma_tile(const Geo& g, const CUtensorMap* tm_bod
         wm[q] = w0[q];
         w0[q] = wp[q];
         wp[q] = ld(q, f0 + k + 4);
-        slope_m[q] = slope0[q];
+        slope_m[q] = up0[q];
       }
     }
   }
@@ -549,7 +561,7 @@ __device__ __forceinline__ void tma_give_up(Ctrl* ctrl, uint64_t* bar, uint32_t 
   mbar_wait(bar, parity, kWaitNs);
 }
 
-template <typename T, int D, int L>
+template <typename T, int D, int L, int RECON = 1>
 __global__ void __launch_bounds__(8 * L, sizeof(T) == 4 ? 96 / L : 1)
     k_sweep_tma(Geo g, const __grid_constant__ CUtensorMap tm_body,
                 const __grid_constant__ CUtensorMap tm_halo, const double* bface, Ptr8<T> F,
@@ -563,7 +575,7 @@ __global__ void __launch_bounds__(8 * L, sizeof(T) == 4 ? 96 / L : 1)
     mbar_fence_init();
   }
   __syncthreads();
-  if (!tma_tile<T, D, L>(g, &tm_body, &tm_halo, bface, F, blockIdx.x, tile, &bar, 0))
+  if (!tma_tile<T, D, L, RECON>(g, &tm_body, &tm_halo, bface, F, blockIdx.x, tile, &bar, 0))
     tma_give_up(ctrl, &bar, 0);
 }
 
@@ -1171,13 +1183,13 @@ void launch_march(idx_sim* s, const Ptr8<T>& W, const double* bface, const Ptr8<
       g, cst(W), bface, F, s->ctrl, check_dt);
 }
 
-template <typename T, int D, int L>
+template <typename T, int D, int L, int RECON = 1>
 void launch_tma(idx_sim* s, const double* bface, const Ptr8<T>& F, int check_dt) {
   const Geo& g = s->geo;
   const int nO = g.n[D == 1 ? 2 : 1];
   const unsigned blocks = (unsigned)((g.n[0] / 32) * (g.n[D] / L) * nO);
   const size_t smem = 7 * (L + 4) * 32 * sizeof(T);
-  k_sweep_tma<T, D, L><<<blocks, 8 * L, smem, s->stream>>>(
+  k_sweep_tma<T, D, L, RECON><<<blocks, 8 * L, smem, s->stream>>>(
       g, s->tm_body[D][L == 32 ? 1 : 0], s->tm_halo[D], bface, F, s->ctrl, check_dt);
 }
 
@@ -1186,6 +1198,8 @@ void allow_tma_smem() {
   const int big = 7 * (32 + 4) * 32 * (int)sizeof(double);
   cudaFuncSetAttribute(k_sweep_tma<double, 1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_sweep_tma<double, 2, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_sweep_tma<double, 1, 32, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_sweep_tma<double, 2, 32, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaGetLastError();
 }
 
@@ -1207,7 +1221,11 @@ template <typename T> void launch_tma_x(idx_sim* s, const double* bface, const P
 template <typename T, int D>
 void launch_sweep_d(idx_sim* s, int shape, const Ptr8<T>& W, const double* bface,
                     const Ptr8<T>& F, int check_dt) {
-  if (s->geo.recon == 3) {  // LimO3: marching sweeps of 16 or 32 faces
+  if (s->geo.recon == 3) {  // LimO3: marching sweeps of 16 or 32 faces, staged y/z tiles
+    if (D != 0 && tma_shape_ok(s, D, shape)) {
+      if (shape == 116) { launch_tma<T, (D == 0 ? 1 : D), 16, 3>(s, bface, F, check_dt); return; }
+      if (shape == 132) { launch_tma<T, (D == 0 ? 1 : D), 32, 3>(s, bface, F, check_dt); return; }
+    }
     if (shape == 32) launch_march<T, D, 32, 3>(s, W, bface, F, check_dt);
     else launch_march<T, D, 16, 3>(s, W, bface, F, check_dt);
     return;
@@ -1267,7 +1285,8 @@ int tune_sweeps(idx_sim* s, const Ptr8<double>& U, const Ptr8<T>& W, Ptr8<T>* F)
     int best_shape = kSegDefault;
     for (int q = 0; q < 9; ++q) {
       const int shape = cand[q];
-      if (g.recon == 3 && shape != 16 && shape != 32) continue;  // LimO3: marching 16 / 32
+      // LimO3: marching 16 / 32 and the staged y/z tiles
+      if (g.recon == 3 && shape != 16 && shape != 32 && shape != 116 && shape != 132) continue;
       if (shape < 0 && d != 0) continue;
       if ((shape > 100 || shape == -2) && !tma_shape_ok(s, d, shape)) continue;
       if (shape > 0 && shape < 100 && shape > 2 * g.n[d]) continue;
@@ -2133,8 +2152,9 @@ int idx_set_sweep_shapes(idx_sim* s, const int shapes[3]) {
     v[d] = g.active[d] ? shapes[d] : 0;
     if (!g.active[d]) continue;
     const int x = v[d];
-    if (g.recon == 3) {  // LimO3 runs the marching sweeps of 16 or 32 faces only
-      if (x != 16 && x != 32) return IDX_EINVAL;
+    if (g.recon == 3) {  // LimO3: marching sweeps of 16 or 32 faces, staged y/z tiles
+      const bool ok = x == 16 || x == 32 || ((x == 116 || x == 132) && tma_shape_ok(s, d, x));
+      if (!ok) return IDX_EINVAL;
       continue;
     }
     const bool march = x == 2 || x == 4 || x == 8 || x == 16 || x == 32;

@@ -73,14 +73,33 @@ def test_segments_and_rk_orders(seg, rk_order):
     s.close()
 
 
-def test_only_marching_shapes_are_accepted():
+def test_shapes_accepted_with_limo3():
+    # marching 16 / 32 and the staged y/z tiles where the grid fits them (here it does not:
+    # ny = 8 is not a multiple of 16)
     ic = inputs.random_smooth((8, 8, 32), seed=1)
     s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, "fp64", recon="limo3")
-    for bad in ((-1, 16, 16), (16, 116, 16), (8, 16, 16), (-2, 16, 16)):
+    for bad in ((-1, 16, 16), (16, 116, 16), (8, 16, 16), (-2, 16, 16), (116, 16, 16)):
         with pytest.raises(idx.IdxError) as e:
             s.set_sweep_shapes(bad)
         assert e.value.code == idx.IDX_EINVAL
     s.set_sweep_shapes((32, 16, 32))
+    s.close()
+
+
+@pytest.mark.parametrize("precision,shapes", [("fp64", (16, 116, 132)), ("fp64", (32, 116, 116)),
+                                              ("fp32", (32, 116, 132))])
+def test_staged_tiles_match_oracle(precision, shapes):
+    # shapes are (x, y, z); grid nx, ny, nz = 64, 48, 32: y tiles of 16 rows (3 per pencil,
+    # at both periodic ends), z tiles of 16 (2) or 32 rows (one tile: both halos wrap)
+    ic = inputs.random_smooth((32, 48, 64), seed=33)
+    o, s = pair(ic, precision=precision, shapes=shapes)
+    assert s.sweep_shapes() == list(shapes)
+    for _ in range(3):
+        o.step()
+        s.step()
+    err = field_errors(s.get_state(), o.u)
+    print(precision, shapes, f"{max(err):.2e}")
+    assert max(err) <= (3 * TOL_STEP if precision == "fp64" else 3e-6), err
     s.close()
 
 
