@@ -2492,6 +2492,8 @@ struct idx_batch {
   int precision;
   cudaStream_t stream;
   bool own_stream;
+  cudaStream_t side = nullptr;  // the solo members' stages, forked from and joined to stream
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   int device;
   int sms;
   std::vector<idx_sim*> sims;
@@ -2678,10 +2680,10 @@ template <typename T> void launch_batch_sweep(idx_batch* b, int d, int stage, in
 
 // The stages of every solo member's own cycle (its RK order and induction form), on the
 // batch's stream (and into its graph).
-void launch_solo_stages(idx_batch* b) {
+void launch_solo_stages(idx_batch* b, cudaStream_t st) {
   for (idx_sim* s : b->solo) {
     const cudaStream_t own = s->stream;
-    s->stream = b->stream;
+    s->stream = st;
     const StagePlan p = stage_plan(s);
     for (int st = 0; st < p.n; ++st) {
       if (s->solver.precision == IDX_FP32_BULK) launch_stage<float>(s, p, st, s->Wf, s->Ff, s->Ef);
@@ -2691,11 +2693,21 @@ void launch_solo_stages(idx_batch* b) {
   }
 }
 
-// One batched cycle: every member's dt, both RK2 stages of the work-list members, each
-// solo member's own stages, then every member's time and speeds.
+// One batched cycle: every member's dt, then -- side by side -- both RK2 stages of the
+// work-list members on the batch stream and each solo member's own stages on the side
+// stream (they touch disjoint buffers and need only the dt), then every member's time and
+// speeds.  The solo kernels fill the SMs that the work-list kernels leave idle in their
+// tails; in the captured graph the fork and join are two edges.
 template <typename T> void launch_batch_cycle(idx_batch* b) {
   const BatchDev<T>* B = (const BatchDev<T>*)b->header;
   kb_begin<T><<<b->sms, kThreads, 0, b->stream>>>(B);
+  const bool fork = !b->solo.empty() && b->side;
+  if (fork) {
+    cudaEventRecord(b->fork_ev, b->stream);
+    cudaStreamWaitEvent(b->side, b->fork_ev, 0);
+    launch_solo_stages(b, b->side);
+    cudaEventRecord(b->join_ev, b->side);
+  }
   for (int st = 0; st < 2; ++st) {
     kb_prims<T><<<b->grid_cell, kThreads, 0, b->stream>>>(B, st, 1);
     for (int d = 0; d < 3; ++d) launch_batch_sweep<T>(b, d, st, 1);
@@ -2703,7 +2715,8 @@ template <typename T> void launch_batch_cycle(idx_batch* b) {
     if (st == 0) kb_update<T, false><<<b->grid_cell, kThreads, 0, b->stream>>>(B);
     else kb_update<T, true><<<b->grid_cell, kThreads, 0, b->stream>>>(B);
   }
-  launch_solo_stages(b);
+  if (fork) cudaStreamWaitEvent(b->stream, b->join_ev, 0);
+  else launch_solo_stages(b, b->stream);
   kb_end<T><<<b->sms, kThreads, 0, b->stream>>>(B);
 }
 
@@ -2861,6 +2874,10 @@ int idx_batch_create(int precision, void* stream, idx_batch** out) {
       if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) rc = IDX_ECUDA;
     }
   }
+  if (rc == IDX_OK && (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming) != cudaSuccess))
+    rc = IDX_ECUDA;
   if (rc == IDX_OK && cudaMalloc(&b->header, 256) != cudaSuccess) rc = IDX_ENOMEM;
   if (rc == IDX_OK) rc = precision == IDX_FP32_BULK ? batch_occupancy<float>(b) : batch_occupancy<double>(b);
   if (rc != IDX_OK) {
@@ -2874,12 +2891,16 @@ int idx_batch_create(int precision, void* stream, idx_batch** out) {
 void idx_batch_destroy(idx_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->side) cudaStreamSynchronize(b->side);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->lists) cudaFree(b->lists);
   if (b->header) cudaFree(b->header);
   if (b->host_gather) cudaFreeHost(b->host_gather);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  if (b->join_ev) cudaEventDestroy(b->join_ev);
+  if (b->side) cudaStreamDestroy(b->side);
   delete b;
 }
 
