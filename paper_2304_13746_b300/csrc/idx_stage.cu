@@ -1108,6 +1108,9 @@ struct idx_sim {
   bool own_stream;
   int device;
   int nsm = 0;          // SMs of the device (0: not known, full-size blocks)
+  // small grids: the y and z sweeps of a stage run on two side streams beside the x sweep
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t fork_ev = nullptr, join_ev[2] = {nullptr, nullptr};
   void* mem;            // single device allocation
   size_t mem_bytes;
   Ptr8<double> U, U1;   // state and first-stage result (FP64)
@@ -1310,12 +1313,29 @@ int tune_sweeps(idx_sim* s, const Ptr8<double>& U, const Ptr8<T>& W, Ptr8<T>* F)
 
 template <typename T>
 void launch_fluxes(idx_sim* s, const Ptr8<double>& Uin, const Ptr8<T>& W, Ptr8<T>* F,
-                   int check_dt) {
+                   int check_dt, bool fork = false) {
   const Geo& g = s->geo;
   k_prims<T><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), W, cell_emf<T>(s),
                                                               s->ctrl, check_dt);
-  for (int d = 0; d < 3; ++d)
-    if (g.active[d]) launch_sweep<T>(s, d, W, Uin.f[5 + d], F[d], check_dt);
+  if (!(fork && s->side[0])) {
+    for (int d = 0; d < 3; ++d)
+      if (g.active[d]) launch_sweep<T>(s, d, W, Uin.f[5 + d], F[d], check_dt);
+    return;
+  }
+  // the three sweeps read the primitives and write their own fluxes: y and z on the side
+  // streams, forked after the primitives and joined before the EMFs
+  const cudaStream_t main = s->stream;
+  cudaEventRecord(s->fork_ev, main);
+  if (g.active[0]) launch_sweep<T>(s, 0, W, Uin.f[5], F[0], check_dt);
+  for (int d = 1; d < 3; ++d) {
+    if (!g.active[d]) continue;
+    cudaStreamWaitEvent(s->side[d - 1], s->fork_ev, 0);
+    s->stream = s->side[d - 1];
+    launch_sweep<T>(s, d, W, Uin.f[5 + d], F[d], check_dt);
+    s->stream = main;
+    cudaEventRecord(s->join_ev[d - 1], s->side[d - 1]);
+    cudaStreamWaitEvent(main, s->join_ev[d - 1], 0);
+  }
 }
 
 // The stages of one cycle (Sec. 2.7, Table 1): input, output and weights (w, w0) of
@@ -1418,7 +1438,7 @@ void launch_fill_ghosts(idx_sim* s, const Ptr8<double>& U) {
 template <typename T>
 void launch_stage(idx_sim* s, const StagePlan& p, int st, const Ptr8<T>& W, Ptr8<T>* F, T** E) {
   launch_fill_ghosts(s, *p.in[st]);
-  launch_fluxes<T>(s, *p.in[st], W, F, 1);
+  launch_fluxes<T>(s, *p.in[st], W, F, 1, true);
   launch_emf<T>(s, p, st, W, F, E);
   launch_update<T>(s, p, st, F, E);
 }
@@ -1477,10 +1497,21 @@ int tune_once(idx_sim* s) {
   return IDX_OK;
 }
 
+// Grids below this many cells run the y and z sweeps beside the x sweep (launch_fluxes):
+// each sweep alone leaves most of the GPU idle there.
+constexpr int kForkMaxCells = 1 << 21;
+
 int build_graph(idx_sim* s) {
   if (s->exec) return IDX_OK;
   int trc = tune_once(s);
   if (trc != IDX_OK) return trc;
+  if (s->geo.ncell < kForkMaxCells && !s->side[0]) {
+    for (int k = 0; k < 2; ++k) {
+      IDX_TRY(cudaStreamCreateWithFlags(&s->side[k], cudaStreamNonBlocking));
+      IDX_TRY(cudaEventCreateWithFlags(&s->join_ev[k], cudaEventDisableTiming));
+    }
+    IDX_TRY(cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming));
+  }
   IDX_TRY(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
   launch_cycle(s);
   cudaError_t e = cudaStreamEndCapture(s->stream, &s->graph);
@@ -1789,6 +1820,11 @@ void idx_destroy(idx_sim* s) {
     cudaStreamSynchronize(s->stream);
   }
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  for (int k = 0; k < 2; ++k) {
+    if (s->side[k]) cudaStreamDestroy(s->side[k]);
+    if (s->join_ev[k]) cudaEventDestroy(s->join_ev[k]);
+  }
+  if (s->fork_ev) cudaEventDestroy(s->fork_ev);
   delete s;
 }
 
