@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -1108,6 +1109,9 @@ struct idx_sim {
   bool own_stream;
   int device;
   int nsm = 0;          // SMs of the device (0: not known, full-size blocks)
+  // unique per sim in the process: a destroyed sim's host address can come back for a new
+  // one, so captured graphs that hold a sim's buffers are matched by serial, not address
+  uint64_t serial = 0;
   // small grids: the y and z sweeps of a stage run on two side streams beside the x sweep
   cudaStream_t side[2] = {nullptr, nullptr};
   cudaEvent_t fork_ev = nullptr, join_ev[2] = {nullptr, nullptr};
@@ -1721,6 +1725,10 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
   s->solver = *solver;
   s->last_bad = -1;
   if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return IDX_ECUDA; }
+  {
+    static std::atomic<uint64_t> next_serial{1};
+    s->serial = next_serial.fetch_add(1);
+  }
   if (cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess)
     s->nsm = 0;
   for (int d = 0; d < 3; ++d) s->bc[d] = bc[d];
@@ -2546,7 +2554,7 @@ struct idx_batch {
   int graph_shape[3], graph_fallback[3];
   int grid_tma[2];     // persistent blocks of the staged sweep, L = 16 / 32
   std::vector<idx_sim*> solo;        // members stepped by their own kernels in the cycle
-  std::vector<idx_sim*> graph_solo;  // the solo members the captured cycle was built with
+  std::vector<uint64_t> graph_solo;  // serials of the solo members the captured cycle holds
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   int grid_cell, grid_sweep;
@@ -2830,7 +2838,9 @@ template <typename T> int batch_prepare(idx_batch* b) {
     const int trc = tune_once(s);
     if (trc != IDX_OK) return trc;
   }
-  bool same = b->exec != nullptr && b->graph_solo == b->solo;
+  std::vector<uint64_t> solo_serials;
+  for (const idx_sim* s : b->solo) solo_serials.push_back(s->serial);
+  bool same = b->exec != nullptr && b->graph_solo == solo_serials;
   for (int d = 0; d < 3; ++d)
     same = same && b->graph_shape[d] == b->shape[d] && b->graph_fallback[d] == b->fallback[d];
   if (same) return IDX_OK;
@@ -2844,7 +2854,7 @@ template <typename T> int batch_prepare(idx_batch* b) {
     b->graph_shape[d] = b->shape[d];
     b->graph_fallback[d] = b->fallback[d];
   }
-  b->graph_solo = b->solo;
+  b->graph_solo = solo_serials;
   return IDX_OK;
 }
 

@@ -213,3 +213,45 @@ def test_solo_members_match_alone(precision):
         b.remove(s)
         s.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_solo_member_replaced_at_a_reused_address(precision):
+    # A finished solo member (>= 2^18 cells: its own kernels, captured into the batch's
+    # graph) is removed and destroyed, and a new one of the same size joins; the allocator
+    # usually hands the new sim the old one's host address.  The batch must capture its
+    # cycle again for the new member's buffers: each newcomer's result equals its run alone.
+    n, t_end = 64, 0.004
+    ref = {}
+    for seed in (11, 12, 13):
+        ic = inputs.turbulent_box(n, seed=seed)
+        s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, precision)
+        s.set_primitive(ic.prim)
+        s.advance(t_end)
+        ref[seed] = s.get_state()
+        s.close()
+    small = inputs.random_smooth((8, 8, 8), seed=5)
+    b = idx.Batch(precision)
+    keep = idx.Sim(small.shape, small.lengths, small.gamma, 0.4, precision)
+    keep.set_primitive(small.prim)
+    b.add(keep, 1e9)               # a work-list member that stays throughout
+    handles = []
+    for seed in (11, 12, 13):
+        ic = inputs.turbulent_box(n, seed=seed)
+        s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, precision)
+        s.set_primitive(ic.prim)
+        handles.append(s.handle)
+        b.add(s, t_end)
+        for _ in range(1000):
+            b.step(4)
+            fin, _ = b.poll()
+            if any(f is s for f in fin):
+                break
+        b.remove(s)
+        assert s.time()[0] == t_end
+        assert scaled_error(s.get_state(), ref[seed]) <= TOL[precision]
+        s.close()
+    b.remove(keep)
+    keep.close()
+    b.close()
+    print("handles", handles)
