@@ -135,3 +135,38 @@ def test_limo3_first_dt_and_conservation():
     div = ((np.roll(bx, -1, 2) - bx) / dx + (np.roll(by, -1, 1) - by) / dy +
            (np.roll(bz, -1, 0) - bz) / dz)
     assert float(np.max(np.abs(div))) < 1e-11
+
+
+def test_scheme_entry_points_keep_plm_bitwise_and_reject_bad_codes():
+    # every oracle cycle now goes through ora_cycle_scheme; with recon = PLM it must give
+    # the bits of the solver/RK entry point it replaced, and unknown codes are refused
+    import ctypes
+    ic = inputs.random_smooth((6, 5, 7), seed=3)
+    cons = oracle.cons_from_prims(ic.prim, ic.lengths, ic.gamma)
+    L = oracle.lib()
+    g = ctypes.byref(oracle._grid(cons[0].shape, ic.lengths))
+    for solver, rk in (("hlld", 2), ("hll", 3), ("rusanov", 2)):
+        a = [c.copy() for c in cons]
+        b = [c.copy() for c in cons]
+        inv0 = oracle.speed_pass(cons, ic.lengths, ic.gamma)
+        ia, ib = ctypes.c_double(inv0), ctypes.c_double(inv0)
+        da, db = ctypes.c_double(), ctypes.c_double()
+        bad = ctypes.c_long(-1)
+        assert L.ora_cycle_rk(g, ic.gamma, 0.4, oracle.SOLVERS[solver], rk, oracle._ptrs(a),
+                              ctypes.byref(ia), 1e9, ctypes.byref(da), ctypes.byref(bad)) == 0
+        assert L.ora_cycle_scheme(g, ic.gamma, 0.4, 1, oracle.SOLVERS[solver], rk,
+                                  oracle._ptrs(b), None, None, ctypes.byref(ib), 1e9,
+                                  ctypes.byref(db), ctypes.byref(bad)) == 0
+        assert da.value == db.value and ia.value == ib.value
+        for f in range(8):
+            assert np.array_equal(a[f], b[f])
+    u = [c.copy() for c in cons]
+    inv = ctypes.c_double(1.0)
+    dt = ctypes.c_double()
+    bad = ctypes.c_long(-1)
+    for recon in (0, 2, 4):
+        assert L.ora_cycle_scheme(g, ic.gamma, 0.4, recon, 4, 2, oracle._ptrs(u), None, None,
+                                  ctypes.byref(inv), 1e9, ctypes.byref(dt),
+                                  ctypes.byref(bad)) == oracle.EINVAL
+        assert L.ora_speed_pass_recon(g, ic.gamma, recon, oracle._ptrs(u), ctypes.byref(inv),
+                                      ctypes.byref(bad)) == oracle.EINVAL
