@@ -65,6 +65,12 @@ def lib():
         L.ora_cycle_rk.argtypes = [G, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                    _P8, _D, ctypes.c_double, _D, ctypes.POINTER(ctypes.c_long)]
         L.ora_count_faces.argtypes = [G, ctypes.c_double, _P8, ctypes.c_int, _D, _D]
+        L.ora_count_cycle_parts.argtypes = [G, ctypes.c_double, ctypes.c_double, _P8,
+                                            ctypes.c_double, _D]
+        L.ora_count_vanleer.argtypes = [ctypes.c_double] * 3 + [_D]
+        L.ora_count_energy_flux.argtypes = [_D, ctypes.c_double, ctypes.c_double, _D, _D]
+        L.ora_count_hlld.argtypes = [_D, _D, ctypes.c_double, ctypes.c_double, _D]
+        L.ora_count_emf_ec.argtypes = [_D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_double, _D]
         L.ora_b_from_potential.argtypes = [G, _P3, _D, _P3]
         L.ora_cycle_vp.argtypes = [G, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                    _P8, _P3, _P3, _D, ctypes.c_double, _D,
@@ -314,6 +320,80 @@ def count_faces(cons, lengths, gamma, d):
                                  int(d), a, b))
     keys = ("add", "mul", "div", "sqrt", "cmp")
     return dict(zip(keys, a[:])), dict(zip(keys, b[:]))
+
+
+OPS = ("add", "mul", "div", "sqrt", "cmp")
+# parts of the method the op counts are split into (ORA_PART_* of oracle.h)
+PARTS = ("prims", "slope", "face", "riemann", "speed", "invdt", "cell_emf", "edge", "diff",
+         "accum", "combine", "dt", "potential")
+
+
+def count_cycle_parts(cons, lengths, gamma, cfl, inv_dt=None):
+    """Per cell-update op counts of one RK2 cycle split by part: {part: {op: count}}.
+    inv_dt: the inverse CFL time the cycle starts from (default: the speed pass's)."""
+    cons = [_c(a) for a in cons]
+    inv = speed_pass(cons, lengths, gamma) if inv_dt is None else float(inv_dt)
+    out = (ctypes.c_double * (5 * len(PARTS)))()
+    _check(lib().ora_count_cycle_parts(ctypes.byref(_grid(cons[0].shape, lengths)), gamma, cfl,
+                                       _ptrs(cons), inv, out))
+    return {p: dict(zip(OPS, out[5 * q:5 * q + 5])) for q, p in enumerate(PARTS)}
+
+
+def flops(counts):
+    """Floating-point operations of an op-count dict: add + mul + div + sqrt (compares and
+    sign operations are not flops; the oracle has no fused operations)."""
+    return counts["add"] + counts["mul"] + counts["div"] + counts["sqrt"]
+
+
+def algorithmic_flops(parts):
+    """Flops per cell-update with each piece of the method's work counted once: the oracle
+    forms each cell's van Leer slope for both faces that use it and each cell-centre EMF at
+    the four edges around it, so half of the slope part and three quarters of the
+    cell-centre EMF part are repeats."""
+    total = sum(flops(c) for c in parts.values())
+    return total - 0.5 * flops(parts["slope"]) - 0.75 * flops(parts["cell_emf"])
+
+
+def fp64_island_flops(parts):
+    """Flops per cell-update that the FP32-bulk variant keeps in FP64: the primitive
+    recovery (energy to pressure), the accumulation into the state and the RK combine."""
+    return flops(parts["prims"]) + flops(parts["accum"]) + flops(parts["combine"])
+
+
+def _counts5(arr):
+    return dict(zip(OPS, arr[:]))
+
+
+def count_vanleer(wm, w0, wp):
+    out = (ctypes.c_double * 5)()
+    _check(lib().ora_count_vanleer(float(wm), float(w0), float(wp), out))
+    return _counts5(out)
+
+
+def count_energy_flux(w, bn, gamma):
+    """(counts of the total energy, counts of the physical flux) of one face state w."""
+    w = (ctypes.c_double * 7)(*[float(x) for x in w])
+    a, b = (ctypes.c_double * 5)(), (ctypes.c_double * 5)()
+    _check(lib().ora_count_energy_flux(w, float(bn), float(gamma), a, b))
+    return _counts5(a), _counts5(b)
+
+
+def count_hlld(wL, wR, bn, gamma):
+    a = (ctypes.c_double * 7)(*[float(x) for x in wL])
+    b = (ctypes.c_double * 7)(*[float(x) for x in wR])
+    out = (ctypes.c_double * 5)()
+    _check(lib().ora_count_hlld(a, b, float(bn), float(gamma), out))
+    return _counts5(out)
+
+
+def count_emf_ec(X, Y, C, Fa, Fb, da, db):
+    arr = [(ctypes.c_double * 2)(*[float(x) for x in v]) for v in (X, Y)]
+    c = (ctypes.c_double * 4)(C[0][0], C[0][1], C[1][0], C[1][1])
+    fa = (ctypes.c_double * 2)(*[float(x) for x in Fa])
+    fb = (ctypes.c_double * 2)(*[float(x) for x in Fb])
+    out = (ctypes.c_double * 5)()
+    _check(lib().ora_count_emf_ec(arr[0], arr[1], c, fa, fb, float(da), float(db), out))
+    return _counts5(out)
 
 
 def threads():

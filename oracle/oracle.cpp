@@ -29,29 +29,40 @@
 namespace {
 
 // ---------------------------------------------------------------------------
-// Operation-counting scalar (single-threaded use only).
+// Operation-counting scalar (single-threaded use only).  Each add/sub, mul, div and
+// square root of a Counted value is tallied, and so is each comparison; negation and
+// absolute value are sign operations and are not.  The tally is kept per part of the
+// method (ORA_PART_* of oracle.h), so that work this plain code repeats for clarity --
+// each cell's van Leer slope is formed for both faces that use it, each cell-centre EMF
+// for the four edges around it -- can be told apart from the method's own work.
 // ---------------------------------------------------------------------------
 struct Tally {
   double add = 0, mul = 0, div = 0, sqrt = 0, cmp = 0;
 };
-Tally g_tally;
+Tally g_parts[ORA_NUM_PARTS];
+int g_part = ORA_PART_DT;
+inline Tally& tally() { return g_parts[g_part]; }
+void reset_tally() {
+  for (int p = 0; p < ORA_NUM_PARTS; ++p) g_parts[p] = Tally();
+  g_part = ORA_PART_DT;
+}
 
 struct Counted {
   double v;
   Counted() : v(0.0) {}
   Counted(double x) : v(x) {}  // NOLINT: implicit on purpose, constants enter as doubles
 };
-inline Counted operator+(Counted a, Counted b) { g_tally.add += 1; return Counted(a.v + b.v); }
-inline Counted operator-(Counted a, Counted b) { g_tally.add += 1; return Counted(a.v - b.v); }
-inline Counted operator*(Counted a, Counted b) { g_tally.mul += 1; return Counted(a.v * b.v); }
-inline Counted operator/(Counted a, Counted b) { g_tally.div += 1; return Counted(a.v / b.v); }
+inline Counted operator+(Counted a, Counted b) { tally().add += 1; return Counted(a.v + b.v); }
+inline Counted operator-(Counted a, Counted b) { tally().add += 1; return Counted(a.v - b.v); }
+inline Counted operator*(Counted a, Counted b) { tally().mul += 1; return Counted(a.v * b.v); }
+inline Counted operator/(Counted a, Counted b) { tally().div += 1; return Counted(a.v / b.v); }
 inline Counted operator-(Counted a) { return Counted(-a.v); }
-inline bool operator<(Counted a, Counted b) { g_tally.cmp += 1; return a.v < b.v; }
-inline bool operator>(Counted a, Counted b) { g_tally.cmp += 1; return a.v > b.v; }
-inline bool operator<=(Counted a, Counted b) { g_tally.cmp += 1; return a.v <= b.v; }
-inline bool operator>=(Counted a, Counted b) { g_tally.cmp += 1; return a.v >= b.v; }
-inline bool operator==(Counted a, Counted b) { g_tally.cmp += 1; return a.v == b.v; }
-inline Counted sq_root(Counted a) { g_tally.sqrt += 1; return Counted(std::sqrt(a.v)); }
+inline bool operator<(Counted a, Counted b) { tally().cmp += 1; return a.v < b.v; }
+inline bool operator>(Counted a, Counted b) { tally().cmp += 1; return a.v > b.v; }
+inline bool operator<=(Counted a, Counted b) { tally().cmp += 1; return a.v <= b.v; }
+inline bool operator>=(Counted a, Counted b) { tally().cmp += 1; return a.v >= b.v; }
+inline bool operator==(Counted a, Counted b) { tally().cmp += 1; return a.v == b.v; }
+inline Counted sq_root(Counted a) { tally().sqrt += 1; return Counted(std::sqrt(a.v)); }
 inline Counted absval(Counted a) { return Counted(std::fabs(a.v)); }
 inline double value(Counted a) { return a.v; }
 
@@ -60,6 +71,11 @@ inline double absval(double a) { return std::fabs(a); }
 inline double value(double a) { return a; }
 
 template <class R> constexpr bool kPar = std::is_same<R, double>::value;
+
+// Sets the part that counted operations are tallied under (no effect for plain doubles).
+template <class R> inline void in_part(int part) {
+  if constexpr (std::is_same<R, Counted>::value) g_part = part;
+}
 
 template <class R> inline R rmax(R a, R b) { return (a < b) ? b : a; }
 template <class R> inline R rmin(R a, R b) { return (b < a) ? b : a; }
@@ -117,6 +133,7 @@ enum { PR = 4 };  // pressure slot in the primitive set (rho, vx, vy, vz, P, Bcx
 // ---------------------------------------------------------------------------
 template <class R>
 int prims(const Grid& G, double gamma, const std::vector<R>* U, std::vector<R>* W, long* bad) {
+  in_part<R>(ORA_PART_PRIMS);
   long first_bad = G.ncell;
 #pragma omp parallel for reduction(min : first_bad) if (kPar<R>)
   for (int k = 0; k < G.n[2]; ++k)
@@ -488,10 +505,13 @@ void face_state(const Grid& G, const std::vector<R>* W, int i, int j, int k, int
   for (int q = 0; q < 7; ++q) {
     const std::vector<R>& f = W[var[q]];
     if (recon == 3) {
+      in_part<R>(ORA_PART_FACE);
       out[q] = (side < 0) ? limo3_face(f[pm], f[p0], f[pp]) : limo3_face(f[pp], f[p0], f[pm]);
       continue;
     }
+    in_part<R>(ORA_PART_SLOPE);
     const R slope = vanleer(f[pm], f[p0], f[pp]);
+    in_part<R>(ORA_PART_FACE);
     out[q] = (side < 0) ? f[p0] + R(0.5) * slope : f[p0] - R(0.5) * slope;
   }
   s->rho = out[0]; s->u = out[1]; s->v = out[2]; s->w = out[3]; s->P = out[4];
@@ -513,6 +533,7 @@ void face_fluxes(const Grid& G, double gamma, const std::vector<R>* U, const std
         face_state(G, W, i, j, k, d, +1, &Rr, recon);
         const R bn = U[5 + d][p];
         R f[7], sL, sR;
+        in_part<R>(ORA_PART_RIEMANN);
         riemann(solver, L, Rr, bn, gamma, f, &sL, &sR);
         F[RHO][p] = f[0];
         F[1 + d][p] = f[1];
@@ -522,6 +543,7 @@ void face_fluxes(const Grid& G, double gamma, const std::vector<R>* U, const std
         F[5 + d][p] = R(0.0);
         F[5 + t1][p] = f[5];
         F[5 + t2][p] = f[6];
+        in_part<R>(ORA_PART_SPEED);
         cface[p] = rmax(absval(sL), absval(sR));
       }
 }
@@ -550,6 +572,7 @@ void face_speeds(const Grid& G, double gamma, const std::vector<R>* U, const std
 // Inverse CFL time of Eq. (10) with no diffusion: max over cells of
 // sum over integrated directions of max(c at the two faces) / dl.
 template <class R> R inverse_dt(const Grid& G, const std::vector<R>* cface) {
+  in_part<R>(ORA_PART_INVDT);
   std::vector<R> plane_max(G.n[2], R(0.0));
 #pragma omp parallel for if (kPar<R>)
   for (int k = 0; k < G.n[2]; ++k)
@@ -592,12 +615,14 @@ void edge_emf(const Grid& G, const std::vector<R>* W, const std::vector<R>* F /*
           Y[c] = F[8 * b + 5 + a][q];
           Fb[c] = F[8 * b + RHO][q];
         }
+        in_part<R>(ORA_PART_CELL_EMF);
         for (int c = 0; c < 2; ++c)
           for (int r = 0; r < 2; ++r) {
             // cell-centre EMF_e = -(v x B)_e = -(v_a B_b - v_b B_a)
             const long q = shift2(G, i, j, k, a, -c, b, -r);
             C[c][r] = -(W[1 + a][q] * W[5 + b][q] - W[1 + b][q] * W[5 + a][q]);
           }
+        in_part<R>(ORA_PART_EDGE);
         Ee[at(G, i, j, k)] = emf_ec(X, Y, C, Fa, Fb, R(G.dl[a]), R(G.dl[b]));
       }
 }
@@ -690,16 +715,19 @@ int stage(const Grid& G, double gamma, R dt, const std::vector<R>* Uin, const st
         const long p = at(G, i, j, k);
         // cell-averaged conserved variables: U* = U - dt sum_d dF_d / dl_d
         for (int f = 0; f < 5; ++f) {
+          in_part<R>(ORA_PART_DIFF);
           R div = R(0.0);
           for (int d = 0; d < 3; ++d) {
             if (!G.active[d]) continue;
             div = div + (F[8 * d + f][shift(G, i, j, k, d, 1)] - F[8 * d + f][p]) / R(G.dl[d]);
           }
+          in_part<R>(ORA_PART_ACCUM);
           Us[f][p] = Uin[f][p] - dt * div;
         }
         // face-centred field: B_d* = B_d - dt (curl E)_d (Eq. 6, Stokes on the face)
         for (int d = 0; d < 3; ++d) {
           const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+          in_part<R>(ORA_PART_DIFF);
           R curl = R(0.0);
           if (G.active[d]) {
             if (G.active[t1])
@@ -715,10 +743,12 @@ int stage(const Grid& G, double gamma, R dt, const std::vector<R>* Uin, const st
                                 R(G.dl[a]);
             }
           }
+          in_part<R>(ORA_PART_ACCUM);
           Us[5 + d][p] = Uin[5 + d][p] - dt * curl;
         }
       }
 
+  in_part<R>(ORA_PART_COMBINE);
   for (int f = 0; f < 8; ++f)
     for (long p = 0; p < N; ++p) {
       if (w0 == 0.0 && w == 1.0)
@@ -727,6 +757,7 @@ int stage(const Grid& G, double gamma, R dt, const std::vector<R>* Uin, const st
         Uout[f][p] = R(w) * Us[f][p] + R(w0) * U0[f][p];
     }
   if (Ain == nullptr) return ORA_OK;
+  in_part<R>(ORA_PART_POTENTIAL);
 
   // Vector-potential form (Eqs. 7-8): A* = A - dt E, A_out = w A* + w0 A_0, and the
   // face field is recomputed from A_out instead of being stepped itself.
@@ -750,6 +781,7 @@ template <class R>
 int cycle(const Grid& G, double gamma, double cfl, std::vector<R>* U, R* inv_dt, double dt_max,
           R* dt_taken, long* bad, int solver = 4, int rk_order = 2, std::vector<R>* A = nullptr,
           const std::vector<R>* Bref = nullptr, int recon = 1) {
+  in_part<R>(ORA_PART_DT);
   R dt = R(cfl) / *inv_dt;
   if (value(dt) > dt_max) dt = R(dt_max);
   const long N = G.ncell;
@@ -772,6 +804,7 @@ int cycle(const Grid& G, double gamma, double cfl, std::vector<R>* U, R* inv_dt,
                          next, &inv_s, bad, solver, A ? prevA : nullptr,
                          (A && st > 0) ? A : nullptr, A ? nextA : nullptr, Bref, recon);
     if (rc != ORA_OK) return rc;
+    in_part<R>(ORA_PART_DT);
     inv = rmax(inv, inv_s);
     for (int f = 0; f < 8; ++f) prev[f].swap(next[f]);
     if (A)
@@ -1075,8 +1108,8 @@ int ora_cycle_scheme(const ora_grid* g, double gamma, double cfl, int recon, int
   return ORA_OK;
 }
 
-int ora_count_cycle(const ora_grid* g, double gamma, double cfl, const double* const u[8],
-                    double inv_dt, double counts[5]) {
+int ora_count_cycle_parts(const ora_grid* g, double gamma, double cfl, const double* const u[8],
+                          double inv_dt, double counts[5 * ORA_NUM_PARTS]) {
   if (!grid_ok(g) || !(gamma > 1.0) || !ptrs_ok((const void* const*)u) || !counts ||
       !(inv_dt > 0.0))
     return ORA_EINVAL;
@@ -1086,18 +1119,99 @@ int ora_count_cycle(const ora_grid* g, double gamma, double cfl, const double* c
     U[f].resize(G.ncell);
     for (long p = 0; p < G.ncell; ++p) U[f][p] = Counted(u[f][p]);
   }
-  g_tally = Tally();
+  reset_tally();
   Counted inv(inv_dt), dt;
   long bad = -1;
   const int st =
       cycle(G, gamma, cfl, U, &inv, std::numeric_limits<double>::infinity(), &dt, &bad);
   const double n = (double)G.ncell;
-  counts[0] = g_tally.add / n;
-  counts[1] = g_tally.mul / n;
-  counts[2] = g_tally.div / n;
-  counts[3] = g_tally.sqrt / n;
-  counts[4] = g_tally.cmp / n;
+  for (int q = 0; q < ORA_NUM_PARTS; ++q) {
+    counts[5 * q + 0] = g_parts[q].add / n;
+    counts[5 * q + 1] = g_parts[q].mul / n;
+    counts[5 * q + 2] = g_parts[q].div / n;
+    counts[5 * q + 3] = g_parts[q].sqrt / n;
+    counts[5 * q + 4] = g_parts[q].cmp / n;
+  }
+  reset_tally();
   return st;
+}
+
+int ora_count_cycle(const ora_grid* g, double gamma, double cfl, const double* const u[8],
+                    double inv_dt, double counts[5]) {
+  if (!counts) return ORA_EINVAL;
+  double parts[5 * ORA_NUM_PARTS];
+  const int st = ora_count_cycle_parts(g, gamma, cfl, u, inv_dt, parts);
+  if (st == ORA_EINVAL) return st;
+  for (int k = 0; k < 5; ++k) {
+    counts[k] = 0.0;
+    for (int q = 0; q < ORA_NUM_PARTS; ++q) counts[k] += parts[5 * q + k];
+  }
+  return st;
+}
+
+namespace {
+// The tally of everything counted since the last reset, into counts[5].
+void total_tally(double counts[5]) {
+  for (int k = 0; k < 5; ++k) counts[k] = 0.0;
+  for (int q = 0; q < ORA_NUM_PARTS; ++q) {
+    counts[0] += g_parts[q].add; counts[1] += g_parts[q].mul; counts[2] += g_parts[q].div;
+    counts[3] += g_parts[q].sqrt; counts[4] += g_parts[q].cmp;
+  }
+}
+State<Counted> counted_state(const double w[7]) {
+  return State<Counted>{w[0], w[1], w[2], w[3], w[4], w[5], w[6]};
+}
+}  // namespace
+
+int ora_count_vanleer(double wm, double w0, double wp, double counts[5]) {
+  if (!counts) return ORA_EINVAL;
+  reset_tally();
+  vanleer<Counted>(wm, w0, wp);
+  total_tally(counts);
+  reset_tally();
+  return ORA_OK;
+}
+
+int ora_count_energy_flux(const double w[7], double bn, double gamma, double counts_energy[5],
+                          double counts_flux[5]) {
+  if (!w || !counts_energy || !counts_flux || !(gamma > 1.0)) return ORA_EINVAL;
+  const State<Counted> s = counted_state(w);
+  reset_tally();
+  const Counted E = total_energy(s, Counted(bn), gamma);
+  total_tally(counts_energy);
+  reset_tally();
+  Counted F[7];
+  physical_flux(s, Counted(bn), Counted(value(E)), F);
+  total_tally(counts_flux);
+  reset_tally();
+  return ORA_OK;
+}
+
+int ora_count_hlld(const double wL[7], const double wR[7], double bn, double gamma,
+                   double counts[5]) {
+  if (!wL || !wR || !counts || !(gamma > 1.0)) return ORA_EINVAL;
+  if (!(wL[0] > 0) || !(wR[0] > 0) || !(wL[4] > 0) || !(wR[4] > 0)) return ORA_ENONPHYS;
+  const State<Counted> L = counted_state(wL), R = counted_state(wR);
+  reset_tally();
+  Counted F[7], sL, sR;
+  hlld(L, R, Counted(bn), gamma, F, &sL, &sR);
+  total_tally(counts);
+  reset_tally();
+  return ORA_OK;
+}
+
+int ora_count_emf_ec(const double X[2], const double Y[2], const double C[2][2],
+                     const double Fa[2], const double Fb[2], double da, double db,
+                     double counts[5]) {
+  if (!X || !Y || !C || !Fa || !Fb || !counts) return ORA_EINVAL;
+  const Counted Xc[2] = {X[0], X[1]}, Yc[2] = {Y[0], Y[1]};
+  const Counted Cc[2][2] = {{C[0][0], C[0][1]}, {C[1][0], C[1][1]}};
+  const Counted Fac[2] = {Fa[0], Fa[1]}, Fbc[2] = {Fb[0], Fb[1]};
+  reset_tally();
+  emf_ec<Counted>(Xc, Yc, Cc, Fac, Fbc, Counted(da), Counted(db));
+  total_tally(counts);
+  reset_tally();
+  return ORA_OK;
 }
 
 int ora_count_faces(const ora_grid* g, double gamma, const double* const u[8], int d,
@@ -1117,22 +1231,23 @@ int ora_count_faces(const ora_grid* g, double gamma, const double* const u[8], i
     Wc[f].resize(G.ncell);
     for (long p = 0; p < G.ncell; ++p) Wc[f][p] = Counted(W[f][p]);
   }
-  Tally recon, riemann;
+  reset_tally();
   for (int k = 0; k < G.n[2]; ++k)
     for (int j = 0; j < G.n[1]; ++j)
       for (int i = 0; i < G.n[0]; ++i) {
         State<Counted> L, R;
-        g_tally = Tally();
-        face_state(G, Wc, i, j, k, d, -1, &L);
+        face_state(G, Wc, i, j, k, d, -1, &L);  // tallied under the slope and face parts
         face_state(G, Wc, i, j, k, d, +1, &R);
-        recon.add += g_tally.add; recon.mul += g_tally.mul; recon.div += g_tally.div;
-        recon.sqrt += g_tally.sqrt; recon.cmp += g_tally.cmp;
-        g_tally = Tally();
+        in_part<Counted>(ORA_PART_RIEMANN);
         Counted F[7], sL, sR;
         hlld(L, R, Counted(u[5 + d][at(G, i, j, k)]), gamma, F, &sL, &sR);
-        riemann.add += g_tally.add; riemann.mul += g_tally.mul; riemann.div += g_tally.div;
-        riemann.sqrt += g_tally.sqrt; riemann.cmp += g_tally.cmp;
       }
+  Tally riemann = g_parts[ORA_PART_RIEMANN], recon;
+  for (int q : {ORA_PART_SLOPE, ORA_PART_FACE}) {
+    recon.add += g_parts[q].add; recon.mul += g_parts[q].mul; recon.div += g_parts[q].div;
+    recon.sqrt += g_parts[q].sqrt; recon.cmp += g_parts[q].cmp;
+  }
+  reset_tally();
   const double n = (double)G.ncell;
   const Tally* t[2] = {&riemann, &recon};
   double* out[2] = {counts_hlld, counts_recon};

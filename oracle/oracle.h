@@ -135,9 +135,45 @@ int ora_cycle(const ora_grid* g, double gamma, double cfl, double* const u[8], d
               double dt_max, double* dt_taken, long* bad_cell);
 
 /* Operation count of one RK2 cycle on the given state, per cell-update:
- * counts[0] add/sub, [1] mul, [2] div, [3] sqrt, [4] compare. */
+ * counts[0] add/sub, [1] mul, [2] div, [3] sqrt, [4] compare.  Every add/sub, mul, div
+ * and square root of the oracle's own arithmetic counts once (it has no fused operations);
+ * negation and absolute value do not count. */
 int ora_count_cycle(const ora_grid* g, double gamma, double cfl, const double* const u[8],
                     double inv_dt, double counts[5]);
+
+/* Parts of the method the counts are split into (ora_count_cycle_parts). */
+enum {
+  ORA_PART_PRIMS = 0,    /* primitive recovery, Sec. 2.1 definitions                    */
+  ORA_PART_SLOPE = 1,    /* van Leer slopes; formed here for both faces that use a cell  */
+  ORA_PART_FACE = 2,     /* face values w +- slope/2 (or LimO3 face values)              */
+  ORA_PART_RIEMANN = 3,  /* Riemann solver per face, Sec. 2.3                            */
+  ORA_PART_SPEED = 4,    /* face signal speed max(|S_L|, |S_R|), Eq. 10                  */
+  ORA_PART_INVDT = 5,    /* inverse CFL time per cell and its maximum, Eq. 10            */
+  ORA_PART_CELL_EMF = 6, /* cell-centre EMF -(v x B); formed here at all 4 edges of a cell */
+  ORA_PART_EDGE = 7,     /* E^c edge EMF from face and cell-centre EMFs, Sec. 2.4        */
+  ORA_PART_DIFF = 8,     /* flux differences and EMF curls over the cell size, Eqs. 5-6  */
+  ORA_PART_ACCUM = 9,    /* U* = U - dt (difference): the accumulation into the state    */
+  ORA_PART_COMBINE = 10, /* RK weights w U* + w0 U0, Eq. 9                               */
+  ORA_PART_DT = 11,      /* dt = cfl / inv and the max over stages, Eq. 10               */
+  ORA_PART_POTENTIAL = 12, /* vector-potential step and curl, Eqs. 7-8                   */
+  ORA_NUM_PARTS = 13
+};
+
+/* ora_count_cycle split by part: counts[5 * part + k], k as in ora_count_cycle. */
+int ora_count_cycle_parts(const ora_grid* g, double gamma, double cfl, const double* const u[8],
+                          double inv_dt, double counts[5 * ORA_NUM_PARTS]);
+
+/* Operation counts of single calls of the oracle's pieces, for hand-counted pins:
+ * one van Leer slope, one total energy and physical flux (Eq. 1 fluxes), one HLLD
+ * solve and one E^c edge EMF.  counts as in ora_count_cycle. */
+int ora_count_vanleer(double wm, double w0, double wp, double counts[5]);
+int ora_count_energy_flux(const double w[7], double bn, double gamma, double counts_energy[5],
+                          double counts_flux[5]);
+int ora_count_hlld(const double wL[7], const double wR[7], double bn, double gamma,
+                   double counts[5]);
+int ora_count_emf_ec(const double X[2], const double Y[2], const double C[2][2],
+                     const double Fa[2], const double Fb[2], double da, double db,
+                     double counts[5]);
 
 /* Operation counts per face of direction d (0, 1, 2) on the given state, split into the
  * HLLD solve and the reconstruction of the two face states (which evaluates the slope of
