@@ -5,9 +5,17 @@ Workload (default): 3D periodic turbulent box 256^3, FP64, rho = 1, P = 1/gamma,
 uniform B0 along x at beta = 1, seeded random-phase solenoidal velocity with
 E(k) ~ k^-2 for 1 <= |k| <= 8 at rms Mach 1, gamma = 5/3, CFL 0.4.  A "step" is one
 full RK2 cycle (two stages: primitives, PLM, HLLD on x/y/z faces, E^c EMFs, CT and
-cell update, CFL reduction, dt).  value = cells x cycles / device time, summed over
-ranks.  Inputs (state 134 MB plus intermediates of several GB) are larger than the
-126 MB L2, so no flush is needed between cycles.
+cell update, CFL reduction, dt).  value = cells x cycles / device time of the median of
+5 timed regions of K cycles each, summed over ranks.  Inputs (state 134 MB plus
+intermediates of several GB) are larger than the 126 MB L2, so no flush is needed
+between cycles.
+
+Beside the headline the default run measures, on the same GPU (each under `variants`):
+FP32 bulk at 256^3 and 512^3 and FP64 at 512^3, each with the roofline of the slower of
+its HBM bytes, FP32 flops and FP64 flops; the batched 64-instance mix, batched vs one at
+a time, FP64 and FP32; a served Poisson stream at 2D 64^2..1024^2 / 3D 64^3..256^3 sizes
+and end times 0.1..1 crossing times, continuous batching vs one at a time, with p50/p99;
+and the paper's 3D Orszag-Tang problem and the RK3, LimO3 and vector-potential forms.
 
 Multi-GPU: the method does not shard here -- `--gpus N` under torchrun runs N
 independent replicas (one box per rank, no data-path collective); a barrier and a
@@ -33,6 +41,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ideal-MHD cell-updates/s per B300 (FP64 vs FP32, plain vs served) + p50/p99"
 UNIT = "cell-updates/s"
+REGIONS = 5                # timed regions of the headline; the median is reported
+BYTES_PER_UPDATE = 320     # algorithmic HBM bytes per cell-update (RK2, FP64 state)
+FP64_NOMINAL_GFLOPS = 1250.0
 
 
 def parse():
@@ -44,16 +55,29 @@ def parse():
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     p.add_argument("--impl", default="idx", choices=["idx", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-variants", action="store_true",
+                   help="headline, roofline and e2e only (profiling runs)")
     p.add_argument("--mode", default="plain", choices=["plain", "batched", "serve", "accuracy"],
-                   help="plain: one box (the headline line); batched: the 64-instance mix, "
-                        "batched vs one at a time")
-    p.add_argument("--cycles", type=int, default=100, help="cycles per instance (batched mode)")
-    p.add_argument("--requests", type=int, default=200, help="requests in the served stream")
+                   help="plain: the default line; batched / serve: that part alone, with all "
+                        "its policies; accuracy: the FP32-bulk error budget")
+    p.add_argument("--cycles", type=int, default=100, help="cycles per instance (batched mix)")
+    p.add_argument("--serve-requests-fp32", type=int, default=16)
+    p.add_argument("--serve-requests-fp64", type=int, default=6)
     p.add_argument("--budget-gb", type=float, default=120.0, help="HBM budget of the server")
     p.add_argument("--serve-precisions", default="fp32,fp64", help="precisions of the serve mode")
     p.add_argument("--serve-caps", default="0",
                    help="comma list of max active cells for admission (0 = no cap), serve mode")
     return p.parse_args()
+
+
+def parse_args_for_test(argv=()):
+    """The options bench.py would take from argv (for host-side tests)."""
+    saved = sys.argv
+    try:
+        sys.argv = ["bench.py", *argv]
+        return parse()
+    finally:
+        sys.argv = saved
 
 
 def dist_env():
@@ -84,7 +108,19 @@ def workload_config(args):
                         "beta=1 B0 along x, random-phase solenoidal v, E(k)~k^-2 (k=1..8), "
                         "rms Mach 1, gamma=5/3, PLM+HLLD+E^c CT+RK2, CFL 0.4",
             "n": args.n, "cells": args.n ** 3, "precision": args.precision, "seed": 0,
+            "timing": f"median of {REGIONS} CUDA-event regions of --steps cycles each",
             "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas"}
+
+
+def measured_peaks():
+    """HBM copy bandwidth (GB/s) from MEASURED_PEAKS.json, else the stated fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback 6.4 TB/s (of fallback)"
 
 
 # ---------------------------------------------------------------- clocks
@@ -158,13 +194,16 @@ def cpu_baseline(n=96, cycles=3):
                       f"{el:.1f} s wall"}
 
 
+REFERENCE_SAMPLE_N = 64
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import oracle
     from paper_2304_13746_b300 import inputs
-    n = 64
+    n = REFERENCE_SAMPLE_N
     ic = inputs.turbulent_box(n, seed=0)
     sim = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, 0.4)
     for _ in range(args.warmup):
@@ -174,37 +213,65 @@ def run_reference(args):
         sim.step()
     el = time.perf_counter() - t0
     value = ic.ncells * args.steps / el
+    sample = (f"each step is one FP64 RK2 cycle of a {n}^3 box of the same recipe ({ic.ncells} "
+              f"cells, seed 0), a bounded sample of the {args.n}^3 workload; value = sample "
+              "cells x steps / host seconds")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args),
+            "reference_sample": {"box": f"{n}^3", "cells_per_step": ic.ncells,
+                                 "note": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(),
-                             "kind": "oracle",
-                             "sample": f"each step one RK2 cycle of a {n}^3 box of the same "
-                                       "recipe on the host cores (bounded sample)"},
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-# ---------------------------------------------------------------- GPU arm
+# ---------------------------------------------------------------- op counts
 # DRAM bytes per face of the dominant kernel, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch, 192^3 box, scaled by faces): reported only while
 # the bench's dominant kernel is the variant that was captured.
 MEASURED_TRAFFIC_PER_FACE = {("fp64", "x", 32): (1.281667e9 + 0.780322e9) / 192 ** 3}
 
 
-def alg_flops_per_face(cons, lengths, gamma):
-    """Algorithmic flops per face of each direction from the oracle's op counter on a
-    small box of the same recipe: HLLD + half of the two-sided reconstruction (each
-    cell's slope counted once)."""
+def op_counts(cons, lengths, gamma):
+    """Algorithmic flops from the oracle's pinned op counter on a sample of the state:
+    per cell-update of one RK2 cycle (whole, and the part the FP32-bulk variant keeps in
+    FP64) and per face of each direction (HLLD, face values and each slope once)."""
     import oracle
-    out = []
-    for d in range(3):
-        h, r = oracle.count_faces(cons, lengths, gamma, d)
-        out.append(sum(h[k] for k in ("add", "mul", "div", "sqrt")) +
-                   0.5 * sum(r[k] for k in ("add", "mul", "div", "sqrt")))
+    parts = oracle.count_cycle_parts(cons, lengths, gamma, 0.4)
+    face = [oracle.algorithmic_face_flops(oracle.count_faces_parts(cons, lengths, gamma, d))
+            for d in range(3)]
+    total = sum(oracle.flops(c) for c in parts.values())
+    return {"cycle_flops_counted": total, "cycle_flops": oracle.algorithmic_flops(parts),
+            "fp64_island_flops": oracle.fp64_island_flops(parts), "face_flops": face,
+            "parts": {p: oracle.flops(c) for p, c in parts.items()}}
+
+
+def roofline_cycle(value, counts, rates, hbm_gbs, precision):
+    """Roofline of a whole cycle: the slower of its algorithmic HBM bytes at the measured
+    copy bandwidth, its FP64 flops at the FP64 flop peak and (FP32 bulk) its FP32 flops at
+    the FP32 flop peak; frac = that bound's time / the measured time per cell-update."""
+    f64 = 2 * rates["fma64"]
+    f32 = 2 * rates["fma32"]
+    t = {"hbm": BYTES_PER_UPDATE / (hbm_gbs * 1e9)}
+    if precision == "fp64":
+        t["fp64"] = counts["cycle_flops"] / f64
+    else:
+        t["fp64"] = counts["fp64_island_flops"] / f64
+        t["fp32"] = (counts["cycle_flops"] - counts["fp64_island_flops"]) / f32
+    bound = max(t, key=t.get)
+    out = {"bound": bound, "bound_cell_updates_per_s": 1.0 / t[bound],
+           "frac": value * t[bound],
+           "ns_per_cell_update": {k: v * 1e9 for k, v in t.items()},
+           "measured_ns_per_cell_update": 1e9 / value,
+           "alg_flops_per_cell_update": counts["cycle_flops"],
+           "bytes_per_cell_update": BYTES_PER_UPDATE}
+    if precision != "fp64":
+        out["fp64_island_flops_per_cell_update"] = counts["fp64_island_flops"]
     return out
 
 
@@ -226,136 +293,159 @@ def c4_instances(seed=4):
     return ics
 
 
-def run_batched(args):
+def batched_mix(ics, precision, K, warmup):
+    """The mix as one batch (K batched cycles) and one at a time (K cycles each)."""
     import torch
+    from paper_2304_13746_b300 import idx
+    cells = sum(ic.ncells for ic in ics)
+    stream = torch.cuda.Stream()
+    sims = [idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, precision, stream=stream.cuda_stream)
+            for ic in ics]
+    for s, ic in zip(sims, ics):
+        s.set_primitive(ic.prim)
+    b = idx.Batch(precision, stream=stream.cuda_stream)
+    for s in sims:
+        b.add(s)
+    b.step(warmup)
+    b.poll()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(K)
+    e1.record(stream)
+    e1.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    shapes = b.shapes()
+    for s in sims:
+        b.remove(s)
+    b.close()
+    for s in sims:
+        s.close()
+    sims = [idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, precision, stream=stream.cuda_stream)
+            for ic in ics]
+    for s, ic in zip(sims, ics):
+        s.set_primitive(ic.prim)
+        for _ in range(warmup):
+            s.step()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s in sims:
+        for _ in range(K):
+            s.step()
+    e1.record(stream)
+    e1.synchronize()
+    ms_s = e0.elapsed_time(e1)
+    for s in sims:
+        s.close()
+    return {"batched": cells * K / (ms_b * 1e-3), "sequential": cells * K / (ms_s * 1e-3),
+            "speedup": ms_s / ms_b, "ms_batched": ms_b, "ms_sequential": ms_s,
+            "batch_sweep_shapes_xyz": shapes}
+
+
+def run_batched(args):
     from paper_2304_13746_b300 import build as idx_build
     from paper_2304_13746_b300 import idx
     idx_build.build()
     idx.lib()
     ics = c4_instances()
     cells = sum(ic.ncells for ic in ics)
-    K = args.cycles
-    results = {}
-    for precision in ("fp64", "fp32"):
-        stream = torch.cuda.Stream()
-        # one batch for all 64 instances
-        sims = [idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, precision, stream=stream.cuda_stream)
-                for ic in ics]
-        for s, ic in zip(sims, ics):
-            s.set_primitive(ic.prim)
-        b = idx.Batch(precision, stream=stream.cuda_stream)
-        for s in sims:
-            b.add(s)
-        b.step(args.warmup)
-        b.poll()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        b.step(K)
-        e1.record(stream)
-        e1.synchronize()
-        ms_b = e0.elapsed_time(e1)
-        shapes = b.shapes()
-        for s in sims:
-            b.remove(s)
-        b.close()
-        for s in sims:
-            s.close()
-        # the same instances one at a time (each a graph of its own cycle)
-        sims = [idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, precision, stream=stream.cuda_stream)
-                for ic in ics]
-        for s, ic in zip(sims, ics):
-            s.set_primitive(ic.prim)
-            for _ in range(args.warmup):
-                s.step()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for s in sims:
-            for _ in range(K):
-                s.step()
-        e1.record(stream)
-        e1.synchronize()
-        ms_s = e0.elapsed_time(e1)
-        for s in sims:
-            s.close()
-        results[precision] = {
-            "batched": cells * K / (ms_b * 1e-3), "sequential": cells * K / (ms_s * 1e-3),
-            "speedup": ms_s / ms_b, "ms_batched": ms_b, "ms_sequential": ms_s,
-            "batch_sweep_shapes_xyz": shapes}
+    results = {p: batched_mix(ics, p, args.cycles, args.warmup) for p in ("fp64", "fp32")}
     line = {"metric": METRIC, "value": results["fp64"]["batched"], "unit": UNIT, "n_gpus": 1,
-            "steps": K, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "batched: 64 independent instances (32 Orszag-Tang 2D, N "
-                                   "log-uniform 64..512; 32 turbulent 3D boxes, N log-uniform "
-                                   "32..128), own CFL dt each, one batch vs one at a time",
-                       "instances": len(ics), "cells": cells, "cycles_per_instance": K},
+            "steps": args.cycles, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": C4_WORKLOAD, "instances": len(ics), "cells": cells,
+                       "cycles_per_instance": args.cycles},
             "batched": results}
     print(json.dumps(line), flush=True)
 
 
+C4_WORKLOAD = ("batched: 64 independent instances (32 Orszag-Tang 2D, N log-uniform 64..512; "
+               "32 turbulent 3D boxes, N log-uniform 32..128), own CFL dt each, one batch vs "
+               "one at a time")
+
+# the served stream at the survey's C5 reading: kind 2D/3D with p = 1/2, 2D Orszag-Tang N
+# log-uniform in [64, 1024], 3D turbulent box N log-uniform in [64, 256], t_end uniform in
+# [0.1, 1.0] crossing times (t_cross = 1 for both), Poisson arrivals, seed 7
+C5 = {"sizes_2d": (64, 1024), "sizes_3d": (64, 256), "t_end": (0.1, 1.0), "seed": 7}
+
+
+def served_stream(precision, nreq, budget, serve_mod, stream, orders=("oldest",), caps=()):
+    """The first nreq requests of the C5 stream, served three ways: all arriving at once
+    (capacity), then at 70 % of that capacity by continuous batching and one at a time."""
+    base = serve_mod.make_payloads(serve_mod.poisson_stream(
+        nreq, 20.0, seed=C5["seed"], sizes_2d=C5["sizes_2d"], sizes_3d=C5["sizes_3d"],
+        t_end=C5["t_end"]))
+
+    def clone(rate):
+        out = []
+        for r in base:
+            q = serve_mod.Request(r.rid, r.arrival * 20.0 / rate, r.kind, r.n, r.t_end, r.seed,
+                                  payload=r.payload)
+            q.cells = r.cells
+            out.append(q)
+        return out
+
+    def served(rate, cap=None, order="oldest"):
+        be = serve_mod.IdxBackend(precision, stream=stream)
+        st = serve_mod.Server(be, budget, cycles_per_poll=4, chunk_s=0.01,
+                              max_active_cells=cap, order=order).run(clone(rate))
+        be.close()
+        return st
+
+    def sequential(rate):
+        return serve_mod.serve_sequential(serve_mod.IdxSequential(precision, stream=stream),
+                                          clone(rate), budget_bytes=budget)
+
+    cap = served(1e9)                     # everything at once: the batch's capacity
+    mean_work = cap["cell_updates"] / max(cap["done"], 1)
+    capacity_rps = cap["cell_updates_per_s"] / mean_work
+    rate70 = 0.7 * capacity_rps
+    r = {"requests": nreq, "capacity_req_per_s": capacity_rps,
+         "capacity_cell_updates_per_s": cap["cell_updates_per_s"],
+         "mean_cell_updates_per_request": mean_work, "all_at_once": cap,
+         "sizes": [f"{q.kind} {q.n}" for q in base], "t_end": [round(q.t_end, 3) for q in base]}
+    for order in orders:
+        key = "served_70pct" if order == "oldest" else f"served_70pct_{order}"
+        r[key] = dict(served(rate70, order=order), rate=rate70, order=order,
+                      offered_load=0.7)
+    for c in caps:
+        r[f"served_70pct_cap{c}"] = dict(served(rate70, c), rate=rate70, max_active_cells=c)
+    r["sequential_70pct"] = dict(sequential(rate70), rate=rate70, offered_load=0.7)
+    s, q = r["served_70pct"], r["sequential_70pct"]
+    r["summary"] = {"served_p50_s": s["p50_s"], "served_p99_s": s["p99_s"],
+                    "sequential_p50_s": q["p50_s"], "sequential_p99_s": q["p99_s"],
+                    "served_cell_updates_per_s": s["cell_updates_per_s"],
+                    "sequential_cell_updates_per_s": q["cell_updates_per_s"]}
+    return r
+
+
 def run_serve(args):
-    """Served stream: seeded Poisson arrivals of 2D/3D requests admitted under an HBM budget
-    into one running batch (continuous batching), against the same stream one at a time."""
+    """Served stream alone, with every admission policy."""
     import torch
     from paper_2304_13746_b300 import build as idx_build
     from paper_2304_13746_b300 import idx, serve
     idx_build.build()
     idx.lib()
     budget = int(args.budget_gb * 1e9)
-    base = serve.make_payloads(serve.poisson_stream(args.requests, 20.0, seed=7))
     stream = torch.cuda.Stream()
-
-    def clone(reqs, rate):
-        out = []
-        for r in reqs:
-            q = serve.Request(r.rid, r.arrival * 20.0 / rate, r.kind, r.n, r.t_end, r.seed,
-                              payload=r.payload)
-            q.cells = r.cells
-            out.append(q)
-        return out
-
-    def served(precision, rate, cap=None, order="oldest"):
-        be = serve.IdxBackend(precision, stream=stream.cuda_stream)
-        st = serve.Server(be, budget, cycles_per_poll=4, chunk_s=0.01,
-                          max_active_cells=cap, order=order).run(clone(base, rate))
-        be.close()
-        return st
-
+    caps = [int(float(c)) for c in args.serve_caps.split(",") if float(c) > 0]
     results = {}
     for precision in args.serve_precisions.split(","):
-        cap = served(precision, 1e9)                    # everything arrives at once
-        mean_work = cap["cell_updates"] / max(cap["done"], 1)
-        capacity_rps = cap["cell_updates_per_s"] / mean_work
-        rate70 = 0.7 * capacity_rps
-        r = {"capacity_req_per_s": capacity_rps, "mean_cell_updates_per_request": mean_work,
-             "all_at_once": cap}
-        r["sequential_all_at_once"] = serve.serve_sequential(
-            serve.IdxSequential(precision, stream=stream.cuda_stream), clone(base, 1e9),
-            budget_bytes=budget)
-        r["served_70pct"] = dict(served(precision, rate70), rate=rate70)
-        for cap in [int(float(c)) for c in args.serve_caps.split(",") if float(c) > 0]:
-            r[f"served_70pct_cap{cap}"] = dict(served(precision, rate70, cap), rate=rate70,
-                                               max_active_cells=cap)
-        r["served_70pct_least_work"] = dict(served(precision, rate70, order="least_work"),
-                                            rate=rate70, order="least_work")
-        r["sequential_70pct"] = dict(serve.serve_sequential(
-            serve.IdxSequential(precision, stream=stream.cuda_stream), clone(base, rate70),
-            budget_bytes=budget), rate=rate70)
-        if precision == "fp32":
-            r["served_20rps"] = dict(served(precision, 20.0), rate=20.0)
-        r["offered_load_at_20rps"] = 20.0 / capacity_rps
-        results[precision] = r
-    head = results.get("fp64", results[next(iter(results))])
+        n = args.serve_requests_fp32 if precision == "fp32" else args.serve_requests_fp64
+        results[precision] = served_stream(precision, n, budget, serve, stream.cuda_stream,
+                                           orders=("oldest", "least_work"), caps=caps)
+    head = results[next(iter(results))]
     line = {"metric": METRIC, "value": head["served_70pct"]["cell_updates_per_s"],
             "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"served: {args.requests} requests, Poisson arrivals (seed 7), "
-                                   "kind 2D/3D p=1/2, 2D Orszag-Tang N log-uniform 64..512, 3D "
-                                   "turbulent box N log-uniform 32..128, t_end U[0.01, 0.1], "
-                                   f"HBM budget {args.budget_gb:g} GB, continuous batching vs "
-                                   "one at a time", "budget_bytes": budget},
-            "served": results}
+            "config": {"workload": C5_WORKLOAD, "budget_bytes": budget}, "served": results}
     print(json.dumps(line), flush=True)
+
+
+C5_WORKLOAD = ("served: Poisson arrivals (seed 7), kind 2D/3D p=1/2, 2D Orszag-Tang N "
+               "log-uniform 64..1024, 3D turbulent box N log-uniform 64..256, t_end U[0.1, 1.0] "
+               "crossing times, HBM budget 120 GB, first R requests of the stream at 70 % of "
+               "the capacity an all-at-once run measures; continuous batching vs one at a time")
 
 
 def run_accuracy(args):
@@ -374,6 +464,14 @@ def run_accuracy(args):
                                    f"discretisation error from {n // 2}^3, p=2)"},
             "accuracy": r}
     print(json.dumps(line), flush=True)
+
+
+def guarded(fn, *a, **kw):
+    """A variant's numbers, or the error that stopped it (the headline line still prints)."""
+    try:
+        return fn(*a, **kw)
+    except Exception as e:  # noqa: BLE001 -- reported in the JSON line
+        return {"error": f"{type(e).__name__}: {e}"}
 
 
 def main():
@@ -400,6 +498,8 @@ def main():
     if dist:
         dist.barrier()
     idx.lib()
+    hbm_gbs, hbm_source = measured_peaks()
+    rates = idx.pipe_rates()
 
     ic = inputs.turbulent_box(args.n, seed=0)
     ncell = ic.ncells
@@ -415,51 +515,57 @@ def main():
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     time.sleep(0.3)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.nvtx.range_push("timed")   # lets a profiler select the timed cycles
-    e0.record(stream)
-    for _ in range(args.steps):
-        sim.step()
-    e1.record(stream)
-    e1.synchronize()
-    torch.cuda.nvtx.range_pop()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    regions = []
+    for _ in range(REGIONS):
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")   # lets a profiler select the timed cycles
+        e0.record(stream)
+        for _ in range(args.steps):
+            sim.step()
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        regions.append(max_over_ranks(e0.elapsed_time(e1), dist))
     clk = clocks.stop()
     sim.time()  # surfaces any device error of the timed cycles
-    ms = max_over_ranks(ms, dist)
+    ms = statistics.median(regions)
     value = aggregate_rate(ncell, args.steps, world, ms)
     n_active = sum(1 for s in ic.shape if s > 1)
     launches_per_cycle = 2 + 2 * (3 + n_active)
 
+    # op counts from the oracle's pinned counter on a 32^3 corner of the box's state
+    sample = ([np.ascontiguousarray(a[:32, :32, :32]) for a in cons_host] if args.n > 32
+              else cons_host)
+    counts = op_counts(sample, (32 / args.n,) * 3 if args.n > 32 else ic.lengths, ic.gamma)
+
     # dominant kernel: per-launch device time of each kernel (events between launches)
     kt = sim.kernel_times(reps=2)
     shapes = sim.sweep_shapes()
-    flops_face = alg_flops_per_face(
-        [np.ascontiguousarray(a[:32, :32, :32]) for a in cons_host] if args.n > 32 else cons_host,
-        (32 / args.n,) * 3 if args.n > 32 else ic.lengths, ic.gamma)
     sweep_ms = {d: kt[f"sweep_{d}"] for d in "xyz"}
     dom = max(sweep_ms, key=sweep_ms.get)
     d_i = "xyz".index(dom)
-    achieved_gflops = flops_face[d_i] * ncell / (sweep_ms[dom] * 1e-3) / 1e9
-    rates = idx.pipe_rates()
-    if args.precision == "fp64":
-        peak = 2 * rates["fma64"] / 1e9
-        peak_note = "measured FP64 FMA rate x 2 flop (idx_pipe_rates, this GPU)"
-    else:
-        peak = 2 * rates["fma32"] / 1e9
-        peak_note = "measured FP32 FMA rate x 2 flop (idx_pipe_rates, this GPU)"
+    achieved_gflops = counts["face_flops"][d_i] * ncell / (sweep_ms[dom] * 1e-3) / 1e9
+    fma = rates["fma64"] if args.precision == "fp64" else rates["fma32"]
+    peak = 2 * fma / 1e9
     tpf = MEASURED_TRAFFIC_PER_FACE.get((args.precision, dom, shapes["xyz".index(dom)]))
+    whole = roofline_cycle(value, counts, rates, hbm_gbs, args.precision)
     roofline = {"bound": "alu", "kernel": f"k_sweep<{'double' if args.precision == 'fp64' else 'float'},{dom}>",
                 "achieved": achieved_gflops, "peak": peak, "unit": "GFLOP/s",
                 "frac": achieved_gflops / peak,
+                "frac_of_nominal_fp64": (achieved_gflops / FP64_NOMINAL_GFLOPS
+                                         if args.precision == "fp64" else None),
                 "traffic": tpf * ncell if tpf else None, "traffic_unit": "bytes per launch",
-                "alg_flops_per_face": flops_face[d_i], "launch_ms": sweep_ms[dom],
-                "peak_source": peak_note, "kernel_ms": kt, "sweep_shapes_xyz": shapes,
-                "pipe_rates_gops": {k: v / 1e9 for k, v in rates.items()}}
+                "alg_flops_per_face": counts["face_flops"][d_i], "launch_ms": sweep_ms[dom],
+                "peak_source": (f"measured {'FP64' if args.precision == 'fp64' else 'FP32'} FMA "
+                                "rate x 2 flop (idx_pipe_rates, this GPU; of measured)"),
+                "kernel_ms": kt, "sweep_shapes_xyz": shapes,
+                "pipe_rates_gops": {k: v / 1e9 for k, v in rates.items()},
+                "whole_cycle": whole, "op_counts": counts, "hbm_gbs": hbm_gbs,
+                "hbm_source": hbm_source}
 
     # end to end through the C ABI with host buffers: H2D state, one cycle, D2H state
     pinned = [torch.from_numpy(a).pin_memory().numpy() for a in cons_host]
@@ -482,25 +588,29 @@ def main():
            "note": "per step: idx_set_state from pinned host (incl. its signal-speed pass), "
                    "idx_step, idx_get_state to pinned host"}
     sim.close()
+    del pinned, out_pinned
 
-    def time_variant(precision, ic_v=None, **kw):
-        # another configuration (same box unless given), same timing rules
+    def time_variant(precision, ic_v=None, steps=None, warmup=None, **kw):
+        # another configuration (same box unless given), same timing rules, one region
         ic_v = ic if ic_v is None else ic_v
-        sv = idx.Sim(ic_v.shape, ic_v.lengths, ic_v.gamma, 0.4, precision, stream=stream.cuda_stream,
-                     **kw)
+        steps = args.steps if steps is None else steps
+        warmup = args.warmup if warmup is None else warmup
+        sv = idx.Sim(ic_v.shape, ic_v.lengths, ic_v.gamma, 0.4, precision,
+                     stream=stream.cuda_stream, **kw)
         sv.set_primitive(ic_v.prim)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             sv.step()
         torch.cuda.synchronize()
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             sv.step()
         e1.record(stream)
         e1.synchronize()
         msv = max_over_ranks(e0.elapsed_time(e1), dist)
         sv.time()
-        out = {"value": aggregate_rate(ncell, args.steps, world, msv), "unit": UNIT,
-               "ms_per_step": msv / args.steps, "sweep_shapes_xyz": sv.sweep_shapes()}
+        out = {"value": aggregate_rate(ic_v.ncells, steps, world, msv), "unit": UNIT,
+               "ms_per_step": msv / steps, "steps": steps,
+               "sweep_shapes_xyz": sv.sweep_shapes()}
         sv.close()
         return out
 
@@ -524,30 +634,59 @@ def main():
         sv.close()
         return out
 
+    def with_roofline(v, precision, cnt):
+        if "value" in v:
+            v["roofline"] = roofline_cycle(v["value"], cnt, rates, hbm_gbs, precision)
+        return v
+
     variants = {}
-    if args.precision == "fp64":
+    if args.precision == "fp64" and not args.no_variants:
+        variants["fp32_bulk"] = with_roofline(guarded(time_variant, "fp32"), "fp32", counts)
+        # the 512^3 box: the FP32-bulk configuration, and FP64 beside it
+        ic512 = inputs.turbulent_box(512, seed=0)
+        variants["fp32_bulk_512"] = with_roofline(guarded(time_variant, "fp32", ic512),
+                                                  "fp32", counts)
+        variants["fp64_512"] = with_roofline(guarded(time_variant, "fp64", ic512, steps=5,
+                                                     warmup=2), "fp64", counts)
+        del ic512
         # the small 2D problem of the paper's Orszag-Tang test, whole run: launch-bound
         ot2 = inputs.orszag_tang_2d(128)
         for prec in ("fp64", "fp32"):
             key = f"{prec}_orszag_tang_2d_128_to_t0.5"
-            variants[key] = time_advance(prec, ot2, 0.5)
+            variants[key] = guarded(time_advance, prec, ot2, 0.5)
             variants[key]["note"] = ("2D Orszag-Tang 128^2 to t = 0.5 through idx_advance (16384 cells: "
                                      "launch-bound, one CUDA graph per cycle)")
-        variants["fp32_bulk"] = time_variant("fp32")
-        variants["fp64_vector_potential"] = time_variant("fp64", induction="potential")
+        variants["fp64_vector_potential"] = guarded(time_variant, "fp64", induction="potential")
         variants["fp64_vector_potential"]["note"] = "Eqs. 7-8: edge potential stepped, B = Bref + curl A"
-        variants["fp64_rk3"] = time_variant("fp64", rk_order=3)
+        variants["fp64_rk3"] = guarded(time_variant, "fp64", rk_order=3)
         variants["fp64_rk3"]["note"] = "RK3 (Table 1): three stages per cycle instead of two"
-        variants["fp64_limo3"] = time_variant("fp64", recon="limo3")
+        variants["fp64_limo3"] = guarded(time_variant, "fp64", recon="limo3")
         variants["fp64_limo3"]["note"] = "LimO3 reconstruction (Sec. 2.3) instead of van Leer PLM"
-        variants["fp64_limo3_rk3"] = time_variant("fp64", recon="limo3", rk_order=3)
+        variants["fp64_limo3_rk3"] = guarded(time_variant, "fp64", recon="limo3", rk_order=3)
         variants["fp64_limo3_rk3"]["note"] = "LimO3 + RK3, the paper's higher-accuracy pairing"
         # the paper's own performance problem (Sec. 5): 3D Orszag-Tang, FP64, at this box size
         ot = inputs.orszag_tang_3d(args.n)
-        variants["fp64_orszag_tang_3d"] = time_variant("fp64", ot)
+        variants["fp64_orszag_tang_3d"] = guarded(time_variant, "fp64", ot)
         variants["fp64_orszag_tang_3d"]["note"] = (
             f"3D Orszag-Tang {args.n}^3 (Sec. 5 performance problem); the paper reports ~121 Mcell/s "
             "per V100 at 256^3 per GPU (4-GPU node, 484 Mcell/s): context, another machine")
+        if world == 1:
+            # batched mix (C4) and the served stream (C5 reading), single GPU
+            ics = c4_instances()
+            variants["batched_mix"] = {
+                "workload": C4_WORKLOAD, "cycles_per_instance": args.cycles,
+                "cells": sum(x.ncells for x in ics),
+                "fp64": guarded(batched_mix, ics, "fp64", args.cycles, args.warmup),
+                "fp32": guarded(batched_mix, ics, "fp32", args.cycles, args.warmup)}
+            del ics
+            from paper_2304_13746_b300 import serve
+            budget = int(args.budget_gb * 1e9)
+            variants["served"] = {"workload": C5_WORKLOAD, "budget_bytes": budget}
+            for prec, nreq in (("fp32", args.serve_requests_fp32),
+                               ("fp64", args.serve_requests_fp64)):
+                if nreq > 0:
+                    variants["served"][prec] = guarded(served_stream, prec, nreq, budget, serve,
+                                                       stream.cuda_stream)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -555,8 +694,11 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if args.precision == "fp64" else "f32/f64",
                 "data": "synthetic", "config": workload_config(args),
-                "gpu_launches": launches_per_cycle * args.steps,
-                "clocks": clk, "roofline": roofline, "e2e": e2e, "variants": variants}
+                "regions_ms": regions,
+                "spread": (max(regions) - min(regions)) / ms,
+                "gpu_launches": launches_per_cycle * args.steps * REGIONS,
+                "clocks": clk, "roofline": roofline,
+                "whole_cycle_frac": whole["frac"], "e2e": e2e, "variants": variants}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

@@ -170,6 +170,28 @@ int idx_footprint_solver(const idx_grid* grid, const idx_solver* solver, uint64_
  * the last failing call, or -1. */
 int idx_last_error_cell(const idx_sim* sim, int64_t* cell);
 
+/* Time-stepping state of a sim beside its fields, for restart dumps (Sec. 3.3: a dump
+ * holds the raw data needed to continue a run).  inv_dt is the inverse CFL time carried
+ * from the last cycle, the larger of its stages' max over cells of sum_d c_max,d / dl_d
+ * (Eq. 10); the next cycle takes dt = cfl / inv_dt.  Restart: idx_get_state +
+ * idx_get_clock on the running sim; idx_create + idx_set_state + idx_set_clock on the new
+ * one.  The field-form run then continues bit for bit as if it had not stopped (same
+ * device, grid, solver and sweep shapes).  A vector-potential sim restarts its gauge at
+ * the given face field (idx_set_state), so it continues to rounding only. */
+typedef struct {
+  double t;        /* simulated time                                    */
+  double inv_dt;   /* carried inverse CFL time (> 0)                    */
+  int64_t nsteps;  /* cycles taken since the state was first set        */
+} idx_clock;
+
+/* Read the clock.  Synchronises; reports a pending device error. */
+int idx_get_clock(const idx_sim* sim, idx_clock* clock);
+
+/* Replace the clock of a sim whose state is set (after idx_set_state, which resets t and
+ * the count and fixes inv_dt by a signal-speed pass).  IDX_EINVAL for a non-finite t, an
+ * inv_dt that is not a finite positive value, or a negative count.  Synchronises. */
+int idx_set_clock(idx_sim* sim, const idx_clock* clock);
+
 /* Device time per launch of each kernel of the stage, averaged over the 2 * reps stages
  * of `reps` cycles launched kernel by kernel with CUDA events between them on the sim's
  * stream: ms[0] primitive recovery, [1] x sweep (PLM + HLLD), [2] y sweep, [3] z sweep,
@@ -208,6 +230,16 @@ int idx_set_sweep_shapes(idx_sim* sim, const int shapes[3]);
 void idx_destroy(idx_sim* sim);
 
 const char* idx_strerror(int code);
+
+/* The bounded mbarrier wait of the TMA-staged sweeps (every device wait of the library is
+ * bounded: on expiry the block records IDX_ETIMEOUT in the sim's control block and
+ * leaves), run alone in one block of a test kernel on `stream` (NULL: the default
+ * stream).  The block announces announce_bytes of transaction bytes on its barrier and
+ * issues no copy, so with announce_bytes > 0 the wait expires after limit_ms and the call
+ * returns IDX_ETIMEOUT; with 0 the barrier completes at once and it returns IDX_OK.  No
+ * copy is ever in flight.  limit_ms in (0, 1000], announce_bytes < 2^20, else IDX_EINVAL.
+ * Synchronises the stream.  A testing aid, not part of the method. */
+int idx_probe_bounded_wait(void* stream, uint32_t announce_bytes, double limit_ms);
 
 /* Measured throughput of the current device's arithmetic pipes, in operations per
  * second: rates[0] FP64 fused multiply-add, [1] FP64 divide, [2] FP64 square root,
@@ -284,15 +316,18 @@ void idx_batch_destroy(idx_batch* batch);
  *
  * Limits and behaviour:
  *   - at most IDX_NOALLOC_MAX_CELLS cells; a larger grid returns IDX_ETOOLARGE;
- *   - the first call on a device looks up the array's device address (once per
- *     device, with that device current); make that first call before any stream
- *     capture;
+ *   - the first call on a device looks up the array's device address, with that device
+ *     current, and later calls reuse it; the lookup is kept per device and CUDA context
+ *     (a context that another framework makes current has its own copy of the array and
+ *     gets its own lookup).  Do not call it after a cudaDeviceReset in the same process:
+ *     a cached address belongs to the context that the reset destroyed;
+ *   - the call reads back dt and the error flag and waits for its stream, which a graph
+ *     capture cannot record: never issue it on a stream that is capturing (IDX_EINVAL);
  *   - every call shares the one array, which keeps the last call's contents (the call
  *     clears what must start at zero): calls that overlap on the GPU race, so issue
  *     them one at a time (same stream, or synchronise between streams and devices
  *     sharing a process);
- *   - the call waits for its stream to finish the cycle (it reads back dt and the
- *     error flag); IDX_ENONPHYS as for idx_step. */
+ *   - it returns when its stream has finished the cycle; IDX_ENONPHYS as for idx_step. */
 #define IDX_ETOOLARGE (-6)                      /* grid exceeds a fixed-size buffer */
 #define IDX_NOALLOC_SCRATCH_BYTES (64u << 20)   /* 64 MiB per GPU                   */
 #define IDX_NOALLOC_MAX_CELLS 195072            /* 256 + 43 x align256(8 n) <= 64 MiB */

@@ -65,6 +65,7 @@ def lib():
         L.ora_cycle_rk.argtypes = [G, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                    _P8, _D, ctypes.c_double, _D, ctypes.POINTER(ctypes.c_long)]
         L.ora_count_faces.argtypes = [G, ctypes.c_double, _P8, ctypes.c_int, _D, _D]
+        L.ora_count_faces_parts.argtypes = [G, ctypes.c_double, _P8, ctypes.c_int, _D]
         L.ora_count_cycle_parts.argtypes = [G, ctypes.c_double, ctypes.c_double, _P8,
                                             ctypes.c_double, _D]
         L.ora_count_vanleer.argtypes = [ctypes.c_double] * 3 + [_D]
@@ -394,6 +395,21 @@ def count_emf_ec(X, Y, C, Fa, Fb, da, db):
     out = (ctypes.c_double * 5)()
     _check(lib().ora_count_emf_ec(arr[0], arr[1], c, fa, fb, float(da), float(db), out))
     return _counts5(out)
+
+
+def count_faces_parts(cons, lengths, gamma, d):
+    """Per-face op counts of direction d split into {"riemann", "slope", "face"}."""
+    cons = [_c(a) for a in cons]
+    out = (ctypes.c_double * 15)()
+    _check(lib().ora_count_faces_parts(ctypes.byref(_grid(cons[0].shape, lengths)), gamma,
+                                       _ptrs(cons), int(d), out))
+    return {p: dict(zip(OPS, out[5 * q:5 * q + 5])) for q, p in enumerate(("riemann", "slope",
+                                                                           "face"))}
+
+
+def algorithmic_face_flops(parts):
+    """Flops per face with each cell's slope counted once (half the slope part)."""
+    return flops(parts["riemann"]) + flops(parts["face"]) + 0.5 * flops(parts["slope"])
 
 
 def threads():

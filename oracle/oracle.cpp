@@ -1214,8 +1214,13 @@ int ora_count_emf_ec(const double X[2], const double Y[2], const double C[2][2],
   return ORA_OK;
 }
 
-int ora_count_faces(const ora_grid* g, double gamma, const double* const u[8], int d,
-                    double counts_hlld[5], double counts_recon[5]) {
+}  // extern "C"
+
+namespace {
+// Per-face counts of direction d: the HLLD solve, the reconstruction of both face states,
+// and (split, nullable) the HLLD solve, the slopes and the face values.
+int count_faces_split(const ora_grid* g, double gamma, const double* const u[8], int d,
+                      double counts_hlld[5], double counts_recon[5], double* split) {
   if (!grid_ok(g) || !(gamma > 1.0) || !ptrs_ok((const void* const*)u) || d < 0 || d > 2 ||
       !counts_hlld || !counts_recon)
     return ORA_EINVAL;
@@ -1247,15 +1252,35 @@ int ora_count_faces(const ora_grid* g, double gamma, const double* const u[8], i
     recon.add += g_parts[q].add; recon.mul += g_parts[q].mul; recon.div += g_parts[q].div;
     recon.sqrt += g_parts[q].sqrt; recon.cmp += g_parts[q].cmp;
   }
+  const Tally slope = g_parts[ORA_PART_SLOPE], face = g_parts[ORA_PART_FACE];
   reset_tally();
   const double n = (double)G.ncell;
-  const Tally* t[2] = {&riemann, &recon};
-  double* out[2] = {counts_hlld, counts_recon};
-  for (int q = 0; q < 2; ++q) {
+  const Tally* t[5] = {&riemann, &recon, &riemann, &slope, &face};
+  double* out[5] = {counts_hlld, counts_recon, split, split ? split + 5 : nullptr,
+                    split ? split + 10 : nullptr};
+  for (int q = 0; q < 5; ++q) {
+    if (!out[q]) continue;
     out[q][0] = t[q]->add / n; out[q][1] = t[q]->mul / n; out[q][2] = t[q]->div / n;
     out[q][3] = t[q]->sqrt / n; out[q][4] = t[q]->cmp / n;
   }
   return ORA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ora_count_faces_parts(const ora_grid* g, double gamma, const double* const u[8], int d,
+                          double counts[15]) {
+  if (!counts) return ORA_EINVAL;
+  double h[5], r[5];
+  return count_faces_split(g, gamma, u, d, h, r, counts);
+}
+
+int ora_count_faces(const ora_grid* g, double gamma, const double* const u[8], int d,
+                    double counts_hlld[5], double counts_recon[5]) {
+  if (!counts_hlld || !counts_recon) return ORA_EINVAL;
+  return count_faces_split(g, gamma, u, d, counts_hlld, counts_recon, nullptr);
 }
 
 int ora_threads(void) {

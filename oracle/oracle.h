@@ -181,6 +181,12 @@ int ora_count_emf_ec(const double X[2], const double Y[2], const double C[2][2],
 int ora_count_faces(const ora_grid* g, double gamma, const double* const u[8], int d,
                     double counts_hlld[5], double counts_recon[5]);
 
+/* The same per-face counts split three ways: counts[0..4] the HLLD solve, [5..9] the van
+ * Leer slopes of both face states (each cell's slope is formed for both of its faces),
+ * [10..14] the face values w +- slope / 2. */
+int ora_count_faces_parts(const ora_grid* g, double gamma, const double* const u[8], int d,
+                          double counts[15]);
+
 /* Number of host threads the oracle uses (OpenMP), for reporting. */
 int ora_threads(void);
 

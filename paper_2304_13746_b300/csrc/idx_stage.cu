@@ -68,6 +68,7 @@ struct Geo {
   int ncell;
   int active[3];   // n_d > 1
   double inv_dl[3];
+  double dl[3];      // cell sizes l / n (the strict-rounding build divides by them)
   double gamma;
   double gm1;        // gamma - 1
   double gm1inv;     // 1 / (gamma - 1)
@@ -762,6 +763,10 @@ __device__ __forceinline__ T edge_emf(const Geo& g, int e, int c, const int ijk[
     return cce ? cce[q] : -(W.f[1 + a][q] * W.f[5 + b][q] - W.f[1 + b][q] * W.f[5 + a][q]);
   };
   const T C00 = cc(c), C01 = cc(cb), C10 = cc(ca), C11 = cc(cab);
+#ifdef IDX_STRICT_ROUNDING
+  if constexpr (sizeof(T) == 8)
+    return emf_ec_plain(X0, X1, Y0, Y1, C00, C01, C10, C11, Fa0, Fa1, Fb0, Fb1, g.dl[a], g.dl[b]);
+#endif
   return emf_ec(X0, X1, Y0, Y1, C00, C01, C10, C11, Fa0, Fa1, Fb0, Fb1);
 }
 
@@ -936,6 +941,50 @@ __device__ __forceinline__ T update_body(const Geo& g, const Ptr8<const double>&
 #pragma unroll
     for (int d = 0; d < 3; ++d) kdt[d] = dt * g.inv_dl[d];
     double out[8];
+#ifdef IDX_STRICT_ROUNDING
+    if constexpr (std::is_same<T, double>::value && !POT) {
+      // strict-rounding build: differences over the cell size summed from zero, then
+      // U - dt (sum) and w U* + w0 U0, each rounded on its own
+#pragma unroll
+      for (int f = 0; f < 5; ++f) {
+        double div = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          if (!g.active[d]) continue;
+          const int s = slot(f, d);
+          div = div + (F[d].f[s][up[d]] - F[d].f[s][c]) / g.dl[d];
+        }
+        out[f] = Uin.f[f][c] - dt * div;
+      }
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+        double curl = 0.0;
+        if (g.active[d]) {
+          if (g.active[t1]) curl = curl + (E[t2][up[t1]] - E[t2][c]) / g.dl[t1];
+          if (g.active[t2]) curl = curl - (E[t1][up[t2]] - E[t1][c]) / g.dl[t2];
+        } else {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            if (a == d || !g.active[a]) continue;
+            const int s = slot(5 + d, a);
+            curl = curl + (F[a].f[s][up[a]] - F[a].f[s][c]) / g.dl[a];
+          }
+        }
+        out[5 + d] = Uin.f[5 + d][c] - dt * curl;
+      }
+#pragma unroll
+      for (int f = 0; f < 8; ++f) Uout.f[f][c] = COMBINE ? w * out[f] + w0 * U0.f[f][c] : out[f];
+      double s = 0.0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (!g.active[d]) continue;
+        const double a = F[d].f[7][c], b = F[d].f[7][up[d]];
+        s = s + (a < b ? b : a) / g.dl[d];
+      }
+      return s;
+    }
+#endif
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
       if constexpr (std::is_same<T, double>::value) {
@@ -1043,7 +1092,11 @@ __global__ void __launch_bounds__(kThreads) k_inv_only(Geo g, Ptr8<const T> Fx, 
     for (int d = 0; d < 3; ++d)
       if (g.active[d]) {
         const int u = shifted(g, c, ijk[d], d, 1);
+#ifdef IDX_STRICT_ROUNDING
+        inv = inv + fmax(double(F[d].f[7][c]), double(F[d].f[7][u])) / g.dl[d];
+#else
         inv += fmax(double(F[d].f[7][c]), double(F[d].f[7][u])) * g.inv_dl[d];
+#endif
       }
   }
 #pragma unroll
@@ -1742,6 +1795,7 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
   for (int d = 0; d < 3; ++d) {
     g.active[d] = g.n[d] > 1;
     g.inv_dl[d] = (double)un[d] / l[d];
+    g.dl[d] = l[d] / (double)un[d];
     g.inv_dlf[d] = (float)g.inv_dl[d];
   }
   geo_set_gamma(g, gamma);
@@ -2252,7 +2306,87 @@ int idx_last_error_cell(const idx_sim* s, int64_t* cell) {
   return IDX_OK;
 }
 
+int idx_get_clock(const idx_sim* cs, idx_clock* clock) {
+  idx_sim* s = const_cast<idx_sim*>(cs);
+  if (!s || !clock) return IDX_EINVAL;
+  int rc = sync_ctrl(s);
+  if (rc != IDX_OK) return rc;
+  rc = pending_error(s);
+  if (rc != IDX_OK) return rc;
+  clock->t = s->host_ctrl->t;
+  std::memcpy(&clock->inv_dt, &s->host_ctrl->inv_prev, sizeof(double));
+  clock->nsteps = (int64_t)s->host_ctrl->nsteps;
+  return IDX_OK;
+}
+
+int idx_set_clock(idx_sim* s, const idx_clock* clock) {
+  if (!s || !clock || !std::isfinite(clock->t) || !(clock->inv_dt > 0.0) ||
+      !std::isfinite(clock->inv_dt) || clock->nsteps < 0)
+    return IDX_EINVAL;
+  int rc = sync_ctrl(s);
+  if (rc != IDX_OK) return rc;
+  rc = pending_error(s);
+  if (rc != IDX_OK) return rc;
+  Ctrl c = *s->host_ctrl;
+  c.t = clock->t;
+  std::memcpy(&c.inv_prev, &clock->inv_dt, sizeof(double));
+  c.nsteps = (long long)clock->nsteps;
+  c.done = 0;
+  IDX_TRY(cudaMemcpyAsync(s->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s->stream));
+  return sync_ctrl(s);
+}
+
 }  // extern "C"
+
+// ===========================================================================
+// idx_probe_bounded_wait: the bounded mbarrier wait of the staged sweeps, run alone in
+// one block, so that tests can make it expire without a fault.  The block initialises
+// an mbarrier, announces `announce` transaction bytes and issues no copy: with bytes
+// announced the phase cannot complete, the wait gives up after limit_ns, and the block
+// records IDX_ETIMEOUT in its control block through the same give-up path as the
+// sweeps (which waits once more, bounded, for copies in flight -- there are none).
+// With announce == 0 the phase completes at once and nothing is recorded.
+// ===========================================================================
+namespace {
+__global__ void k_wait_probe(Ctrl* ctrl, uint32_t announce, uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, announce);
+  const bool landed = mbar_wait(&bar, 0, limit_ns);
+  if (__syncthreads_or(!landed)) {
+    if (threadIdx.x == 0) flag_timeout(ctrl);
+    mbar_wait(&bar, 0, limit_ns);  // copies in flight: none were issued
+  }
+}
+}  // namespace
+
+extern "C" int idx_probe_bounded_wait(void* stream, uint32_t announce_bytes, double limit_ms) {
+  if (!(limit_ms > 0.0) || !(limit_ms <= 1000.0) || announce_bytes >= (1u << 20)) return IDX_EINVAL;
+  const cudaStream_t st = (cudaStream_t)stream;
+  Ctrl* d = nullptr;
+  if (cudaMallocAsync(&d, sizeof(Ctrl), st) != cudaSuccess) {
+    cudaGetLastError();
+    return IDX_ENOMEM;
+  }
+  Ctrl h;
+  std::memset(&h, 0, sizeof(h));
+  int rc = IDX_OK;
+  if (cudaMemcpyAsync(d, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, st) != cudaSuccess) rc = IDX_ECUDA;
+  if (rc == IDX_OK) {
+    k_wait_probe<<<1, 64, 0, st>>>(d, announce_bytes, (uint64_t)(limit_ms * 1e6));
+    if (cudaGetLastError() != cudaSuccess) rc = IDX_ECUDA;
+  }
+  if (rc == IDX_OK && cudaMemcpyAsync(&h, d, sizeof(Ctrl), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    rc = IDX_ECUDA;
+  cudaFreeAsync(d, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) rc = IDX_ECUDA;
+  if (rc != IDX_OK) return rc;
+  return h.err;
+}
 
 // ===========================================================================
 // idx_step_noalloc: one FP64 cycle on caller-owned device state with no allocation.
@@ -2273,20 +2407,46 @@ static_assert(sizeof(Ctrl) <= 256, "control block must fit its 256-byte slot");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // In host code g_noalloc_scratch names a host-side stand-in, not device memory: the
-// device address is looked up once per device (with that device current) and cached.
-constexpr int kNoAllocMaxDevices = 64;
-void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+// device address is looked up once per device and CUDA context (with that device
+// current) and cached.  Each context that loads the library's module has its own copy of
+// the array at its own address, so a caller that makes another context current (another
+// framework's own context) gets that context's copy.
+using CtxGetCurrent = CUresult (*)(CUcontext*);
+
+CtxGetCurrent ctx_get_current() {
+  static CtxGetCurrent fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrent>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+std::map<std::pair<int, CUcontext>, void*> g_noalloc_addr;
 std::mutex g_noalloc_mutex;
 
 int noalloc_scratch(int device, void** out) {
-  if (device < 0 || device >= kNoAllocMaxDevices) return IDX_EINVAL;
+  CtxGetCurrent get = ctx_get_current();
+  CUcontext ctx = nullptr;
+  // the runtime makes the device's primary context current on first use
+  if (cudaFree(nullptr) != cudaSuccess) return IDX_ECUDA;
+  if (!get || get(&ctx) != CUDA_SUCCESS) return IDX_ECUDA;
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_addr[device]) {
+  const auto key = std::make_pair(device, ctx);
+  auto it = g_noalloc_addr.find(key);
+  if (it == g_noalloc_addr.end()) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return IDX_ECUDA;
-    g_noalloc_addr[device] = p;
+    it = g_noalloc_addr.emplace(key, p).first;
   }
-  *out = g_noalloc_addr[device];
+  *out = it->second;
   return IDX_OK;
 }
 
@@ -2308,6 +2468,13 @@ extern "C" int idx_step_noalloc(const idx_grid* grid, double gamma, double cfl,
   }
   const long long ncell = (long long)grid->nx * grid->ny * grid->nz;
   if (ncell > IDX_NOALLOC_MAX_CELLS) return IDX_ETOOLARGE;
+  {
+    // the call reads back the control block and waits for its stream: neither may be
+    // recorded into a graph, so a stream that is capturing is refused
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess) return IDX_ECUDA;
+    if (cap != cudaStreamCaptureStatusNone) return IDX_EINVAL;
+  }
 
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess) return IDX_ECUDA;
@@ -2332,6 +2499,7 @@ extern "C" int idx_step_noalloc(const idx_grid* grid, double gamma, double cfl,
   for (int d = 0; d < 3; ++d) {
     g.active[d] = g.n[d] > 1;
     g.inv_dl[d] = (double)g.n[d] / l[d];
+    g.dl[d] = l[d] / (double)g.n[d];
     g.inv_dlf[d] = (float)g.inv_dl[d];
   }
   geo_set_gamma(g, gamma);

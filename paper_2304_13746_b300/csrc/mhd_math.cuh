@@ -157,7 +157,11 @@ template <typename T> __device__ __forceinline__ T vanleer_half(T dl, T dr) {
 // and 0 * inf give NaN; a positive product bounds |dl + dr| >= 2 sqrt(dl dr) > 4e-162.
 template <> __device__ __forceinline__ double vanleer_half<double>(double dl, double dr) {
   const double prod = dl * dr;
+#ifdef IDX_STRICT_ROUNDING
+  return gt0(prod) ? prod / (dl + dr) : 0.0;  // one correctly rounded quotient
+#else
   return gt0(prod) ? prod * (1.0 / (dl + dr)) : 0.0;
+#endif
 }
 
 // x with its sign flipped where y is negative (x * sign(y), signed zeros included), on the
@@ -351,6 +355,160 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   }
 }
 
+#ifdef IDX_STRICT_ROUNDING
+// ---------------------------------------------------------------------------
+// Strict-rounding build (a test build, compiled with -fmad=false): the FP64 HLLD with
+// every formula of Miyoshi & Kusano (2005) evaluated in its plain written order -- each
+// quotient a correctly rounded division, both fast speeds with their own square roots,
+// both sides' star states in full, sums left to right -- so that this build rounds the
+// way a plain reading of the method does.  It exists to show, on the GPU, that what
+// separates the production kernels from such a reading is rounding order only: near the
+// single-star degeneracy (D -> 0) any reordering is amplified by ~1/|D|.
+// ---------------------------------------------------------------------------
+struct StarPlain {
+  double rho, v, w, by, bz, E;
+};
+
+__device__ __forceinline__ double energy_plain(const Side<double>& s, double bx, double gm1) {
+  return s.p / gm1 + 0.5 * s.r * (s.u * s.u + s.v * s.v + s.w * s.w) +
+         0.5 * (bx * bx + s.b1 * s.b1 + s.b2 * s.b2);
+}
+
+__device__ __forceinline__ double fast_plain(const Side<double>& s, double bx, double gamma) {
+  const double gp = gamma * s.p;
+  const double b2 = bx * bx + s.b1 * s.b1 + s.b2 * s.b2;
+  const double a = gp + b2;
+  const double disc = a * a - 4.0 * gp * bx * bx;
+  return sqrt((a + sqrt(disc > 0.0 ? disc : 0.0)) / (2.0 * s.r));
+}
+
+__device__ __forceinline__ void flux_plain(const Side<double>& s, double bx, double E,
+                                           double F[7]) {
+  const double pT = s.p + 0.5 * (bx * bx + s.b1 * s.b1 + s.b2 * s.b2);
+  const double vb = s.u * bx + s.v * s.b1 + s.w * s.b2;
+  F[0] = s.r * s.u;
+  F[1] = s.r * s.u * s.u + pT - bx * bx;
+  F[2] = s.r * s.u * s.v - bx * s.b1;
+  F[3] = s.r * s.u * s.w - bx * s.b2;
+  F[4] = (E + pT) * s.u - bx * vb;
+  F[5] = s.b1 * s.u - bx * s.v;
+  F[6] = s.b2 * s.u - bx * s.w;
+}
+
+// max(|S_L|, |S_R|) of the outer speeds (MK05 eq. 67), plain form; also returns S_L, S_R
+__device__ __forceinline__ double outer_plain(const Side<double>& L, const Side<double>& R,
+                                              double bx, double gamma, double& SL, double& SR) {
+  const double cfL = fast_plain(L, bx, gamma), cfR = fast_plain(R, bx, gamma);
+  const double cfm = cfL < cfR ? cfR : cfL;
+  SL = (R.u < L.u ? R.u : L.u) - cfm;
+  SR = (L.u < R.u ? R.u : L.u) + cfm;
+  const double aL = fabs(SL), aR = fabs(SR);
+  return aL < aR ? aR : aL;
+}
+
+__device__ __forceinline__ void hlld_plain(const Side<double>& L, const Side<double>& R,
+                                           double bx, double gamma, double F[7], double& c) {
+  const double gm1 = gamma - 1.0;
+  const double EL = energy_plain(L, bx, gm1), ER = energy_plain(R, bx, gm1);
+  const double bx2 = bx * bx;
+  const double pTL = L.p + 0.5 * (bx2 + L.b1 * L.b1 + L.b2 * L.b2);
+  const double pTR = R.p + 0.5 * (bx2 + R.b1 * R.b1 + R.b2 * R.b2);
+  double SL, SR;
+  c = outer_plain(L, R, bx, gamma, SL, SR);
+  double FL[7], FR[7];
+  flux_plain(L, bx, EL, FL);
+  flux_plain(R, bx, ER, FR);
+  if (SL > 0.0) {
+    for (int q = 0; q < 7; ++q) F[q] = FL[q];
+    return;
+  }
+  if (SR < 0.0) {
+    for (int q = 0; q < 7; ++q) F[q] = FR[q];
+    return;
+  }
+  const double UL[7] = {L.r, L.r * L.u, L.r * L.v, L.r * L.w, EL, L.b1, L.b2};
+  const double UR[7] = {R.r, R.r * R.u, R.r * R.v, R.r * R.w, ER, R.b1, R.b2};
+  // contact speed and star total pressure (MK05 eqs. 38, 41)
+  const double aL = (SL - L.u) * L.r, aR = (SR - R.u) * R.r;
+  const double SM = (aR * R.u - aL * L.u - pTR + pTL) / (aR - aL);
+  const double pTs = pTL + L.r * (SL - L.u) * (SM - L.u);
+  // single-star states (MK05 eqs. 43-48)
+  auto star = [&](const Side<double>& s, double S, double E, double pT) {
+    StarPlain o;
+    const double su = S - s.u, ssm = S - SM;
+    o.rho = s.r * su / ssm;
+    const double D = s.r * su * ssm - bx2;
+    const double scale = fabs(s.r * su * ssm) + bx2;
+    if (fabs(D) <= Eps<double>::degen * scale) {
+      o.v = s.v; o.w = s.w; o.by = s.b1; o.bz = s.b2;
+    } else {
+      o.v = s.v - bx * s.b1 * (SM - s.u) / D;
+      o.w = s.w - bx * s.b2 * (SM - s.u) / D;
+      const double num = s.r * su * su - bx2;
+      o.by = s.b1 * num / D;
+      o.bz = s.b2 * num / D;
+    }
+    const double vb = s.u * bx + s.v * s.b1 + s.w * s.b2;
+    const double vbs = SM * bx + o.v * o.by + o.w * o.bz;
+    o.E = (su * E - pT * s.u + pTs * SM + bx * (vb - vbs)) / ssm;
+    return o;
+  };
+  const StarPlain sl = star(L, SL, EL, pTL), sr = star(R, SR, ER, pTR);
+  const double UsL[7] = {sl.rho, sl.rho * SM, sl.rho * sl.v, sl.rho * sl.w, sl.E, sl.by, sl.bz};
+  const double UsR[7] = {sr.rho, sr.rho * SM, sr.rho * sr.v, sr.rho * sr.w, sr.E, sr.by, sr.bz};
+  // double-star states (MK05 eqs. 51, 59-63), skipped in the HLLC limit
+  const double sqL = sqrt(sl.rho), sqR = sqrt(sr.rho);
+  const double SsL = SM - fabs(bx) / sqL, SsR = SM + fabs(bx) / sqR;
+  double UssL[7], UssR[7];
+  if (0.5 * bx2 < Eps<double>::hllc * pTs) {
+    for (int q = 0; q < 7; ++q) { UssL[q] = UsL[q]; UssR[q] = UsR[q]; }
+  } else {
+    const double sgn = bx < 0.0 ? -1.0 : 1.0;
+    const double isum = 1.0 / (sqL + sqR);
+    const double v2 = (sqL * sl.v + sqR * sr.v + (sr.by - sl.by) * sgn) * isum;
+    const double w2 = (sqL * sl.w + sqR * sr.w + (sr.bz - sl.bz) * sgn) * isum;
+    const double by2 = (sqL * sr.by + sqR * sl.by + sqL * sqR * (sr.v - sl.v) * sgn) * isum;
+    const double bz2 = (sqL * sr.bz + sqR * sl.bz + sqL * sqR * (sr.w - sl.w) * sgn) * isum;
+    const double vb2 = SM * bx + v2 * by2 + w2 * bz2;
+    const double vbL = SM * bx + sl.v * sl.by + sl.w * sl.bz;
+    const double vbR = SM * bx + sr.v * sr.by + sr.w * sr.bz;
+    const double E2L = sl.E - sqL * (vbL - vb2) * sgn;
+    const double E2R = sr.E + sqR * (vbR - vb2) * sgn;
+    UssL[0] = sl.rho; UssL[1] = sl.rho * SM; UssL[2] = sl.rho * v2; UssL[3] = sl.rho * w2;
+    UssL[4] = E2L; UssL[5] = by2; UssL[6] = bz2;
+    UssR[0] = sr.rho; UssR[1] = sr.rho * SM; UssR[2] = sr.rho * v2; UssR[3] = sr.rho * w2;
+    UssR[4] = E2R; UssR[5] = by2; UssR[6] = bz2;
+  }
+  // flux of the region that holds x/t = 0 (MK05 eq. 66)
+  if (SsL >= 0.0) {
+    for (int q = 0; q < 7; ++q) F[q] = FL[q] + SL * (UsL[q] - UL[q]);
+  } else if (SM >= 0.0) {
+    for (int q = 0; q < 7; ++q) F[q] = FL[q] + SL * (UsL[q] - UL[q]) + SsL * (UssL[q] - UsL[q]);
+  } else if (SsR >= 0.0) {
+    for (int q = 0; q < 7; ++q) F[q] = FR[q] + SR * (UsR[q] - UR[q]) + SsR * (UssR[q] - UsR[q]);
+  } else {
+    for (int q = 0; q < 7; ++q) F[q] = FR[q] + SR * (UsR[q] - UR[q]);
+  }
+}
+
+// E^c edge EMF (Gardiner & Stone 2005) in its written form, with the one-sided
+// derivatives 2 (a - b) / d and the corrections (d / 8)(q3 - q1); arguments as emf_ec,
+// da and db the cell sizes along a and b.
+__device__ __forceinline__ double emf_ec_plain(double X0, double X1, double Y0, double Y1,
+                                               double C00, double C01, double C10, double C11,
+                                               double Fa0, double Fa1, double Fb0, double Fb1,
+                                               double da, double db) {
+  auto pick = [](double f, double up, double dn) {
+    return f > 0.0 ? up : (f < 0.0 ? dn : 0.5 * (up + dn));
+  };
+  const double dB1 = pick(Fa0, 2.0 * (C10 - Y1) / db, 2.0 * (C00 - Y0) / db);
+  const double dB3 = pick(Fa1, 2.0 * (Y1 - C11) / db, 2.0 * (Y0 - C01) / db);
+  const double dA1 = pick(Fb0, 2.0 * (C01 - X1) / da, 2.0 * (C00 - X0) / da);
+  const double dA3 = pick(Fb1, 2.0 * (X1 - C11) / da, 2.0 * (X0 - C10) / da);
+  return 0.25 * (X0 + X1 + Y0 + Y1) + (db / 8.0) * (dB3 - dB1) + (da / 8.0) * (dA3 - dA1);
+}
+#endif  // IDX_STRICT_ROUNDING
+
 // The two more diffusive solvers of the paper's list (Sec. 2.3), same interface as hlld
 // and the same outer speed estimates (so the CFL speed c does not depend on the solver):
 //   Rusanov:  F = (F_L + F_R)/2 - (S_max/2)(U_R - U_L), S_max = max(|u_L|+c_fL, |u_R|+c_fR)
@@ -445,6 +603,14 @@ __device__ __forceinline__ void hll(const Side<T>& L, const Side<T>& R, T bx, T 
 template <typename T>
 __device__ __forceinline__ T outer_speed(int solver, const Side<T>& L, const Side<T>& R, T bx,
                                          T gamma) {
+#ifdef IDX_STRICT_ROUNDING
+  if constexpr (sizeof(T) == 8) {
+    if (solver == 4) {
+      double SL, SR;
+      return outer_plain(L, R, bx, gamma, SL, SR);
+    }
+  }
+#endif
   T cfm;
   if (solver == 4) {
     const T bx2 = bx * bx;
@@ -470,6 +636,14 @@ __device__ __forceinline__ T outer_speed(int solver, const Side<T>& L, const Sid
 template <typename T>
 __device__ __forceinline__ void riemann_flux(int solver, const Side<T>& L, const Side<T>& R, T bx,
                                              T gamma, T gm1inv, T F[7], T& c) {
+#ifdef IDX_STRICT_ROUNDING
+  if constexpr (sizeof(T) == 8) {
+    if (solver == 4) {
+      hlld_plain(L, R, bx, gamma, F, c);
+      return;
+    }
+  }
+#endif
   if (solver == 4) hlld(L, R, bx, gamma, gm1inv, F, c);
   else if (solver == 2) hll(L, R, bx, gamma, gm1inv, F, c);
   else rusanov(L, R, bx, gamma, gm1inv, F, c);

@@ -13,6 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libidx.so")
 
 IDX_OK, IDX_EINVAL, IDX_ENOMEM, IDX_ENONPHYS, IDX_ECUDA, IDX_ETIMEOUT = 0, -1, -2, -3, -4, -5
+IDX_ETOOLARGE = -6
 IDX_FP64, IDX_FP32_BULK = 0, 1
 PRECISIONS = {"fp64": IDX_FP64, "fp32": IDX_FP32_BULK, "fp32_bulk": IDX_FP32_BULK}
 RIEMANN = {"rusanov": 1, "hll": 2, "hlld": 4}
@@ -47,6 +48,11 @@ class Solver(ctypes.Structure):
     _fields_ = [("recon", ctypes.c_int), ("riemann", ctypes.c_int), ("emf", ctypes.c_int),
                 ("rk_order", ctypes.c_int), ("cfl", ctypes.c_double), ("precision", ctypes.c_int),
                 ("induction", ctypes.c_int)]
+
+
+class Clock(ctypes.Structure):
+    """idx_clock: simulated time, carried inverse CFL time (Eq. 10), cycle count."""
+    _fields_ = [("t", ctypes.c_double), ("inv_dt", ctypes.c_double), ("nsteps", ctypes.c_int64)]
 
 
 P8 = ctypes.c_void_p * 8
@@ -98,6 +104,9 @@ def lib(path=LIB_PATH):
     L.idx_batch_set_shapes.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.idx_batch_destroy.argtypes = [vp]
     L.idx_batch_destroy.restype = None
+    L.idx_get_clock.argtypes = [vp, ctypes.POINTER(Clock)]
+    L.idx_set_clock.argtypes = [vp, ctypes.POINTER(Clock)]
+    L.idx_probe_bounded_wait.argtypes = [vp, ctypes.c_uint32, ctypes.c_double]
     _lib = L
     return L
 
@@ -114,6 +123,13 @@ def pipe_rates():
         raise IdxError(rc, "idx_pipe_rates")
     keys = ("fma64", "div64", "sqrt64", "fma32", "div32", "sqrt32")
     return dict(zip(keys, out[:]))
+
+
+def probe_bounded_wait(announce_bytes, limit_ms, stream=None):
+    """Run the library's bounded mbarrier wait alone (idx_probe_bounded_wait); returns the
+    code it ends with: IDX_ETIMEOUT when bytes were announced and never arrive, else IDX_OK."""
+    return lib().idx_probe_bounded_wait(ctypes.c_void_p(stream) if stream else None,
+                                        int(announce_bytes), float(limit_ms))
 
 
 def footprint(shape, precision="fp64", rk_order=2, induction="field", riemann="hlld",
@@ -297,6 +313,17 @@ class Sim:
         n = ctypes.c_int64()
         self._check(lib().idx_step_count(self._h, ctypes.byref(n)), "idx_step_count")
         return n.value
+
+    def get_clock(self):
+        """(t, inv_dt, nsteps): the time-stepping state to store beside the fields."""
+        c = Clock()
+        self._check(lib().idx_get_clock(self._h, ctypes.byref(c)), "idx_get_clock")
+        return c.t, c.inv_dt, c.nsteps
+
+    def set_clock(self, clock):
+        """Restore (t, inv_dt, nsteps) after set_state, to continue a stored run."""
+        c = Clock(*clock)
+        self._check(lib().idx_set_clock(self._h, ctypes.byref(c)), "idx_set_clock")
 
     def time(self):
         t, dt = ctypes.c_double(), ctypes.c_double()

@@ -137,3 +137,21 @@ def test_footprint_of_a_padded_grid(L):
     padded = 8 * 20 * 36
     assert got == pytest.approx(per_cell * padded + 256, rel=1e-3)
     assert idx.footprint((1, 16, 32), bc=(0, 0, 1)) == idx.footprint((1, 16, 32))
+
+
+def test_clock_and_probe_reject_bad_arguments_without_a_gpu(L):
+    c = idx.Clock(0.0, 1.0, 0)
+    assert L.idx_get_clock(None, ctypes.byref(c)) == idx.IDX_EINVAL
+    assert L.idx_set_clock(None, ctypes.byref(c)) == idx.IDX_EINVAL
+    # limits are checked before any device call
+    assert L.idx_probe_bounded_wait(None, 64, 0.0) == idx.IDX_EINVAL
+    assert L.idx_probe_bounded_wait(None, 64, 2000.0) == idx.IDX_EINVAL
+    assert L.idx_probe_bounded_wait(None, 1 << 20, 1.0) == idx.IDX_EINVAL
+
+
+def test_strict_rounding_build_exports_the_same_entry_points():
+    # the test build of tests/test_gpu_strict_rounding.py; loaded here by ctypes alone
+    path = idx_build.build(variant="strict")
+    S = ctypes.CDLL(path)
+    for n in declared_symbols():
+        assert hasattr(S, n), n

@@ -62,3 +62,22 @@ def test_reference_arm_under_torchrun_two_ranks():
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["reference_sample"]["cells_per_step"] == bench.REFERENCE_SAMPLE_N ** 3
+    assert d["config"] == bench.workload_config(bench.parse_args_for_test())
+
+
+def test_roofline_of_a_cycle_picks_the_slowest_bound():
+    rates = {"fma64": 500e9, "fma32": 32e12}
+    counts = {"cycle_flops": 3000.0, "fp64_island_flops": 100.0}
+    # FP64: 3000 flop at 1 TFLOP/s = 3 ns against 320 B at 6.4 TB/s = 0.05 ns
+    r = bench.roofline_cycle(1e8, counts, rates, 6400.0, "fp64")
+    assert r["bound"] == "fp64"
+    assert r["ns_per_cell_update"]["fp64"] == pytest.approx(3.0)
+    assert r["frac"] == pytest.approx(1e8 * 3e-9)
+    # FP32 bulk: islands 100 flop at 1 TFLOP/s = 0.1 ns, 2900 flop at 64 TFLOP/s = 0.045 ns,
+    # HBM 0.05 ns: the FP64 islands bind
+    r = bench.roofline_cycle(5e9, counts, rates, 6400.0, "fp32")
+    assert r["bound"] == "fp64"
+    assert r["ns_per_cell_update"]["fp32"] == pytest.approx(2900 / 64e12 * 1e9)
+    assert r["ns_per_cell_update"]["hbm"] == pytest.approx(320 / 6400e9 * 1e9)
+    assert r["frac"] == pytest.approx(5e9 * 0.1e-9)

@@ -151,6 +151,13 @@ def test_whole_cycle_count_on_a_supersonic_box_is_the_sum_of_hand_counts():
         h, r = oracle.count_faces(cons, lengths, GAMMA, d)
         assert h == HLLD_SUPERSONIC_L
         assert r == plus(times(VL_FLAT, 14), times(FACE_VALUE, 14))
+        split = oracle.count_faces_parts(cons, lengths, GAMMA, d)
+        assert split == {"riemann": HLLD_SUPERSONIC_L, "slope": times(VL_FLAT, 14),
+                         "face": times(FACE_VALUE, 14)}
+        # per face, each of the 7 + 7 slopes counted once: 7 of the 14 evaluations
+        assert oracle.algorithmic_face_flops(split) == (oracle.flops(HLLD_SUPERSONIC_L) +
+                                                        14 * oracle.flops(FACE_VALUE) +
+                                                        7 * oracle.flops(VL_FLAT))
 
 
 def test_algorithmic_count_removes_exactly_the_repeated_slopes_and_cell_emfs():

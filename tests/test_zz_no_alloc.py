@@ -4,8 +4,10 @@ idx_step_noalloc serves callers that cannot allocate device memory (another fram
 pool, a device budget, a latency-bound path): its scratch is a fixed device array in
 the library.  Two calls in a row on caller-owned device state must match two idx_step
 cycles of a sim made from the same state, within the parity bound used for the GPU
-path (1e-12 of each field's scale), including the carried inverse CFL time; a grid above
-IDX_NOALLOC_MAX_CELLS must be refused.  This file is collected last on purpose.
+path (1e-12 of each field's scale), including the carried inverse CFL time -- also for a
+2D grid right after a 3D one, a non-cubic grid and a side stream, with the device's free
+memory and torch's allocations unchanged across calls; a grid above IDX_NOALLOC_MAX_CELLS
+and a capturing stream must be refused.  This file is collected last on purpose.
 """
 import ctypes
 
@@ -68,6 +70,80 @@ def test_noalloc_two_cycles_match_idx_step():
         assert dt.value == pytest.approx(dt_ref, rel=1e-14)
         assert ref.time()[1] == pytest.approx(0.4 / inv.value, rel=1e-14)
     ref.close()
+
+
+def _noalloc_cycles(L, ic, ncycles, stream=None):
+    """ncycles calls of idx_step_noalloc on device copies of ic's state against idx_step;
+    returns the worst field error and asserts dt and the carried bound each call."""
+    import torch
+    cons = oracle.cons_from_prims(ic.prim, ic.lengths, ic.gamma)
+    nz, ny, nx = ic.shape
+    grid = idx.Grid(nx, ny, nz, *ic.lengths)
+    ref = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4)
+    ref.set_state(cons)
+    state = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in cons]
+    torch.cuda.synchronize()
+    ptrs = idx.P8(*[t.data_ptr() for t in state])
+    inv = ctypes.c_double(0.0)
+    worst = 0.0
+    free_before = alloc_before = None
+    for call in range(ncycles):
+        dt_ref = ref.step(want_dt=True)
+        want = ref.get_state()
+        torch.cuda.synchronize()
+        if call == 1:
+            # from the second call on, nothing new may appear on the device
+            free_before = torch.cuda.mem_get_info()[0]
+            alloc_before = torch.cuda.memory_allocated()
+        dt = ctypes.c_double()
+        rc = L.idx_step_noalloc(ctypes.byref(grid), ic.gamma, 0.4, ptrs, ctypes.byref(inv),
+                                ctypes.byref(dt), stream)
+        assert rc == idx.IDX_OK, rc
+        got = [t.cpu().numpy() for t in state]
+        sc = _scales(want)
+        err = max(float(np.max(np.abs(got[f] - want[f]))) / sc[f] for f in range(8))
+        assert err <= 1e-12, (call, err)
+        worst = max(worst, err)
+        assert dt.value == pytest.approx(dt_ref, rel=1e-14)
+        assert ref.time()[1] == pytest.approx(0.4 / inv.value, rel=1e-14)
+    torch.cuda.synchronize()
+    if free_before is not None:
+        assert torch.cuda.mem_get_info()[0] == free_before
+        assert torch.cuda.memory_allocated() == alloc_before
+    ref.close()
+    return worst
+
+
+def test_noalloc_after_a_3d_call_runs_2d_non_cubic_and_side_stream_grids():
+    # the shared array keeps the previous call's contents: a 2D grid right after a 3D one
+    # (its inactive direction's arrays hold 3D leftovers), a non-cubic grid, and calls on
+    # a side stream must each match idx_step
+    import torch
+    L = _lib()
+    _noalloc_cycles(L, inputs.turbulent_box(40, seed=11), 2)
+    _noalloc_cycles(L, inputs.orszag_tang_2d(64), 3)
+    _noalloc_cycles(L, inputs.random_smooth((20, 24, 28), seed=8, lengths=(1.0, 0.9, 0.7)), 3)
+    side = torch.cuda.Stream()
+    _noalloc_cycles(L, inputs.turbulent_box(32, seed=12), 3, stream=side.cuda_stream)
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    import torch
+    L = _lib()
+    ic = inputs.random_smooth((8, 8, 8), seed=2)
+    nz, ny, nx = ic.shape
+    grid = idx.Grid(nx, ny, nz, *ic.lengths)
+    inv = ctypes.c_double(0.0)
+    dummy = idx.P8(*([1] * 8))                       # never dereferenced: refused first
+    side = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            rc = L.idx_step_noalloc(ctypes.byref(grid), ic.gamma, 0.4, dummy, ctypes.byref(inv),
+                                    None, ctypes.c_void_p(side.cuda_stream))
+            torch.zeros(1, device="cuda")          # something for the graph to hold
+    assert rc == idx.IDX_EINVAL
+    assert inv.value == 0.0
 
 
 def test_noalloc_refuses_grids_above_its_limit():
