@@ -195,8 +195,10 @@ int idx_set_clock(idx_sim* sim, const idx_clock* clock);
 /* Device time per launch of each kernel of the stage, averaged over the 2 * reps stages
  * of `reps` cycles launched kernel by kernel with CUDA events between them on the sim's
  * stream: ms[0] primitive recovery, [1] x sweep (PLM + HLLD), [2] y sweep, [3] z sweep,
- * [4] E^c edge EMFs, [5] update (0 for a direction that is not integrated).  The cycles
- * are real: the sim advances by `reps` cycles.  A measurement aid, not part of the method. */
+ * [4] E^c edge EMFs, [5] update (0 for a direction that is not integrated).  With the fused
+ * FP32-bulk stage (idx_stage_kernels) ms[5] is the fused kernel and ms[1..4] are 0.  The
+ * cycles are real: the sim advances by `reps` cycles.  A measurement aid, not part of the
+ * method. */
 int idx_kernel_times(idx_sim* sim, int reps, double ms[6]);
 
 /* Sweep shape per direction chosen by the autotuner, which runs before a sim's first
@@ -225,6 +227,20 @@ int idx_sweep_shapes(const idx_sim* sim, int shapes[3]);
  * (with LimO3, anything but 16, 32, 116 or 132).
  * A measurement and testing aid, not part of the method; call it before stepping. */
 int idx_set_sweep_shapes(idx_sim* sim, const int shapes[3]);
+
+/* The FP32-bulk stage as one fused kernel: for every-direction-integrated PLM field-form
+ * grids with nx % 32 == 0 and ny % 8 == 0, a CTA stages 32 x 8 tiles of the primitives
+ * (with their 2-cell periodic halo) plane by plane into shared memory by bulk tensor
+ * copies, forms the x/y/z Riemann fluxes, the E^c EMFs and the update of its cells there,
+ * and writes only the new state; the primitive recovery stays a kernel of its own.
+ * mode: 0 automatic (the split kernels, which are faster on this GPU), 1 the split kernels
+ * (primitives, three sweeps, E^c, update), 2 the fused kernel (IDX_EINVAL where it does not
+ * fit).  The two do the same arithmetic per face, edge and cell in the same order.
+ * A measurement and testing aid; call it before stepping. */
+int idx_set_stage_kernels(idx_sim* sim, int mode);
+
+/* *fused_in_use = 1 if the sim's stages run the fused kernel, else 0. */
+int idx_stage_kernels(const idx_sim* sim, int* fused_in_use);
 
 /* Free the sim and its device memory (and its stream, if the library made it). */
 void idx_destroy(idx_sim* sim);

@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdint>
@@ -1148,6 +1149,8 @@ __device__ __forceinline__ void end_body(Ctrl* c) {
 __global__ void k_begin(Ctrl* c) { begin_body(c); }
 __global__ void k_end(Ctrl* c) { end_body(c); }
 
+#include "fused_stage.cuh"
+
 }  // namespace
 
 // ===========================================================================
@@ -1194,6 +1197,12 @@ struct idx_sim {
   CUtensorMap tm_halo[3];     // per direction: box of the 2 halo rows
   bool tma_ok[3][2];          // maps encoded for L = 16 / 32 and nx % 32 == 0
   bool tuned;
+  // FP32 bulk: the fused stage kernel (k_stage_fused) in place of the sweeps, E^c and update
+  FusedMaps fmaps;            // primitive-plane boxes of its tiles
+  bool fused_ok;              // the grid and solver fit it
+  int fused_zc;               // z-planes per CTA
+  int stage_mode;             // 0 automatic, 1 split kernels, 2 fused kernel
+  bool use_fused;             // the choice the captured cycle holds
 };
 
 namespace {
@@ -1255,6 +1264,10 @@ void launch_tma(idx_sim* s, const double* bface, const Ptr8<T>& F, int check_dt)
 
 // The FP64 tile of 32 rows takes 63 KB of shared memory, above the 48 KB default.
 void allow_tma_smem() {
+  cudaFuncSetAttribute(k_stage_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)fused::SMEM_BYTES);
+  cudaFuncSetAttribute(k_stage_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)fused::SMEM_BYTES);
   const int big = 7 * (32 + 4) * 32 * (int)sizeof(double);
   cudaFuncSetAttribute(k_sweep_tma<double, 1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_sweep_tma<double, 2, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -1492,9 +1505,40 @@ void launch_fill_ghosts(idx_sim* s, const Ptr8<double>& U) {
   }
 }
 
+// The fused FP32-bulk stage: primitives (without the cell-centre EMFs, which the fused
+// kernel forms from the primitives in shared memory), then one kernel for the rest.
+void launch_fused(idx_sim* s, const StagePlan& p, int st, double dt_fixed = 0.0) {
+  const Geo& g = s->geo;
+  const Ptr8<double>& Uin = *p.in[st];
+  const unsigned blocks = (unsigned)((g.n[0] / fused::TX) * (g.n[1] / fused::TY) *
+                                     (g.n[2] / s->fused_zc));
+  if (st > 0)
+    k_stage_fused<true><<<blocks, fused::NT, fused::SMEM_BYTES, s->stream>>>(
+        g, s->fmaps, Uin.f[5], Uin.f[6], Uin.f[7], cst(Uin), cst(s->U), *p.out[st], s->ctrl,
+        s->fused_zc, p.w[st], p.w0[st], dt_fixed);
+  else
+    k_stage_fused<false><<<blocks, fused::NT, fused::SMEM_BYTES, s->stream>>>(
+        g, s->fmaps, Uin.f[5], Uin.f[6], Uin.f[7], cst(Uin), cst(s->U), *p.out[st], s->ctrl,
+        s->fused_zc, p.w[st], p.w0[st], dt_fixed);
+}
+
+void launch_prims_only(idx_sim* s, const Ptr8<double>& Uin, int check_dt) {
+  const Geo& g = s->geo;
+  k_prims<float><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), s->Wf,
+                                                                  CellEmf<float>{}, s->ctrl,
+                                                                  check_dt);
+}
+
 template <typename T>
 void launch_stage(idx_sim* s, const StagePlan& p, int st, const Ptr8<T>& W, Ptr8<T>* F, T** E) {
   launch_fill_ghosts(s, *p.in[st]);
+  if constexpr (std::is_same<T, float>::value) {
+    if (s->use_fused) {
+      launch_prims_only(s, *p.in[st], 1);
+      launch_fused(s, p, st);
+      return;
+    }
+  }
   launch_fluxes<T>(s, *p.in[st], W, F, 1, true);
   launch_emf<T>(s, p, st, W, F, E);
   launch_update<T>(s, p, st, F, E);
@@ -1526,7 +1570,16 @@ std::mutex g_tune_mutex;
 // Tune the sweep shapes of a sim before its first stepping (sims stepped only inside a
 // batch never need it).  The tuning sweeps recompute the current state's fluxes into
 // scratch; the cycle recomputes everything it reads.
+// The fused stage kernel runs only when asked for (idx_set_stage_kernels): it does the
+// split kernels' arithmetic bit for bit, but measured 2x slower at 256^3 (4.4 ms against
+// 2.2 ms for the sweeps, E^c and update it replaces) -- its halo faces and per-face address
+// arithmetic make it instruction-bound at two CTAs per SM.
+void choose_stage_kernels(idx_sim* s) {
+  s->use_fused = s->fused_ok && s->stage_mode == 2;
+}
+
 int tune_once(idx_sim* s) {
+  choose_stage_kernels(s);
   if (s->tuned) return IDX_OK;
   s->tuned = true;
   if (s->geo.ncell < kTuneMinCells) return IDX_OK;
@@ -1718,6 +1771,43 @@ void encode_sweep_maps(idx_sim* s, void* wbase, size_t elem, size_t field_stride
   }
 }
 
+// The fused FP32-bulk stage: fits every-direction-integrated PLM field-form grids with
+// nx % 32 == 0 and ny % 8 == 0 (padded grids included: their ghosts are refilled before
+// the stage), with a z-chunk that divides nz.  The chunk is the longest of 32, 16, 8, 4, 2
+// that still gives every SM two CTAs, so small grids trade some recomputation for work.
+void encode_fused_maps(idx_sim* s, void* wbase, size_t field_stride) {
+  const Geo& g = s->geo;
+  s->fused_ok = false;
+  s->fused_zc = 0;
+  if (s->solver.recon != 1 || s->pot || !g.active[0] || !g.active[1] || !g.active[2]) return;
+  if (g.n[0] % fused::TX != 0 || g.n[1] % fused::TY != 0) return;
+  const long tiles_xy = (long)(g.n[0] / fused::TX) * (g.n[1] / fused::TY);
+  int zc = 0;
+  for (const int c : {32, 16, 8, 4, 2}) {
+    if (g.n[2] % c != 0) continue;
+    zc = c;
+    if (tiles_xy * (g.n[2] / c) >= 2L * (s->nsm > 0 ? s->nsm : 148)) break;
+  }
+  if (zc == 0) return;
+  EncodeTiled enc = tensor_map_encoder();
+  if (!enc) return;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2], 8};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.n[0] * sizeof(float),
+                                 (cuuint64_t)g.n[0] * g.n[1] * sizeof(float),
+                                 (cuuint64_t)field_stride};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const cuuint32_t bx[2] = {4, (cuuint32_t)fused::TX}, by[2] = {2, (cuuint32_t)fused::TY};
+  for (int m = 0; m < 4; ++m) {
+    const cuuint32_t box[4] = {bx[m & 1], by[m >> 1], 1, 8};
+    if (enc(&s->fmaps.box[m], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, wbase, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return;
+  }
+  s->fused_zc = zc;
+  s->fused_ok = true;
+}
+
 // Boundary kinds of a grid (periodic along a one-cell direction) and the padded cell
 // counts; false for an unknown kind or a non-periodic direction of fewer than 2 cells.
 bool grid_bc(const idx_grid* grid, int bc[3], int pn[3]) {
@@ -1856,6 +1946,7 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
   s->ctrl = (Ctrl*)p;
   if (f32) encode_sweep_maps(s, s->Wf.f[0], sizeof(float), arr_t);
   else encode_sweep_maps(s, s->Wd.f[0], sizeof(double), arr_t);
+  if (f32) encode_fused_maps(s, s->Wf.f[0], arr_t);
   allow_tma_smem();
   int rc = IDX_OK;
   if (cudaMallocHost(&s->host_ctrl, sizeof(Ctrl)) != cudaSuccess) rc = IDX_ENOMEM;
@@ -2197,6 +2288,19 @@ int idx_kernel_times(idx_sim* s, int reps, double ms[6]) {
       const Ptr8<double>& Uin = *plan.in[st];
       launch_fill_ghosts(s, Uin);
       IDX_TRY(cudaEventRecord(ev[0], s->stream));
+      if (f32 && s->use_fused) {
+        // fused stage: primitives in ms[0], the fused kernel in ms[5], nothing in between
+        launch_prims_only(s, Uin, 1);
+        for (int q = 1; q <= 5; ++q) IDX_TRY(cudaEventRecord(ev[q], s->stream));
+        launch_fused(s, plan, st);
+        IDX_TRY(cudaEventRecord(ev[6], s->stream));
+        IDX_TRY(cudaEventSynchronize(ev[6]));
+        float t[6];
+        for (int q = 0; q < 6; ++q) IDX_TRY(cudaEventElapsedTime(&t[q], ev[q], ev[q + 1]));
+        for (int q = 0; q < 6; ++q) acc[q] += t[q];
+        ++n_stage;
+        continue;
+      }
       if (f32) {
         k_prims<float><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), s->Wf, s->Cf, s->ctrl, 1);
       } else {
@@ -2265,6 +2369,25 @@ int idx_set_sweep_shapes(idx_sim* s, const int shapes[3]) {
   // the captured cycle holds the old shapes
   if (s->exec) { cudaGraphExecDestroy(s->exec); s->exec = nullptr; }
   if (s->graph) { cudaGraphDestroy(s->graph); s->graph = nullptr; }
+  return IDX_OK;
+}
+
+int idx_set_stage_kernels(idx_sim* s, int mode) {
+  if (!s || mode < 0 || mode > 2) return IDX_EINVAL;
+  if (mode == 2 && !s->fused_ok) return IDX_EINVAL;
+  s->stage_mode = mode;
+  choose_stage_kernels(s);
+  // the captured cycle holds the old kernels
+  if (s->exec) { cudaGraphExecDestroy(s->exec); s->exec = nullptr; }
+  if (s->graph) { cudaGraphDestroy(s->graph); s->graph = nullptr; }
+  return IDX_OK;
+}
+
+int idx_stage_kernels(const idx_sim* cs, int* fused_in_use) {
+  idx_sim* s = const_cast<idx_sim*>(cs);
+  if (!s || !fused_in_use) return IDX_EINVAL;
+  choose_stage_kernels(s);
+  *fused_in_use = s->use_fused ? 1 : 0;
   return IDX_OK;
 }
 
@@ -2700,12 +2823,15 @@ template <typename T> __global__ void kb_gather(const BatchDev<T>* B) {
 
 }  // namespace
 
+constexpr int kSoloStreams = 4;
+
 struct idx_batch {
   int precision;
   cudaStream_t stream;
   bool own_stream;
-  cudaStream_t side = nullptr;  // the solo members' stages, forked from and joined to stream
-  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  // the solo members' stages, forked from and joined to stream over kSoloStreams streams
+  cudaStream_t side[kSoloStreams] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[kSoloStreams] = {};
   int device;
   int sms;
   std::vector<idx_sim*> sims;
@@ -2731,6 +2857,21 @@ struct idx_batch {
 namespace {
 
 template <typename T> InstT<T> inst_of(idx_sim* s);
+
+std::vector<std::vector<idx_sim*>> solo_lanes(const idx_batch* b) {
+  std::vector<idx_sim*> order(b->solo.begin(), b->solo.end());
+  std::stable_sort(order.begin(), order.end(), [](const idx_sim* a, const idx_sim* c) {
+    return a->geo.ncell > c->geo.ncell;
+  });
+  std::vector<std::vector<idx_sim*>> lanes(kSoloStreams);
+  std::vector<long long> load(kSoloStreams, 0);
+  for (idx_sim* s : order) {
+    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    lanes[k].push_back(s);
+    load[k] += s->geo.ncell;
+  }
+  return lanes;
+}
 
 // Members of at least this many cells run the single-sim kernels inside the batched cycle:
 // their own launch parameters and tuned shapes beat the work-list kernels once a member
@@ -2890,35 +3031,43 @@ template <typename T> void launch_batch_sweep(idx_batch* b, int d, int stage, in
   else launch_batch_sweep_d<T, 2>(b, sd, stage, check);
 }
 
-// The stages of every solo member's own cycle (its RK order and induction form), on the
-// batch's stream (and into its graph).
-void launch_solo_stages(idx_batch* b, cudaStream_t st) {
-  for (idx_sim* s : b->solo) {
-    const cudaStream_t own = s->stream;
-    s->stream = st;
-    const StagePlan p = stage_plan(s);
-    for (int st = 0; st < p.n; ++st) {
-      if (s->solver.precision == IDX_FP32_BULK) launch_stage<float>(s, p, st, s->Wf, s->Ff, s->Ef);
-      else launch_stage<double>(s, p, st, s->Wd, s->Fd, s->Ed);
-    }
-    s->stream = own;
+// The stages of one solo member's own cycle (its RK order and induction form), on stream
+// st (and into the batch's graph).
+void launch_solo_stages(idx_sim* s, cudaStream_t st) {
+  const cudaStream_t own = s->stream;
+  s->stream = st;
+  const StagePlan p = stage_plan(s);
+  for (int q = 0; q < p.n; ++q) {
+    if (s->solver.precision == IDX_FP32_BULK) launch_stage<float>(s, p, q, s->Wf, s->Ff, s->Ef);
+    else launch_stage<double>(s, p, q, s->Wd, s->Fd, s->Ed);
   }
+  s->stream = own;
 }
+
+// Solo members over the side streams: largest first, each onto the stream with the fewest
+// cells so far, so that members' kernels run side by side and fill each other's tails.
+std::vector<std::vector<idx_sim*>> solo_lanes(const idx_batch* b);
 
 // One batched cycle: every member's dt, then -- side by side -- both RK2 stages of the
 // work-list members on the batch stream and each solo member's own stages on the side
-// stream (they touch disjoint buffers and need only the dt), then every member's time and
-// speeds.  The solo kernels fill the SMs that the work-list kernels leave idle in their
-// tails; in the captured graph the fork and join are two edges.
+// streams (they touch disjoint buffers and need only the dt), then every member's time and
+// speeds.  The solo kernels fill the SMs that the work-list kernels and each other leave
+// idle in their tails; in the captured graph the forks and joins are edges.
 template <typename T> void launch_batch_cycle(idx_batch* b) {
   const BatchDev<T>* B = (const BatchDev<T>*)b->header;
   kb_begin<T><<<b->sms, kThreads, 0, b->stream>>>(B);
-  const bool fork = !b->solo.empty() && b->side;
+  const bool fork = !b->solo.empty() && b->side[0];
+  int used = 0;
   if (fork) {
     cudaEventRecord(b->fork_ev, b->stream);
-    cudaStreamWaitEvent(b->side, b->fork_ev, 0);
-    launch_solo_stages(b, b->side);
-    cudaEventRecord(b->join_ev, b->side);
+    const std::vector<std::vector<idx_sim*>> lanes = solo_lanes(b);
+    for (size_t k = 0; k < lanes.size(); ++k) {
+      if (lanes[k].empty()) continue;
+      cudaStreamWaitEvent(b->side[k], b->fork_ev, 0);
+      for (idx_sim* s : lanes[k]) launch_solo_stages(s, b->side[k]);
+      cudaEventRecord(b->join_ev[k], b->side[k]);
+      used |= 1 << k;
+    }
   }
   for (int st = 0; st < 2; ++st) {
     kb_prims<T><<<b->grid_cell, kThreads, 0, b->stream>>>(B, st, 1);
@@ -2927,8 +3076,12 @@ template <typename T> void launch_batch_cycle(idx_batch* b) {
     if (st == 0) kb_update<T, false><<<b->grid_cell, kThreads, 0, b->stream>>>(B);
     else kb_update<T, true><<<b->grid_cell, kThreads, 0, b->stream>>>(B);
   }
-  if (fork) cudaStreamWaitEvent(b->stream, b->join_ev, 0);
-  else launch_solo_stages(b, b->stream);
+  if (fork) {
+    for (int k = 0; k < kSoloStreams; ++k)
+      if (used & (1 << k)) cudaStreamWaitEvent(b->stream, b->join_ev[k], 0);
+  } else {
+    for (idx_sim* s : b->solo) launch_solo_stages(s, b->stream);
+  }
   kb_end<T><<<b->sms, kThreads, 0, b->stream>>>(B);
 }
 
@@ -3088,10 +3241,12 @@ int idx_batch_create(int precision, void* stream, idx_batch** out) {
       if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) rc = IDX_ECUDA;
     }
   }
-  if (rc == IDX_OK && (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
-                       cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
-                       cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming) != cudaSuccess))
+  if (rc == IDX_OK && cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess)
     rc = IDX_ECUDA;
+  for (int k = 0; k < kSoloStreams && rc == IDX_OK; ++k)
+    if (cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->join_ev[k], cudaEventDisableTiming) != cudaSuccess)
+      rc = IDX_ECUDA;
   if (rc == IDX_OK && cudaMalloc(&b->header, 256) != cudaSuccess) rc = IDX_ENOMEM;
   if (rc == IDX_OK) rc = precision == IDX_FP32_BULK ? batch_occupancy<float>(b) : batch_occupancy<double>(b);
   if (rc != IDX_OK) {
@@ -3105,7 +3260,8 @@ int idx_batch_create(int precision, void* stream, idx_batch** out) {
 void idx_batch_destroy(idx_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
-  if (b->side) cudaStreamSynchronize(b->side);
+  for (int k = 0; k < kSoloStreams; ++k)
+    if (b->side[k]) cudaStreamSynchronize(b->side[k]);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->lists) cudaFree(b->lists);
@@ -3113,8 +3269,10 @@ void idx_batch_destroy(idx_batch* b) {
   if (b->host_gather) cudaFreeHost(b->host_gather);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   if (b->fork_ev) cudaEventDestroy(b->fork_ev);
-  if (b->join_ev) cudaEventDestroy(b->join_ev);
-  if (b->side) cudaStreamDestroy(b->side);
+  for (int k = 0; k < kSoloStreams; ++k) {
+    if (b->join_ev[k]) cudaEventDestroy(b->join_ev[k]);
+    if (b->side[k]) cudaStreamDestroy(b->side[k]);
+  }
   delete b;
 }
 

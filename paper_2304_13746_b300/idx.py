@@ -104,6 +104,8 @@ def lib(path=LIB_PATH):
     L.idx_batch_set_shapes.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.idx_batch_destroy.argtypes = [vp]
     L.idx_batch_destroy.restype = None
+    L.idx_set_stage_kernels.argtypes = [vp, ctypes.c_int]
+    L.idx_stage_kernels.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.idx_get_clock.argtypes = [vp, ctypes.POINTER(Clock)]
     L.idx_set_clock.argtypes = [vp, ctypes.POINTER(Clock)]
     L.idx_probe_bounded_wait.argtypes = [vp, ctypes.c_uint32, ctypes.c_double]
@@ -308,6 +310,19 @@ class Sim:
         """Fix the sweep shapes (x, y, z) instead of autotuning them (see idx_sweep_shapes)."""
         arr = (ctypes.c_int * 3)(*[int(v) for v in shapes])
         self._check(lib().idx_set_sweep_shapes(self._h, arr), "idx_set_sweep_shapes")
+
+    STAGE_KERNELS = {"auto": 0, "split": 1, "fused": 2}
+
+    def set_stage_kernels(self, mode):
+        """FP32 bulk: "auto", "split" (six kernels per stage) or "fused" (idx_set_stage_kernels)."""
+        self._check(lib().idx_set_stage_kernels(self._h, self.STAGE_KERNELS[mode]),
+                    "idx_set_stage_kernels")
+
+    def stage_kernels(self):
+        """"fused" if the stages run the fused kernel, else "split"."""
+        v = ctypes.c_int()
+        self._check(lib().idx_stage_kernels(self._h, ctypes.byref(v)), "idx_stage_kernels")
+        return "fused" if v.value else "split"
 
     def step_count(self):
         n = ctypes.c_int64()
