@@ -61,6 +61,9 @@ def parse():
                    help="plain: the default line; batched / serve: that part alone, with all "
                         "its policies; accuracy: the FP32-bulk error budget")
     p.add_argument("--cycles", type=int, default=100, help="cycles per instance (batched mix)")
+    p.add_argument("--instances", type=int, default=64,
+                   help="batched mode: the first N instances of the 64-instance mix")
+    p.add_argument("--batch-precisions", default="fp64,fp32", help="precisions of the batched mode")
     p.add_argument("--serve-requests-fp32", type=int, default=16)
     p.add_argument("--serve-requests-fp64", type=int, default=6)
     p.add_argument("--budget-gb", type=float, default=120.0, help="HBM budget of the server")
@@ -348,9 +351,12 @@ def run_batched(args):
     idx_build.build()
     idx.lib()
     ics = c4_instances()
+    ics = ics[:32][:max(0, args.instances // 2)] + ics[32:][:max(0, args.instances - args.instances // 2)]
     cells = sum(ic.ncells for ic in ics)
-    results = {p: batched_mix(ics, p, args.cycles, args.warmup) for p in ("fp64", "fp32")}
-    line = {"metric": METRIC, "value": results["fp64"]["batched"], "unit": UNIT, "n_gpus": 1,
+    results = {p: batched_mix(ics, p, args.cycles, args.warmup)
+               for p in args.batch_precisions.split(",")}
+    line = {"metric": METRIC, "value": results[next(iter(results))]["batched"], "unit": UNIT,
+            "n_gpus": 1,
             "steps": args.cycles, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": C4_WORKLOAD, "instances": len(ics), "cells": cells,

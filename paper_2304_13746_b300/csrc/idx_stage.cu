@@ -379,16 +379,23 @@ __device__ __forceinline__ void sweep_body(const Geo& g, const Ptr8<const T>& W,
     }
     Side<T> L, R;
     T slope0[7], up0[7];
+    if constexpr (RECON == 3) {
 #pragma unroll
-    for (int q = 0; q < 7; ++q) {
-      const T dl = w0[q] - wm[q], dr = wp[q] - w0[q];
-      if constexpr (RECON == 3) {
+      for (int q = 0; q < 7; ++q) {
+        const T dl = w0[q] - wm[q], dr = wp[q] - w0[q];
         slope0[q] = limo3_half(dr, dl);
         up0[q] = limo3_half(dl, dr);
-      } else {
-        slope0[q] = vanleer_half(dl, dr);
-        up0[q] = slope0[q];
       }
+    } else {
+      T dl[7], dr[7];
+#pragma unroll
+      for (int q = 0; q < 7; ++q) {
+        dl[q] = w0[q] - wm[q];
+        dr[q] = wp[q] - w0[q];
+      }
+      vanleer_half7(dl, dr, slope0);
+#pragma unroll
+      for (int q = 0; q < 7; ++q) up0[q] = slope0[q];
     }
     L.r = wm[0] + slope_m[0]; R.r = w0[0] - slope0[0];
     L.u = wm[1] + slope_m[1]; R.u = w0[1] - slope0[1];
@@ -520,16 +527,23 @@ __device__ __forceinline__ bool tma_tile(const Geo& g, const CUtensorMap* tm_bod
   for (int k = 0; k < 4; ++k) {
     Side<T> Ls, Rs;
     T slope0[7], up0[7];
+    if constexpr (RECON == 3) {
 #pragma unroll
-    for (int q = 0; q < 7; ++q) {
-      const T dl = w0[q] - wm[q], dr = wp[q] - w0[q];
-      if constexpr (RECON == 3) {
+      for (int q = 0; q < 7; ++q) {
+        const T dl = w0[q] - wm[q], dr = wp[q] - w0[q];
         slope0[q] = limo3_half(dr, dl);
         up0[q] = limo3_half(dl, dr);
-      } else {
-        slope0[q] = vanleer_half(dl, dr);
-        up0[q] = slope0[q];
       }
+    } else {
+      T dl[7], dr[7];
+#pragma unroll
+      for (int q = 0; q < 7; ++q) {
+        dl[q] = w0[q] - wm[q];
+        dr[q] = wp[q] - w0[q];
+      }
+      vanleer_half7(dl, dr, slope0);
+#pragma unroll
+      for (int q = 0; q < 7; ++q) up0[q] = slope0[q];
     }
     Ls.r = wm[0] + slope_m[0]; Rs.r = w0[0] - slope0[0];
     Ls.u = wm[1] + slope_m[1]; Rs.u = w0[1] - slope0[1];

@@ -164,6 +164,56 @@ template <> __device__ __forceinline__ double vanleer_half<double>(double dl, do
 #endif
 }
 
+// The half slopes of the 7 reconstructed variables of one cell, from their one-sided
+// differences.  In FP64 the 7 quotients share one reciprocal (Montgomery's trick: prefix
+// products of the denominators, one reciprocal of the last, then each reciprocal by one
+// product walking back), 18 products and one reciprocal in place of 7 reciprocals, on the
+// FP64 pipe that bounds the sweeps.  Each reciprocal is then within a few ulps of 1/x.
+// The trick runs when every denominator's exponent lies within 2^+-130, so that no prefix
+// product can leave the double range; otherwise (steep fronts into near-vacuum, with
+// differences near the subnormal range) each slope takes its own reciprocal.  The FP32 bulk
+// and the strict-rounding build form each slope by itself.
+template <typename T> __device__ __forceinline__ void vanleer_half7(const T dl[7], const T dr[7],
+                                                                   T out[7]) {
+#pragma unroll
+  for (int q = 0; q < 7; ++q) out[q] = vanleer_half(dl[q], dr[q]);
+}
+#ifndef IDX_STRICT_ROUNDING
+template <> __device__ __forceinline__ void vanleer_half7<double>(const double dl[7],
+                                                                  const double dr[7],
+                                                                  double out[7]) {
+  double prod[7], den[7];
+  bool pos[7];
+  unsigned long long bad = 0;
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    prod[q] = dl[q] * dr[q];
+    pos[q] = gt0(prod[q]);
+    den[q] = pos[q] ? dl[q] + dr[q] : 1.0;
+    // biased exponent outside [1023 - 130, 1023 + 130]
+    const unsigned e = (unsigned)((unsigned long long)ibits(den[q]) >> 52) & 0x7ffu;
+    bad |= (unsigned long long)((e - 893u) > 260u);
+  }
+  if (bad) {
+#pragma unroll
+    for (int q = 0; q < 7; ++q) out[q] = pos[q] ? prod[q] * (1.0 / den[q]) : 0.0;
+    return;
+  }
+  double pre[7];
+  pre[0] = den[0];
+#pragma unroll
+  for (int q = 1; q < 7; ++q) pre[q] = pre[q - 1] * den[q];
+  double inv = 1.0 / pre[6];  // 1 / (den[0] ... den[6])
+#pragma unroll
+  for (int q = 6; q >= 1; --q) {
+    const double r = inv * pre[q - 1];  // 1 / den[q]
+    inv = inv * den[q];                 // 1 / (den[0] ... den[q-1])
+    out[q] = pos[q] ? prod[q] * r : 0.0;
+  }
+  out[0] = pos[0] ? prod[0] * inv : 0.0;
+}
+#endif
+
 // x with its sign flipped where y is negative (x * sign(y), signed zeros included), on the
 // bit patterns.
 __device__ __forceinline__ double xsign(double x, double y) {
