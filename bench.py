@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     p.add_argument("--impl", default="idx", choices=["idx", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--stage-kernels", default="auto", choices=["auto", "split", "fused"],
+                   help="kernels of a stage for the headline box (fused: FP32 bulk only)")
     p.add_argument("--no-variants", action="store_true",
                    help="headline, roofline and e2e only (profiling runs)")
     p.add_argument("--mode", default="plain", choices=["plain", "batched", "serve", "accuracy"],
@@ -112,7 +114,8 @@ def workload_config(args):
                         "rms Mach 1, gamma=5/3, PLM+HLLD+E^c CT+RK2, CFL 0.4",
             "n": args.n, "cells": args.n ** 3, "precision": args.precision, "seed": 0,
             "timing": f"median of {REGIONS} CUDA-event regions of --steps cycles each",
-            "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas"}
+            "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas",
+            "stage_kernels": args.stage_kernels}
 
 
 def measured_peaks():
@@ -512,6 +515,8 @@ def main():
     stream = torch.cuda.Stream()
     sim = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, args.precision, stream=stream.cuda_stream)
     sim.set_primitive(ic.prim)
+    sim.set_stage_kernels(args.stage_kernels)
+    fused = sim.stage_kernels() == "fused"
     cons_host = sim.get_state()
 
     for _ in range(args.warmup):
@@ -555,17 +560,27 @@ def main():
     dom = max(sweep_ms, key=sweep_ms.get)
     d_i = "xyz".index(dom)
     achieved_gflops = counts["face_flops"][d_i] * ncell / (sweep_ms[dom] * 1e-3) / 1e9
+    kname = f"k_sweep<{'double' if args.precision == 'fp64' else 'float'},{dom}>"
+    dom_ms, dom_flops = sweep_ms[dom], counts["face_flops"][d_i]
+    if fused:
+        # one kernel does a stage's faces, edges and update: its share of a cycle's count
+        # is all of it but the primitive recovery, over the two stages
+        dom_ms = kt["update"]
+        dom_flops = (counts["cycle_flops"] - counts["parts"]["prims"]) / 2
+        achieved_gflops = dom_flops * ncell / (dom_ms * 1e-3) / 1e9
+        kname = "k_stage_fused<float>"
     fma = rates["fma64"] if args.precision == "fp64" else rates["fma32"]
     peak = 2 * fma / 1e9
     tpf = MEASURED_TRAFFIC_PER_FACE.get((args.precision, dom, shapes["xyz".index(dom)]))
     whole = roofline_cycle(value, counts, rates, hbm_gbs, args.precision)
-    roofline = {"bound": "alu", "kernel": f"k_sweep<{'double' if args.precision == 'fp64' else 'float'},{dom}>",
+    roofline = {"bound": "alu", "kernel": kname,
                 "achieved": achieved_gflops, "peak": peak, "unit": "GFLOP/s",
                 "frac": achieved_gflops / peak,
                 "frac_of_nominal_fp64": (achieved_gflops / FP64_NOMINAL_GFLOPS
                                          if args.precision == "fp64" else None),
-                "traffic": tpf * ncell if tpf else None, "traffic_unit": "bytes per launch",
-                "alg_flops_per_face": counts["face_flops"][d_i], "launch_ms": sweep_ms[dom],
+                "traffic": tpf * ncell if (tpf and not fused) else None,
+                "traffic_unit": "bytes per launch",
+                "alg_flops_per_unit": dom_flops, "launch_ms": dom_ms,
                 "peak_source": (f"measured {'FP64' if args.precision == 'fp64' else 'FP32'} FMA "
                                 "rate x 2 flop (idx_pipe_rates, this GPU; of measured)"),
                 "kernel_ms": kt, "sweep_shapes_xyz": shapes,

@@ -162,16 +162,6 @@ __device__ __forceinline__ void fused_face(const Geo& g, int d, const float* con
   out[7 * nface] = cmax;
 }
 
-// float -> double for the accumulation: the integer-pipe conversion, the converter only
-// in warps that hold a subnormal, infinite or NaN value
-__device__ __forceinline__ double f2d_warp(float x) {
-  bool slow;
-  const unsigned long long b = f2d_bits(__float_as_uint(x), &slow);
-  double r = __longlong_as_double((long long)b);
-  if (__any_sync(__activemask(), slow)) r = slow ? (double)x : r;
-  return r;
-}
-
 template <bool COMBINE>
 __global__ void __launch_bounds__(fused::NT, 2)
     k_stage_fused(Geo g, const __grid_constant__ FusedMaps M, const double* bx_face,

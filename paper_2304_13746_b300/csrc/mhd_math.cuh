@@ -132,6 +132,15 @@ __device__ __forceinline__ float d2f(double x) {
   if (__builtin_expect(slow, 0)) r = d2f_slow(x);
   return r;
 }
+// float -> double with the converter only in warps that hold a subnormal, infinite or NaN
+// value (no select that would run it on every lane).
+__device__ __forceinline__ double f2d_warp(float x) {
+  bool slow;
+  const unsigned long long b = f2d_bits(__float_as_uint(x), &slow);
+  double r = __longlong_as_double((long long)b);
+  if (__any_sync(__activemask(), slow)) r = slow ? (double)x : r;
+  return r;
+}
 // The vote names only the lanes executing it (__activemask): callers may sit behind an
 // early return or a bounds test, where the rest of the warp never gets here.
 __device__ __forceinline__ float d2f_warp(double x) {
