@@ -394,16 +394,25 @@ def served_stream(precision, nreq, budget, serve_mod, stream, orders=("oldest",)
             out.append(q)
         return out
 
+    def failures(reqs):
+        # a request whose state turns non-physical ends with its error (the method has no
+        # positivity safeguard); it is the same request alone and in the mix
+        return [{"rid": q.rid, "kind": q.kind, "n": q.n, "t_end": round(q.t_end, 3),
+                 "error": q.error} for q in reqs if q.status == "failed"]
+
     def served(rate, cap=None, order="oldest"):
         be = serve_mod.IdxBackend(precision, stream=stream)
+        reqs = clone(rate)
         st = serve_mod.Server(be, budget, cycles_per_poll=4, chunk_s=0.01,
-                              max_active_cells=cap, order=order).run(clone(rate))
+                              max_active_cells=cap, order=order).run(reqs)
         be.close()
-        return st
+        return dict(st, failed_requests=failures(reqs))
 
     def sequential(rate):
-        return serve_mod.serve_sequential(serve_mod.IdxSequential(precision, stream=stream),
-                                          clone(rate), budget_bytes=budget)
+        reqs = clone(rate)
+        st = serve_mod.serve_sequential(serve_mod.IdxSequential(precision, stream=stream),
+                                        reqs, budget_bytes=budget)
+        return dict(st, failed_requests=failures(reqs))
 
     cap = served(1e9)                     # everything at once: the batch's capacity
     mean_work = cap["cell_updates"] / max(cap["done"], 1)
