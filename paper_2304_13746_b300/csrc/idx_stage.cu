@@ -140,8 +140,8 @@ __device__ __forceinline__ void flag_bad(Ctrl* ctrl, int c) {
 }
 
 // ---------------------------------------------------------------------------
-// Primitive recovery (FP64 for both variants): rho, v = m/rho, P from E, and the
-// cell-centre B as the mean of the two bounding faces.  W is stored as T.
+// Primitive recovery: rho, v = m/rho, P from E (at FP64 accuracy in both variants), and
+// the cell-centre B as the mean of the two bounding faces.  W is stored as T.
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void prims_body(const Geo& g, const Ptr8<const double>& U,
@@ -171,32 +171,66 @@ __device__ __forceinline__ void prims_body(const Geo& g, const Ptr8<const double
       cc.f[2][c] = -(vx * by - vy * bx);
     }
   } else {
-    // FP32 bulk: the energy-to-pressure recovery stays FP64 (kinetic and magnetic
-    // energies from the FP64 state); the velocities and cell-centre B go out in FP32.
-    // 1/rho only scales the kinetic energy: an FP32 seed refined by one Newton-Raphson
-    // step y1 = y0 + y0 (1 - rho y0), which squares the seed's relative error (~1e-14
-    // after the step), in place of an FP64 division (densities inside the FP32 range,
-    // which the FP32 sweeps need anyway).  The step is taken on y0/2, giving 1/(2 rho).
-    const float rhof = d2f(rho);
-    const float y0f = __frcp_rn(rhof);
-    const double y0h = f2d(0.5f * y0f);
-    const double irh = fma(y0h, fma(-rho, f2d(y0f), 1.0), y0h);
+    // FP32 bulk: the velocities and cell-centre B go out in FP32; the pressure keeps
+    // FP64 accuracy.  Where every lane's rho, m and face B lie in [2^-32, 2^32) (or are
+    // 0), the kinetic and magnetic energies are formed in double-float arithmetic on the
+    // FP32 pipe (each input split exactly into 24 + 23 bits; error-free products and
+    // sums; ~2^-46 relative) and only the cancellation E - K - M and the factor
+    // (gamma - 1) take FP64 operations, 3 per cell.  Elsewhere all of it is FP64.
     const double mx = U.f[1][c], my = U.f[2][c], mz = U.f[3][c];
-    const double sx = U.f[5][c] + U.f[5][shifted(g, c, i, 0, 1)];  // 2 B_c
-    const double sy = U.f[6][c] + U.f[6][shifted(g, c, j, 1, 1)];
-    const double sz = U.f[7][c] + U.f[7][shifted(g, c, k, 2, 1)];
-    // P = (gamma - 1) (E - |m|^2 / (2 rho) - |2 B_c|^2 / 8), FP64 with fused steps
-    const double msq = fma(mx, mx, fma(my, my, mz * mz));
-    const double ssq = fma(sx, sx, fma(sy, sy, sz * sz));
-    const double P = g.gm1 * fma(-0.125, ssq, fma(-msq, irh, U.f[4][c]));
-    const float irf = 2.0f * d2f(irh);
-    const float vx = d2f(mx) * irf, vy = d2f(my) * irf, vz = d2f(mz) * irf;
+    const double bx0 = U.f[5][c], bx1 = U.f[5][shifted(g, c, i, 0, 1)];
+    const double by0 = U.f[6][c], by1 = U.f[6][shifted(g, c, j, 1, 1)];
+    const double bz0 = U.f[7][c], bz1 = U.f[7][shifted(g, c, k, 2, 1)];
+    const bool in_range = df_in_range(rho) & df_in_range(mx) & df_in_range(my) &
+                          df_in_range(mz) & df_in_range(bx0) & df_in_range(bx1) &
+                          df_in_range(by0) & df_in_range(by1) & df_in_range(bz0) &
+                          df_in_range(bz1);
+    double P;
+    float rhof, irf, vx, vy, vz, bx, by, bz;
+    if (__all_sync(__activemask(), in_range)) {
+      const DF rd = df_split(rho), mxd = df_split(mx), myd = df_split(my), mzd = df_split(mz);
+      // 1/rho: the FP32 reciprocal y of the high part, one Newton-Raphson step on the
+      // double-float rho: 1/rho = y (1 + r) + O(r^2), r = 1 - rho y
+      const float y = __frcp_rn(rd.h);
+      const float r = __fmaf_rn(-rd.l, y, __fmaf_rn(-rd.h, y, 1.0f));
+      const float yr = __fmul_rn(y, r);
+      const DF ir2 = {0.5f * y, 0.5f * yr};  // 1 / (2 rho)
+      const DF sx = df_add(df_split(bx0), df_split(bx1));  // 2 B_c
+      const DF sy = df_add(df_split(by0), df_split(by1));
+      const DF sz = df_add(df_split(bz0), df_split(bz1));
+      const DF kin = df_mul(df_sum3(df_sqr(mxd), df_sqr(myd), df_sqr(mzd)), ir2);
+      const DF ssq = df_sum3(df_sqr(sx), df_sqr(sy), df_sqr(sz));
+      const DF km = df_add(kin, DF{0.125f * ssq.h, 0.125f * ssq.l});  // K + |B_c|^2 / 2
+      P = g.gm1 * ((U.f[4][c] - f2d_warp(km.h)) - f2d_warp(km.l));
+      rhof = __fadd_rn(rd.h, rd.l);
+      irf = __fadd_rn(y, yr);
+      vx = __fadd_rn(mxd.h, mxd.l) * irf;
+      vy = __fadd_rn(myd.h, myd.l) * irf;
+      vz = __fadd_rn(mzd.h, mzd.l) * irf;
+      bx = 0.5f * __fadd_rn(sx.h, sx.l);
+      by = 0.5f * __fadd_rn(sy.h, sy.l);
+      bz = 0.5f * __fadd_rn(sz.h, sz.l);
+    } else {
+      // 1/rho only scales the kinetic energy: an FP32 seed refined by one Newton-Raphson
+      // step y1 = y0 + y0 (1 - rho y0) in FP64 (taken on y0/2, giving 1/(2 rho))
+      rhof = d2f_warp(rho);
+      const float y0f = __frcp_rn(rhof);
+      const double y0h = f2d(0.5f * y0f);
+      const double irh = fma(y0h, fma(-rho, f2d(y0f), 1.0), y0h);
+      const double sx = bx0 + bx1, sy = by0 + by1, sz = bz0 + bz1;  // 2 B_c
+      // P = (gamma - 1) (E - |m|^2 / (2 rho) - |2 B_c|^2 / 8), FP64 with fused steps
+      const double msq = fma(mx, mx, fma(my, my, mz * mz));
+      const double ssq = fma(sx, sx, fma(sy, sy, sz * sz));
+      P = g.gm1 * fma(-0.125, ssq, fma(-msq, irh, U.f[4][c]));
+      irf = 2.0f * d2f_warp(irh);
+      vx = d2f_warp(mx) * irf; vy = d2f_warp(my) * irf; vz = d2f_warp(mz) * irf;
+      bx = 0.5f * d2f_warp(sx); by = 0.5f * d2f_warp(sy); bz = 0.5f * d2f_warp(sz);
+    }
     // 0 < rho, P < infinity, tested on the bit patterns (FP64 compares take FP64 slots)
     if (!pos_finite(rho) || !pos_finite(P) || !isfinite(vx) || !isfinite(vy) || !isfinite(vz))
       flag_bad(ctrl, c);
     W.f[0][c] = rhof; W.f[1][c] = vx; W.f[2][c] = vy; W.f[3][c] = vz;
-    W.f[4][c] = d2f(P);
-    const float bx = 0.5f * d2f(sx), by = 0.5f * d2f(sy), bz = 0.5f * d2f(sz);
+    W.f[4][c] = d2f_warp(P);
     W.f[5][c] = bx; W.f[6][c] = by; W.f[7][c] = bz;
     if (cc.f[0]) {
       cc.f[0][c] = -(vy * bz - vz * by);
@@ -207,7 +241,7 @@ __device__ __forceinline__ void prims_body(const Geo& g, const Ptr8<const double
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_prims(Geo g, Ptr8<const double> U, Ptr8<T> W,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 8) k_prims(Geo g, Ptr8<const double> U, Ptr8<T> W,
                                                     CellEmf<T> cc, Ctrl* ctrl, int check_dt) {
   if (check_dt && !(ctrl->dt > 0.0)) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -598,26 +632,31 @@ __global__ void __launch_bounds__(8 * L, sizeof(T) == 4 ? 96 / L : 1)
 
 // ---------------------------------------------------------------------------
 // TMA-staged sweep along x.  A block owns 32 x-faces of 8 consecutive y-rows at one z.
-// The 7 rotated variables arrive by bulk tensor copies: the body (32 cells) and the two
-// halos of 4 cells (the start of a copy must sit on a 16-byte boundary, so a 2-cell halo
-// is fetched as 4), each wrapped periodically by hand.  Warp r takes row r, lane f face f,
-// and forms its face from cells f-2 .. f+1 in shared memory (each cell's slope is formed
-// by the two faces that use it).  Needs nx % 32 == 0 and ny % 8 == 0.
+// Each of the 7 rotated variables arrives as one bulk tensor copy of 40 x 8 cells, the
+// 32 cells of the rows with 4 more on each side (the start of a copy must sit on a
+// 16-byte boundary, so the 2-cell halo is fetched 4 wide).  Where the box runs past an
+// end of the row the copy fills zeros and the block patches those 4 columns with the
+// periodic images by plain loads.  Warp r takes row r, lane f face f: it forms the slope
+// of cell f once, keeps w - slope as the face's right state and hands w + slope to lane
+// f + 1 as that face's left state; the left state of face 0 (cell -1, one per row) is
+// formed beforehand by 56 threads, one per (row, variable).  Needs nx % 32 == 0 and
+// ny % 8 == 0.
 // ---------------------------------------------------------------------------
 constexpr int kXRows = 8;
+constexpr int kXBox = 40;   // cells per row in the staged box: 4 + 32 + 4
 
 template <typename T>
 __global__ void __launch_bounds__(32 * kXRows)
-    k_sweep_tma_x(Geo g, const __grid_constant__ CUtensorMap tm_body,
-                  const __grid_constant__ CUtensorMap tm_halo, const double* bface, Ptr8<T> F,
-                  Ctrl* ctrl, int check_dt) {
+    k_sweep_tma_x(Geo g, const __grid_constant__ CUtensorMap tm_row, Ptr8<const T> W,
+                  const double* bface, Ptr8<T> F, Ctrl* ctrl, int check_dt) {
   if (check_dt && !(ctrl->dt > 0.0)) return;
   constexpr int R = kXRows;
-  constexpr int PB = 32 * R, PH = 4 * R;          // body / halo plane sizes (elements)
-  constexpr int PLANE = PB + 2 * PH;
-  __shared__ __align__(128) T tile[7 * PLANE];     // [var]{lo [R][4], body [R][32], hi [R][4]}
+  constexpr int PLANE = R * kXBox;
+  __shared__ __align__(128) T tile[7 * PLANE];     // [var][row][col], col = x - x0 + 4
+  __shared__ T left0[7][R];                         // left state of face 0 per row
   __shared__ __align__(8) uint64_t bar;
-  const int ntx = g.n[0] >> 5, nty = g.n[1] / R;
+  const int nx = g.n[0];
+  const int ntx = nx >> 5, nty = g.n[1] / R;
   int b = blockIdx.x;
   const int x0 = (b % ntx) * 32;
   b /= ntx;
@@ -631,17 +670,8 @@ __global__ void __launch_bounds__(32 * kXRows)
   __syncthreads();
   if (threadIdx.x == 0) {
     mbar_arrive_expect_tx(&bar, 7u * PLANE * sizeof(T));
-    int lo = x0 - 4;
-    if (lo < 0) lo += g.n[0];
-    int hi = x0 + 32;
-    if (hi >= g.n[0]) hi -= g.n[0];
 #pragma unroll
-    for (int q = 0; q < 7; ++q) {
-      T* dst = tile + q * PLANE;
-      tma_load_4d(dst, &tm_halo, lo, y0, z, var[q], &bar);
-      tma_load_4d(dst + PH, &tm_body, x0, y0, z, var[q], &bar);
-      tma_load_4d(dst + PH + PB, &tm_halo, hi, y0, z, var[q], &bar);
-    }
+    for (int q = 0; q < 7; ++q) tma_load_4d(tile + q * PLANE, &tm_row, x0 - 4, y0, z, var[q], &bar);
   }
   const int f = threadIdx.x & 31, r = threadIdx.x >> 5;
   const int c = (x0 + f) + (y0 + r) * g.stride[1] + z * g.stride[2];
@@ -651,20 +681,45 @@ __global__ void __launch_bounds__(32 * kXRows)
     tma_give_up(ctrl, &bar, 0);
     return;
   }
-  // cell at column col (-4 .. 35) of row r of variable q
-  auto ld = [&](int q, int col) {
-    const T* base = tile + q * PLANE;
-    if (col < 0) return base[r * 4 + col + 4];
-    if (col < 32) return base[PH + r * 32 + col];
-    return base[PH + PB + r * 4 + col - 32];
-  };
+  // periodic images of the columns the copy filled with zeros (block-uniform branches)
+  const bool wrap_lo = x0 == 0, wrap_hi = x0 + 32 == nx;
+  if (wrap_lo || wrap_hi) {
+    // 8 rows x 4 columns per side, one thread each, all 7 variables
+    if (threadIdx.x < 4 * R) {
+      const int k = threadIdx.x & 3, row = threadIdx.x >> 2;
+      const int rowoff = (y0 + row) * g.stride[1] + z * g.stride[2];
+#pragma unroll
+      for (int q = 0; q < 7; ++q) {
+        T* dst = tile + q * PLANE + row * kXBox;
+        if (wrap_lo) dst[k] = W.f[var[q]][rowoff + nx - 4 + k];
+        if (wrap_hi) dst[36 + k] = W.f[var[q]][rowoff + k];
+      }
+    }
+    __syncthreads();
+  }
+  // cell at column col (-4 .. 35) of row rr of variable q
+  auto ld = [&](int q, int rr, int col) { return tile[q * PLANE + rr * kXBox + col + 4]; };
+  if (threadIdx.x < 7 * R) {
+    const int q = threadIdx.x / R, rr = threadIdx.x % R;
+    const T wmm = ld(q, rr, -2), wm = ld(q, rr, -1), w0 = ld(q, rr, 0);
+    left0[q][rr] = wm + vanleer_half(wm - wmm, w0 - wm);
+  }
+  __syncthreads();
   Side<T> Ls, Rs;
-  T Lq[7], Rq[7];
+  T Lq[7], Rq[7], wc[7], dl[7], dr[7], hs[7];
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
-    const T wmm = ld(q, f - 2), wm = ld(q, f - 1), w0 = ld(q, f), wp = ld(q, f + 1);
-    Lq[q] = wm + vanleer_half(wm - wmm, w0 - wm);
-    Rq[q] = w0 - vanleer_half(w0 - wm, wp - w0);
+    const T wm = ld(q, r, f - 1), wp = ld(q, r, f + 1);
+    wc[q] = ld(q, r, f);
+    dl[q] = wc[q] - wm;
+    dr[q] = wp - wc[q];
+  }
+  vanleer_half7(dl, dr, hs);   // FP64: the cell's 7 slopes share one reciprocal
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    Rq[q] = wc[q] - hs[q];
+    const T up = __shfl_up_sync(0xffffffffu, wc[q] + hs[q], 1);
+    Lq[q] = f == 0 ? left0[q][r] : up;
   }
   Ls.r = Lq[0]; Ls.u = Lq[1]; Ls.v = Lq[2]; Ls.w = Lq[3]; Ls.p = Lq[4]; Ls.b1 = Lq[5]; Ls.b2 = Lq[6];
   Rs.r = Rq[0]; Rs.u = Rq[1]; Rs.v = Rq[2]; Rs.w = Rq[3]; Rs.p = Rq[4]; Rs.b1 = Rq[5]; Rs.b2 = Rq[6];
@@ -938,13 +993,15 @@ __device__ __forceinline__ T update_body(const Geo& g, const Ptr8<const double>&
       if constexpr (std::is_same<T, double>::value) return g.inv_dl[d];
       else return g.inv_dlf[d];
     };
-    [[maybe_unused]] const float dtf = std::is_same<T, float>::value ? d2f_warp(dt) : 0.f;
+    // the scaled step is formed once per cell (one FP64 product), not once per field
+    [[maybe_unused]] const float dtf =
+        std::is_same<T, float>::value ? d2f_warp(COMBINE ? w * dt : dt) : 0.f;
     auto accumulate = [&](int f, T div) -> double {
       if constexpr (std::is_same<T, double>::value) {
         return Uin.f[f][c] - dt * div;
       } else {
         if (COMBINE) {
-          const float wdt = d2f_warp(w * dt);
+          const float wdt = dtf;
           if (w == w0) return fma(w, U0.f[f][c] + Uin.f[f][c], f2d(-wdt * div));
           return fma(w0, U0.f[f][c], w * Uin.f[f][c]) + f2d(-wdt * div);
         }
@@ -1297,12 +1354,12 @@ bool tma_shape_ok(const idx_sim* s, int d, int shape) {
   return d != 0 && s->tma_ok[d][shape == 132 ? 1 : 0] && s->geo.n[d] % (shape - 100) == 0;
 }
 
-template <typename T> void launch_tma_x(idx_sim* s, const double* bface, const Ptr8<T>& F,
-                                        int check_dt) {
+template <typename T> void launch_tma_x(idx_sim* s, const Ptr8<T>& W, const double* bface,
+                                        const Ptr8<T>& F, int check_dt) {
   const Geo& g = s->geo;
   const unsigned blocks = (unsigned)((g.n[0] / 32) * (g.n[1] / kXRows) * g.n[2]);
-  k_sweep_tma_x<T><<<blocks, 32 * kXRows, 0, s->stream>>>(g, s->tm_body[0][0], s->tm_halo[0],
-                                                          bface, F, s->ctrl, check_dt);
+  k_sweep_tma_x<T><<<blocks, 32 * kXRows, 0, s->stream>>>(g, s->tm_body[0][0], cst(W), bface,
+                                                          F, s->ctrl, check_dt);
 }
 
 template <typename T, int D>
@@ -1318,7 +1375,7 @@ void launch_sweep_d(idx_sim* s, int shape, const Ptr8<T>& W, const double* bface
     return;
   }
   if (D == 0 && shape == -2 && tma_shape_ok(s, 0, -2)) {
-    launch_tma_x<T>(s, bface, F, check_dt);
+    launch_tma_x<T>(s, W, bface, F, check_dt);
     return;
   }
   if (D != 0 && tma_shape_ok(s, D, shape)) {
@@ -1759,15 +1816,14 @@ void encode_sweep_maps(idx_sim* s, void* wbase, size_t elem, size_t field_stride
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   const CUtensorMapDataType dt =
       elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
-  // x: body of 32 cells and halos of 4, 8 rows deep
+  // x: rows of 40 cells (32 and a 4-cell halo on each side), 8 rows deep; the parts
+  // past the ends of a row are filled with zeros
   if (g.active[0] && g.n[1] % kXRows == 0) {
-    auto encode_x = [&](unsigned width, CUtensorMap* m) {
-      const cuuint32_t box[4] = {width, (cuuint32_t)kXRows, 1, 1};
-      return enc(m, dt, 4, wbase, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                 CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-    };
-    s->tma_ok[0][0] = encode_x(4, &s->tm_halo[0]) && encode_x(32, &s->tm_body[0][0]);
+    const cuuint32_t box[4] = {(cuuint32_t)kXBox, (cuuint32_t)kXRows, 1, 1};
+    s->tma_ok[0][0] = enc(&s->tm_body[0][0], dt, 4, wbase, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   }
   for (int d = 1; d <= 2; ++d) {
     if (!g.active[d]) continue;

@@ -151,6 +151,64 @@ __device__ __forceinline__ float d2f_warp(double x) {
   return r;
 }
 
+// Double-float values (an unevaluated sum h + l of two binary32 numbers, Dekker 1971) for
+// the FP32-bulk energy-to-pressure recovery: the kinetic and magnetic energies formed on
+// the FP32 pipe to ~2^-46 relative, so that only the cancellation E - K - M needs FP64.
+struct DF {
+  float h, l;
+};
+// |x| in [2^-32, 2^32), or x = 0: the range where df_split is exact to 2^-46
+__device__ __forceinline__ bool df_in_range(double x) {
+  const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+  const unsigned ahw = hw & 0x7fffffffu;
+  return (ahw | lw) == 0u || ((ahw >> 20) - 991u) < 64u;  // biased exponent 1023 -/+ 32
+}
+// x = h + l with h the first 24 significant bits of x (truncated) and l the next 23, from
+// the bit layout alone (integer pipe and one FP32 multiply), for x in df_in_range.
+__device__ __forceinline__ DF df_split(double x) {
+  DF r;
+  const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+  const unsigned ahw = hw & 0x7fffffffu, sgn = hw & 0x80000000u;
+  const unsigned e = ahw >> 20;  // biased exponent
+  const bool zero = (ahw | lw) == 0u;
+  // high part: exponent rebiased by 1023 - 127, top 23 bits of the 52-bit mantissa
+  const unsigned hb = sgn | (((ahw - 0x38000000u) << 3) | (lw >> 29));
+  // low part: the remaining 29 mantissa bits less their last 6, i.e. an integer below
+  // 2^23 (exact through the 2^23 magic constant) in units of 2^(e - 1075 + 6)
+  const float m = __fsub_rn(__uint_as_float(0x4b000000u | ((lw & 0x1fffffffu) >> 6)), 8388608.0f);
+  const float sc = __uint_as_float((e - 942u) << 23);  // 2^(e - 1069)
+  r.h = zero ? 0.f : __uint_as_float(hb);
+  r.l = zero ? 0.f : __uint_as_float(__float_as_uint(__fmul_rn(m, sc)) | sgn);
+  return r;
+}
+// s + t = a + b exactly (Knuth's two-sum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+  s = __fadd_rn(a, b);
+  const float v = __fsub_rn(s, a);
+  t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  DF r;
+  float t;
+  two_sum(a.h, b.h, r.h, t);
+  r.l = __fadd_rn(t, __fadd_rn(a.l, b.l));
+  return r;
+}
+// a^2, dropping l^2 (2^-46 relative)
+__device__ __forceinline__ DF df_sqr(DF a) {
+  DF r;
+  r.h = __fmul_rn(a.h, a.h);
+  r.l = __fmaf_rn(a.h + a.h, a.l, __fmaf_rn(a.h, a.h, -r.h));
+  return r;
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  DF r;
+  r.h = __fmul_rn(a.h, b.h);
+  r.l = __fmaf_rn(a.l, b.h, __fmaf_rn(a.h, b.l, __fmaf_rn(a.h, b.h, -r.h)));
+  return r;
+}
+__device__ __forceinline__ DF df_sum3(DF a, DF b, DF c) { return df_add(df_add(a, b), c); }
+
 // van Leer (harmonic) limited slope from the two one-sided differences (Sec. 2.3).
 // The kernels use half the slope, dl dr / (dl + dr) (the slope is 2 dl dr / (dl + dr)): the
 // face states take w -/+ slope / 2, and forming the half directly gives the same bits (the
