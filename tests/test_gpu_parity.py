@@ -339,6 +339,41 @@ def test_fp32_bulk_close_to_fp64():
     s.close()
 
 
+def _fp32_prims_case(name):
+    ic = inputs.turbulent_box(32, seed=5)
+    prim = [a.copy() for a in ic.prim]
+    if name == "low_beta":
+        # P / (K + M) ~ 5e-3: E - K - M cancels 2-3 digits (double-float energies)
+        prim[4] *= 1e-2
+    elif name == "tiny_fields":
+        # |B_t| = 1e-12 (below 2^-32) in a slab: its warps take the all-FP64 branch,
+        # the others the double-float one
+        prim[6][:, :, 8:12] = 1e-12
+        prim[7][:, :, 8:12] = -1e-12
+    elif name == "large_scale":
+        # rho and P scaled by 2^40: every |m| and E beyond 2^32, all-FP64 branch everywhere
+        prim[0] *= 2.0 ** 40
+        prim[4] *= 2.0 ** 40
+        for f in (5, 6, 7):
+            prim[f] *= 2.0 ** 20
+    return inputs.IC(prim, ic.lengths, ic.gamma, name)
+
+
+@pytest.mark.parametrize("name", ["low_beta", "tiny_fields", "large_scale"])
+def test_fp32_bulk_pressure_recovery_branches(name):
+    # the FP32-bulk primitive recovery forms the pressure from double-float energies where
+    # the inputs lie in [2^-32, 2^32), with plain FP64 elsewhere; both meet the FP32 bar
+    ic = _fp32_prims_case(name)
+    o = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, 0.4)
+    s = gpu_sim(ic, precision="fp32")
+    o.step()
+    s.step()
+    err = field_errors(s.get_state(), o.u)
+    print(name, f"fp32 vs oracle {max(err):.2e}")
+    assert max(err) <= 1e-5, err
+    s.close()
+
+
 def test_pipe_rates_and_kernel_times():
     r = idx.pipe_rates()
     assert r["fma64"] > 1e11 and r["fma32"] > 10 * r["fma64"]
