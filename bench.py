@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--stage-kernels", default="auto", choices=["auto", "split", "fused"],
                    help="kernels of a stage for the headline box (fused: FP32 bulk only)")
+    p.add_argument("--sweep-shapes", default="",
+                   help="x,y,z sweep shapes for the headline box instead of the autotuner's "
+                        "(profiling runs; e.g. 32,116,116)")
     p.add_argument("--no-variants", action="store_true",
                    help="headline, roofline and e2e only (profiling runs)")
     p.add_argument("--mode", default="plain", choices=["plain", "batched", "serve", "accuracy"],
@@ -115,7 +118,8 @@ def workload_config(args):
             "n": args.n, "cells": args.n ** 3, "precision": args.precision, "seed": 0,
             "timing": f"median of {REGIONS} CUDA-event regions of --steps cycles each",
             "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas",
-            "stage_kernels": args.stage_kernels}
+            "stage_kernels": args.stage_kernels,
+            "sweep_shapes": args.sweep_shapes or "autotuned"}
 
 
 def measured_peaks():
@@ -240,7 +244,11 @@ def run_reference(args):
 # DRAM bytes per face of the dominant kernel, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch, 192^3 box, scaled by faces): reported only while
 # the bench's dominant kernel is the variant that was captured.
-MEASURED_TRAFFIC_PER_FACE = {("fp64", "x", 32): (1.281667e9 + 0.780322e9) / 192 ** 3}
+# DRAM bytes per face of the dominant sweep, from one ncu capture at 192^3 of the current
+# kernel (dram__bytes_read.sum + dram__bytes_write.sum over the faces of the launch)
+MEASURED_TRAFFIC_PER_FACE = {("fp64", "x", 32): (1283676928 + 783192064) / 192 ** 3,
+                             ("fp64", "x", -2): (453604864 + 412544768) / 192 ** 3,
+                             ("fp32", "x", -2): (254.861056e6 + 189.744640e6) / 192 ** 3}
 
 
 def op_counts(cons, lengths, gamma):
@@ -517,7 +525,6 @@ def main():
         dist.barrier()
     idx.lib()
     hbm_gbs, hbm_source = measured_peaks()
-    rates = idx.pipe_rates()
 
     ic = inputs.turbulent_box(args.n, seed=0)
     ncell = ic.ncells
@@ -525,6 +532,8 @@ def main():
     sim = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, args.precision, stream=stream.cuda_stream)
     sim.set_primitive(ic.prim)
     sim.set_stage_kernels(args.stage_kernels)
+    if args.sweep_shapes:
+        sim.set_sweep_shapes(tuple(int(v) for v in args.sweep_shapes.split(",")))
     fused = sim.stage_kernels() == "fused"
     cons_host = sim.get_state()
 
@@ -551,6 +560,9 @@ def main():
         torch.cuda.synchronize()
         regions.append(max_over_ranks(e0.elapsed_time(e1), dist))
     clk = clocks.stop()
+    # the pipe-rate probe runs with the GPU hot from the timed cycles: the first probe of a
+    # process read ~6 % low while the clocks were still coming up from idle
+    rates = idx.pipe_rates()
     sim.time()  # surfaces any device error of the timed cycles
     ms = statistics.median(regions)
     value = aggregate_rate(ncell, args.steps, world, ms)

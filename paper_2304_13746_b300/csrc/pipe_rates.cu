@@ -3,8 +3,9 @@
 // Supplies the denominators of the ALU roofline: each kernel runs ITERS x NACC
 // independent operations per thread (no dependency chain longer than ITERS, eight
 // chains per thread, 8 blocks of 256 threads per SM) and is timed with CUDA events,
-// best of three.  Divide and square-root kernels add one dependent add per
-// operation, whose cost is subtracted using the measured add rate.
+// best of five.  About 0.2 s of FP64 work runs first, untimed, so that the clocks have
+// left idle before the first timing.  Divide and square-root kernels add one dependent
+// add per operation, whose cost is subtracted using the measured add rate.
 #include <cuda_runtime.h>
 
 #include "../../include/idx.h"
@@ -41,7 +42,7 @@ int time_kernel(int blocks, T* out, double* ops_per_s) {
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return IDX_ECUDA; }
   k_pipe<T, OP><<<blocks, 256>>>(out, T(1));
   float best = 1e30f;
-  for (int r = 0; r < 3; ++r) {
+  for (int r = 0; r < 5; ++r) {
     cudaEventRecord(e0);
     k_pipe<T, OP><<<blocks, 256>>>(out, T(1));
     cudaEventRecord(e1);
@@ -69,7 +70,10 @@ extern "C" int idx_pipe_rates(double rates[6]) {
   void* buf = nullptr;
   if (cudaMalloc(&buf, (size_t)blocks * 256 * sizeof(double)) != cudaSuccess) return IDX_ENOMEM;
   double fma64, div64, sq64, fma32, div32, sq32;
-  int rc = time_kernel<double, 0>(blocks, (double*)buf, &fma64);
+  // warm-up: ~40 launches of the FP64 FMA kernel (~5 ms each), untimed
+  for (int r = 0; r < 40; ++r) k_pipe<double, 0><<<blocks, 256>>>((double*)buf, 1.0);
+  int rc = cudaDeviceSynchronize() == cudaSuccess ? IDX_OK : IDX_ECUDA;
+  if (rc == IDX_OK) rc = time_kernel<double, 0>(blocks, (double*)buf, &fma64);
   if (rc == IDX_OK) rc = time_kernel<double, 1>(blocks, (double*)buf, &div64);
   if (rc == IDX_OK) rc = time_kernel<double, 2>(blocks, (double*)buf, &sq64);
   if (rc == IDX_OK) rc = time_kernel<float, 0>(blocks, (float*)buf, &fma32);
