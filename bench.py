@@ -567,7 +567,8 @@ def main():
     ms = statistics.median(regions)
     value = aggregate_rate(ncell, args.steps, world, ms)
     n_active = sum(1 for s in ic.shape if s > 1)
-    launches_per_cycle = 2 + 2 * (3 + n_active)
+    # k_begin, k_end, and per stage: prims, the sweeps, E^c, update (fused: prims + one kernel)
+    launches_per_cycle = 2 + 2 * (2 if fused else 3 + n_active)
 
     # op counts from the oracle's pinned counter on a 32^3 corner of the box's state
     sample = ([np.ascontiguousarray(a[:32, :32, :32]) for a in cons_host] if args.n > 32
