@@ -74,11 +74,11 @@ __device__ __forceinline__ bool same_sign_nz(double dl, double dr, double) {
   return (a ^ b) >= 0 && (a << 1) != 0 && (b << 1) != 0;
 }
 __device__ __forceinline__ bool same_sign_nz(float, float, float prod) { return prod > 0.f; }
-__device__ __forceinline__ double tsqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ double tsqrt(double a);   // below the conversion helpers
 __device__ __forceinline__ float tsqrt(float a) { return sqrtf(a); }
 __device__ __forceinline__ double tabs(double a) { return fabs(a); }
 __device__ __forceinline__ float tabs(float a) { return fabsf(a); }
-__device__ __forceinline__ double trsqrt(double a) { return rsqrt(a); }
+__device__ __forceinline__ double trsqrt(double a);
 __device__ __forceinline__ float trsqrt(float a) { return rsqrtf(a); }
 // 1/a: the correctly rounded reciprocal in FP64; in the FP32 bulk the fast one (within 2 ulp
 // of 1/a for |a| < 2^126), far below the variant's own FP32 rounding budget, where the
@@ -150,6 +150,52 @@ __device__ __forceinline__ float d2f_warp(double x) {
   if (__any_sync(__activemask(), slow)) r = slow ? (float)x : r;
   return r;
 }
+
+// FP64 square root and reciprocal square root of the production kernels.  On this part
+// the library's correctly rounded FP64 square root costs about 7.6 FMA slots of the FP64
+// pipe, which bounds the FP64 sweeps.  Here: the FP32 hardware estimate y ~ 1/sqrt(x)
+// (from x's float image, truncated; ~2^-21 relative), then two Newton-Raphson steps in
+// FP64 in residual form (Markstein 1990: s <- s + (x - s^2) y/2 for the root,
+// y <- y + y (1 - x y^2)/2 for its reciprocal; each residual formed by an FMA).  The
+// error falls to ~1.5 e^2 after one step and ~e^3 after the second, ~2^-62 before the
+// final rounding: faithful (within 1 ulp of the exact value), nearly always correctly
+// rounded, and 5 (root) or 6 (reciprocal root) FP64 operations.  A warp with an argument
+// outside (2^-120, 2^121), or zero, negative, infinite or NaN, takes the library function.
+__device__ __forceinline__ bool nr_root_ok(double x) {
+  // positive with biased exponent in [1023 - 120, 1023 + 120]; a set sign bit fails
+  return ((unsigned)__double2hiint(x) >> 20) - (1023u - 120u) <= 240u;
+}
+__device__ __forceinline__ float nr_root_seed(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  return rsqrtf(__uint_as_float(((hi - 0x38000000u) << 3) | (lo >> 29)));
+}
+__device__ __forceinline__ double f2d_normal(float x) {  // x a normal float: exact
+  bool slow;
+  return __longlong_as_double((long long)f2d_bits(__float_as_uint(x), &slow));
+}
+__device__ __forceinline__ double sqrt_nr(double x) {
+  if (!__all_sync(__activemask(), nr_root_ok(x))) return sqrt(x);
+  const float y = nr_root_seed(x);
+  const double h = f2d_normal(0.5f * y);  // y / 2, exact
+  double s = x * f2d_normal(y);
+  s = fma(fma(-s, s, x), h, s);
+  return fma(fma(-s, s, x), h, s);
+}
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  if (!__all_sync(__activemask(), nr_root_ok(x))) return rsqrt(x);
+  const float y0 = nr_root_seed(x);
+  const double h = f2d_normal(0.5f * y0);
+  double y = f2d_normal(y0);
+  y = fma(fma(-(x * y), y, 1.0), h, y);
+  return fma(fma(-(x * y), y, 1.0), h, y);
+}
+#ifdef IDX_STRICT_ROUNDING
+__device__ __forceinline__ double tsqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ double trsqrt(double a) { return rsqrt(a); }
+#else
+__device__ __forceinline__ double tsqrt(double a) { return sqrt_nr(a); }
+__device__ __forceinline__ double trsqrt(double a) { return rsqrt_nr(a); }
+#endif
 
 // Double-float values (an unevaluated sum h + l of two binary32 numbers, Dekker 1971) for
 // the FP32-bulk energy-to-pressure recovery: the kinetic and magnetic energies formed on
@@ -330,8 +376,9 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   // 0.5/rho_L and 0.5/rho_R from one reciprocal (cheaper than a division; the factor 1/2
   // is exact)
   const T hLR = T(0.5) * trcp(L.r * R.r);
-  // only the larger fast speed enters: sqrt is correctly rounded and monotone, so the root
-  // of the larger square equals the larger root, bit for bit, at one square root fewer
+  // only the larger fast speed enters, the root of the larger square: one square root fewer
+  // (with a correctly rounded root this equals the larger root bit for bit; with the
+  // faithful FP64 root of the production build, within its ulp)
   const T cf2L = (aL + tsqrt(dL)) * (R.r * hLR);
   const T cf2R = (aR + tsqrt(dR)) * (L.r * hLR);
   const T cfm = tsqrt(max_nn(cf2L, cf2R));

@@ -37,3 +37,24 @@ def test_bit_recipes_match_host_conversions(harness):
 def test_device_conversions_match_hardware(harness):
     bad, checked = _run(harness, "device", 200_000_000)
     assert bad == 0 and checked == 400_000_000
+
+
+@pytest.fixture(scope="module")
+def root_harness(tmp_path_factory):
+    exe = str(tmp_path_factory.mktemp("roots") / "root_check")
+    subprocess.run([NVCC, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-std=c++17",
+                    "-o", exe, os.path.join(HERE, "native", "root_check.cu")], check=True)
+    return exe
+
+
+@pytest.mark.gpu
+def test_fp64_roots_within_one_ulp(root_harness):
+    # the production FP64 square root and reciprocal square root (FP32 estimate and two
+    # Newton-Raphson steps) are faithful: within 1 ulp of the exact root in the fast range;
+    # warps with an argument outside it equal the library functions bit for bit
+    out = subprocess.run([root_harness, "4000000"], capture_output=True, text=True, timeout=600)
+    words = out.stdout.split()
+    assert out.returncode == 0 and words[:1] == ["mismatches"], (out.stdout, out.stderr)
+    print(out.stdout)
+    assert int(words[1]) == 0 and int(words[3]) >= 4_000_000
+    assert float(words[5]) <= 1.0 and float(words[7]) <= 1.0
