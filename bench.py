@@ -55,8 +55,8 @@ def parse():
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     p.add_argument("--impl", default="idx", choices=["idx", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--stage-kernels", default="auto", choices=["auto", "split", "fused"],
-                   help="kernels of a stage for the headline box (fused: FP32 bulk only)")
+    p.add_argument("--stage-kernels", default="auto", choices=["auto", "split", "fused", "carry"],
+                   help="kernels of a stage for the headline box (fused, carry: FP32 bulk only)")
     p.add_argument("--sweep-shapes", default="",
                    help="x,y,z sweep shapes for the headline box instead of the autotuner's "
                         "(profiling runs; e.g. 32,116,116)")
@@ -535,6 +535,7 @@ def main():
     if args.sweep_shapes:
         sim.set_sweep_shapes(tuple(int(v) for v in args.sweep_shapes.split(",")))
     fused = sim.stage_kernels() == "fused"
+    carry = sim.stage_kernels() == "carry"
     cons_host = sim.get_state()
 
     for _ in range(args.warmup):
@@ -567,8 +568,9 @@ def main():
     ms = statistics.median(regions)
     value = aggregate_rate(ncell, args.steps, world, ms)
     n_active = sum(1 for s in ic.shape if s > 1)
-    # k_begin, k_end, and per stage: prims, the sweeps, E^c, update (fused: prims + one kernel)
-    launches_per_cycle = 2 + 2 * (2 if fused else 3 + n_active)
+    # k_begin, k_end, and per stage: prims, the sweeps, E^c, update (fused: prims + one kernel;
+    # carry: no prims kernel, the update recovers the next stage's primitives)
+    launches_per_cycle = 2 + 2 * (2 if fused else (2 if carry else 3) + n_active)
 
     # op counts from the oracle's pinned counter on a 32^3 corner of the box's state
     sample = ([np.ascontiguousarray(a[:32, :32, :32]) for a in cons_host] if args.n > 32
@@ -633,7 +635,8 @@ def main():
     sim.close()
     del pinned, out_pinned
 
-    def time_variant(precision, ic_v=None, steps=None, warmup=None, **kw):
+    def time_variant(precision, ic_v=None, steps=None, warmup=None, stage=None, kernels=False,
+                     **kw):
         # another configuration (same box unless given), same timing rules, one region
         ic_v = ic if ic_v is None else ic_v
         steps = args.steps if steps is None else steps
@@ -641,6 +644,8 @@ def main():
         sv = idx.Sim(ic_v.shape, ic_v.lengths, ic_v.gamma, 0.4, precision,
                      stream=stream.cuda_stream, **kw)
         sv.set_primitive(ic_v.prim)
+        if stage:
+            sv.set_stage_kernels(stage)
         for _ in range(warmup):
             sv.step()
         torch.cuda.synchronize()
@@ -653,7 +658,9 @@ def main():
         sv.time()
         out = {"value": aggregate_rate(ic_v.ncells, steps, world, msv), "unit": UNIT,
                "ms_per_step": msv / steps, "steps": steps,
-               "sweep_shapes_xyz": sv.sweep_shapes()}
+               "sweep_shapes_xyz": sv.sweep_shapes(), "stage_kernels": sv.stage_kernels()}
+        if kernels:
+            out["kernel_ms"] = sv.kernel_times(reps=2)
         sv.close()
         return out
 
@@ -684,7 +691,11 @@ def main():
 
     variants = {}
     if args.precision == "fp64" and not args.no_variants:
-        variants["fp32_bulk"] = with_roofline(guarded(time_variant, "fp32"), "fp32", counts)
+        variants["fp32_bulk"] = with_roofline(guarded(time_variant, "fp32", kernels=True),
+                                              "fp32", counts)
+        # the six kernels per stage (primitive recovery a kernel of its own), for comparison
+        variants["fp32_bulk_split"] = with_roofline(
+            guarded(time_variant, "fp32", stage="split", kernels=True), "fp32", counts)
         # the 512^3 box: the FP32-bulk configuration, and FP64 beside it
         ic512 = inputs.turbulent_box(512, seed=0)
         variants["fp32_bulk_512"] = with_roofline(guarded(time_variant, "fp32", ic512),

@@ -158,8 +158,9 @@ int idx_time(const idx_sim* sim, double* t, double* next_dt);
 int idx_step_count(const idx_sim* sim, int64_t* nsteps);
 
 /* Device bytes idx_create allocates for this grid and precision with RK2 (FP64 432 B per
- * cell, FP32 bulk 280 B per cell, plus alignment; RK3 adds 64 B per cell); no device
- * call.  For admission control. */
+ * cell, FP32 bulk 304 B per cell on a periodic grid -- 24 B of it the stage-1 face fields
+ * of the carried-primitive stages -- and 280 B on a padded one, plus alignment; RK3 adds
+ * 64 B per cell and drops those 24 B); no device call.  For admission control. */
 int idx_footprint(const idx_grid* grid, int precision, uint64_t* bytes);
 
 /* Device bytes idx_create allocates for this grid and any valid solver (RK order and
@@ -196,7 +197,9 @@ int idx_set_clock(idx_sim* sim, const idx_clock* clock);
  * of `reps` cycles launched kernel by kernel with CUDA events between them on the sim's
  * stream: ms[0] primitive recovery, [1] x sweep (PLM + HLLD), [2] y sweep, [3] z sweep,
  * [4] E^c edge EMFs, [5] update (0 for a direction that is not integrated).  With the fused
- * FP32-bulk stage (idx_stage_kernels) ms[5] is the fused kernel and ms[1..4] are 0.  The
+ * FP32-bulk stage (idx_stage_kernels) ms[5] is the fused kernel and ms[1..4] are 0; with
+ * the carried-primitive stages ms[0] is 0 and ms[5] is the update that also forms the next
+ * stage's primitives.  The
  * cycles are real: the sim advances by `reps` cycles.  A measurement aid, not part of the
  * method. */
 int idx_kernel_times(idx_sim* sim, int reps, double ms[6]);
@@ -233,14 +236,25 @@ int idx_set_sweep_shapes(idx_sim* sim, const int shapes[3]);
  * (with their 2-cell periodic halo) plane by plane into shared memory by bulk tensor
  * copies, forms the x/y/z Riemann fluxes, the E^c EMFs and the update of its cells there,
  * and writes only the new state; the primitive recovery stays a kernel of its own.
- * mode: 0 automatic (the split kernels, which are faster on this GPU), 1 the split kernels
- * (primitives, three sweeps, E^c, update), 2 the fused kernel (IDX_EINVAL where it does not
- * fit).  The two do the same arithmetic per face, edge and cell in the same order.
+ * mode: 0 automatic (the carried-primitive stages where they fit, else the split kernels),
+ * 1 the split kernels (primitives, three sweeps, E^c, update), 2 the fused kernel, 3 the
+ * carried-primitive stages (IDX_EINVAL for 2 or 3 where they do not fit).  The fused and
+ * split kernels do the same arithmetic per face, edge and cell in the same order.
+ * The carried-primitive stages (FP32 bulk, RK2, field form, periodic grid) run the three
+ * sweeps and E^c as the split kernels do, but each update also recovers the primitives of
+ * the state it forms (its cells' upper face fields formed there too), so no stage has a
+ * primitive kernel, and the RK2 combine of Eq. 9 is carried as the half sum
+ * S = (U^n + U*)/2 = U^n + (dt/2) L(U^n): stage 1 writes S and the face fields of U*,
+ * stage 2 forms U^{n+1} = S + (dt/2) L(U*) from S alone.  This changes FP64 rounding order
+ * only.  A state that another path changed (a batch's work-list kernels, the split
+ * kernels) gets its primitives recovered before the next carried cycle.  A non-physical
+ * cell found at the end of a cycle becomes the error of the next cycle, as with the split
+ * kernels, whose primitive recovery finds it there.
  * A measurement and testing aid; call it before stepping. */
 int idx_set_stage_kernels(idx_sim* sim, int mode);
 
-/* *fused_in_use = 1 if the sim's stages run the fused kernel, else 0. */
-int idx_stage_kernels(const idx_sim* sim, int* fused_in_use);
+/* *in_use = the stage kernels the sim runs: 1 split, 2 fused, 3 carried primitives. */
+int idx_stage_kernels(const idx_sim* sim, int* in_use);
 
 /* Free the sim and its device memory (and its stream, if the library made it). */
 void idx_destroy(idx_sim* sim);

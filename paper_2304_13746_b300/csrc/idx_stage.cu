@@ -56,6 +56,10 @@ struct Ctrl {
   unsigned long long inv_prev;     // bits of the inverse CFL time for the next dt
   unsigned long long inv_acc;      // running max (bits) over the current cycle's stages
   unsigned long long bad_cell;     // min flat index of a non-physical cell
+  // min flat index of a non-physical cell of the state a cycle ended with, found by the
+  // update that also formed that state's primitives; it becomes the error when the next
+  // cycle starts, where the primitive recovery of the split kernels would have found it
+  unsigned long long bad_next;
   long long nsteps;
   int done;
   int err;
@@ -138,6 +142,82 @@ __device__ __forceinline__ void flag_bad(Ctrl* ctrl, int c) {
   atomicCAS(&ctrl->err, 0, IDX_ENONPHYS);
   atomicMin(&ctrl->bad_cell, (unsigned long long)c);
 }
+__device__ __forceinline__ void flag_bad_next(Ctrl* ctrl, int c) {
+  atomicMin(&ctrl->bad_next, (unsigned long long)c);
+}
+
+// FP32-bulk primitive recovery of cell c from its FP64 conserved values (rho, m, E)
+// and its six face fields (lower and upper face per direction), held in registers;
+// writes W and the cell-centre EMFs and returns true for a non-physical cell.
+__device__ __forceinline__ bool prims_f32_vals(const Geo& g, double rho, double mx, double my,
+                                               double mz, double en, double bx0,
+                                               double bx1, double by0, double by1,
+                                               double bz0, double bz1,
+                                               const Ptr8<float>& W,
+                                               const CellEmf<float>& cc, int c) {
+  // The velocities and cell-centre B go out in FP32; the pressure keeps FP64 accuracy.  Where every lane's rho, m and face B lie in [2^-32, 2^32) (or are
+  // 0), the kinetic and magnetic energies are formed in double-float arithmetic on the
+  // FP32 pipe (each input split exactly into 24 + 23 bits; error-free products and
+  // sums; ~2^-46 relative) and only the cancellation E - K - M and the factor
+  // (gamma - 1) take FP64 operations, 3 per cell.  Elsewhere all of it is FP64.
+  const bool in_range = df_in_range(rho) & df_in_range(mx) & df_in_range(my) &
+                        df_in_range(mz) & df_in_range(bx0) & df_in_range(bx1) &
+                        df_in_range(by0) & df_in_range(by1) & df_in_range(bz0) &
+                        df_in_range(bz1);
+  double P;
+  float rhof, irf, vx, vy, vz, bx, by, bz;
+  if (__all_sync(__activemask(), in_range)) {
+    const DF rd = df_split(rho), mxd = df_split(mx), myd = df_split(my), mzd = df_split(mz);
+    // 1/rho: the FP32 reciprocal y of the high part, one Newton-Raphson step on the
+    // double-float rho: 1/rho = y (1 + r) + O(r^2), r = 1 - rho y
+    const float y = __frcp_rn(rd.h);
+    const float r = __fmaf_rn(-rd.l, y, __fmaf_rn(-rd.h, y, 1.0f));
+    const float yr = __fmul_rn(y, r);
+    const DF ir2 = {0.5f * y, 0.5f * yr};  // 1 / (2 rho)
+    const DF sx = df_add(df_split(bx0), df_split(bx1));  // 2 B_c
+    const DF sy = df_add(df_split(by0), df_split(by1));
+    const DF sz = df_add(df_split(bz0), df_split(bz1));
+    const DF kin = df_mul(df_sum3(df_sqr(mxd), df_sqr(myd), df_sqr(mzd)), ir2);
+    const DF ssq = df_sum3(df_sqr(sx), df_sqr(sy), df_sqr(sz));
+    const DF km = df_add(kin, DF{0.125f * ssq.h, 0.125f * ssq.l});  // K + |B_c|^2 / 2
+    P = g.gm1 * ((en - f2d_warp(km.h)) - f2d_warp(km.l));
+    rhof = __fadd_rn(rd.h, rd.l);
+    irf = __fadd_rn(y, yr);
+    vx = __fadd_rn(mxd.h, mxd.l) * irf;
+    vy = __fadd_rn(myd.h, myd.l) * irf;
+    vz = __fadd_rn(mzd.h, mzd.l) * irf;
+    bx = 0.5f * __fadd_rn(sx.h, sx.l);
+    by = 0.5f * __fadd_rn(sy.h, sy.l);
+    bz = 0.5f * __fadd_rn(sz.h, sz.l);
+  } else {
+    // 1/rho only scales the kinetic energy: an FP32 seed refined by one Newton-Raphson
+    // step y1 = y0 + y0 (1 - rho y0) in FP64 (taken on y0/2, giving 1/(2 rho))
+    rhof = d2f_warp(rho);
+    const float y0f = __frcp_rn(rhof);
+    const double y0h = f2d(0.5f * y0f);
+    const double irh = fma(y0h, fma(-rho, f2d(y0f), 1.0), y0h);
+    const double sx = bx0 + bx1, sy = by0 + by1, sz = bz0 + bz1;  // 2 B_c
+    // P = (gamma - 1) (E - |m|^2 / (2 rho) - |2 B_c|^2 / 8), FP64 with fused steps
+    const double msq = fma(mx, mx, fma(my, my, mz * mz));
+    const double ssq = fma(sx, sx, fma(sy, sy, sz * sz));
+    P = g.gm1 * fma(-0.125, ssq, fma(-msq, irh, en));
+    irf = 2.0f * d2f_warp(irh);
+    vx = d2f_warp(mx) * irf; vy = d2f_warp(my) * irf; vz = d2f_warp(mz) * irf;
+    bx = 0.5f * d2f_warp(sx); by = 0.5f * d2f_warp(sy); bz = 0.5f * d2f_warp(sz);
+  }
+  // 0 < rho, P < infinity, tested on the bit patterns (FP64 compares take FP64 slots)
+  const bool bad =
+      !pos_finite(rho) || !pos_finite(P) || !isfinite(vx) || !isfinite(vy) || !isfinite(vz);
+  W.f[0][c] = rhof; W.f[1][c] = vx; W.f[2][c] = vy; W.f[3][c] = vz;
+  W.f[4][c] = d2f_warp(P);
+  W.f[5][c] = bx; W.f[6][c] = by; W.f[7][c] = bz;
+  if (cc.f[0]) {
+    cc.f[0][c] = -(vy * bz - vz * by);
+    cc.f[1][c] = -(vz * bx - vx * bz);
+    cc.f[2][c] = -(vx * by - vy * bx);
+  }
+  return bad;
+}
 
 // ---------------------------------------------------------------------------
 // Primitive recovery: rho, v = m/rho, P from E (at FP64 accuracy in both variants), and
@@ -171,72 +251,12 @@ __device__ __forceinline__ void prims_body(const Geo& g, const Ptr8<const double
       cc.f[2][c] = -(vx * by - vy * bx);
     }
   } else {
-    // FP32 bulk: the velocities and cell-centre B go out in FP32; the pressure keeps
-    // FP64 accuracy.  Where every lane's rho, m and face B lie in [2^-32, 2^32) (or are
-    // 0), the kinetic and magnetic energies are formed in double-float arithmetic on the
-    // FP32 pipe (each input split exactly into 24 + 23 bits; error-free products and
-    // sums; ~2^-46 relative) and only the cancellation E - K - M and the factor
-    // (gamma - 1) take FP64 operations, 3 per cell.  Elsewhere all of it is FP64.
     const double mx = U.f[1][c], my = U.f[2][c], mz = U.f[3][c];
     const double bx0 = U.f[5][c], bx1 = U.f[5][shifted(g, c, i, 0, 1)];
     const double by0 = U.f[6][c], by1 = U.f[6][shifted(g, c, j, 1, 1)];
     const double bz0 = U.f[7][c], bz1 = U.f[7][shifted(g, c, k, 2, 1)];
-    const bool in_range = df_in_range(rho) & df_in_range(mx) & df_in_range(my) &
-                          df_in_range(mz) & df_in_range(bx0) & df_in_range(bx1) &
-                          df_in_range(by0) & df_in_range(by1) & df_in_range(bz0) &
-                          df_in_range(bz1);
-    double P;
-    float rhof, irf, vx, vy, vz, bx, by, bz;
-    if (__all_sync(__activemask(), in_range)) {
-      const DF rd = df_split(rho), mxd = df_split(mx), myd = df_split(my), mzd = df_split(mz);
-      // 1/rho: the FP32 reciprocal y of the high part, one Newton-Raphson step on the
-      // double-float rho: 1/rho = y (1 + r) + O(r^2), r = 1 - rho y
-      const float y = __frcp_rn(rd.h);
-      const float r = __fmaf_rn(-rd.l, y, __fmaf_rn(-rd.h, y, 1.0f));
-      const float yr = __fmul_rn(y, r);
-      const DF ir2 = {0.5f * y, 0.5f * yr};  // 1 / (2 rho)
-      const DF sx = df_add(df_split(bx0), df_split(bx1));  // 2 B_c
-      const DF sy = df_add(df_split(by0), df_split(by1));
-      const DF sz = df_add(df_split(bz0), df_split(bz1));
-      const DF kin = df_mul(df_sum3(df_sqr(mxd), df_sqr(myd), df_sqr(mzd)), ir2);
-      const DF ssq = df_sum3(df_sqr(sx), df_sqr(sy), df_sqr(sz));
-      const DF km = df_add(kin, DF{0.125f * ssq.h, 0.125f * ssq.l});  // K + |B_c|^2 / 2
-      P = g.gm1 * ((U.f[4][c] - f2d_warp(km.h)) - f2d_warp(km.l));
-      rhof = __fadd_rn(rd.h, rd.l);
-      irf = __fadd_rn(y, yr);
-      vx = __fadd_rn(mxd.h, mxd.l) * irf;
-      vy = __fadd_rn(myd.h, myd.l) * irf;
-      vz = __fadd_rn(mzd.h, mzd.l) * irf;
-      bx = 0.5f * __fadd_rn(sx.h, sx.l);
-      by = 0.5f * __fadd_rn(sy.h, sy.l);
-      bz = 0.5f * __fadd_rn(sz.h, sz.l);
-    } else {
-      // 1/rho only scales the kinetic energy: an FP32 seed refined by one Newton-Raphson
-      // step y1 = y0 + y0 (1 - rho y0) in FP64 (taken on y0/2, giving 1/(2 rho))
-      rhof = d2f_warp(rho);
-      const float y0f = __frcp_rn(rhof);
-      const double y0h = f2d(0.5f * y0f);
-      const double irh = fma(y0h, fma(-rho, f2d(y0f), 1.0), y0h);
-      const double sx = bx0 + bx1, sy = by0 + by1, sz = bz0 + bz1;  // 2 B_c
-      // P = (gamma - 1) (E - |m|^2 / (2 rho) - |2 B_c|^2 / 8), FP64 with fused steps
-      const double msq = fma(mx, mx, fma(my, my, mz * mz));
-      const double ssq = fma(sx, sx, fma(sy, sy, sz * sz));
-      P = g.gm1 * fma(-0.125, ssq, fma(-msq, irh, U.f[4][c]));
-      irf = 2.0f * d2f_warp(irh);
-      vx = d2f_warp(mx) * irf; vy = d2f_warp(my) * irf; vz = d2f_warp(mz) * irf;
-      bx = 0.5f * d2f_warp(sx); by = 0.5f * d2f_warp(sy); bz = 0.5f * d2f_warp(sz);
-    }
-    // 0 < rho, P < infinity, tested on the bit patterns (FP64 compares take FP64 slots)
-    if (!pos_finite(rho) || !pos_finite(P) || !isfinite(vx) || !isfinite(vy) || !isfinite(vz))
+    if (prims_f32_vals(g, rho, mx, my, mz, U.f[4][c], bx0, bx1, by0, by1, bz0, bz1, W, cc, c))
       flag_bad(ctrl, c);
-    W.f[0][c] = rhof; W.f[1][c] = vx; W.f[2][c] = vy; W.f[3][c] = vz;
-    W.f[4][c] = d2f_warp(P);
-    W.f[5][c] = bx; W.f[6][c] = by; W.f[7][c] = bz;
-    if (cc.f[0]) {
-      cc.f[0][c] = -(vy * bz - vz * by);
-      cc.f[1][c] = -(vz * bx - vx * bz);
-      cc.f[2][c] = -(vx * by - vy * bx);
-    }
   }
 }
 
@@ -969,7 +989,10 @@ __device__ __forceinline__ void block_max_to(unsigned long long* bits, V v) {
 }
 
 // Returns the cell's inverse CFL contribution (0 outside the grid), in the bulk type.
-template <typename T, bool COMBINE, bool POT = false>
+// FP32 bulk converts its 8 FP32 increments to FP64 with one warp vote (ONE_VOTE), or each
+// by a select (fewer registers live at once: the batch kernels, which also hold a member's
+// header, keep their occupancy that way).
+template <typename T, bool COMBINE, bool POT = false, bool ONE_VOTE = true>
 __device__ __forceinline__ T update_body(const Geo& g, const Ptr8<const double>& Uin,
                                               const Ptr8<const double>& U0,
                                               const Ptr8<const T>& Fx, const Ptr8<const T>& Fy,
@@ -996,17 +1019,15 @@ __device__ __forceinline__ T update_body(const Geo& g, const Ptr8<const double>&
     // the scaled step is formed once per cell (one FP64 product), not once per field
     [[maybe_unused]] const float dtf =
         std::is_same<T, float>::value ? d2f_warp(COMBINE ? w * dt : dt) : 0.f;
-    auto accumulate = [&](int f, T div) -> double {
-      if constexpr (std::is_same<T, double>::value) {
-        return Uin.f[f][c] - dt * div;
-      } else {
-        if (COMBINE) {
-          const float wdt = dtf;
-          if (w == w0) return fma(w, U0.f[f][c] + Uin.f[f][c], f2d(-wdt * div));
-          return fma(w0, U0.f[f][c], w * Uin.f[f][c]) + f2d(-wdt * div);
-        }
-        return Uin.f[f][c] + f2d(-dtf * div);
+    // FP32 bulk: the FP32 increments -w dt (div) of the 8 fields, converted to FP64 together
+    // (one warp vote for the rare subnormal lanes) and then accumulated
+    [[maybe_unused]] float finc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    auto accumulate = [&](int f, double dinc) -> double {
+      if (COMBINE) {
+        if (w == w0) return fma(w, U0.f[f][c] + Uin.f[f][c], dinc);
+        return fma(w0, U0.f[f][c], w * Uin.f[f][c]) + dinc;
       }
+      return Uin.f[f][c] + dinc;
     };
     // FP64: dt folded into the inverse cell sizes, each difference accumulated by one FMA
     double kdt[3];
@@ -1076,7 +1097,7 @@ __device__ __forceinline__ T update_body(const Geo& g, const Ptr8<const double>&
           const int s = slot(f, d);
           div += (F[d].f[s][up[d]] - F[d].f[s][c]) * idl(d);
         }
-        out[f] = accumulate(f, div);
+        finc[f] = -dtf * div;
       }
     }
 #pragma unroll
@@ -1118,7 +1139,19 @@ __device__ __forceinline__ T update_body(const Geo& g, const Ptr8<const double>&
           curl += (F[a].f[s][up[a]] - F[a].f[s][c]) * idl(a);
         }
       }
-      out[5 + d] = accumulate(5 + d, curl);
+      finc[5 + d] = -dtf * curl;
+    }
+    if constexpr (std::is_same<T, float>::value) {
+      double dinc[8];
+      if constexpr (ONE_VOTE) {
+        f2d_many(finc, dinc);
+      } else {
+#pragma unroll
+        for (int f = 0; f < 8; ++f) dinc[f] = f2d(finc[f]);
+      }
+#pragma unroll
+      for (int f = 0; f < 8; ++f)
+        if (!(POT && f >= 5)) out[f] = accumulate(f, dinc[f]);
     }
 #pragma unroll
     for (int f = 0; f < 8; ++f)
@@ -1148,6 +1181,136 @@ __global__ void __launch_bounds__(kThreads) k_update(Geo g, Ptr8<const double> U
                                              w0, &pot);
   // block max -> one atomic per block (positive doubles order like their bit patterns)
   block_max_to(&ctrl->inv_acc, inv);
+}
+
+// FP32 bulk, RK2, field form: the update of a stage that also recovers the primitives of
+// the state it forms, for the next stage (or the next cycle), so that the primitive
+// recovery reads no state of its own from HBM.  The RK2 combine U^{n+1} = (U^n + U*)/2 +
+// (dt/2) L(U*) (Eq. 9) is carried as the half sum S = (U^n + U*)/2 = U^n + (dt/2) L(U^n):
+//   stage 1 (STAGE2 false): U* = U^n + dt L(U^n) only in registers, for its primitives;
+//                           S -> Uout (all 8 fields), the face fields of U* -> Bs (the
+//                           normal field the stage-2 sweeps read);
+//   stage 2 (STAGE2 true):  U^{n+1} = S + (dt/2) L(U*) -> Uout, from S alone.
+// Each cell forms the stepped fields of its three lower faces and, for the cell-centre B
+// of its primitives, of its three upper faces (the lower faces of its upper neighbours,
+// formed again there).  The increments are FP32 (as in k_update<float>); every sum into the
+// state is FP64.  Stage-2 primitives belong to the next cycle: a non-physical cell there is
+// recorded in bad_next, which the next cycle's k_begin turns into the error.
+template <bool STAGE2>
+__global__ void __launch_bounds__(kThreads, 5) k_update_carry(Geo g, Ptr8<const double> Uin,
+                                                           Ptr8<const float> Fx,
+                                                           Ptr8<const float> Fy,
+                                                           Ptr8<const float> Fz,
+                                                           const float* Ex, const float* Ey,
+                                                           const float* Ez, Ptr8<double> Uout,
+                                                           Ptr3 Bs, Ptr8<float> W,
+                                                           CellEmf<float> cc, Ctrl* ctrl) {
+  const double dt = ctrl->dt;
+  if (!(dt > 0.0)) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  float inv = 0.f;
+  if (c < g.ncell) {
+    int ijk[3];
+    coords(g, c, ijk[0], ijk[1], ijk[2]);
+    const Ptr8<const float> F[3] = {Fx, Fy, Fz};
+    const float* E[3] = {Ex, Ey, Ez};
+    int up[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) up[d] = shifted(g, c, ijk[d], d, 1);
+    // stage 1 steps by dt, stage 2 by dt/2 (the RK2 weight of L(U*))
+    const float dtf = d2f_warp(STAGE2 ? 0.5 * dt : dt);
+    // FP32 increments: the 5 cell fields, then the field normal to d on the lower d-face
+    // (5 + d) and on the upper one (8 + d, the lower face of the upper neighbour, whose
+    // coordinates along the other two directions are those of c)
+    float inc[11];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+      float div = 0.f;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (!g.active[d]) continue;
+        const int sl = slot(f, d);
+        div += (F[d].f[sl][up[d]] - F[d].f[sl][c]) * g.inv_dlf[d];
+      }
+      inc[f] = -dtf * div;
+    }
+    auto face_inc = [&](int d, int q) -> float {
+      const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+      float curl = 0.f;
+      if (g.active[d]) {
+        if (g.active[t1])
+          curl += (E[t2][shifted(g, q, ijk[t1], t1, 1)] - E[t2][q]) * g.inv_dlf[t1];
+        if (g.active[t2])
+          curl -= (E[t1][shifted(g, q, ijk[t2], t2, 1)] - E[t1][q]) * g.inv_dlf[t2];
+      } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          if (a == d || !g.active[a]) continue;
+          const int sl = slot(5 + d, a);
+          curl += (F[a].f[sl][shifted(g, q, ijk[a], a, 1)] - F[a].f[sl][q]) * g.inv_dlf[a];
+        }
+      }
+      return -dtf * curl;
+    };
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      inc[5 + d] = face_inc(d, c);
+      // a one-cell direction: the upper face is the lower one
+      inc[8 + d] = g.active[d] ? face_inc(d, up[d]) : inc[5 + d];
+    }
+    double dinc[11];
+    f2d_many(inc, dinc);
+    double u[5], b0[3], b1[3];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) u[f] = Uin.f[f][c] + dinc[f];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      b0[d] = Uin.f[5 + d][c] + dinc[5 + d];
+      b1[d] = g.active[d] ? Uin.f[5 + d][up[d]] + dinc[8 + d] : b0[d];
+    }
+    if (STAGE2) {
+#pragma unroll
+      for (int f = 0; f < 5; ++f) Uout.f[f][c] = u[f];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Uout.f[5 + d][c] = b0[d];
+    } else {
+      // the half sum S = U^n + inc / 2 (the halving is exact in FP32 above 2^-125)
+      float half[8];
+#pragma unroll
+      for (int f = 0; f < 8; ++f) half[f] = 0.5f * inc[f];
+      double dhalf[8];
+      f2d_many(half, dhalf);
+#pragma unroll
+      for (int f = 0; f < 8; ++f) Uout.f[f][c] = Uin.f[f][c] + dhalf[f];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Bs.f[d][c] = b0[d];
+    }
+    if (prims_f32_vals(g, u[0], u[1], u[2], u[3], u[4], b0[0], b1[0], b0[1], b1[1], b0[2],
+                       b1[2], W, cc, c)) {
+      if (STAGE2) flag_bad_next(ctrl, c);
+      else flag_bad(ctrl, c);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if (g.active[d]) inv += max_nn(F[d].f[7][c], F[d].f[7][up[d]]) * g.inv_dlf[d];
+  }
+  block_max_to(&ctrl->inv_acc, inv);
+}
+
+// Primitives of the state U for the first cycle of the carried-primitive stages (after
+// another path changed the state): a non-physical cell goes to bad_next, as if the last
+// cycle's update had found it.
+__global__ void __launch_bounds__(kThreads, 6) k_prims_next(Geo g, Ptr8<const double> U,
+                                                            Ptr8<float> W, CellEmf<float> cc,
+                                                            Ctrl* ctrl) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  int i, j, k;
+  coords(g, c, i, j, k);
+  if (prims_f32_vals(g, U.f[0][c], U.f[1][c], U.f[2][c], U.f[3][c], U.f[4][c], U.f[5][c],
+                     U.f[5][shifted(g, c, i, 0, 1)], U.f[6][c], U.f[6][shifted(g, c, j, 1, 1)],
+                     U.f[7][c], U.f[7][shifted(g, c, k, 2, 1)], W, cc, c))
+    flag_bad_next(ctrl, c);
 }
 
 // Inverse CFL time of a state from the face speeds alone (first cycle).
@@ -1204,6 +1367,11 @@ __device__ __forceinline__ void begin_body(Ctrl* c) {
   c->dt = dt;
   c->clamped = clamped;
   c->inv_acc = 0ull;
+  if (c->bad_next != ~0ull) {  // the cycle starts from a non-physical state
+    c->err = IDX_ENONPHYS;
+    c->bad_cell = c->bad_next < c->bad_cell ? c->bad_next : c->bad_cell;
+    c->bad_next = ~0ull;
+  }
 }
 
 // Cycle epilogue: advance t, keep the larger stage speed bound for the next dt.
@@ -1272,8 +1440,14 @@ struct idx_sim {
   FusedMaps fmaps;            // primitive-plane boxes of its tiles
   bool fused_ok;              // the grid and solver fit it
   int fused_zc;               // z-planes per CTA
-  int stage_mode;             // 0 automatic, 1 split kernels, 2 fused kernel
+  int stage_mode;             // 0 automatic, 1 split kernels, 2 fused kernel, 3 carried
   bool use_fused;             // the choice the captured cycle holds
+  // FP32 bulk, RK2, field form, periodic: the updates also recover the next stage's
+  // primitives (k_update_carry), so a stage has no primitive-recovery kernel
+  bool carry_ok;              // the sim fits it (Bs allocated)
+  bool use_carry;             // the choice the captured cycle holds
+  bool w_fresh;               // W and the cell-centre EMFs hold the primitives of U
+  Ptr3 Bs;                    // stage-1 face fields (the stage-2 sweeps' normal field)
 };
 
 namespace {
@@ -1452,31 +1626,40 @@ int tune_sweeps(idx_sim* s, const Ptr8<double>& U, const Ptr8<T>& W, Ptr8<T>* F)
   return rc;
 }
 
+// The sweeps of a stage, with the normal face field of direction d from bface[d].
 template <typename T>
-void launch_fluxes(idx_sim* s, const Ptr8<double>& Uin, const Ptr8<T>& W, Ptr8<T>* F,
-                   int check_dt, bool fork = false) {
+void launch_sweeps(idx_sim* s, const double* const bface[3], const Ptr8<T>& W, Ptr8<T>* F,
+                   int check_dt, bool fork) {
   const Geo& g = s->geo;
-  k_prims<T><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), W, cell_emf<T>(s),
-                                                              s->ctrl, check_dt);
   if (!(fork && s->side[0])) {
     for (int d = 0; d < 3; ++d)
-      if (g.active[d]) launch_sweep<T>(s, d, W, Uin.f[5 + d], F[d], check_dt);
+      if (g.active[d]) launch_sweep<T>(s, d, W, bface[d], F[d], check_dt);
     return;
   }
   // the three sweeps read the primitives and write their own fluxes: y and z on the side
   // streams, forked after the primitives and joined before the EMFs
   const cudaStream_t main = s->stream;
   cudaEventRecord(s->fork_ev, main);
-  if (g.active[0]) launch_sweep<T>(s, 0, W, Uin.f[5], F[0], check_dt);
+  if (g.active[0]) launch_sweep<T>(s, 0, W, bface[0], F[0], check_dt);
   for (int d = 1; d < 3; ++d) {
     if (!g.active[d]) continue;
     cudaStreamWaitEvent(s->side[d - 1], s->fork_ev, 0);
     s->stream = s->side[d - 1];
-    launch_sweep<T>(s, d, W, Uin.f[5 + d], F[d], check_dt);
+    launch_sweep<T>(s, d, W, bface[d], F[d], check_dt);
     s->stream = main;
     cudaEventRecord(s->join_ev[d - 1], s->side[d - 1]);
     cudaStreamWaitEvent(main, s->join_ev[d - 1], 0);
   }
+}
+
+template <typename T>
+void launch_fluxes(idx_sim* s, const Ptr8<double>& Uin, const Ptr8<T>& W, Ptr8<T>* F,
+                   int check_dt, bool fork = false) {
+  const Geo& g = s->geo;
+  k_prims<T><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(g, cst(Uin), W, cell_emf<T>(s),
+                                                              s->ctrl, check_dt);
+  const double* const bface[3] = {Uin.f[5], Uin.f[6], Uin.f[7]};
+  launch_sweeps<T>(s, bface, W, F, check_dt, fork);
 }
 
 // The stages of one cycle (Sec. 2.7, Table 1): input, output and weights (w, w0) of
@@ -1615,8 +1798,54 @@ void launch_stage(idx_sim* s, const StagePlan& p, int st, const Ptr8<T>& W, Ptr8
   launch_update<T>(s, p, st, F, E);
 }
 
+// The update of stage st of the carried-primitive cycle.
+void launch_update_carry(idx_sim* s, int st) {
+  const Geo& g = s->geo;
+  if (st == 0)
+    k_update_carry<false><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
+        g, cst(s->U), cst(s->Ff[0]), cst(s->Ff[1]), cst(s->Ff[2]), s->Ef[0], s->Ef[1],
+        s->Ef[2], s->U1, s->Bs, s->Wf, s->Cf, s->ctrl);
+  else
+    k_update_carry<true><<<blocks_for(g.ncell), kThreads, 0, s->stream>>>(
+        g, cst(s->U1), cst(s->Ff[0]), cst(s->Ff[1]), cst(s->Ff[2]), s->Ef[0], s->Ef[1],
+        s->Ef[2], s->U, s->Bs, s->Wf, s->Cf, s->ctrl);
+}
+
+// Normal face fields the sweeps of stage st read: those of U^n, then those of U*.
+void carry_bface(const idx_sim* s, int st, const double* bface[3]) {
+  for (int d = 0; d < 3; ++d) bface[d] = st == 0 ? s->U.f[5 + d] : s->Bs.f[d];
+}
+
+// Both stages of the carried-primitive cycle: sweeps, E^c, update (which also forms the
+// primitives of the state it writes).  W and the cell-centre EMFs hold the primitives of
+// U on entry and on exit.
+void launch_carry_stages(idx_sim* s) {
+  const StagePlan p = stage_plan(s);
+  for (int st = 0; st < 2; ++st) {
+    const double* bface[3];
+    carry_bface(s, st, bface);
+    launch_sweeps<float>(s, bface, s->Wf, s->Ff, 1, true);
+    launch_emf<float>(s, p, st, s->Wf, s->Ff, s->Ef);
+    launch_update_carry(s, st);
+  }
+}
+
+// Before a carried-primitive cycle on stream st: the primitives of U, unless the last
+// thing that changed U left them in W already.
+void refresh_carry(idx_sim* s, cudaStream_t st) {
+  if (!s->use_carry || s->w_fresh) return;
+  const Geo& g = s->geo;
+  k_prims_next<<<blocks_for(g.ncell), kThreads, 0, st>>>(g, cst(s->U), s->Wf, s->Cf, s->ctrl);
+  s->w_fresh = true;
+}
+
 void launch_cycle(idx_sim* s) {
   k_begin<<<1, 1, 0, s->stream>>>(s->ctrl);
+  if (s->use_carry) {
+    launch_carry_stages(s);
+    k_end<<<1, 1, 0, s->stream>>>(s->ctrl);
+    return;
+  }
   const StagePlan p = stage_plan(s);
   for (int st = 0; st < p.n; ++st) {
     if (s->solver.precision == IDX_FP32_BULK)
@@ -1645,8 +1874,11 @@ std::mutex g_tune_mutex;
 // split kernels' arithmetic bit for bit, but measured 2x slower at 256^3 (4.4 ms against
 // 2.2 ms for the sweeps, E^c and update it replaces) -- its halo faces and per-face address
 // arithmetic make it instruction-bound at two CTAs per SM.
+// The carried-primitive stages are the default where they fit (FP32 bulk, RK2, field
+// form, periodic).
 void choose_stage_kernels(idx_sim* s) {
   s->use_fused = s->fused_ok && s->stage_mode == 2;
+  s->use_carry = s->carry_ok && (s->stage_mode == 0 || s->stage_mode == 3);
 }
 
 int tune_once(idx_sim* s) {
@@ -1761,25 +1993,36 @@ int after_new_state(idx_sim* s) {
   c.t_end = std::numeric_limits<double>::infinity();
   c.cfl = s->solver.cfl;
   c.bad_cell = ~0ull;
+  c.bad_next = ~0ull;
   IDX_TRY(cudaMemcpyAsync(s->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s->stream));
   // the speed pass of the first cycle
   if (s->solver.precision == IDX_FP32_BULK) launch_speed_pass<float>(s, s->U, s->Wf, s->Ff);
   else launch_speed_pass<double>(s, s->U, s->Wd, s->Fd);
   IDX_TRY(cudaGetLastError());
+  s->w_fresh = true;  // the speed pass recovered the primitives of U
   int rc = sync_ctrl(s);
   if (rc != IDX_OK) return rc;
   s->last_bad = -1;
   return pending_error(s);
 }
 
+// The carried-primitive stages (k_update_carry): FP32 bulk, RK2, field form, periodic (a
+// padded grid refills its ghosts before each stage's primitives).
+bool carry_fits(bool f32, bool rk3, bool pot, bool bounded) {
+  return f32 && !rk3 && !pot && !bounded;
+}
+
 // Device bytes of one sim (the single allocation of idx_create); RK3 adds a state, the
 // vector-potential form adds Bref and one edge potential per RK register.
-size_t sim_bytes(long long ncell, bool f32, bool rk3 = false, bool pot = false) {
+size_t sim_bytes(long long ncell, bool f32, bool rk3 = false, bool pot = false,
+                 bool bounded = false) {
   auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t arr_d = align(sizeof(double) * ncell);
   const size_t arr_t = align((f32 ? sizeof(float) : sizeof(double)) * ncell);
   const size_t pot_arrays = pot ? (rk3 ? 12 : 9) : 0;
-  return ((rk3 ? 24 : 16) + pot_arrays) * arr_d + (8 + 24 + 3 + 3) * arr_t + align(sizeof(Ctrl));
+  const size_t carry_arrays = carry_fits(f32, rk3, pot, bounded) ? 3 : 0;  // Bs
+  return ((rk3 ? 24 : 16) + pot_arrays + carry_arrays) * arr_d + (8 + 24 + 3 + 3) * arr_t +
+         align(sizeof(Ctrl));
 }
 
 using EncodeTiled = PFN_cuTensorMapEncodeTiled_v12000;
@@ -1969,7 +2212,7 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
   const size_t arr_d = align(sizeof(double) * ncell), arr_t = align(tsz * ncell);
   const bool rk3 = solver->rk_order == 3;
   s->pot = solver->induction == IDX_INDUCTION_POTENTIAL;
-  const size_t bytes = sim_bytes(ncell, f32, rk3, s->pot);
+  const size_t bytes = sim_bytes(ncell, f32, rk3, s->pot, bounded);
   if (stream) {
     s->stream = (cudaStream_t)stream;
     s->own_stream = false;
@@ -1993,6 +2236,9 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
   for (int f = 0; f < 8; ++f) { s->U1.f[f] = (double*)p; p += arr_d; }
   if (rk3)
     for (int f = 0; f < 8; ++f) { s->U2.f[f] = (double*)p; p += arr_d; }
+  s->carry_ok = carry_fits(f32, rk3, s->pot, bounded);
+  if (s->carry_ok)
+    for (int d = 0; d < 3; ++d) { s->Bs.f[d] = (double*)p; p += arr_d; }
   if (s->pot) {
     for (int e = 0; e < 3; ++e) { s->Bref.f[e] = (double*)p; p += arr_d; }
     for (int e = 0; e < 3; ++e) { s->A.f[e] = (double*)p; p += arr_d; }
@@ -2269,7 +2515,9 @@ int idx_step(idx_sim* s, double* dt_taken) {
   if (!s) return IDX_EINVAL;
   int rc = build_graph(s);
   if (rc != IDX_OK) return rc;
+  refresh_carry(s, s->stream);
   IDX_TRY(cudaGraphLaunch(s->exec, s->stream));
+  if (!s->use_carry) s->w_fresh = false;
   if (!dt_taken) return IDX_OK;
   rc = sync_ctrl(s);
   if (rc != IDX_OK) return rc;
@@ -2305,6 +2553,8 @@ int idx_advance(idx_sim* s, double t_end, int64_t* nsteps) {
     return std::max(1, (int)std::ceil(left) + 1);
   };
   int chunk = chunk_for(c);
+  refresh_carry(s, s->stream);
+  if (!s->use_carry) s->w_fresh = false;
   while (true) {
     for (int q = 0; q < chunk; ++q) IDX_TRY(cudaGraphLaunch(s->exec, s->stream));
     rc = sync_ctrl(s);
@@ -2351,6 +2601,8 @@ int idx_kernel_times(idx_sim* s, int reps, double ms[6]) {
   int n_stage = 0;
   const Geo& g = s->geo;
   const bool f32 = s->solver.precision == IDX_FP32_BULK;
+  refresh_carry(s, s->stream);
+  if (!s->use_carry) s->w_fresh = false;
   for (int r = 0; r < reps; ++r) {
     k_begin<<<1, 1, 0, s->stream>>>(s->ctrl);
     const StagePlan plan = stage_plan(s);
@@ -2358,6 +2610,26 @@ int idx_kernel_times(idx_sim* s, int reps, double ms[6]) {
       const Ptr8<double>& Uin = *plan.in[st];
       launch_fill_ghosts(s, Uin);
       IDX_TRY(cudaEventRecord(ev[0], s->stream));
+      if (s->use_carry) {
+        // carried primitives: no primitive kernel (ms[0] = 0), the update forms them
+        IDX_TRY(cudaEventRecord(ev[1], s->stream));
+        const double* bface[3];
+        carry_bface(s, st, bface);
+        for (int d = 0; d < 3; ++d) {
+          if (g.active[d]) launch_sweep<float>(s, d, s->Wf, bface[d], s->Ff[d], 1);
+          IDX_TRY(cudaEventRecord(ev[2 + d], s->stream));
+        }
+        launch_emf<float>(s, plan, st, s->Wf, s->Ff, s->Ef);
+        IDX_TRY(cudaEventRecord(ev[5], s->stream));
+        launch_update_carry(s, st);
+        IDX_TRY(cudaEventRecord(ev[6], s->stream));
+        IDX_TRY(cudaEventSynchronize(ev[6]));
+        float t[6];
+        for (int q = 0; q < 6; ++q) IDX_TRY(cudaEventElapsedTime(&t[q], ev[q], ev[q + 1]));
+        for (int q = 0; q < 6; ++q) acc[q] += t[q];
+        ++n_stage;
+        continue;
+      }
       if (f32 && s->use_fused) {
         // fused stage: primitives in ms[0], the fused kernel in ms[5], nothing in between
         launch_prims_only(s, Uin, 1);
@@ -2443,8 +2715,9 @@ int idx_set_sweep_shapes(idx_sim* s, const int shapes[3]) {
 }
 
 int idx_set_stage_kernels(idx_sim* s, int mode) {
-  if (!s || mode < 0 || mode > 2) return IDX_EINVAL;
+  if (!s || mode < 0 || mode > 3) return IDX_EINVAL;
   if (mode == 2 && !s->fused_ok) return IDX_EINVAL;
+  if (mode == 3 && !s->carry_ok) return IDX_EINVAL;
   s->stage_mode = mode;
   choose_stage_kernels(s);
   // the captured cycle holds the old kernels
@@ -2453,11 +2726,11 @@ int idx_set_stage_kernels(idx_sim* s, int mode) {
   return IDX_OK;
 }
 
-int idx_stage_kernels(const idx_sim* cs, int* fused_in_use) {
+int idx_stage_kernels(const idx_sim* cs, int* in_use) {
   idx_sim* s = const_cast<idx_sim*>(cs);
-  if (!s || !fused_in_use) return IDX_EINVAL;
+  if (!s || !in_use) return IDX_EINVAL;
   choose_stage_kernels(s);
-  *fused_in_use = s->use_fused ? 1 : 0;
+  *in_use = s->use_fused ? 2 : (s->use_carry ? 3 : 1);
   return IDX_OK;
 }
 
@@ -2477,7 +2750,8 @@ int idx_footprint(const idx_grid* grid, int precision, uint64_t* bytes) {
   if (!grid_bc(grid, bc, pn)) return IDX_EINVAL;
   const long long ncell = (long long)pn[0] * pn[1] * pn[2];
   if (ncell >= (1ll << 31)) return IDX_EINVAL;
-  *bytes = (uint64_t)sim_bytes(ncell, precision == IDX_FP32_BULK);
+  const bool bounded = bc[0] || bc[1] || bc[2];
+  *bytes = (uint64_t)sim_bytes(ncell, precision == IDX_FP32_BULK, false, false, bounded);
   return IDX_OK;
 }
 
@@ -2488,8 +2762,9 @@ int idx_footprint_solver(const idx_grid* grid, const idx_solver* solver, uint64_
   if (!grid_bc(grid, bc, pn)) return IDX_EINVAL;
   const long long ncell = (long long)pn[0] * pn[1] * pn[2];
   if (ncell >= (1ll << 31)) return IDX_EINVAL;
+  const bool bounded = bc[0] || bc[1] || bc[2];
   *bytes = (uint64_t)sim_bytes(ncell, solver->precision == IDX_FP32_BULK, solver->rk_order == 3,
-                               solver->induction == IDX_INDUCTION_POTENTIAL);
+                               solver->induction == IDX_INDUCTION_POTENTIAL, bounded);
   return IDX_OK;
 }
 
@@ -2716,6 +2991,7 @@ extern "C" int idx_step_noalloc(const idx_grid* grid, double gamma, double cfl,
   c.t_end = std::numeric_limits<double>::infinity();
   c.cfl = cfl;
   c.bad_cell = ~0ull;
+  c.bad_next = ~0ull;
   if (*inv_dt > 0.0) std::memcpy(&c.inv_prev, inv_dt, sizeof(double));
   IDX_TRY(cudaMemcpyAsync(s.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s.stream));
   if (!(*inv_dt > 0.0)) {
@@ -2868,7 +3144,7 @@ __global__ void __launch_bounds__(kThreads) kb_update(const BatchDev<T>* B) {
     const double dt = I->ctrl->dt;
     if (!(dt > 0.0)) continue;  // uniform over the block: one item per block
     const Geo g = I->g;
-    const T inv = update_body<T, COMBINE>(
+    const T inv = update_body<T, COMBINE, false, false>(
         g, dconst(COMBINE ? I->U1 : I->U), dconst(I->U), dconst(I->F[0]), dconst(I->F[1]),
         dconst(I->F[2]), I->E[0], I->E[1], I->E[2], COMBINE ? I->U : I->U1, dt,
         w.begin + threadIdx.x);
@@ -3106,6 +3382,11 @@ template <typename T> void launch_batch_sweep(idx_batch* b, int d, int stage, in
 void launch_solo_stages(idx_sim* s, cudaStream_t st) {
   const cudaStream_t own = s->stream;
   s->stream = st;
+  if (s->use_carry) {
+    launch_carry_stages(s);
+    s->stream = own;
+    return;
+  }
   const StagePlan p = stage_plan(s);
   for (int q = 0; q < p.n; ++q) {
     if (s->solver.precision == IDX_FP32_BULK) launch_stage<float>(s, p, q, s->Wf, s->Ff, s->Ef);
@@ -3224,10 +3505,12 @@ template <typename T> int batch_prepare(idx_batch* b) {
     if (rc != IDX_OK) return rc;
     b->dirty = false;
   }
-  // solo members' own shapes, tuned before the capture (cached per grid)
+  // solo members' own shapes, tuned before the capture (cached per grid); the primitives
+  // of a carried-primitive member's state before its first batched cycle
   for (idx_sim* s : b->solo) {
     const int trc = tune_once(s);
     if (trc != IDX_OK) return trc;
+    refresh_carry(s, b->stream);
   }
   std::vector<uint64_t> solo_serials;
   for (const idx_sim* s : b->solo) solo_serials.push_back(s->serial);
@@ -3355,6 +3638,7 @@ int idx_batch_add(idx_batch* b, idx_sim* s, double t_end) {
   IDX_TRY(cudaStreamSynchronize(s->stream));  // the sim's own work (its state upload) first
   int rc = arm_end_time(b->stream, s, t_end);
   if (rc != IDX_OK) return rc;
+  s->w_fresh = false;  // a work-list member's W does not follow its state
   b->sims.push_back(s);
   b->dirty = true;
   return IDX_OK;

@@ -141,6 +141,23 @@ __device__ __forceinline__ double f2d_warp(float x) {
   if (__any_sync(__activemask(), slow)) r = slow ? (double)x : r;
   return r;
 }
+// N values float -> double with one vote: the converter runs only in warps where some
+// lane holds a subnormal, infinite or NaN value among them (a select per value would run
+// it on every lane, at the FP64 pipe's rate).
+template <int N>
+__device__ __forceinline__ void f2d_many(const float (&x)[N], double (&y)[N]) {
+  bool slow = false;
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    bool s;
+    y[q] = __longlong_as_double((long long)f2d_bits(__float_as_uint(x[q]), &s));
+    slow |= s;
+  }
+  if (__any_sync(__activemask(), slow)) {
+#pragma unroll
+    for (int q = 0; q < N; ++q) y[q] = (double)x[q];
+  }
+}
 // The vote names only the lanes executing it (__activemask): callers may sit behind an
 // early return or a bounds test, where the rest of the warp never gets here.
 __device__ __forceinline__ float d2f_warp(double x) {

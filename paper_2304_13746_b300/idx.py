@@ -311,18 +311,19 @@ class Sim:
         arr = (ctypes.c_int * 3)(*[int(v) for v in shapes])
         self._check(lib().idx_set_sweep_shapes(self._h, arr), "idx_set_sweep_shapes")
 
-    STAGE_KERNELS = {"auto": 0, "split": 1, "fused": 2}
+    STAGE_KERNELS = {"auto": 0, "split": 1, "fused": 2, "carry": 3}
 
     def set_stage_kernels(self, mode):
-        """FP32 bulk: "auto", "split" (six kernels per stage) or "fused" (idx_set_stage_kernels)."""
+        """FP32 bulk: "auto", "split" (six kernels per stage), "fused" (one stage kernel) or
+        "carry" (the update also recovers the next stage's primitives); idx_set_stage_kernels."""
         self._check(lib().idx_set_stage_kernels(self._h, self.STAGE_KERNELS[mode]),
                     "idx_set_stage_kernels")
 
     def stage_kernels(self):
-        """"fused" if the stages run the fused kernel, else "split"."""
+        """The stage kernels in use: "split", "fused" or "carry" (idx_stage_kernels)."""
         v = ctypes.c_int()
         self._check(lib().idx_stage_kernels(self._h, ctypes.byref(v)), "idx_stage_kernels")
-        return "fused" if v.value else "split"
+        return {1: "split", 2: "fused", 3: "carry"}[v.value]
 
     def step_count(self):
         n = ctypes.c_int64()

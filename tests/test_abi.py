@@ -83,7 +83,7 @@ def test_null_arguments(L):
 
 
 @pytest.mark.parametrize("precision,rk,induction,per_cell", [
-    ("fp64", 2, "field", 432), ("fp32", 2, "field", 280),
+    ("fp64", 2, "field", 432), ("fp32", 2, "field", 304),
     ("fp64", 3, "field", 496), ("fp64", 2, "potential", 504),
     ("fp64", 3, "potential", 592), ("fp32", 2, "potential", 352),
 ])
@@ -98,6 +98,16 @@ def test_footprint_per_cell(L, precision, rk, induction, per_cell):
         assert L.idx_footprint(ctypes.byref(idx.Grid(64, 64, 64, 1, 1, 1)), idx.PRECISIONS[precision],
                                ctypes.byref(out)) == idx.IDX_OK
         assert out.value == got
+
+
+def test_footprint_of_the_carried_primitive_stages():
+    # FP32 bulk with RK2, the field form and a periodic grid keeps the stage-1 face fields
+    # (3 FP64 arrays) for the carried-primitive stages; RK3 and padded grids do not
+    n = 64 ** 3
+    assert idx.footprint((64, 64, 64), "fp32") == 304 * n + 256
+    assert idx.footprint((64, 64, 64), "fp32", rk_order=3) == 280 * n + 256 + 8 * 8 * n
+    padded = 64 * 64 * 68
+    assert idx.footprint((64, 64, 64), "fp32", bc=(1, 0, 0)) == 280 * padded + 256
 
 
 def test_footprint_rejects_invalid_solver(L):

@@ -93,15 +93,30 @@ def test_fused_on_a_padded_grid_with_walls():
 def test_stage_kernel_choice():
     big = inputs.random_smooth((64, 64, 64), seed=1)
     s = idx.Sim(big.shape, big.lengths, big.gamma, 0.4, "fp32")
-    assert s.stage_kernels() == "split"          # the default
+    assert s.stage_kernels() == "carry"          # the default for FP32 bulk, RK2, periodic
     s.set_stage_kernels("fused")
     assert s.stage_kernels() == "fused"
-    s.set_stage_kernels("auto")
+    s.set_stage_kernels("split")
     assert s.stage_kernels() == "split"
+    s.set_stage_kernels("auto")
+    assert s.stage_kernels() == "carry"
     s.close()
     small = inputs.random_smooth((32, 32, 32), seed=1)
     s = idx.Sim(small.shape, small.lengths, small.gamma, 0.4, "fp32")
+    assert s.stage_kernels() == "carry"
+    s.close()
+    # the carried primitives need RK2, the field form and a periodic grid; FP64 stays split
+    for kw in [dict(rk_order=3), dict(induction="potential"), dict(bc=("outflow", "periodic", "periodic"))]:
+        s = idx.Sim((32, 8, 8), (1.0, 1.0, 1.0), 5.0 / 3.0, 0.4, "fp32", **kw)
+        assert s.stage_kernels() == "split", kw
+        with pytest.raises(idx.IdxError) as e:
+            s.set_stage_kernels("carry")
+        assert e.value.code == idx.IDX_EINVAL
+        s.close()
+    s = idx.Sim((32, 32, 32), (1.0, 1.0, 1.0), 5.0 / 3.0, 0.4, "fp64")
     assert s.stage_kernels() == "split"
+    with pytest.raises(idx.IdxError):
+        s.set_stage_kernels("carry")
     s.close()
     for shape, prec in [((32, 32, 40), "fp32"), ((32, 12, 32), "fp32"), ((1, 32, 32), "fp32"),
                         ((32, 32, 32), "fp64")]:
