@@ -17,6 +17,10 @@
 // A cycle is k_begin (dt from the previous cycle's speeds, clamp to t_end) + 2 stages +
 // k_end (t, step count, speeds for the next dt), captured once into a CUDA graph and
 // replayed; time, dt and the error flag stay on the device.
+//
+// FP32 bulk (RK2, field form, periodic) runs k_update_carry in place of k_update: it also
+// recovers the primitives of the state it forms, for the next stage, so k_prims drops out
+// of the cycle, and it carries the RK2 combine as the half sum (U^n + U*)/2.
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
