@@ -75,7 +75,14 @@ __device__ __forceinline__ bool same_sign_nz(double dl, double dr, double) {
 }
 __device__ __forceinline__ bool same_sign_nz(float, float, float prod) { return prod > 0.f; }
 __device__ __forceinline__ double tsqrt(double a);   // below the conversion helpers
-__device__ __forceinline__ float tsqrt(float a) { return sqrtf(a); }
+// FP32 bulk: the hardware's approximate square root (one instruction, relative error near
+// 2^-23) in place of the correctly rounded FP32 root, a sequence of about 11 FMA-pipe slots;
+// FP32 rounding already bounds the bulk arithmetic.
+__device__ __forceinline__ float tsqrt(float a) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
 __device__ __forceinline__ double tabs(double a) { return fabs(a); }
 __device__ __forceinline__ float tabs(float a) { return fabsf(a); }
 __device__ __forceinline__ double trsqrt(double a);
