@@ -881,7 +881,7 @@ __device__ __forceinline__ void emf_body(const Geo& g, const Ptr8<const T>& W,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_emf(Geo g, Ptr8<const T> W, Ptr8<const T> Fx,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 8 : 1) k_emf(Geo g, Ptr8<const T> W, Ptr8<const T> Fx,
                                                   Ptr8<const T> Fy, Ptr8<const T> Fz,
                                                   CellEmf<T> cc, T* Ex, T* Ey, T* Ez,
                                                   const Ctrl* ctrl) {
