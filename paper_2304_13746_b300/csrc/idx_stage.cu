@@ -3022,7 +3022,10 @@ extern "C" int idx_step_noalloc(const idx_grid* grid, double gamma, double cfl,
 // cycle serves every membership: instances join and leave between graph replays by
 // rewriting the list, without re-capture.  The per-cell arithmetic is the same device
 // code as the single-sim kernels, so a sim gives the same result, to rounding (FMA
-// contraction may differ between kernel instantiations), alone and in a batch.
+// contraction may differ between kernel instantiations), alone and in a batch.  The FP32
+// work-list kernels carry a member's header in registers beside the cell's arithmetic;
+// their launch bounds hold them to 3-6 resident blocks per SM (a few spilled words), which
+// measured faster on the batched mix than the 2-3 blocks their register counts gave.
 // ===========================================================================
 namespace {
 
@@ -3063,7 +3066,7 @@ template <typename T> __device__ __forceinline__ Ptr8<const T> dconst(const Ptr8
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) kb_prims(const BatchDev<T>* B, int stage, int check) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 1) kb_prims(const BatchDev<T>* B, int stage, int check) {
   const int n = B->n_cell;
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
     const Item w = B->cell[it];
@@ -3076,7 +3079,7 @@ __global__ void __launch_bounds__(kThreads) kb_prims(const BatchDev<T>* B, int s
 }
 
 template <typename T, int D, int SEG>
-__global__ void __launch_bounds__(kThreads) kb_sweep(const BatchDev<T>* B, int stage, int check) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) kb_sweep(const BatchDev<T>* B, int stage, int check) {
   const int n = B->n_sweep[D];
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
     const Item w = B->sweep[D][it];
@@ -3125,7 +3128,7 @@ __global__ void __launch_bounds__(8 * L, sizeof(T) == 4 ? 96 / L : 1)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) kb_emf(const BatchDev<T>* B) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 1) kb_emf(const BatchDev<T>* B) {
   const int n = B->n_cell;
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
     const Item w = B->cell[it];
@@ -3140,7 +3143,7 @@ __global__ void __launch_bounds__(kThreads) kb_emf(const BatchDev<T>* B) {
 }
 
 template <typename T, bool COMBINE>
-__global__ void __launch_bounds__(kThreads) kb_update(const BatchDev<T>* B) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1) kb_update(const BatchDev<T>* B) {
   const int n = B->n_cell;
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
     const Item w = B->cell[it];
