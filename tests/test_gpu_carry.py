@@ -42,16 +42,16 @@ CASES = {
 }
 
 
-def _sim(ic, mode, prim=None):
-    s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, "fp32")
+def _sim(ic, mode, prim=None, **kw):
+    s = idx.Sim(ic.shape, ic.lengths, ic.gamma, 0.4, "fp32", **kw)
     s.set_primitive(ic.prim if prim is None else prim)
     s.set_stage_kernels(mode)
     assert s.stage_kernels() == mode
     return s
 
 
-def run(ic, mode, cycles, prim=None):
-    s = _sim(ic, mode, prim)
+def run(ic, mode, cycles, prim=None, **kw):
+    s = _sim(ic, mode, prim, **kw)
     for _ in range(cycles):
         s.step()
     out = s.get_state()
@@ -76,6 +76,20 @@ def test_carry_matches_split(name):
     err = field_errors(a, b)
     print(name, f"carry vs split {max(err):.2e}")
     assert max(err) <= TOL_SPLIT, err
+
+
+@pytest.mark.parametrize("kw", [{"recon": "limo3"}, {"riemann": "hll"}, {"riemann": "rusanov"}])
+def test_carry_with_limo3_and_other_solvers(kw):
+    # the carried primitives change only the update, so every reconstruction and solver of
+    # the sweeps runs with them; one cycle against the oracle, five against the split kernels
+    ic = inputs.turbulent_box(32, seed=12)
+    o = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, 0.4,
+                              solver=kw.get("riemann", "hlld"),
+                              recon=kw.get("recon", "plm"))
+    o.step()
+    assert max(field_errors(run(ic, "carry", 1, **kw), o.u)) <= TOL_ORACLE, kw
+    err = field_errors(run(ic, "carry", 5, **kw), run(ic, "split", 5, **kw))
+    assert max(err) <= TOL_SPLIT, (kw, err)
 
 
 def test_carry_advance_matches_split_and_oracle():
