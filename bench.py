@@ -423,12 +423,15 @@ def served_stream(precision, nreq, budget, serve_mod, stream, orders=("oldest",)
         return dict(st, failed_requests=failures(reqs))
 
     cap = served(1e9)                     # everything at once: the batch's capacity
+    seq_cap = sequential(1e9)             # everything at once, one at a time
     mean_work = cap["cell_updates"] / max(cap["done"], 1)
     capacity_rps = cap["cell_updates_per_s"] / mean_work
     rate70 = 0.7 * capacity_rps
     r = {"requests": nreq, "capacity_req_per_s": capacity_rps,
          "capacity_cell_updates_per_s": cap["cell_updates_per_s"],
          "mean_cell_updates_per_request": mean_work, "all_at_once": cap,
+         "all_at_once_sequential": seq_cap,
+         "capacity_vs_sequential": cap["cell_updates_per_s"] / max(seq_cap["cell_updates_per_s"], 1e-30),
          "sizes": [f"{q.kind} {q.n}" for q in base], "t_end": [round(q.t_end, 3) for q in base]}
     for order in orders:
         key = "served_70pct" if order == "oldest" else f"served_70pct_{order}"
@@ -438,7 +441,9 @@ def served_stream(precision, nreq, budget, serve_mod, stream, orders=("oldest",)
         r[f"served_70pct_cap{c}"] = dict(served(rate70, c), rate=rate70, max_active_cells=c)
     r["sequential_70pct"] = dict(sequential(rate70), rate=rate70, offered_load=0.7)
     s, q = r["served_70pct"], r["sequential_70pct"]
-    r["summary"] = {"served_p50_s": s["p50_s"], "served_p99_s": s["p99_s"],
+    r["summary"] = {"capacity_cell_updates_per_s": cap["cell_updates_per_s"],
+                    "sequential_capacity_cell_updates_per_s": seq_cap["cell_updates_per_s"],
+                    "served_p50_s": s["p50_s"], "served_p99_s": s["p99_s"],
                     "sequential_p50_s": q["p50_s"], "sequential_p99_s": q["p99_s"],
                     "served_cell_updates_per_s": s["cell_updates_per_s"],
                     "sequential_cell_updates_per_s": q["cell_updates_per_s"]}
