@@ -846,13 +846,31 @@ __device__ __forceinline__ void riemann_flux(int solver, const Side<T>& L, const
 template <typename T>
 __device__ __forceinline__ T emf_ec(T X0, T X1, T Y0, T Y1, T C00, T C01, T C10, T C11, T Fa0,
                                     T Fa1, T Fb0, T Fb1) {
-  auto pick = [](T f, T up, T dn) {
-    return gt0(f) ? up : (lt0(f) ? dn : T(0.5) * (up + dn));
+  // FP64 (bound by the FP64 pipe): each one-sided difference p - q is formed once, from
+  // operands chosen by the flux sign (selects in the integer pipe, not arithmetic); where a
+  // flux is exactly 0 the mean of both differences is formed instead, in the rare warps
+  // that hold such a lane.  Same values as forming both differences and choosing between
+  // them.  FP32 (bound by load latency, where the extra vote cost more than the two
+  // subtractions) forms both differences and chooses.
+  auto pick = [](T f, T p_up, T q_up, T p_dn, T q_dn) {
+    if constexpr (sizeof(T) == 8) {
+      const bool up = gt0(f);
+      T r = (up ? p_up : p_dn) - (up ? q_up : q_dn);
+      const bool zero = !up && !lt0(f);
+      if (__any_sync(__activemask(), zero)) {
+        const T m = T(0.5) * ((p_up - q_up) + (p_dn - q_dn));
+        r = zero ? m : r;
+      }
+      return r;
+    } else {
+      const T up = p_up - q_up, dn = p_dn - q_dn;
+      return gt0(f) ? up : (lt0(f) ? dn : T(0.5) * (up + dn));
+    }
   };
-  const T dB1 = pick(Fa0, C10 - Y1, C00 - Y0);
-  const T dB3 = pick(Fa1, Y1 - C11, Y0 - C01);
-  const T dA1 = pick(Fb0, C01 - X1, C00 - X0);
-  const T dA3 = pick(Fb1, X1 - C11, X0 - C10);
+  const T dB1 = pick(Fa0, C10, Y1, C00, Y0);
+  const T dB3 = pick(Fa1, Y1, C11, Y0, C01);
+  const T dA1 = pick(Fb0, C01, X1, C00, X0);
+  const T dA3 = pick(Fb1, X1, C11, X0, C10);
   return T(0.25) * ((X0 + X1) + (Y0 + Y1) + (dB3 - dB1) + (dA3 - dA1));
 }
 
