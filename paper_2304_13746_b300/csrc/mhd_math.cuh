@@ -543,6 +543,163 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   }
 }
 
+// HLLD as above, for the FP64 sweeps, which the FP64 pipe bounds: the single-star state and
+// sqrt(rho*) of the side that contains x/t = 0 are formed first, the other side's only on
+// faces inside the Alfven fan, where the double-star average needs them (an Alfven root
+// and about 10 operations fewer elsewhere; the same values).  The FP32 sweeps, bound by
+// instruction issue, measured faster with both sides formed at once (hlld).
+template <typename T>
+__device__ __forceinline__ void hlld_lazy(const Side<T>& L, const Side<T>& R, T bx, T gamma,
+                                     T gm1inv, T F[7], T& c) {
+  const T bx2 = bx * bx;
+  const T b2L = bx2 + L.b1 * L.b1 + L.b2 * L.b2, b2R = bx2 + R.b1 * R.b1 + R.b2 * R.b2;
+  const T magL = T(0.5) * b2L, magR = T(0.5) * b2R;
+  const T pTL = L.p + magL, pTR = R.p + magR;
+
+  // outer speeds from the fast magnetosonic speeds (MK05 eq. 67)
+  const T gpL = gamma * L.p, gpR = gamma * R.p;
+  const T aL = gpL + b2L, aR = gpR + b2R;  // 2 magL is b2L exactly
+  const T bx2x4 = T(4) * bx2;               // exact scaling, shared by both sides
+  const T dL = pos_part(aL * aL - gpL * bx2x4);
+  const T dR = pos_part(aR * aR - gpR * bx2x4);
+  // 0.5/rho_L and 0.5/rho_R from one reciprocal (cheaper than a division; the factor 1/2
+  // is exact)
+  const T hLR = T(0.5) * trcp(L.r * R.r);
+  // only the larger fast speed enters, the root of the larger square: one square root fewer
+  // (with a correctly rounded root this equals the larger root bit for bit; with the
+  // faithful FP64 root of the production build, within its ulp)
+  const T cf2L = (aL + tsqrt(dL)) * (R.r * hLR);
+  const T cf2R = (aR + tsqrt(dR)) * (L.r * hLR);
+  const T cfm = tsqrt(max_nn(cf2L, cf2R));
+  const T SL = imin(L.u, R.u) - cfm;
+  const T SR = imax(L.u, R.u) + cfm;
+  c = max_nn(tabs(SL), tabs(SR));
+
+  const bool sup_l = gt0(SL);
+  if (sup_l || lt0(SR)) {  // supersonic: upwind physical flux
+    const Side<T>& s = sup_l ? L : R;
+    const T pT = sup_l ? pTL : pTR;
+    const T E = s.p * gm1inv + T(0.5) * s.r * (s.u * s.u + s.v * s.v + s.w * s.w) +
+                (sup_l ? magL : magR);
+    const T vb = s.u * bx + s.v * s.b1 + s.w * s.b2;
+    const T ru = s.r * s.u;
+    F[0] = ru;
+    F[1] = ru * s.u + pT - bx2;
+    F[2] = ru * s.v - bx * s.b1;
+    F[3] = ru * s.w - bx * s.b2;
+    F[4] = (E + pT) * s.u - bx * vb;
+    F[5] = s.b1 * s.u - bx * s.v;
+    F[6] = s.b2 * s.u - bx * s.w;
+    return;
+  }
+
+  // contact speed and star total pressure
+  const T sLu = SL - L.u, sRu = SR - R.u;
+  const T qL = sLu * L.r, qR = sRu * R.r;
+  const T SM = (qR * R.u - qL * L.u - pTR + pTL) * trcp(qR - qL);
+  const T pTs = pTL + qL * (SM - L.u);
+
+  // single-star transverse states, both sides (needed by the double-star average), with
+  // D = rho (S - u)(S - S_M) - Bx^2 per side (MK05 eqs. 44-47); a side where D vanishes
+  // against its terms keeps its transverse state (the HLLC limit)
+  const T eL = SL - SM, eR = SR - SM;
+  const T qeL = qL * eL, qeR = qR * eR;
+  const T DL = qeL - bx2, DR = qeR - bx2;
+  const bool degL = le_nn(tabs(DL), Eps<T>::degen * (tabs(qeL) + bx2));
+  const bool degR = le_nn(tabs(DR), Eps<T>::degen * (tabs(qeR) + bx2));
+  // 1/(S_L - S_M), 1/(S_R - S_M), 1/D_L and 1/D_R from one division of their product
+  // (S_L < S_M < S_R: the e's are O(c_f); a degenerate side's D stays out of it)
+  const T kL = degL ? T(1) : DL, kR = degR ? T(1) : DR;
+  const T eLR = eL * eR, kLR = kL * kR;
+  const T inv = trcp(eLR * kLR);
+  const T iLR = kLR * inv, eLRinv = eLR * inv;
+  const T iL = eR * iLR, iR = eL * iLR;
+  const T iDL = kR * eLRinv, iDR = kL * eLRinv;
+  const T rsL = qL * iL, rsR = qR * iR;  // rho*
+  // single-star transverse state of one side (MK05 eqs. 44-47)
+  auto star_t = [&](const Side<T>& w, T q, T su, T iD, bool deg, T& vs, T& ws, T& b1s, T& b2s) {
+    if (deg) {
+      vs = w.v; ws = w.w; b1s = w.b1; b2s = w.b2;
+    } else {
+      const T t = bx * (SM - w.u) * iD;
+      vs = w.v - w.b1 * t;
+      ws = w.w - w.b2 * t;
+      const T g = (q * su - bx2) * iD;
+      b1s = w.b1 * g;
+      b2s = w.b2 * g;
+    }
+  };
+
+  // the side that contains x/t = 0: its single-star state and Alfven speed now; the other
+  // side's only where the double-star states need them
+  const bool left = ge0(SM);
+  const Side<T>& s = left ? L : R;
+  const T S = left ? SL : SR;
+  const T su = left ? sLu : sRu;
+  const T is = left ? iL : iR;
+  const T rs = left ? rsL : rsR;
+  const T pT = left ? pTL : pTR;
+  T vs, ws, b1s, b2s;
+  star_t(s, left ? qL : qR, su, left ? iDL : iDR, left ? degL : degR, vs, ws, b1s, b2s);
+  // sqrt(rho*) and |Bx|/sqrt(rho*) from one reciprocal square root
+  const T rq = trsqrt(rs);
+  const T abx = tabs(bx);
+  const T Ss = left ? SM - abx * rq : SM + abx * rq;  // the Alfven speed on that side
+
+  const T E = s.p * gm1inv + T(0.5) * s.r * (s.u * s.u + s.v * s.v + s.w * s.w) +
+              (left ? magL : magR);
+  const T vb = s.u * bx + s.v * s.b1 + s.w * s.b2;
+  const T vbs = SM * bx + vs * b1s + ws * b2s;
+  const T Es = (su * E - pT * s.u + pTs * SM + bx * (vb - vbs)) * is;
+
+  // physical flux and conserved vector of the side
+  const T ru = s.r * s.u;
+  T Fs[7], Us[7], Ustar[7];
+  Fs[0] = ru;
+  Fs[1] = ru * s.u + pT - bx2;
+  Fs[2] = ru * s.v - bx * s.b1;
+  Fs[3] = ru * s.w - bx * s.b2;
+  Fs[4] = (E + pT) * s.u - bx * vb;
+  Fs[5] = s.b1 * s.u - bx * s.v;
+  Fs[6] = s.b2 * s.u - bx * s.w;
+  Us[0] = s.r; Us[1] = ru; Us[2] = s.r * s.v; Us[3] = s.r * s.w; Us[4] = E;
+  Us[5] = s.b1; Us[6] = s.b2;
+  Ustar[0] = rs; Ustar[1] = rs * SM; Ustar[2] = rs * vs; Ustar[3] = rs * ws; Ustar[4] = Es;
+  Ustar[5] = b1s; Ustar[6] = b2s;
+#pragma unroll
+  for (int q = 0; q < 7; ++q) F[q] = Fs[q] + S * (Ustar[q] - Us[q]);
+
+  const bool dbl = left ? lt0(Ss) : ge0(Ss);
+  if (dbl && !lt_nn(T(0.5) * bx2, Eps<T>::hllc * pTs)) {
+    // the other side's single-star state and sqrt(rho*)
+    T vso, wso, b1so, b2so;
+    star_t(left ? R : L, left ? qR : qL, left ? sRu : sLu, left ? iDR : iDL,
+           left ? degR : degL, vso, wso, b1so, b2so);
+    const T rso = left ? rsR : rsL;
+    const T sq = rs * rq, sqo = rso * trsqrt(rso);
+    const T sqL = left ? sq : sqo, sqR = left ? sqo : sq;
+    const T vsL = left ? vs : vso, vsR = left ? vso : vs;
+    const T wsL = left ? ws : wso, wsR = left ? wso : ws;
+    const T b1sL = left ? b1s : b1so, b1sR = left ? b1so : b1s;
+    const T b2sL = left ? b2s : b2so, b2sR = left ? b2so : b2s;
+    const T sgn = lt0(bx) ? T(-1) : T(1);
+    const T isum = trcp(sqL + sqR);
+    const T v2 = (sqL * vsL + sqR * vsR + (b1sR - b1sL) * sgn) * isum;
+    const T w2 = (sqL * wsL + sqR * wsR + (b2sR - b2sL) * sgn) * isum;
+    const T sLR = sqL * sqR;
+    const T b12 = (sqL * b1sR + sqR * b1sL + sLR * (vsR - vsL) * sgn) * isum;
+    const T b22 = (sqL * b2sR + sqR * b2sL + sLR * (wsR - wsL) * sgn) * isum;
+    const T vb2 = SM * bx + v2 * b12 + w2 * b22;
+    const T E2 = left ? Es - sq * (vbs - vb2) * sgn : Es + sq * (vbs - vb2) * sgn;
+    F[2] += Ss * (rs * v2 - Ustar[2]);
+    F[3] += Ss * (rs * w2 - Ustar[3]);
+    F[4] += Ss * (E2 - Es);
+    F[5] += Ss * (b12 - b1s);
+    F[6] += Ss * (b22 - b2s);
+    // rho and m_n are continuous across the rotational waves: no change in F[0], F[1]
+  }
+}
+
 #ifdef IDX_STRICT_ROUNDING
 // ---------------------------------------------------------------------------
 // Strict-rounding build (a test build, compiled with -fmad=false): the FP64 HLLD with
@@ -832,8 +989,10 @@ __device__ __forceinline__ void riemann_flux(int solver, const Side<T>& L, const
     }
   }
 #endif
-  if (solver == 4) hlld(L, R, bx, gamma, gm1inv, F, c);
-  else if (solver == 2) hll(L, R, bx, gamma, gm1inv, F, c);
+  if (solver == 4) {
+    if constexpr (sizeof(T) == 8) hlld_lazy(L, R, bx, gamma, gm1inv, F, c);
+    else hlld(L, R, bx, gamma, gm1inv, F, c);
+  } else if (solver == 2) hll(L, R, bx, gamma, gm1inv, F, c);
   else rusanov(L, R, bx, gamma, gm1inv, F, c);
 }
 
