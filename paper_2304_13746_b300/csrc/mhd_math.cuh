@@ -543,6 +543,41 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   }
 }
 
+// The two HLLD threshold tests in FP64 (the degeneracy |D| <= 1e-12 (|q e| + Bx^2) of a
+// side, and the HLLC limit Bx^2 / 2 < 1e-12 p_T*), decided from the binary exponents in the
+// integer pipe wherever those settle them, and by the FP64 comparison otherwise, in the
+// warps that hold such a lane: the same decisions as the comparisons alone.  With e_x the
+// biased exponent (|x| in [2^(e_x - 1023), 2^(e_x - 1022))) and 1e-12 < 2^-39.8:
+//   degeneracy: 1e-12 (|q e| + Bx^2) < 2^-39.8 * 2^(e_m - 1021) with e_m the larger exponent
+//     of the two terms, so e_D >= e_m - 37 gives |D| >= 2^(e_m - 1060) above it: not degenerate;
+//   HLLC limit (p_T* positive and normal): e_b >= e_p - 37 with Bx^2 normal gives Bx^2/2 >=
+//     2^(e_b - 1024) above 1e-12 p_T* (not the limit); e_b < e_p - 41 gives Bx^2/2 <
+//     2^(e_p - 1064) below it (the limit).  Zero and subnormal values go to the comparison.
+__device__ __forceinline__ int bexp(double x) {
+  return (int)(((unsigned)__double2hiint(x) >> 20) & 0x7ffu);
+}
+__device__ __forceinline__ bool degenerate_fp64(double D, double qe, double bx2) {
+  const int eq = bexp(qe), eb = bexp(bx2), eD = bexp(D);
+  const bool undecided = eD == 0 || eD < (eq > eb ? eq : eb) - 37;  // D = 0 or subnormal too
+  bool deg = false;
+  if (__any_sync(__activemask(), undecided)) {
+    const bool exact = le_nn(tabs(D), Eps<double>::degen * (tabs(qe) + bx2));
+    deg = undecided && exact;
+  }
+  return deg;
+}
+__device__ __forceinline__ bool hllc_limit_fp64(double bx2, double pTs) {
+  const int eb = bexp(bx2), ep = bexp(pTs);
+  const bool quick = ep > 0 && !(__double2hiint(pTs) < 0);  // p_T* positive and normal
+  bool lim = quick && eb < ep - 41;
+  const bool undecided = !quick || (!lim && (eb == 0 || eb < ep - 37));
+  if (__any_sync(__activemask(), undecided)) {
+    const bool exact = lt_nn(0.5 * bx2, Eps<double>::hllc * pTs);
+    lim = undecided ? exact : lim;
+  }
+  return lim;
+}
+
 // HLLD as above, for the FP64 sweeps, which the FP64 pipe bounds: the single-star state and
 // sqrt(rho*) of the side that contains x/t = 0 are formed first, the other side's only on
 // faces inside the Alfven fan, where the double-star average needs them (an Alfven root
@@ -605,8 +640,8 @@ __device__ __forceinline__ void hlld_lazy(const Side<T>& L, const Side<T>& R, T 
   const T eL = SL - SM, eR = SR - SM;
   const T qeL = qL * eL, qeR = qR * eR;
   const T DL = qeL - bx2, DR = qeR - bx2;
-  const bool degL = le_nn(tabs(DL), Eps<T>::degen * (tabs(qeL) + bx2));
-  const bool degR = le_nn(tabs(DR), Eps<T>::degen * (tabs(qeR) + bx2));
+  const bool degL = degenerate_fp64(DL, qeL, bx2);
+  const bool degR = degenerate_fp64(DR, qeR, bx2);
   // 1/(S_L - S_M), 1/(S_R - S_M), 1/D_L and 1/D_R from one division of their product
   // (S_L < S_M < S_R: the e's are O(c_f); a degenerate side's D stays out of it)
   const T kL = degL ? T(1) : DL, kR = degR ? T(1) : DR;
@@ -670,7 +705,7 @@ __device__ __forceinline__ void hlld_lazy(const Side<T>& L, const Side<T>& R, T 
   for (int q = 0; q < 7; ++q) F[q] = Fs[q] + S * (Ustar[q] - Us[q]);
 
   const bool dbl = left ? lt0(Ss) : ge0(Ss);
-  if (dbl && !lt_nn(T(0.5) * bx2, Eps<T>::hllc * pTs)) {
+  if (dbl && !hllc_limit_fp64(bx2, pTs)) {
     // the other side's single-star state and sqrt(rho*)
     T vso, wso, b1so, b2so;
     star_t(left ? R : L, left ? qR : qL, left ? sRu : sLu, left ? iDR : iDL,
