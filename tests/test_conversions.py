@@ -58,3 +58,27 @@ def test_fp64_roots_within_one_ulp(root_harness):
     print(out.stdout)
     assert int(words[1]) == 0 and int(words[3]) >= 4_000_000
     assert float(words[5]) <= 1.0 and float(words[7]) <= 1.0
+
+
+@pytest.fixture(scope="module")
+def threshold_harness(tmp_path_factory):
+    exe = str(tmp_path_factory.mktemp("thr") / "threshold_check")
+    subprocess.run([NVCC, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-std=c++17",
+                    "-o", exe, os.path.join(HERE, "native", "threshold_check.cu")], check=True)
+    return exe
+
+
+@pytest.mark.gpu
+def test_fp64_hlld_threshold_tests_match_the_comparisons(threshold_harness):
+    # the FP64 HLLD degeneracy and HLLC-limit tests decide from the binary exponents where
+    # those settle the question and compare in FP64 otherwise: every decision equals the
+    # plain comparison's, on values across the exponent range, near both thresholds, zeros,
+    # subnormals and negative values, mixed within warps
+    out = subprocess.run([threshold_harness, "8000000"], capture_output=True, text=True,
+                         timeout=600)
+    words = out.stdout.split()
+    assert out.returncode == 0 and words[:1] == ["mismatches"], (out.stdout, out.stderr)
+    print(out.stdout)
+    assert int(words[1]) == 0 and int(words[3]) >= 8_000_000
+    # the near-threshold cases do reach the comparisons
+    assert int(words[5]) > 0 and int(words[7]) > 0
