@@ -85,7 +85,26 @@ struct Geo {
   float gammaf, gm1invf;
   int riemann;       // 1 Rusanov, 2 HLL, 4 HLLD
   int recon;         // 1 PLM (van Leer), 3 LimO3
+  // floor(c / nx) and floor(c / (nx ny)) for 0 <= c < 2^31 as (c m) >> s (geo_set_divisors)
+  unsigned div_m[2];
+  int div_s[2];
 };
+
+// Division by an invariant integer as a multiply and a shift (Granlund and Montgomery
+// 1994, Thm. 4.2, with N = 31): for 1 <= d < 2^31, l = ceil(log2 d) and
+// m = ceil(2^(31 + l) / d), m d - 2^(31 + l) < d <= 2^l, so floor(n / d) =
+// floor(n m / 2^(31 + l)) for every 0 <= n < 2^31; m < 2^32 and n m < 2^63.
+inline void div_magic(unsigned d, unsigned& m, int& sh) {
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  const unsigned long long p = 1ull << (31 + l);
+  m = (unsigned)((p + d - 1) / d);
+  sh = 31 + l;
+}
+inline void geo_set_divisors(Geo& g) {
+  div_magic((unsigned)g.n[0], g.div_m[0], g.div_s[0]);
+  div_magic((unsigned)g.stride[2], g.div_m[1], g.div_s[1]);
+}
 
 // gamma and 1/(gamma - 1) in the bulk type, formed once on the host
 template <typename T> __device__ __forceinline__ T geo_gamma(const Geo& g);
@@ -123,10 +142,9 @@ __device__ __forceinline__ double to_f64(double x) { return x; }
 __device__ __forceinline__ double to_f64(float x) { return f2d(x); }
 
 __device__ __forceinline__ void coords(const Geo& g, int c, int& i, int& j, int& k) {
-  const int nxy = g.n[0] * g.n[1];
-  k = c / nxy;
-  const int r = c - k * nxy;
-  j = r / g.n[0];
+  k = (int)(((unsigned long long)(unsigned)c * g.div_m[1]) >> g.div_s[1]);
+  const int r = c - k * g.stride[2];
+  j = (int)(((unsigned long long)(unsigned)r * g.div_m[0]) >> g.div_s[0]);
   i = r - j * g.n[0];
 }
 
@@ -140,6 +158,22 @@ __device__ __forceinline__ int shifted(const Geo& g, int c, int coord, int d, in
   if (q >= n) q -= n;
   if (q >= n) q -= n;
   return c + (q - coord) * g.stride[d];
+}
+
+// Offsets from a cell at coordinates ijk to its upper neighbour along each direction
+// (periodic wrap; 0 along a one-cell direction).
+__device__ __forceinline__ void upper_offsets(const Geo& g, const int ijk[3], int up[3]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) up[d] = (ijk[d] + 1 < g.n[d] ? 1 : 1 - g.n[d]) * g.stride[d];
+}
+// Offsets from cell c to its lower neighbour along each direction (periodic wrap).
+__device__ __forceinline__ void lower_offsets(const Geo& g, int c, int dn[3]) {
+  int ijk[3];
+  coords(g, c, ijk[0], ijk[1], ijk[2]);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) dn[d] = (ijk[d] > 0 ? 0 : g.n[d]) - 1;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) dn[d] *= g.stride[d];
 }
 
 __device__ __forceinline__ void flag_bad(Ctrl* ctrl, int c) {
@@ -840,15 +874,15 @@ __global__ void __launch_bounds__(kThreads) k_sweep_x(Geo g, Ptr8<const T> W, co
 // EMF = +F_b[B_a] (slot 6 of direction b), cell-centre EMF = -(v_a B_b - v_b B_a).
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ T edge_emf(const Geo& g, int e, int c, const int ijk[3],
+__device__ __forceinline__ T edge_emf(const Geo& g, int e, int c, const int dn[3],
                                       const Ptr8<const T>& W, const Ptr8<const T>* F,
                                       const T* cce) {
   const int a = (e + 1) % 3, b = (e + 2) % 3;
   const Ptr8<const T>& Fa = F[a];
   const Ptr8<const T>& Fb = F[b];
-  const int cb = shifted(g, c, ijk[b], b, -1);   // c - e_b
-  const int ca = shifted(g, c, ijk[a], a, -1);   // c - e_a
-  const int cab = shifted(g, ca, ijk[b], b, -1); // c - e_a - e_b
+  const int cb = c + dn[b];          // c - e_b
+  const int ca = c + dn[a];          // c - e_a
+  const int cab = c + dn[a] + dn[b];  // c - e_a - e_b
   const T X0 = -Fa.f[5][c], X1 = -Fa.f[5][cb];
   const T Y0 = Fb.f[6][c], Y1 = Fb.f[6][ca];
   const T Fa0 = Fa.f[0][c], Fa1 = Fa.f[0][cb];
@@ -869,14 +903,14 @@ __device__ __forceinline__ void emf_body(const Geo& g, const Ptr8<const T>& W,
                                          const Ptr8<const T>& Fx, const Ptr8<const T>& Fy,
                                          const Ptr8<const T>& Fz, const CellEmf<T>& cc, T* Ex,
                                          T* Ey, T* Ez, int c) {
-  int ijk[3];
-  coords(g, c, ijk[0], ijk[1], ijk[2]);
+  int dn[3];
+  lower_offsets(g, c, dn);
   const Ptr8<const T> F[3] = {Fx, Fy, Fz};
   T* out[3] = {Ex, Ey, Ez};
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
     const int a = (e + 1) % 3, b = (e + 2) % 3;
-    if (g.active[a] && g.active[b]) out[e][c] = edge_emf<T>(g, e, c, ijk, W, F, cc.f[e]);
+    if (g.active[a] && g.active[b]) out[e][c] = edge_emf<T>(g, e, c, dn, W, F, cc.f[e]);
   }
 }
 
@@ -931,14 +965,14 @@ __global__ void __launch_bounds__(kThreads) k_emf_pot(Geo g, Ptr8<const T> W, Pt
   if (!(dt > 0.0)) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
-  int ijk[3];
-  coords(g, c, ijk[0], ijk[1], ijk[2]);
+  int dn[3];
+  lower_offsets(g, c, dn);
   const Ptr8<const T> F[3] = {Fx, Fy, Fz};
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
     const int a = (e + 1) % 3, b = (e + 2) % 3;
     double E = 0.0;  // neither transverse direction integrated: A_e enters no face field
-    if (g.active[a] && g.active[b]) E = to_f64(edge_emf<T>(g, e, c, ijk, W, F, cc.f[e]));
+    if (g.active[a] && g.active[b]) E = to_f64(edge_emf<T>(g, e, c, dn, W, F, cc.f[e]));
     else if (g.active[a]) E = -to_f64(F[a].f[slot(5 + b, a)][c]);
     else if (g.active[b]) E = to_f64(F[b].f[slot(5 + a, b)][c]);
     const double As = P.in[e][c] - dt * E;
@@ -1011,8 +1045,9 @@ __device__ __forceinline__ T update_body(const Geo& g, const Ptr8<const double>&
     const Ptr8<const T> F[3] = {Fx, Fy, Fz};
     const T* E[3] = {Ex, Ey, Ez};
     int up[3];
+    upper_offsets(g, ijk, up);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) up[d] = shifted(g, c, ijk[d], d, 1);
+    for (int d = 0; d < 3; ++d) up[d] += c;
     // flux divergence and EMF curl in the bulk type T; the accumulation into the
     // state is FP64 in both variants.  FP32 bulk also forms dt * div in FP32 (the
     // increment only needs FP32 precision) and adds it to the FP64 state.
@@ -1200,8 +1235,12 @@ __global__ void __launch_bounds__(kThreads) k_update(Geo g, Ptr8<const double> U
 // formed again there).  The increments are FP32 (as in k_update<float>); every sum into the
 // state is FP64.  Stage-2 primitives belong to the next cycle: a non-physical cell there is
 // recorded in bad_next, which the next cycle's k_begin turns into the error.
+// The kernel is bound by latency and instruction issue more than by its bytes (the same
+// loads and stores without the arithmetic run at the copy bandwidth): neighbour offsets
+// are formed once per cell, coordinates by multiply-and-shift division, and stage 2 runs
+// 6 blocks per SM (40 registers); stage 1, which holds more values, 5.
 template <bool STAGE2>
-__global__ void __launch_bounds__(kThreads, 5) k_update_carry(Geo g, Ptr8<const double> Uin,
+__global__ void __launch_bounds__(kThreads, STAGE2 ? 6 : 5) k_update_carry(Geo g, Ptr8<const double> Uin,
                                                            Ptr8<const float> Fx,
                                                            Ptr8<const float> Fy,
                                                            Ptr8<const float> Fz,
@@ -1218,9 +1257,12 @@ __global__ void __launch_bounds__(kThreads, 5) k_update_carry(Geo g, Ptr8<const 
     coords(g, c, ijk[0], ijk[1], ijk[2]);
     const Ptr8<const float> F[3] = {Fx, Fy, Fz};
     const float* E[3] = {Ex, Ey, Ez};
-    int up[3];
+    // offsets of the upper neighbour along each direction (periodic wrap); the cell's edges
+    // and faces sit at c plus sums of them
+    int off[3], up[3];
+    upper_offsets(g, ijk, off);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) up[d] = shifted(g, c, ijk[d], d, 1);
+    for (int d = 0; d < 3; ++d) up[d] = c + off[d];
     // stage 1 steps by dt, stage 2 by dt/2 (the RK2 weight of L(U*))
     const float dtf = d2f_warp(STAGE2 ? 0.5 * dt : dt);
     // FP32 increments: the 5 cell fields, then the field normal to d on the lower d-face
@@ -1242,16 +1284,14 @@ __global__ void __launch_bounds__(kThreads, 5) k_update_carry(Geo g, Ptr8<const 
       const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
       float curl = 0.f;
       if (g.active[d]) {
-        if (g.active[t1])
-          curl += (E[t2][shifted(g, q, ijk[t1], t1, 1)] - E[t2][q]) * g.inv_dlf[t1];
-        if (g.active[t2])
-          curl -= (E[t1][shifted(g, q, ijk[t2], t2, 1)] - E[t1][q]) * g.inv_dlf[t2];
+        if (g.active[t1]) curl += (E[t2][q + off[t1]] - E[t2][q]) * g.inv_dlf[t1];
+        if (g.active[t2]) curl -= (E[t1][q + off[t2]] - E[t1][q]) * g.inv_dlf[t2];
       } else {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           if (a == d || !g.active[a]) continue;
           const int sl = slot(5 + d, a);
-          curl += (F[a].f[sl][shifted(g, q, ijk[a], a, 1)] - F[a].f[sl][q]) * g.inv_dlf[a];
+          curl += (F[a].f[sl][q + off[a]] - F[a].f[sl][q]) * g.inv_dlf[a];
         }
       }
       return -dtf * curl;
@@ -1278,14 +1318,9 @@ __global__ void __launch_bounds__(kThreads, 5) k_update_carry(Geo g, Ptr8<const 
 #pragma unroll
       for (int d = 0; d < 3; ++d) Uout.f[5 + d][c] = b0[d];
     } else {
-      // the half sum S = U^n + inc / 2 (the halving is exact in FP32 above 2^-125)
-      float half[8];
+      // the half sum S = U^n + inc / 2 (halving the FP64 image of inc: exact)
 #pragma unroll
-      for (int f = 0; f < 8; ++f) half[f] = 0.5f * inc[f];
-      double dhalf[8];
-      f2d_many(half, dhalf);
-#pragma unroll
-      for (int f = 0; f < 8; ++f) Uout.f[f][c] = Uin.f[f][c] + dhalf[f];
+      for (int f = 0; f < 8; ++f) Uout.f[f][c] = Uin.f[f][c] + half_of_f32_image(dinc[f]);
 #pragma unroll
       for (int d = 0; d < 3; ++d) Bs.f[d][c] = b0[d];
     }
@@ -2197,6 +2232,7 @@ int idx_create(const idx_grid* grid, double gamma, const idx_solver* solver, voi
   g.n[0] = pn[0]; g.n[1] = pn[1]; g.n[2] = pn[2];
   g.stride[0] = 1; g.stride[1] = pn[0]; g.stride[2] = pn[0] * pn[1];
   g.ncell = (int)ncell;
+  geo_set_divisors(g);
   const double l[3] = {grid->lx, grid->ly, grid->lz};
   const int un[3] = {grid->nx, grid->ny, grid->nz};
   for (int d = 0; d < 3; ++d) {
@@ -2967,6 +3003,7 @@ extern "C" int idx_step_noalloc(const idx_grid* grid, double gamma, double cfl,
   g.n[0] = grid->nx; g.n[1] = grid->ny; g.n[2] = grid->nz;
   g.stride[0] = 1; g.stride[1] = grid->nx; g.stride[2] = grid->nx * grid->ny;
   g.ncell = (int)ncell;
+  geo_set_divisors(g);
   const double l[3] = {grid->lx, grid->ly, grid->lz};
   for (int d = 0; d < 3; ++d) {
     g.active[d] = g.n[d] > 1;

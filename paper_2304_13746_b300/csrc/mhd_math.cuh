@@ -165,6 +165,14 @@ __device__ __forceinline__ void f2d_many(const float (&x)[N], double (&y)[N]) {
     for (int q = 0; q < N; ++q) y[q] = (double)x[q];
   }
 }
+// x / 2 for x the FP64 image of a float (so x is 0, infinite, NaN or has an exponent far
+// above the subnormal range): the exponent field less one, in the integer pipe; exact.
+__device__ __forceinline__ double half_of_f32_image(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  const unsigned h = (e - 1u) < 0x7feu ? hi - 0x00100000u : hi;  // 0, inf, NaN unchanged
+  return __hiloint2double((int)h, __double2loint(x));
+}
 // The vote names only the lanes executing it (__activemask): callers may sit behind an
 // early return or a bounds test, where the rest of the warp never gets here.
 __device__ __forceinline__ float d2f_warp(double x) {
