@@ -551,6 +551,27 @@ __device__ __forceinline__ void hlld(const Side<T>& L, const Side<T>& R, T bx, T
   }
 }
 
+// x * 2^K (K = -2, -1 or 2) by the exponent field in the integer pipe, for the FP64
+// kernels that the FP64 pipe bounds: exact, the same bits as the product, where x and the
+// result are normal (zeros unchanged); a warp with any other value multiplies.
+template <int K>
+__device__ __forceinline__ double pow2_fp64(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  constexpr unsigned kLo = K < 0 ? 1u - K : 1u;              // smallest exponent field kept normal
+  constexpr unsigned kHi = K > 0 ? 0x7feu - K : 0x7feu;      // largest
+  const bool fast = (e - kLo) <= (kHi - kLo);
+  const bool zero = ((hi & 0x7fffffffu) | lo) == 0u;
+  double r = __hiloint2double((int)(fast ? hi + (unsigned)(K * (1 << 20)) : hi), (int)lo);
+  if (!__all_sync(__activemask(), fast || zero)) r = x * (K == 2 ? 4.0 : (K == -1 ? 0.5 : 0.25));
+  return r;
+}
+template <int K, typename T>
+__device__ __forceinline__ T pow2_scale(T x) {
+  if constexpr (sizeof(T) == 8) return pow2_fp64<K>(x);
+  else return x * T(K == 2 ? 4.0 : (K == -1 ? 0.5 : 0.25));
+}
+
 // The two HLLD threshold tests in FP64 (the degeneracy |D| <= 1e-12 (|q e| + Bx^2) of a
 // side, and the HLLC limit Bx^2 / 2 < 1e-12 p_T*), decided from the binary exponents in the
 // integer pipe wherever those settle them, and by the FP64 comparison otherwise, in the
@@ -596,18 +617,18 @@ __device__ __forceinline__ void hlld_lazy(const Side<T>& L, const Side<T>& R, T 
                                      T gm1inv, T F[7], T& c) {
   const T bx2 = bx * bx;
   const T b2L = bx2 + L.b1 * L.b1 + L.b2 * L.b2, b2R = bx2 + R.b1 * R.b1 + R.b2 * R.b2;
-  const T magL = T(0.5) * b2L, magR = T(0.5) * b2R;
-  const T pTL = L.p + magL, pTR = R.p + magR;
+  // p_T = p + |B|^2 / 2 with the exact halving inside the FMA (the same bits as the sum)
+  const T pTL = fma(T(0.5), b2L, L.p), pTR = fma(T(0.5), b2R, R.p);
 
   // outer speeds from the fast magnetosonic speeds (MK05 eq. 67)
   const T gpL = gamma * L.p, gpR = gamma * R.p;
-  const T aL = gpL + b2L, aR = gpR + b2R;  // 2 magL is b2L exactly
-  const T bx2x4 = T(4) * bx2;               // exact scaling, shared by both sides
+  const T aL = gpL + b2L, aR = gpR + b2R;
+  const T bx2x4 = pow2_scale<2>(bx2);       // exact scaling, shared by both sides
   const T dL = pos_part(aL * aL - gpL * bx2x4);
   const T dR = pos_part(aR * aR - gpR * bx2x4);
   // 0.5/rho_L and 0.5/rho_R from one reciprocal (cheaper than a division; the factor 1/2
   // is exact)
-  const T hLR = T(0.5) * trcp(L.r * R.r);
+  const T hLR = pow2_scale<-1>(trcp(L.r * R.r));
   // only the larger fast speed enters, the root of the larger square: one square root fewer
   // (with a correctly rounded root this equals the larger root bit for bit; with the
   // faithful FP64 root of the production build, within its ulp)
@@ -622,8 +643,8 @@ __device__ __forceinline__ void hlld_lazy(const Side<T>& L, const Side<T>& R, T 
   if (sup_l || lt0(SR)) {  // supersonic: upwind physical flux
     const Side<T>& s = sup_l ? L : R;
     const T pT = sup_l ? pTL : pTR;
-    const T E = s.p * gm1inv + T(0.5) * s.r * (s.u * s.u + s.v * s.v + s.w * s.w) +
-                (sup_l ? magL : magR);
+    const T E = fma(T(0.5), sup_l ? b2L : b2R,
+                    s.p * gm1inv + pow2_scale<-1>(s.r) * (s.u * s.u + s.v * s.v + s.w * s.w));
     const T vb = s.u * bx + s.v * s.b1 + s.w * s.b2;
     const T ru = s.r * s.u;
     F[0] = ru;
@@ -689,8 +710,8 @@ __device__ __forceinline__ void hlld_lazy(const Side<T>& L, const Side<T>& R, T 
   const T abx = tabs(bx);
   const T Ss = left ? SM - abx * rq : SM + abx * rq;  // the Alfven speed on that side
 
-  const T E = s.p * gm1inv + T(0.5) * s.r * (s.u * s.u + s.v * s.v + s.w * s.w) +
-              (left ? magL : magR);
+  const T E = fma(T(0.5), left ? b2L : b2R,
+                  s.p * gm1inv + pow2_scale<-1>(s.r) * (s.u * s.u + s.v * s.v + s.w * s.w));
   const T vb = s.u * bx + s.v * s.b1 + s.w * s.b2;
   const T vbs = SM * bx + vs * b1s + ws * b2s;
   const T Es = (su * E - pT * s.u + pTs * SM + bx * (vb - vbs)) * is;
@@ -1073,7 +1094,7 @@ __device__ __forceinline__ T emf_ec(T X0, T X1, T Y0, T Y1, T C00, T C01, T C10,
   const T dB3 = pick(Fa1, Y1, C11, Y0, C01);
   const T dA1 = pick(Fb0, C01, X1, C00, X0);
   const T dA3 = pick(Fb1, X1, C11, X0, C10);
-  return T(0.25) * ((X0 + X1) + (Y0 + Y1) + (dB3 - dB1) + (dA3 - dA1));
+  return pow2_scale<-2>((X0 + X1) + (Y0 + Y1) + (dB3 - dB1) + (dA3 - dA1));
 }
 
 }  // namespace idx
