@@ -246,9 +246,9 @@ def run_reference(args):
 # the bench's dominant kernel is the variant that was captured.
 # DRAM bytes per face of the dominant sweep, from one ncu capture at 192^3 of the current
 # kernel (dram__bytes_read.sum + dram__bytes_write.sum over the faces of the launch)
-MEASURED_TRAFFIC_PER_FACE = {("fp64", "x", 32): (1275007488 + 782223104) / 192 ** 3,
-                             ("fp64", "x", -2): (453113600 + 412169728) / 192 ** 3,
-                             ("fp32", "x", -2): (254843904 + 188305664) / 192 ** 3}
+MEASURED_TRAFFIC_PER_FACE = {("fp64", "x", 32): (1278596096 + 785182976) / 192 ** 3,
+                             ("fp64", "x", -2): (453105920 + 412378880) / 192 ** 3,
+                             ("fp32", "x", -2): (254834944 + 188080128) / 192 ** 3}
 
 
 def op_counts(cons, lengths, gamma):
