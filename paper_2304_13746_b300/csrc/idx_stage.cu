@@ -39,6 +39,7 @@
 #include <tuple>
 
 #include "../../include/idx.h"
+#include "divmagic.cuh"
 #include "mhd_math.cuh"
 #include "tma.cuh"
 
@@ -85,22 +86,11 @@ struct Geo {
   float gammaf, gm1invf;
   int riemann;       // 1 Rusanov, 2 HLL, 4 HLLD
   int recon;         // 1 PLM (van Leer), 3 LimO3
-  // floor(c / nx) and floor(c / (nx ny)) for 0 <= c < 2^31 as (c m) >> s (geo_set_divisors)
+  // floor(c / nx) and floor(c / (nx ny)) for 0 <= c < 2^31 as (c m) >> s (divmagic.cuh)
   unsigned div_m[2];
   int div_s[2];
 };
 
-// Division by an invariant integer as a multiply and a shift (Granlund and Montgomery
-// 1994, Thm. 4.2, with N = 31): for 1 <= d < 2^31, l = ceil(log2 d) and
-// m = ceil(2^(31 + l) / d), m d - 2^(31 + l) < d <= 2^l, so floor(n / d) =
-// floor(n m / 2^(31 + l)) for every 0 <= n < 2^31; m < 2^32 and n m < 2^63.
-inline void div_magic(unsigned d, unsigned& m, int& sh) {
-  int l = 0;
-  while ((1ull << l) < d) ++l;
-  const unsigned long long p = 1ull << (31 + l);
-  m = (unsigned)((p + d - 1) / d);
-  sh = 31 + l;
-}
 inline void geo_set_divisors(Geo& g) {
   div_magic((unsigned)g.n[0], g.div_m[0], g.div_s[0]);
   div_magic((unsigned)g.stride[2], g.div_m[1], g.div_s[1]);
@@ -142,9 +132,9 @@ __device__ __forceinline__ double to_f64(double x) { return x; }
 __device__ __forceinline__ double to_f64(float x) { return f2d(x); }
 
 __device__ __forceinline__ void coords(const Geo& g, int c, int& i, int& j, int& k) {
-  k = (int)(((unsigned long long)(unsigned)c * g.div_m[1]) >> g.div_s[1]);
+  k = (int)div_by_magic((uint32_t)c, g.div_m[1], g.div_s[1]);
   const int r = c - k * g.stride[2];
-  j = (int)(((unsigned long long)(unsigned)r * g.div_m[0]) >> g.div_s[0]);
+  j = (int)div_by_magic((uint32_t)r, g.div_m[0], g.div_s[0]);
   i = r - j * g.n[0];
 }
 

@@ -558,8 +558,8 @@ template <int K>
 __device__ __forceinline__ double pow2_fp64(double x) {
   const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
   const unsigned e = (hi >> 20) & 0x7ffu;
-  constexpr unsigned kLo = K < 0 ? 1u - K : 1u;              // smallest exponent field kept normal
-  constexpr unsigned kHi = K > 0 ? 0x7feu - K : 0x7feu;      // largest
+  constexpr unsigned kLo = K < 0 ? (unsigned)(1 - K) : 1u;   // smallest exponent field kept normal
+  constexpr unsigned kHi = K > 0 ? (unsigned)(0x7fe - K) : 0x7feu;  // largest
   const bool fast = (e - kLo) <= (kHi - kLo);
   const bool zero = ((hi & 0x7fffffffu) | lo) == 0u;
   double r = __hiloint2double((int)(fast ? hi + (unsigned)(K * (1 << 20)) : hi), (int)lo);

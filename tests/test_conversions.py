@@ -82,3 +82,36 @@ def test_fp64_hlld_threshold_tests_match_the_comparisons(threshold_harness):
     assert int(words[1]) == 0 and int(words[3]) >= 8_000_000
     # the near-threshold cases do reach the comparisons
     assert int(words[5]) > 0 and int(words[7]) > 0
+
+
+@pytest.fixture(scope="module")
+def pow2_harness(tmp_path_factory):
+    exe = str(tmp_path_factory.mktemp("pow2") / "pow2_check")
+    subprocess.run([NVCC, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-std=c++17",
+                    "-o", exe, os.path.join(HERE, "native", "pow2_check.cu")], check=True)
+    return exe
+
+
+@pytest.mark.gpu
+def test_fp64_power_of_two_scalings_equal_the_products(pow2_harness):
+    # x/4, x/2 and 4x of the FP64 HLLD and E^c by the exponent field: bit for bit the
+    # products, in warps that take the integer path and in warps where a zero, subnormal,
+    # end-of-range, infinite or NaN lane sends the warp to the multiply
+    out = subprocess.run([pow2_harness, "4000000"], capture_output=True, text=True, timeout=600)
+    words = out.stdout.split()
+    assert out.returncode == 0 and words[:1] == ["mismatches"], (out.stdout, out.stderr)
+    print(out.stdout)
+    assert int(words[1]) == 0 and int(words[3]) >= 12_000_000
+    assert int(words[5]) >= 4_000_000 // 32 // 2 - 1000  # half the warps take the integer path
+
+
+def test_multiply_and_shift_division_equals_the_quotient(tmp_path):
+    # the cell-coordinate division of the kernels (divmagic.cuh, host side; the same
+    # function runs on the device) against the division operator, on the host
+    exe = str(tmp_path / "divmagic_check")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-o", exe,
+                    os.path.join(HERE, "native", "divmagic_check.cpp")], check=True)
+    out = subprocess.run([exe, "200000"], capture_output=True, text=True, timeout=300)
+    words = out.stdout.split()
+    assert out.returncode == 0 and words[:1] == ["mismatches"], (out.stdout, out.stderr)
+    assert int(words[1]) == 0 and int(words[3]) > 4_000_000
