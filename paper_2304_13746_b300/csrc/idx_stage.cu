@@ -430,8 +430,11 @@ __device__ __forceinline__ void sweep_body(const Geo& g, const Ptr8<const T>& W,
     q = (q >= nd) ? q - nd : q;
     return base + q * sd;
   };
-  // rotated variable slots in W: rho, v_n, v_t1, v_t2, P, B_t1, B_t2
-  constexpr int var[7] = {0, 1 + D, 1 + A, 1 + B, 4, 5 + A, 5 + B};
+  // rotated variable slots in W: rho, v_n, v_t1, v_t2, P, B_t1, B_t2; the speed-only pass
+  // reconstructs the 5 that the outer speeds use (rho, v_n, P, B_t1, B_t2)
+  constexpr int NV = SPEEDS ? 5 : 7;
+  constexpr int var[7] = {0, 1 + D, SPEEDS ? 4 : 1 + A, SPEEDS ? 5 + A : 1 + B,
+                          SPEEDS ? 5 + B : 4, 5 + A, 5 + B};
   const T gamma = geo_gamma<T>(g);
   const T gm1inv = geo_gm1inv<T>(g);
 
@@ -443,7 +446,7 @@ __device__ __forceinline__ void sweep_body(const Geo& g, const Ptr8<const T>& W,
   {
     const int cm2 = cell(f0 - 2), cm1 = cell(f0 - 1), c0 = cell(f0), cp = cell(f0 + 1);
 #pragma unroll
-    for (int q = 0; q < 7; ++q) {
+    for (int q = 0; q < NV; ++q) {
       const T a = W.f[var[q]][cm2];
       wm[q] = W.f[var[q]][cm1];
       w0[q] = W.f[var[q]][c0];
@@ -457,35 +460,44 @@ __device__ __forceinline__ void sweep_body(const Geo& g, const Ptr8<const T>& W,
     if (f + 1 < f1) {
       const int cn = cell(f + 2);
 #pragma unroll
-      for (int q = 0; q < 7; ++q) wn[q] = W.f[var[q]][cn];
+      for (int q = 0; q < NV; ++q) wn[q] = W.f[var[q]][cn];
     }
     Side<T> L, R;
     T slope0[7], up0[7];
     if constexpr (RECON == 3) {
 #pragma unroll
-      for (int q = 0; q < 7; ++q) {
+      for (int q = 0; q < NV; ++q) {
         const T dl = w0[q] - wm[q], dr = wp[q] - w0[q];
         slope0[q] = limo3_half(dr, dl);
         up0[q] = limo3_half(dl, dr);
       }
     } else {
-      T dl[7], dr[7];
+      T dl[NV], dr[NV];
 #pragma unroll
-      for (int q = 0; q < 7; ++q) {
+      for (int q = 0; q < NV; ++q) {
         dl[q] = w0[q] - wm[q];
         dr[q] = wp[q] - w0[q];
       }
-      vanleer_half7(dl, dr, slope0);
+      vanleer_half_n<NV>(dl, dr, slope0);
 #pragma unroll
-      for (int q = 0; q < 7; ++q) up0[q] = slope0[q];
+      for (int q = 0; q < NV; ++q) up0[q] = slope0[q];
     }
-    L.r = wm[0] + slope_m[0]; R.r = w0[0] - slope0[0];
-    L.u = wm[1] + slope_m[1]; R.u = w0[1] - slope0[1];
-    L.v = wm[2] + slope_m[2]; R.v = w0[2] - slope0[2];
-    L.w = wm[3] + slope_m[3]; R.w = w0[3] - slope0[3];
-    L.p = wm[4] + slope_m[4]; R.p = w0[4] - slope0[4];
-    L.b1 = wm[5] + slope_m[5]; R.b1 = w0[5] - slope0[5];
-    L.b2 = wm[6] + slope_m[6]; R.b2 = w0[6] - slope0[6];
+    if constexpr (SPEEDS) {
+      L.r = wm[0] + slope_m[0]; R.r = w0[0] - slope0[0];
+      L.u = wm[1] + slope_m[1]; R.u = w0[1] - slope0[1];
+      L.v = L.w = R.v = R.w = T(0);  // the outer speeds do not use the transverse velocity
+      L.p = wm[2] + slope_m[2]; R.p = w0[2] - slope0[2];
+      L.b1 = wm[3] + slope_m[3]; R.b1 = w0[3] - slope0[3];
+      L.b2 = wm[4] + slope_m[4]; R.b2 = w0[4] - slope0[4];
+    } else {
+      L.r = wm[0] + slope_m[0]; R.r = w0[0] - slope0[0];
+      L.u = wm[1] + slope_m[1]; R.u = w0[1] - slope0[1];
+      L.v = wm[2] + slope_m[2]; R.v = w0[2] - slope0[2];
+      L.w = wm[3] + slope_m[3]; R.w = w0[3] - slope0[3];
+      L.p = wm[4] + slope_m[4]; R.p = w0[4] - slope0[4];
+      L.b1 = wm[5] + slope_m[5]; R.b1 = w0[5] - slope0[5];
+      L.b2 = wm[6] + slope_m[6]; R.b2 = w0[6] - slope0[6];
+    }
     const T bn = to_bulk<T>(bface[cf]);
     if constexpr (SPEEDS) {
       F.f[7][cf] = outer_speed(g.riemann, L, R, bn, gamma);
@@ -497,7 +509,7 @@ __device__ __forceinline__ void sweep_body(const Geo& g, const Ptr8<const T>& W,
       F.f[7][cf] = cmax;
     }
 #pragma unroll
-    for (int q = 0; q < 7; ++q) {
+    for (int q = 0; q < NV; ++q) {
       wm[q] = w0[q];
       w0[q] = wp[q];
       wp[q] = wn[q];

@@ -318,46 +318,58 @@ template <> __device__ __forceinline__ double vanleer_half<double>(double dl, do
 // product can leave the double range; otherwise (steep fronts into near-vacuum, with
 // differences near the subnormal range) each slope takes its own reciprocal.  The FP32 bulk
 // and the strict-rounding build form each slope by itself.
-template <typename T> __device__ __forceinline__ void vanleer_half7(const T dl[7], const T dr[7],
-                                                                   T out[7]) {
+template <int N, typename T> struct VanLeerN {
+  static __device__ __forceinline__ void run(const T dl[N], const T dr[N], T out[N]) {
 #pragma unroll
-  for (int q = 0; q < 7; ++q) out[q] = vanleer_half(dl[q], dr[q]);
-}
+    for (int q = 0; q < N; ++q) out[q] = vanleer_half(dl[q], dr[q]);
+  }
+};
 #ifndef IDX_STRICT_ROUNDING
-template <> __device__ __forceinline__ void vanleer_half7<double>(const double dl[7],
-                                                                  const double dr[7],
-                                                                  double out[7]) {
-  double prod[7], den[7];
-  bool pos[7];
-  unsigned long long bad = 0;
+template <int N> struct VanLeerN<N, double> {
+  static __device__ __forceinline__ void run(const double dl[N], const double dr[N],
+                                             double out[N]) {
+    double prod[N], den[N];
+    bool pos[N];
+    unsigned long long bad = 0;
 #pragma unroll
-  for (int q = 0; q < 7; ++q) {
-    prod[q] = dl[q] * dr[q];
-    pos[q] = gt0(prod[q]);
-    den[q] = pos[q] ? dl[q] + dr[q] : 1.0;
-    // biased exponent outside [1023 - 130, 1023 + 130]
-    const unsigned e = (unsigned)((unsigned long long)ibits(den[q]) >> 52) & 0x7ffu;
-    bad |= (unsigned long long)((e - 893u) > 260u);
+    for (int q = 0; q < N; ++q) {
+      prod[q] = dl[q] * dr[q];
+      pos[q] = gt0(prod[q]);
+      den[q] = pos[q] ? dl[q] + dr[q] : 1.0;
+      // biased exponent outside [1023 - 130, 1023 + 130]
+      const unsigned e = (unsigned)((unsigned long long)ibits(den[q]) >> 52) & 0x7ffu;
+      bad |= (unsigned long long)((e - 893u) > 260u);
+    }
+    if (bad) {
+#pragma unroll
+      for (int q = 0; q < N; ++q) out[q] = pos[q] ? prod[q] * (1.0 / den[q]) : 0.0;
+      return;
+    }
+    double pre[N];
+    pre[0] = den[0];
+#pragma unroll
+    for (int q = 1; q < N; ++q) pre[q] = pre[q - 1] * den[q];
+    double inv = 1.0 / pre[N - 1];  // 1 / (den[0] ... den[N-1])
+#pragma unroll
+    for (int q = N - 1; q >= 1; --q) {
+      const double r = inv * pre[q - 1];  // 1 / den[q]
+      inv = inv * den[q];                 // 1 / (den[0] ... den[q-1])
+      out[q] = pos[q] ? prod[q] * r : 0.0;
+    }
+    out[0] = pos[0] ? prod[0] * inv : 0.0;
   }
-  if (bad) {
-#pragma unroll
-    for (int q = 0; q < 7; ++q) out[q] = pos[q] ? prod[q] * (1.0 / den[q]) : 0.0;
-    return;
-  }
-  double pre[7];
-  pre[0] = den[0];
-#pragma unroll
-  for (int q = 1; q < 7; ++q) pre[q] = pre[q - 1] * den[q];
-  double inv = 1.0 / pre[6];  // 1 / (den[0] ... den[6])
-#pragma unroll
-  for (int q = 6; q >= 1; --q) {
-    const double r = inv * pre[q - 1];  // 1 / den[q]
-    inv = inv * den[q];                 // 1 / (den[0] ... den[q-1])
-    out[q] = pos[q] ? prod[q] * r : 0.0;
-  }
-  out[0] = pos[0] ? prod[0] * inv : 0.0;
-}
+};
 #endif
+// the half slopes of N variables of one cell (N = 7 for the flux sweeps, 5 for the
+// speed-only pass); FP64 forms them with one reciprocal as above
+template <int N, typename T>
+__device__ __forceinline__ void vanleer_half_n(const T dl[N], const T dr[N], T out[N]) {
+  VanLeerN<N, T>::run(dl, dr, out);
+}
+template <typename T>
+__device__ __forceinline__ void vanleer_half7(const T dl[7], const T dr[7], T out[7]) {
+  VanLeerN<7, T>::run(dl, dr, out);
+}
 
 // x with its sign flipped where y is negative (x * sign(y), signed zeros included), on the
 // bit patterns.
@@ -1026,10 +1038,10 @@ __device__ __forceinline__ T outer_speed(int solver, const Side<T>& L, const Sid
     const T b2L = bx2 + L.b1 * L.b1 + L.b2 * L.b2, b2R = bx2 + R.b1 * R.b1 + R.b2 * R.b2;
     const T gpL = gamma * L.p, gpR = gamma * R.p;
     const T aL = gpL + b2L, aR = gpR + b2R;
-    const T bx2x4 = T(4) * bx2;
+    const T bx2x4 = pow2_scale<2>(bx2);  // exact scalings, as in hlld_lazy
     const T dL = pos_part(aL * aL - gpL * bx2x4);
     const T dR = pos_part(aR * aR - gpR * bx2x4);
-    const T hLR = T(0.5) * trcp(L.r * R.r);
+    const T hLR = pow2_scale<-1>(trcp(L.r * R.r));
     cfm = tsqrt(max_nn((aL + tsqrt(dL)) * (R.r * hLR), (aR + tsqrt(dR)) * (L.r * hLR)));
   } else if (solver == 2) {
     cfm = fast_speed_max(L, R, bx, gamma);
