@@ -7,7 +7,8 @@ cycles of a sim made from the same state, within the parity bound used for the G
 path (1e-12 of each field's scale), including the carried inverse CFL time -- also for a
 2D grid right after a 3D one, a non-cubic grid and a side stream, with the device's free
 memory and torch's allocations unchanged across calls; a grid above IDX_NOALLOC_MAX_CELLS
-and a capturing stream must be refused.  This file is collected last on purpose.
+and a capturing stream must be refused.  The same calls also match the oracle's own cycles
+directly.  This file is collected last on purpose.
 """
 import ctypes
 
@@ -112,6 +113,39 @@ def _noalloc_cycles(L, ic, ncycles, stream=None):
         assert torch.cuda.memory_allocated() == alloc_before
     ref.close()
     return worst
+
+
+def test_noalloc_cycles_match_the_oracle():
+    # the same calls against the oracle's own cycles (no path shared with idx_step): a 2D
+    # and a non-cubic 3D grid, two cycles each, state within the parity bound and each dt
+    # and carried inverse CFL time to rounding
+    import torch
+    L = _lib()
+    cases = (inputs.orszag_tang_2d(32),
+             inputs.random_smooth((12, 10, 8), seed=3, lengths=(1.0, 0.9, 0.7)))
+    for ic in cases:
+        o = oracle.Sim.from_prims(ic.prim, ic.lengths, ic.gamma, 0.4)
+        cons = oracle.cons_from_prims(ic.prim, ic.lengths, ic.gamma)
+        nz, ny, nx = ic.shape
+        grid = idx.Grid(nx, ny, nz, *ic.lengths)
+        state = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in cons]
+        torch.cuda.synchronize()
+        ptrs = idx.P8(*[t.data_ptr() for t in state])
+        inv = ctypes.c_double(0.0)
+        for call in range(2):
+            dt_o = o.step()
+            dt = ctypes.c_double()
+            rc = L.idx_step_noalloc(ctypes.byref(grid), ic.gamma, 0.4, ptrs, ctypes.byref(inv),
+                                    ctypes.byref(dt), None)
+            assert rc == idx.IDX_OK, rc
+            got = [t.cpu().numpy() for t in state]
+            want = [np.asarray(a) for a in o.u]
+            sc = _scales(want)
+            err = max(float(np.max(np.abs(got[f] - want[f]))) / sc[f] for f in range(8))
+            print(ic.name, call, f"noalloc vs oracle {err:.2e}")
+            assert err <= 1e-12, (ic.name, call, err)
+            assert dt.value == pytest.approx(dt_o, rel=1e-14)
+            assert 0.4 / inv.value == pytest.approx(o.next_dt(), rel=1e-14)
 
 
 def test_noalloc_after_a_3d_call_runs_2d_non_cubic_and_side_stream_grids():
