@@ -874,6 +874,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep_x(Geo g, Ptr8<const T> W, co
 // Edge EMFs: E_e at the edge along e bounded by the lower a- and b-faces of cell c,
 // a = e+1, b = e+2.  a-face EMF = -F_a[B_b] (rotated slot 5 of direction a), b-face
 // EMF = +F_b[B_a] (slot 6 of direction b), cell-centre EMF = -(v_a B_b - v_b B_a).
+// dn: the offsets from c to its lower neighbour along each direction (lower_offsets).
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ T edge_emf(const Geo& g, int e, int c, const int dn[3],
